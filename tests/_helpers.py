@@ -1,0 +1,165 @@
+"""Test-side helpers: logical database state, property checks, linear
+extensions.  Pure numpy/python; shared by oracle and GPU parity tests."""
+from __future__ import annotations
+
+import itertools
+import random
+
+import numpy as np
+
+CLS_R, CLS_W, CLS_A = 0, 1, 2
+
+
+def conflicts(c1: int, c2: int) -> bool:
+    """Two basic operations on one item conflict unless both read or both are
+    blind additions (Section 4.1, plus the ADD refinement)."""
+    if c1 == CLS_R and c2 == CLS_R:
+        return False
+    if c1 == CLS_A and c2 == CLS_A:
+        return False
+    return True
+
+
+def conflict_pairs(obj, cls):
+    """All (i, j) with i < j whose transactions conflict, as a set."""
+    n, K = obj.shape
+    by_obj: dict = {}
+    for i in range(n):
+        for j in range(K):
+            if obj[i, j] >= 0:
+                by_obj.setdefault(int(obj[i, j]), []).append((i, int(cls[i, j])))
+    pairs = set()
+    for accs in by_obj.values():
+        for (a, ca), (b, cb) in itertools.combinations(accs, 2):
+            if a != b and conflicts(ca, cb):
+                pairs.add((min(a, b), max(a, b)))
+    return pairs
+
+
+def check_properties(level, obj, cls):
+    """Property 1 (a k-set is conflict-free) and Property 2 (every member of
+    a k-set, k >= 1, conflicts with an earlier member of the (k-1)-set).
+    Returns a list of violations (empty when both hold)."""
+    bad = []
+    pairs = conflict_pairs(obj, cls)
+    preds: dict = {}
+    for a, b in pairs:
+        if level[a] == level[b]:
+            bad.append(("P1", a, b))
+        preds.setdefault(b, []).append(a)
+    for t in range(len(level)):
+        if level[t] >= 1:
+            if not any(level[p] == level[t] - 1 for p in preds.get(t, [])):
+                bad.append(("P2", t))
+        elif t in preds and level[t] == 0:
+            bad.append(("source-with-pred", t))
+    return bad
+
+
+def linear_extensions(n, pairs, limit=400, seed=0):
+    """Up to ``limit`` orders of 0..n-1 that respect every (a, b) in pairs
+    (a before b).  Exhaustive when there are at most ``limit``; otherwise a
+    random sample (including the identity)."""
+    succ = {i: set() for i in range(n)}
+    indeg = [0] * n
+    for a, b in pairs:
+        if b not in succ[a]:
+            succ[a].add(b)
+            indeg[b] += 1
+    out = []
+
+    def rec(prefix, indeg, avail):
+        if len(out) > limit:
+            return
+        if len(prefix) == n:
+            out.append(list(prefix))
+            return
+        for v in sorted(avail):
+            nd = indeg[:]
+            na = set(avail)
+            na.discard(v)
+            for s in succ[v]:
+                nd[s] -= 1
+                if nd[s] == 0:
+                    na.add(s)
+            prefix.append(v)
+            rec(prefix, nd, na)
+            prefix.pop()
+
+    rec([], indeg, {i for i in range(n) if indeg[i] == 0})
+    if len(out) <= limit:
+        return out
+    rng = random.Random(seed)
+    sample = [list(range(n))]
+    while len(sample) < limit:
+        nd = indeg[:]
+        avail = [i for i in range(n) if nd[i] == 0]
+        order = []
+        while avail:
+            v = avail.pop(rng.randrange(len(avail)))
+            order.append(v)
+            for s in succ[v]:
+                nd[s] -= 1
+                if nd[s] == 0:
+                    avail.append(s)
+        sample.append(order)
+    return sample
+
+
+def oracle_logical_state(db):
+    """The oracle database as comparable arrays; append-only tables are
+    compared as multisets keyed by their primary keys (physical row order is
+    not part of the state)."""
+    st = {}
+    for k in ("acc_bal", "tel_bal", "br_bal", "sub", "ai_present", "ai_data",
+              "sf_present", "sf_active", "sf_err", "sf_data_a", "sf_data_b",
+              "w_ytd", "d_ytd", "d_next_o_id", "c_balance", "c_ytd",
+              "c_payment_cnt", "c_last_o_id", "s_quantity", "s_ytd", "s_order_cnt"):
+        if k in db.a:
+            st[k] = db.a[k].copy()
+    if "cf_present" in db.a:
+        p = db.a["cf_present"].astype(bool)
+        st["cf_present"] = p.copy()
+        st["cf_end"] = np.where(p, db.a["cf_end"], 0)
+        st["cf_numberx"] = np.where(p, db.a["cf_numberx"], 0)
+    if "hist" in db.a:
+        h = db.history()
+        st["history"] = h[np.argsort(h[:, 0], kind="stable")].copy()
+    if "ord" in db.a:
+        orders = db.orders()
+        ol = db.order_lines()
+        rows = []
+        for r, o in enumerate(orders):
+            lines = ol[o[5]: o[5] + o[4]]
+            lines = sorted((int(x[1]), int(x[2]), int(x[3]), int(x[4])) for x in lines)
+            rows.append((int(o[0]), int(o[1]), int(o[2]), int(o[3]), int(o[4]), tuple(lines)))
+        st["orders"] = sorted(rows)
+    return st
+
+
+def states_equal(a, b):
+    if a.keys() != b.keys():
+        return False
+    for k in a:
+        x, y = a[k], b[k]
+        if isinstance(x, np.ndarray):
+            if x.shape != y.shape or not np.array_equal(x, y):
+                return False
+        elif x != y:
+            return False
+    return True
+
+
+def state_diff(a, b):
+    out = []
+    for k in sorted(set(a) | set(b)):
+        if k not in a or k not in b:
+            out.append(k)
+            continue
+        x, y = a[k], b[k]
+        if isinstance(x, np.ndarray):
+            if x.shape != y.shape or not np.array_equal(x, y):
+                out.append(k)
+        elif x != y:
+            out.append(k)
+    return out
