@@ -1,0 +1,405 @@
+#!/usr/bin/env python3
+"""Benchmark of bulk transaction execution on one GB300.
+
+Workload (debit-credit at scale): 1,000 branches, 10,000 tellers, 10,000,000
+accounts with int64 balances; bulks of 2^22 transactions (account uniform or
+Zipf(theta) then scrambled, delta uniform in [-99999, 99999]).  One step = one
+bulk through the whole path: bulk hand-over, basic-operation extraction,
+grouping sort, ranks and depths, (level, type) regrouping, execution, results
+left on the device.  The headline is the plain per-bulk K-SET path with the
+paper's read/write conflict model; a bounded sweep reports every strategy,
+conflict model, skew and bulk size beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gputx|reference]
+
+The reference arm times the CPU oracle (plain serial execution in timestamp
+order) on the host cores on the same workload.  Under torchrun each rank runs
+an independent replica (the path does not shard); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+BRANCHES, TELLERS, ACCOUNTS = 1000, 10_000, 10_000_000
+METRIC = "txns/sec on 1 GB300 per strategy & bulk size vs plain path; p50/p99 latency"
+# algorithmic bytes of one debit-credit transaction in the executor: params
+# (account, delta) 16 B + ts 8 B + its index in the level order 4 B + account,
+# teller, branch balance read+write 3 x 16 B + history row 40 B + output 8 B +
+# status 4 B
+EXEC_BYTES_PER_TXN = 16 + 8 + 4 + 48 + 40 + 8 + 4
+L2_FLUSH_BYTES = 256 << 20
+
+
+def env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return float(json.load(open(p))["hbm_gbs"]), "measured"
+        except (ValueError, KeyError):
+            pass
+    return 6800.0, "fallback"
+
+
+def make_bulks(n, theta, count, seed0):
+    return [W.dc_bulk(n, ACCOUNTS, theta, seed=W.seed_for(2, seed0 + i)) for i in range(count)]
+
+
+# ---------------------------------------------------------------------------
+# engine arm
+# ---------------------------------------------------------------------------
+def run_engine(args, rank, world, local_rank):
+    import torch
+    import paper_1103_3105_gb300 as G
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    n = 1 << args.bulk_log2
+    K, Wm = args.steps, args.warmup
+    stream = torch.cuda.current_stream()
+    cap = (2 * (K + Wm) + 8) * n
+    db = G.Database(dc=(BRANCHES, TELLERS, ACCOUNTS), history_capacity=cap, max_bulk=n,
+                    stream=stream.cuda_stream)
+    db.register(G.DC_TYPES)
+    bulks = make_bulks(n, args.theta, 3, 100 * rank)
+    dbulks = [{k: torch.from_numpy(b[k]).to(dev) for k in ("ts", "type", "params")} for b in bulks]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    mode = G.CONFLICT_ADD if args.mode == "add" else G.CONFLICT_PAPER
+
+    def step(i, timing=False):
+        d = dbulks[i % len(dbulks)]
+        b = db.submit(d["ts"], d["type"], d["params"])
+        b.execute(args.strategy, conflict_mode=mode, timing=timing)
+        return b
+
+    for i in range(Wm):
+        step(i).free()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches0 = G.gputx_launch_count()
+    times, exec_ms, sort_ms, stats = [], [], [], None
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for i in range(K):
+            flush.fill_(i & 0xFF)          # L2 flush between steps (outside the events)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b = step(i, timing=True)
+            e1.record(stream)
+            stats = b.sync()
+            times.append(e0.elapsed_time(e1))
+            exec_ms.append(stats["ms_execute"])
+            sort_ms.append(stats["ms_sort"])
+            b.free()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    launches = G.gputx_launch_count() - launches0
+    # count only the engine's kernels: the L2 flushes are torch's
+    total_ms = sum(times)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = n * K * world / (total_ms / 1e3)
+
+    # end to end through the public API with host buffers: H2D + D2H inside
+    pinned = []
+    for b in bulks:
+        pinned.append({k: torch.from_numpy(b[k]).pin_memory() for k in ("ts", "type", "params")})
+    st_h = torch.empty(n, dtype=torch.int32).pin_memory()
+    out_h = torch.empty((n, db.width), dtype=torch.int64).pin_memory()
+    for i in range(max(1, Wm)):
+        p = pinned[i % len(pinned)]
+        b = db.submit(p["ts"].numpy(), p["type"].numpy(), p["params"].numpy())
+        b.execute(args.strategy, conflict_mode=mode)
+        b.results(st_h.numpy(), out_h.numpy())
+        b.free()
+    e2e_times = []
+    for i in range(K):
+        flush.fill_(i & 0xFF)
+        p = pinned[i % len(pinned)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b = db.submit(p["ts"].numpy(), p["type"].numpy(), p["params"].numpy())
+        b.execute(args.strategy, conflict_mode=mode)
+        b.results(st_h.numpy(), out_h.numpy())
+        e2e_times.append(time.perf_counter() - t0)
+        b.free()
+    e2e_total = sum(e2e_times)
+    if dist:
+        t = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = n * K * world / e2e_total
+
+    sweep = None
+    if args.sweep and rank == 0:
+        db.close()
+        sweep = run_sweep(args, G, torch, dev, stream, flush)
+
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = measured_peak_hbm()
+    ex = statistics.median(exec_ms)
+    achieved = n * EXEC_BYTES_PER_TXN / (ex / 1e3) / 1e9
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "txn/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": Wm,
+        "ms_per_step": total_ms / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int64",
+        "data": "synthetic (seeded debit-credit bulks, random-free initial tables)",
+        "config": {"workload": f"debit-credit at scale: {BRANCHES} branches, {TELLERS} tellers, "
+                               f"{ACCOUNTS} accounts, bulk 2^{args.bulk_log2}, theta {args.theta}",
+                   "strategy": args.strategy, "conflict_mode": args.mode, "bulk": n,
+                   "theta": args.theta, "l2": "flushed between steps (256 MiB write, outside the step events)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": "txn/s", "h2d_bytes_per_step": n * (8 + 4 + 16),
+                "d2h_bytes_per_step": n * (4 + 8 * db.width)},
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": "kset_kernel" if args.strategy == "kset" else f"{args.strategy}_kernel",
+                     "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_kind,
+                     "algorithmic_bytes_per_txn": EXEC_BYTES_PER_TXN,
+                     "kernel_ms": ex, "traffic": None},
+        "phases_ms": {"execute": ex, "op_sort": statistics.median(sort_ms),
+                      "analysis": stats["ms_analysis"] if stats else None},
+        "graph": {"depth": stats["depth"], "w0": stats["w0"], "cross": stats["cross"]} if stats else None,
+        "clocks": clk.summary(),
+        "wall_s_timed": wall,
+    }
+    if args.cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, bulks)
+    if sweep is not None:
+        line["sweep"] = sweep
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_sweep(args, G, torch, dev, stream, flush):
+    """Every strategy x conflict model x skew x bulk size, a few steps each,
+    within a time budget (points past the budget are reported as skipped)."""
+    t_start = time.perf_counter()
+    out = []
+    sizes = [14, 16, 18, 20, 22]
+    # history rows for every bulk the sweep can run
+    rows = 3 * 5 * 3 * sum(1 << lg for lg in sizes)
+    db = G.Database(dc=(BRANCHES, TELLERS, ACCOUNTS), history_capacity=rows, max_bulk=1 << 22,
+                    stream=stream.cuda_stream)
+    db.register(G.DC_TYPES)
+    for theta in (0.0, 0.5, 0.99):
+        big = W.dc_bulk(1 << 22, ACCOUNTS, theta, seed=W.seed_for(2, 900 + int(theta * 100)))
+        dbig = {k: torch.from_numpy(big[k]).to(dev) for k in ("ts", "type", "params")}
+        for lg in sizes:
+            n = 1 << lg
+            for strategy in ("kset", "part", "tpl"):
+                for mode_name, mode in (("paper", G.CONFLICT_PAPER), ("add", G.CONFLICT_ADD)):
+                    if strategy == "part" and mode_name == "add":
+                        continue   # PART runs partitions serially: the model does not change it
+                    rec = {"theta": theta, "bulk": n, "strategy": strategy, "mode": mode_name}
+                    if time.perf_counter() - t_start > args.sweep_budget_s:
+                        rec["skipped"] = "time budget"
+                        out.append(rec)
+                        continue
+                    ts = []
+                    st = None
+                    for i in range(3):
+                        flush.fill_(i)
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        b = db.submit(dbig["ts"][:n], dbig["type"][:n], dbig["params"][:n])
+                        b.execute(strategy, conflict_mode=mode, timing=True)
+                        e1.record(stream)
+                        st = b.sync()
+                        b.free()
+                        if i:
+                            ts.append(e0.elapsed_time(e1))
+                    ms = statistics.median(ts)
+                    rec.update({"ms": ms, "txn_per_s": n / (ms / 1e3), "depth": st["depth"],
+                                "w0": st["w0"], "exec_ms": st["ms_execute"], "sort_ms": st["ms_sort"]})
+                    out.append(rec)
+    db.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_rate(bulks, budget_s, max_bulks=None):
+    import oracle
+    oracle.build()
+    o = oracle.OracleDB(dc=W.dc_tables(BRANCHES, TELLERS, ACCOUNTS),
+                        hist_cap=len(bulks[0]["ts"]) * (max_bulks or 64))
+    done, t_exec = 0, 0.0
+    k = 0
+    while k == 0 or (t_exec < budget_s and (max_bulks is None or k < max_bulks)):
+        b = bulks[k % len(bulks)]
+        if o.hist_n + len(b["ts"]) > o.s.hist_cap:
+            o.s.hist_n = 0   # reuse the history area; balances keep accumulating
+        t0 = time.perf_counter()
+        o.execute(b, R=1)
+        t_exec += time.perf_counter() - t0
+        done += len(b["ts"])
+        k += 1
+    return done, t_exec, k
+
+
+def cpu_baseline(args, bulks):
+    done, t, k = oracle_rate(bulks, args.cpu_budget_s)
+    return {"value": done / t, "unit": "txn/s", "cores": 1, "kind": "oracle",
+            "sample": f"{k} bulks of {len(bulks[0]['ts'])} transactions, serial execution in "
+                      f"timestamp order (Definition 1), {t:.1f} s on one host core"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    n = 1 << args.bulk_log2
+    bulks = make_bulks(n, args.theta, 2, 0)
+    # warm-up then timed steps, each a bounded sample: one bulk of n
+    for i in range(args.warmup):
+        oracle_rate(bulks[i % 2:], 0.0, max_bulks=1)
+    times = []
+    for i in range(args.steps):
+        done, t, _ = oracle_rate(bulks[i % 2:], 0.0, max_bulks=1)
+        times.append(t)
+    value = n * args.steps / sum(times)
+    line = {
+        "metric": METRIC, "value": value, "unit": "txn/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"debit-credit at scale: {BRANCHES} branches, {TELLERS} tellers, "
+                               f"{ACCOUNTS} accounts, bulk 2^{args.bulk_log2}, theta {args.theta}",
+                   "strategy": "serial", "bulk": n, "theta": args.theta},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": "txn/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step one bulk of {n} transactions executed serially"},
+        "e2e": {"value": value, "unit": "txn/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gputx", choices=["gputx", "reference"])
+    ap.add_argument("--strategy", default="kset", choices=["kset", "part", "tpl", "auto"])
+    ap.add_argument("--mode", default="paper", choices=["paper", "add"])
+    ap.add_argument("--theta", type=float, default=0.0)
+    ap.add_argument("--bulk-log2", type=int, default=22)
+    ap.add_argument("--sweep", dest="sweep", action="store_true", default=True)
+    ap.add_argument("--no-sweep", dest="sweep", action="store_false")
+    ap.add_argument("--sweep-budget-s", type=float, default=60.0)
+    ap.add_argument("--cpu-baseline", dest="cpu_baseline", action="store_true", default=True)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-budget-s", type=float, default=10.0)
+    args = ap.parse_args()
+    rank, world = env_int("RANK", 0), env_int("WORLD_SIZE", 1)
+    local_rank = env_int("LOCAL_RANK", 0)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_engine(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

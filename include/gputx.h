@@ -1,0 +1,241 @@
+/*
+ * gputx.h -- C ABI of the GB300 bulk transaction engine.
+ *
+ * Implements the bulk execution model of "High-Throughput Transaction
+ * Executions on Graphics Processors" (He & Yu):
+ *   - transactions are instances of registered stored procedures, each with a
+ *     signature <id, type, parameter list> whose id is its timestamp
+ *     (Section 3.2);
+ *   - a bulk of transactions executes on the GPU as one task, and the result
+ *     database and per-transaction outputs equal serial execution in
+ *     increasing timestamp order (Definition 1, Section 3.1);
+ *   - three strategies: K-SET (Section 5.3), PART (Section 5.2) and TPL
+ *     (Section 5.1), all driven by the sort-based dependency analysis of
+ *     Section 4.2; AUTO picks one by Algorithm 1 (Appendix D).
+ *
+ * Conventions (every function):
+ *   - Returns a gputx_status; never aborts the process.  The text of the last
+ *     failure of a database is available from gputx_last_error().
+ *   - Host arrays belong to the caller.  The library copies what it needs
+ *     and keeps no host pointer after a call returns.
+ *   - All device memory belongs to the database or bulk that allocated it and
+ *     is released by gputx_destroy_db / gputx_free_bulk.
+ *   - Work is enqueued on the database's CUDA stream.  gputx_execute returns
+ *     once the work is enqueued; failures detected on the device (invalid
+ *     bulk contents, a bounded wait that ran out, a full insert area) are
+ *     returned by the next synchronising call on that bulk:
+ *     gputx_sync_bulk or gputx_read_results.
+ *   - Integer columns wrap on overflow (two's complement).
+ */
+#ifndef GPUTX_H
+#define GPUTX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GPUTX_OK = 0,
+    GPUTX_EINVAL = 1,     /* bad argument or bulk contents (type, key, ts order) */
+    GPUTX_ENOMEM = 2,     /* device allocation failed or admission refused */
+    GPUTX_ECUDA = 3,      /* a CUDA runtime call failed */
+    GPUTX_ETIMEOUT = 4,   /* a bounded device wait ran out (no forward progress) */
+    GPUTX_EBOUNDS = 5,    /* a device-side bounds check failed */
+    GPUTX_ESTATE = 6,     /* call out of order (e.g. executing a bulk twice) */
+    GPUTX_ECAPACITY = 7   /* an append-only table or hash index is full */
+} gputx_status;
+
+typedef enum {
+    GPUTX_KSET = 0,       /* Section 5.3: k-sets level by level */
+    GPUTX_PART = 1,       /* Section 5.2: one thread per partition */
+    GPUTX_TPL = 2,        /* Section 5.1: ordered counter locks */
+    GPUTX_AUTO = 3        /* Algorithm 1 over the measured d, w0, c */
+} gputx_strategy;
+
+typedef enum {
+    /* Section 4.1: every basic operation is a read or a write. */
+    GPUTX_CONFLICT_PAPER = 0,
+    /* Refinement beyond the paper: increments whose old value is never read
+     * (debit-credit teller/branch, order-entry warehouse/district ytd) are a
+     * third class ADD that conflicts with reads and writes but not with other
+     * ADDs, and execute as atomic additions.  Results are identical because
+     * wrapping integer addition is commutative and associative. */
+    GPUTX_CONFLICT_ADD = 1
+} gputx_conflict_mode;
+
+typedef enum { GPUTX_MEM_HOST = 0, GPUTX_MEM_DEVICE = 1 } gputx_mem;
+
+/* Registered transaction types (the combined kernel's switch, Section 3.2). */
+enum {
+    GPUTX_T_DC_DEBIT_CREDIT = 0,      /* params: account, delta */
+    GPUTX_T_SUB_GET_SUBSCRIBER = 1,   /* params: s_id */
+    GPUTX_T_SUB_GET_ACCESS = 2,       /* params: s_id, ai_type */
+    GPUTX_T_SUB_GET_NEW_DEST = 3,     /* params: s_id, sf_type, start_time, end_time */
+    GPUTX_T_SUB_UPDATE_LOCATION = 4,  /* params: s_id, location */
+    GPUTX_T_SUB_UPDATE_FACILITY = 5,  /* params: s_id, sf_type, bit, data_a */
+    GPUTX_T_SUB_INSERT_CF = 6,        /* params: s_id, sf_type, start_time, end_time, numberx */
+    GPUTX_T_SUB_DELETE_CF = 7,        /* params: s_id, sf_type, start_time */
+    GPUTX_T_OE_NEW_ORDER = 8,         /* params: w, d, c, ol_cnt, ol_cnt packed lines */
+    GPUTX_T_OE_PAYMENT = 9,           /* params: w, d, c, amount */
+    GPUTX_T_OE_ORDER_STATUS = 10,     /* params: w, d, c */
+    GPUTX_NUM_TYPES = 11
+};
+
+/* Tables, addressed for loading and reading back.  Row transfer format is a
+ * fixed number of int64 fields per row (listed beside each table). */
+typedef enum {
+    GPUTX_TBL_DC_BRANCH = 0,          /* 1: balance (row = branch id) */
+    GPUTX_TBL_DC_TELLER = 1,          /* 1: balance (row = teller id) */
+    GPUTX_TBL_DC_ACCOUNT = 2,         /* 1: balance (row = account id) */
+    GPUTX_TBL_DC_HISTORY = 3,         /* 5: ts, account, teller, branch, delta (read only) */
+    GPUTX_TBL_SUB_SUBSCRIBER = 4,     /* 16: int32 fields f0..f15 (row = s_id) */
+    GPUTX_TBL_SUB_ACCESS_INFO = 5,    /* 6: s_id, ai_type, data1..data4 */
+    GPUTX_TBL_SUB_SPECIAL_FACILITY = 6, /* 6: s_id, sf_type, is_active, error_cntrl, data_a, data_b */
+    GPUTX_TBL_SUB_CALL_FORWARDING = 7,  /* 5: s_id, sf_type, start_time, end_time, numberx */
+    GPUTX_TBL_OE_WAREHOUSE = 8,       /* 2: tax, ytd (row = w) */
+    GPUTX_TBL_OE_DISTRICT = 9,        /* 3: tax, ytd, next_o_id (row = w*10+d) */
+    GPUTX_TBL_OE_CUSTOMER = 10,       /* 5: discount, balance, ytd_payment, payment_cnt, last_o_id */
+    GPUTX_TBL_OE_ITEM = 11,           /* 1: price */
+    GPUTX_TBL_OE_STOCK = 12,          /* 3: quantity, ytd, order_cnt (row = w*n_items+item) */
+    GPUTX_TBL_OE_ORDER = 13,          /* 5: w, d, o_id, c, ol_cnt (read only) */
+    GPUTX_TBL_OE_ORDER_LINE = 14,     /* 7: w, d, o_id, item, supply_w, qty, amount (read only) */
+    GPUTX_NUM_TABLES = 15
+} gputx_table;
+
+/* Sizes of the three built-in schemas; a zero count leaves a schema out. */
+typedef struct {
+    int64_t dc_branches, dc_tellers, dc_accounts;   /* tellers and accounts are
+                                                       multiples of branches */
+    int64_t dc_history_capacity;                    /* rows */
+    int64_t sub_subscribers;
+    int64_t sub_child_capacity;  /* rows per child table (0 = 4 per subscriber
+                                    + room for inserts) */
+    int64_t oe_warehouses, oe_items;
+    int64_t oe_order_capacity, oe_orderline_capacity;
+} gputx_schema_desc;
+
+/* Engine configuration; zero fields take the documented defaults. */
+typedef struct {
+    int64_t max_bulk;         /* largest bulk (transactions); default 1<<22 */
+    int32_t block_threads;    /* executor CTA size: 128..1024, default 256 */
+    int32_t part_size;        /* root keys per PART partition; default 1 for
+                                 debit-credit and order-entry, 128 for the
+                                 subscriber schema (Appendix E) */
+    int64_t spin_limit_ns;    /* bound on every device-side wait; default 2 s */
+    int64_t kset_w0_min;      /* Algorithm 1 thresholds; defaults below */
+    int64_t part_c_max;
+    int64_t part_d_min;
+} gputx_config;
+
+/* Filled by gputx_sync_bulk / gputx_read_results when requested. */
+typedef struct {
+    int32_t strategy;         /* strategy actually run */
+    int32_t fallback;         /* 1 when PART fell back to TPL (Section 5.2) */
+    int64_t n;                /* transactions */
+    int64_t n_ops;            /* basic operations extracted */
+    int64_t depth;            /* d: depth of the T-dependency graph */
+    int64_t w0;               /* size of the 0-set */
+    int64_t cross;            /* c: cross-partition transactions */
+    int64_t fixpoint_rounds;  /* refinement rounds after the one-pass ranks */
+    float ms_h2d, ms_analysis, ms_sort, ms_execute, ms_d2h, ms_total;
+} gputx_exec_stats;
+
+typedef struct {
+    int32_t conflict_mode;    /* gputx_conflict_mode */
+    int32_t block_threads;    /* 0 = database default */
+    int32_t part_size;        /* 0 = database default */
+    int32_t timing;           /* 1 = record per-phase CUDA events in stats */
+} gputx_exec_opts;
+
+typedef struct gputx_db gputx_db;
+typedef struct gputx_bulk gputx_bulk;
+
+/* Creates a database on the current CUDA device.  `cuda_stream` is a
+ * cudaStream_t (NULL = a new non-blocking stream owned by the database).
+ * Allocates every table of the schemas whose sizes are non-zero, zeroed, and
+ * the dependency-analysis state.  EINVAL on inconsistent sizes, ENOMEM when
+ * device memory is short. */
+gputx_status gputx_create_db(const gputx_schema_desc *schema, const gputx_config *cfg,
+                             void *cuda_stream, gputx_db **out);
+void gputx_destroy_db(gputx_db *db);
+const char *gputx_last_error(const gputx_db *db);
+
+/* Selects which compiled-in procedures this database accepts (Section 3.2:
+ * registering a type = adding its procedure to the combined kernel, which
+ * here is compiled in; registration enables it).  EINVAL on an unknown id or
+ * a type whose schema was not created. */
+gputx_status gputx_register_types(gputx_db *db, const int32_t *type_ids, int n);
+
+/* Bulk loading (initialisation, excluded from throughput by Appendix E):
+ * `rows` is n_rows x fields int64 on the host in the table's transfer format.
+ * Keyed tables (row = id) take exactly their row count; child tables
+ * (access_info, special_facility, call_forwarding) take any number of rows
+ * with distinct keys and build their hash index.  EINVAL on a read-only
+ * table, a wrong row count, an out-of-range or duplicate key. */
+gputx_status gputx_load_table(gputx_db *db, int table, const int64_t *rows, size_t n_rows);
+
+/* Reads the live rows of a table into `rows` (host, capacity_rows x fields
+ * int64).  *n_rows receives the live row count; rows == NULL only counts.
+ * Child, order and history tables return rows in storage order.
+ * Synchronises the database stream. */
+gputx_status gputx_read_table(gputx_db *db, int table, int64_t *rows, size_t capacity_rows,
+                              size_t *n_rows);
+
+/* Submits a bulk: n transactions as structure-of-arrays, ts[n] strictly
+ * increasing int64 timestamps (the ids of Section 3.2), type[n] registered
+ * type ids, params[n x params_per_txn] int64.  `mem` says whether the three
+ * arrays are host or device memory; host arrays are copied (asynchronously
+ * when pinned), device arrays are copied on the device.  Contents are
+ * validated on the device; an invalid bulk executes nothing and reports
+ * EINVAL at its sync.  EINVAL here for null pointers, n > max_bulk or too few
+ * parameters for the registered types; ENOMEM when the bulk's buffers cannot
+ * be allocated. */
+gputx_status gputx_submit_bulk(gputx_db *db, const int64_t *ts, const int32_t *type,
+                               const int64_t *params, int params_per_txn, size_t n, int mem,
+                               gputx_bulk **out);
+
+/* Executes a submitted bulk with the given strategy (gputx_strategy).  `opts`
+ * may be NULL.  Bulks execute in the order they are passed to this call, so
+ * the database after several bulks equals serial execution of them in call
+ * order.  ESTATE if the bulk already executed. */
+gputx_status gputx_execute(gputx_db *db, gputx_bulk *bulk, int strategy,
+                           const gputx_exec_opts *opts);
+
+/* Waits for the bulk and returns its device-side status (OK, EINVAL,
+ * ETIMEOUT, EBOUNDS, ECAPACITY); fills *stats when non-NULL. */
+gputx_status gputx_sync_bulk(gputx_bulk *bulk, gputx_exec_stats *stats);
+
+/* Copies per-transaction results to host memory after synchronising:
+ * status[n] int32 (0 = committed, 1 = not found / aborted in the read phase,
+ * 2 = duplicate key on insert) and values[n x n_values] int64 (the
+ * procedure's outputs, zero-filled).  Either pointer may be NULL.  EINVAL if
+ * n differs from the bulk size or n_values is not the database's output
+ * width (gputx_output_width). */
+gputx_status gputx_read_results(gputx_bulk *bulk, int32_t *status, int64_t *values, size_t n,
+                                int n_values);
+
+/* Device pointers of the result arrays (status int32[n], values int64[n x
+ * width]) for callers that keep results on the device. */
+gputx_status gputx_bulk_results_device(gputx_bulk *bulk, const int32_t **status,
+                                       const int64_t **values);
+
+/* Number of int64 outputs per transaction: 1 for debit-credit, 8 when the
+ * subscriber schema exists, 4 for order-entry (the maximum over schemas). */
+int gputx_output_width(const gputx_db *db);
+
+void gputx_free_bulk(gputx_bulk *bulk);
+
+/* Library version string. */
+const char *gputx_version(void);
+
+/* Number of CUDA kernels this library has launched since it was loaded, all
+ * databases together (for tracing and launch accounting). */
+unsigned long long gputx_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPUTX_H */

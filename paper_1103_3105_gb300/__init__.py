@@ -1,0 +1,307 @@
+"""Python binding of the GB300 bulk transaction engine (libgputx.so).
+
+Argument marshalling only: every step of bulk execution runs in the CUDA
+library behind the C ABI declared in ``include/gputx.h``.  Functions named
+``gputx_*`` mirror the C entry points one to one; ``Database`` and ``Bulk``
+are thin conveniences over them.  Importing works without a GPU; any call that
+needs the library raises ``GputxError`` if ``libgputx.so`` has not been built
+(``__graft_entry__.build()``) -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgputx.so")
+
+# --- constants mirrored from include/gputx.h --------------------------------
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBOUNDS, ESTATE, ECAPACITY = range(8)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ETIMEOUT", "EBOUNDS", "ESTATE", "ECAPACITY"]
+KSET, PART, TPL, AUTO = range(4)
+STRATEGIES = {"kset": KSET, "part": PART, "tpl": TPL, "auto": AUTO}
+CONFLICT_PAPER, CONFLICT_ADD = 0, 1
+MEM_HOST, MEM_DEVICE = 0, 1
+
+(T_DC_DEBIT_CREDIT, T_SUB_GET_SUBSCRIBER, T_SUB_GET_ACCESS, T_SUB_GET_NEW_DEST,
+ T_SUB_UPDATE_LOCATION, T_SUB_UPDATE_FACILITY, T_SUB_INSERT_CF, T_SUB_DELETE_CF,
+ T_OE_NEW_ORDER, T_OE_PAYMENT, T_OE_ORDER_STATUS) = range(11)
+NUM_TYPES = 11
+DC_TYPES = (T_DC_DEBIT_CREDIT,)
+SUB_TYPES = tuple(range(1, 8))
+OE_TYPES = (8, 9, 10)
+
+(TBL_DC_BRANCH, TBL_DC_TELLER, TBL_DC_ACCOUNT, TBL_DC_HISTORY, TBL_SUB_SUBSCRIBER,
+ TBL_SUB_ACCESS_INFO, TBL_SUB_SPECIAL_FACILITY, TBL_SUB_CALL_FORWARDING, TBL_OE_WAREHOUSE,
+ TBL_OE_DISTRICT, TBL_OE_CUSTOMER, TBL_OE_ITEM, TBL_OE_STOCK, TBL_OE_ORDER,
+ TBL_OE_ORDER_LINE) = range(15)
+TABLE_FIELDS = (1, 1, 1, 5, 16, 6, 6, 5, 2, 3, 5, 1, 3, 5, 7)
+
+EXPORTED = ("gputx_create_db", "gputx_destroy_db", "gputx_last_error", "gputx_register_types",
+            "gputx_load_table", "gputx_read_table", "gputx_submit_bulk", "gputx_execute",
+            "gputx_sync_bulk", "gputx_read_results", "gputx_bulk_results_device",
+            "gputx_output_width", "gputx_free_bulk", "gputx_version", "gputx_launch_count")
+
+
+class GputxError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {msg}")
+
+
+class SchemaDesc(C.Structure):
+    _fields_ = [("dc_branches", C.c_int64), ("dc_tellers", C.c_int64), ("dc_accounts", C.c_int64),
+                ("dc_history_capacity", C.c_int64), ("sub_subscribers", C.c_int64),
+                ("sub_child_capacity", C.c_int64), ("oe_warehouses", C.c_int64),
+                ("oe_items", C.c_int64), ("oe_order_capacity", C.c_int64),
+                ("oe_orderline_capacity", C.c_int64)]
+
+
+class Config(C.Structure):
+    _fields_ = [("max_bulk", C.c_int64), ("block_threads", C.c_int32), ("part_size", C.c_int32),
+                ("spin_limit_ns", C.c_int64), ("kset_w0_min", C.c_int64),
+                ("part_c_max", C.c_int64), ("part_d_min", C.c_int64)]
+
+
+class ExecStats(C.Structure):
+    _fields_ = [("strategy", C.c_int32), ("fallback", C.c_int32), ("n", C.c_int64),
+                ("n_ops", C.c_int64), ("depth", C.c_int64), ("w0", C.c_int64),
+                ("cross", C.c_int64), ("fixpoint_rounds", C.c_int64),
+                ("ms_h2d", C.c_float), ("ms_analysis", C.c_float), ("ms_sort", C.c_float),
+                ("ms_execute", C.c_float), ("ms_d2h", C.c_float), ("ms_total", C.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ExecOpts(C.Structure):
+    _fields_ = [("conflict_mode", C.c_int32), ("block_threads", C.c_int32),
+                ("part_size", C.c_int32), ("timing", C.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library; raises if it was not built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise GputxError(ECUDA, f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH, mode=C.RTLD_GLOBAL)
+        p, i32, i64, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t
+        sig = {
+            "gputx_create_db": ([C.POINTER(SchemaDesc), C.POINTER(Config), p, C.POINTER(p)], C.c_int),
+            "gputx_destroy_db": ([p], None),
+            "gputx_last_error": ([p], C.c_char_p),
+            "gputx_register_types": ([p, p, C.c_int], C.c_int),
+            "gputx_load_table": ([p, C.c_int, p, sz], C.c_int),
+            "gputx_read_table": ([p, C.c_int, p, sz, C.POINTER(sz)], C.c_int),
+            "gputx_submit_bulk": ([p, p, p, p, C.c_int, sz, C.c_int, C.POINTER(p)], C.c_int),
+            "gputx_execute": ([p, p, C.c_int, C.POINTER(ExecOpts)], C.c_int),
+            "gputx_sync_bulk": ([p, C.POINTER(ExecStats)], C.c_int),
+            "gputx_read_results": ([p, p, p, sz, C.c_int], C.c_int),
+            "gputx_bulk_results_device": ([p, C.POINTER(p), C.POINTER(p)], C.c_int),
+            "gputx_output_width": ([p], C.c_int),
+            "gputx_free_bulk": ([p], None),
+            "gputx_version": ([], C.c_char_p),
+            "gputx_launch_count": ([], C.c_ulonglong),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    """Address of a numpy array, a torch tensor (host or device) or None."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+# --- one-to-one wrappers of the C entry points -------------------------------
+def _check(db, st):
+    if st != OK:
+        msg = lib().gputx_last_error(db).decode() if db else ""
+        raise GputxError(st, msg)
+
+
+def gputx_version() -> str:
+    return lib().gputx_version().decode()
+
+
+def gputx_launch_count() -> int:
+    return int(lib().gputx_launch_count())
+
+
+def gputx_create_db(schema: SchemaDesc, cfg: Config | None = None, stream: int | None = None):
+    out = C.c_void_p()
+    st = lib().gputx_create_db(C.byref(schema), C.byref(cfg) if cfg else None,
+                               C.c_void_p(stream) if stream else None, C.byref(out))
+    if st != OK:
+        raise GputxError(st, "create_db")
+    return out
+
+
+def gputx_destroy_db(db):
+    lib().gputx_destroy_db(db)
+
+
+def gputx_last_error(db) -> str:
+    return lib().gputx_last_error(db).decode()
+
+
+def gputx_register_types(db, type_ids):
+    arr = np.ascontiguousarray(type_ids, dtype=np.int32)
+    _check(db, lib().gputx_register_types(db, _ptr(arr), len(arr)))
+
+
+def gputx_load_table(db, table: int, rows):
+    rows = np.ascontiguousarray(rows, dtype=np.int64).reshape(-1, TABLE_FIELDS[table])
+    _check(db, lib().gputx_load_table(db, table, _ptr(rows), rows.shape[0]))
+
+
+def gputx_read_table(db, table: int) -> np.ndarray:
+    n = C.c_size_t()
+    _check(db, lib().gputx_read_table(db, table, None, 0, C.byref(n)))
+    rows = np.zeros((n.value, TABLE_FIELDS[table]), dtype=np.int64)
+    _check(db, lib().gputx_read_table(db, table, _ptr(rows), n.value, C.byref(n)))
+    return rows[: n.value]
+
+
+def gputx_submit_bulk(db, ts, type_, params, params_per_txn: int, n: int, mem: int = MEM_HOST):
+    out = C.c_void_p()
+    _check(db, lib().gputx_submit_bulk(db, _ptr(ts), _ptr(type_), _ptr(params), params_per_txn,
+                                       n, mem, C.byref(out)))
+    return out
+
+
+def gputx_execute(db, bulk, strategy: int, opts: ExecOpts | None = None):
+    _check(db, lib().gputx_execute(db, bulk, strategy, C.byref(opts) if opts else None))
+
+
+def gputx_sync_bulk(db, bulk) -> ExecStats:
+    stats = ExecStats()
+    _check(db, lib().gputx_sync_bulk(bulk, C.byref(stats)))
+    return stats
+
+
+def gputx_read_results(db, bulk, n: int, width: int, status=None, values=None):
+    if status is None:
+        status = np.zeros(n, dtype=np.int32)
+    if values is None:
+        values = np.zeros((n, width), dtype=np.int64)
+    _check(db, lib().gputx_read_results(bulk, _ptr(status), _ptr(values), n, width))
+    return status, values
+
+
+def gputx_bulk_results_device(bulk):
+    s, v = C.c_void_p(), C.c_void_p()
+    lib().gputx_bulk_results_device(bulk, C.byref(s), C.byref(v))
+    return s.value, v.value
+
+
+def gputx_output_width(db) -> int:
+    return lib().gputx_output_width(db)
+
+
+def gputx_free_bulk(bulk):
+    lib().gputx_free_bulk(bulk)
+
+
+# --- conveniences --------------------------------------------------------------
+class Bulk:
+    def __init__(self, db: "Database", handle, n: int, keep=()):
+        self.db, self.h, self.n = db, handle, n
+        self._keep = keep   # device inputs referenced in place stay alive
+
+    def execute(self, strategy="kset", conflict_mode=CONFLICT_PAPER, block_threads=0, part_size=0,
+                timing=False):
+        s = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
+        gputx_execute(self.db.h, self.h, s, ExecOpts(conflict_mode, block_threads, part_size, int(timing)))
+        return self
+
+    def sync(self) -> dict:
+        return gputx_sync_bulk(self.db.h, self.h).as_dict()
+
+    def results(self, status=None, values=None):
+        return gputx_read_results(self.db.h, self.h, self.n, self.db.width, status, values)
+
+    def free(self):
+        if self.h:
+            gputx_free_bulk(self.h)
+            self.h = None
+            self._keep = ()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Database:
+    """A device-resident database of the built-in schemas."""
+
+    def __init__(self, dc=None, sub=None, oe=None, history_capacity=0, sub_child_capacity=0,
+                 order_capacity=0, orderline_capacity=0, max_bulk=1 << 22, block_threads=256,
+                 part_size=0, spin_limit_ns=0, stream=None, **alg1):
+        sch = SchemaDesc()
+        if dc is not None:
+            sch.dc_branches, sch.dc_tellers, sch.dc_accounts = dc
+            sch.dc_history_capacity = history_capacity
+        if sub is not None:
+            sch.sub_subscribers = sub
+            sch.sub_child_capacity = sub_child_capacity
+        if oe is not None:
+            sch.oe_warehouses, sch.oe_items = oe
+            sch.oe_order_capacity = order_capacity
+            sch.oe_orderline_capacity = orderline_capacity
+        cfg = Config(max_bulk, block_threads, part_size, spin_limit_ns,
+                     alg1.get("kset_w0_min", 0), alg1.get("part_c_max", 0), alg1.get("part_d_min", 0))
+        self.h = gputx_create_db(sch, cfg, stream)
+        self.width = gputx_output_width(self.h)
+
+    def register(self, types):
+        gputx_register_types(self.h, list(types))
+
+    def load(self, table: int, rows):
+        gputx_load_table(self.h, table, rows)
+
+    def read(self, table: int) -> np.ndarray:
+        return gputx_read_table(self.h, table)
+
+    def submit(self, ts, type_, params, mem=None) -> Bulk:
+        """Host numpy arrays or CUDA tensors (mem inferred from the first)."""
+        n = len(ts)
+        if mem is None:
+            mem = MEM_DEVICE if getattr(ts, "is_cuda", False) else MEM_HOST
+        if mem == MEM_HOST:
+            ts = np.ascontiguousarray(ts, dtype=np.int64)
+            type_ = np.ascontiguousarray(type_, dtype=np.int32)
+            params = np.ascontiguousarray(params, dtype=np.int64)
+        P = params.shape[1] if params.ndim == 2 else 1
+        h = gputx_submit_bulk(self.h, ts, type_, params, P, n, mem)
+        return Bulk(self, h, n, keep=(ts, type_, params) if mem == MEM_DEVICE else ())
+
+    def submit_dict(self, bulk: dict, mem=None) -> Bulk:
+        return self.submit(bulk["ts"], bulk["type"], bulk["params"], mem)
+
+    def close(self):
+        if self.h:
+            gputx_destroy_db(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,575 @@
+// analysis.cu -- bulk generation on the device (Section 4.2, Section 5.2 step
+// 1-2, Appendix D): basic-operation extraction, grouping by data item with a
+// radix sort, per-group ranks, transaction depths (k-set levels), regrouping
+// by (level, type), insert slots, partition ids.
+#include <cstdio>
+
+#include "engine.h"
+#include "procs.cuh"
+#include "scan.cuh"
+
+namespace gtx {
+
+namespace {
+
+constexpr int TB = 256;  // threads per block of the simple map kernels
+
+inline unsigned grid_for(int64_t n, int block = TB)
+{
+    int64_t g = (n + block - 1) / block;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+// ---------------------------------------------------------------------------
+// bulk begin / finish: insert bases from the device cursors
+// ---------------------------------------------------------------------------
+__global__ void begin_kernel(const InsertBase *cursor, BulkCtl *ctl, int64_t hist_rows)
+{
+    ctl->base = *cursor;
+    ctl->total.hist = hist_rows;
+}
+
+__global__ void finish_kernel(InsertBase *cursor, const BulkCtl *ctl)
+{
+    if (ctl->err) return;
+    cursor->hist += ctl->total.hist;
+    cursor->cf += ctl->total.cf;
+    cursor->ord += ctl->total.ord;
+    cursor->ol += ctl->total.ol;
+}
+
+// ---------------------------------------------------------------------------
+// a2: basic-operation extraction (map), with validation and partition ids
+// ---------------------------------------------------------------------------
+struct ExtractArgs {
+    DevDB db;
+    DevBulk b;
+    BulkCtl *ctl;
+    uint32_t *keys, *vals;         // op keys / payloads
+    const uint32_t *op_off;        // exclusive op offsets or null (uniform)
+    int uniform_k;
+    int mode;
+    int part_size;
+    uint32_t *pid_key, *pid_val;   // PART: partition id and txn per transaction (or null)
+    bool write_ops;
+};
+
+__device__ __forceinline__ bool txn_valid(const DevDB &db, const DevBulk &b, int64_t t)
+{
+    const int64_t *p = b.params + t * b.P;
+    if (!valid_txn(db, b.type[t], p, b.P)) return false;
+    if (t > 0 && !(b.ts[t] > b.ts[t - 1])) return false;   // ids strictly increase
+    return true;
+}
+
+__global__ void count_ops_kernel(DevDB db, DevBulk b, BulkCtl *ctl, uint32_t *cnt)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= b.n) return;
+    int c = 0;
+    if (txn_valid(db, b, t)) c = op_count(db, b.type[t], b.params + t * b.P);
+    else set_err(&ctl->err, ERR_INVAL);
+    cnt[t] = (uint32_t)c;
+}
+
+__global__ void extract_kernel(ExtractArgs a)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool cross = false;
+    if (t < a.b.n) {
+        const int64_t *p = a.b.params + t * a.b.P;
+        const int64_t off = a.op_off ? (int64_t)a.op_off[t] : t * a.uniform_k;
+        const bool ok = txn_valid(a.db, a.b, t);
+        uint32_t obj[MAX_OPS], root[MAX_OPS];
+        uint8_t cls[MAX_OPS];
+        int k = 0;
+        if (ok) {
+            k = access_set(a.db, a.b.type[t], p, a.mode, obj, cls, root);
+        } else {
+            set_err(&a.ctl->err, ERR_INVAL);
+        }
+        if (a.op_off == nullptr) {
+            // uniform layout: always fill K slots (dummy reads on object 0 for
+            // an invalid transaction; the bulk will not execute)
+            for (int j = k; j < a.uniform_k; j++) { obj[j] = 0; cls[j] = CLS_R; root[j] = 0; }
+            k = a.uniform_k;
+        }
+        const uint32_t pid = k ? root[0] / (uint32_t)a.part_size : 0;
+        for (int j = 0; j < k; j++) {
+            if (a.write_ops) {
+                a.keys[off + j] = obj[j];
+                a.vals[off + j] = ((uint32_t)t << 7) | ((uint32_t)j << 2) | cls[j];
+            }
+            cross |= (root[j] / (uint32_t)a.part_size) != pid;
+        }
+        if (a.pid_key) {
+            a.pid_key[t] = pid;
+            a.pid_val[t] = (uint32_t)t;
+        }
+    }
+    const uint32_t cross_mask = __ballot_sync(0xffffffffu, cross);
+    if ((threadIdx.x & 31) == 0 && cross_mask) atomicAdd(&a.ctl->cross, (uint32_t)__popc(cross_mask));
+}
+
+// exclusive op offsets from per-transaction counts
+struct OffsetMode {
+    const uint32_t *cnt;
+    uint32_t *off;
+    int64_t n;
+    __device__ uint64_t element(int64_t i) const { return DualSeg::make(0, 0, 0, cnt[i]); }
+    __device__ void output(int64_t i, uint64_t s) const
+    {
+        off[i + 1] = DualSeg::v2(s);
+        if (i == 0) off[0] = 0;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// a4/a5: ranks in each group and transaction depth (Section 4.2 steps 2-5)
+// ---------------------------------------------------------------------------
+// Within a group (one data item, operations in timestamp order) an operation
+// starts a new run unless it and its predecessor are both reads or both ADDs.
+// rank = run index within the group; depth(t) = max rank over t's operations.
+struct RankMode {
+    const uint32_t *sk, *sv;
+    uint32_t *level;
+    uint32_t *rid;   // optional: global run id, bit 31 = first run of its group
+    __device__ uint64_t element(int64_t i) const
+    {
+        const uint32_t k = sk[i], v = sv[i];
+        const bool head = (i == 0) || sk[i - 1] != k;
+        uint32_t runhead = 1;
+        if (!head) {
+            const uint32_t c = v & 3u, pc = sv[i - 1] & 3u;
+            runhead = !(c == pc && c != CLS_W);
+        }
+        return DualSeg::make(head, head ? 0u : runhead, 0, runhead);
+    }
+    __device__ void output(int64_t i, uint64_t s) const
+    {
+        const uint32_t rank = DualSeg::v1(s);
+        const uint32_t txn = sv[i] >> 7;
+        atomicMax(&level[txn], rank);
+        if (rid) rid[i] = (DualSeg::v2(s) - 1u) | (rank == 0 ? 0x80000000u : 0u);
+    }
+};
+
+// TPL tickets: number of operations of the group before this operation's run
+// (Section 5.1 key values, read with ticket semantics).
+struct TicketMode {
+    const uint32_t *sk, *sv;
+    uint32_t *lock_key, *lock_ticket;
+    const uint32_t *op_off;
+    int uniform_k;
+    __device__ uint64_t element(int64_t i) const
+    {
+        const uint32_t k = sk[i], v = sv[i];
+        const bool head = (i == 0) || sk[i - 1] != k;
+        uint32_t runhead = 1;
+        if (!head) {
+            const uint32_t c = v & 3u, pc = sv[i - 1] & 3u;
+            runhead = !(c == pc && c != CLS_W);
+        }
+        return DualSeg::make(head, 1, runhead, 1);
+    }
+    __device__ void output(int64_t i, uint64_t s) const
+    {
+        const uint32_t v = sv[i];
+        const uint32_t txn = v >> 7, j = (v >> 2) & 31u;
+        const int64_t slot = (op_off ? (int64_t)op_off[txn] : (int64_t)txn * uniform_k) + j;
+        lock_key[slot] = sk[i];
+        lock_ticket[slot] = DualSeg::v1(s) - DualSeg::v2(s);
+    }
+};
+
+// one Jacobi round of the exact-depth refinement (Section 4.1's longest
+// path): every operation of a run after its group's first run conflicts with
+// all operations of the run before it, so its transaction needs depth at
+// least 1 + the largest depth in that run.  Starting from the one-pass ranks
+// (a lower bound) the rounds climb to the longest-path depths.
+__global__ void runmax_kernel(const uint32_t *sv, const uint32_t *rid, const uint32_t *level, uint32_t *runmax,
+                              int64_t m, const uint32_t *err)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m || *err) return;
+    atomicMax(&runmax[rid[i] & 0x7fffffffu], level[sv[i] >> 7]);
+}
+
+__global__ void relax_kernel(const uint32_t *sv, const uint32_t *rid, const uint32_t *runmax, uint32_t *level,
+                             BulkCtl *ctl, int64_t m)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool grew = false;
+    if (i < m && !ctl->err) {
+        const uint32_t r = rid[i];
+        if (!(r & 0x80000000u)) {
+            const uint32_t cand = runmax[(r & 0x7fffffffu) - 1u] + 1u;
+            grew = atomicMax(&level[sv[i] >> 7], cand) < cand;
+        }
+    }
+    if (__any_sync(0xffffffffu, grew) && (threadIdx.x & 31) == 0) ctl->changed = 1;
+}
+
+// d and w0 (Appendix D structural parameters)
+__global__ void level_stats_kernel(const uint32_t *level, int64_t n, BulkCtl *ctl)
+{
+    __shared__ uint32_t s_max, s_zero;
+    if (threadIdx.x == 0) { s_max = 0; s_zero = 0; }
+    __syncthreads();
+    uint32_t mx = 0, zero = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t l = level[i];
+        mx = l > mx ? l : mx;
+        zero += (l == 0);
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    zero = __reduce_add_sync(0xffffffffu, zero);
+    if ((threadIdx.x & 31) == 0) { atomicMax(&s_max, mx); atomicAdd(&s_zero, zero); }
+    __syncthreads();
+    if (threadIdx.x == 0) { atomicMax(&ctl->depth, s_max); atomicAdd(&ctl->w0, s_zero); }
+}
+
+// ---------------------------------------------------------------------------
+// a6: regroup by (level, type) -- Appendix D's grouping by type, per level
+// ---------------------------------------------------------------------------
+__global__ void regroup_keys_kernel(const uint32_t *level, const int32_t *type, int64_t n, int tbits,
+                                    uint32_t *keys, uint32_t *vals)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    keys[t] = (level[t] << tbits) | (tbits ? (uint32_t)type[t] : 0u);
+    vals[t] = (uint32_t)t;
+}
+
+__global__ void level_off_kernel(const uint32_t *skeys, int64_t n, int tbits, uint32_t *level_off,
+                                 const uint32_t *err)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n || *err) return;
+    const uint32_t lv = skeys[i] >> tbits;
+    const uint32_t prev = i ? (skeys[i - 1] >> tbits) : 0u;
+    if (i == 0) {
+        for (uint32_t k = 0; k <= lv; k++) level_off[k] = 0;
+    } else if (lv != prev) {
+        for (uint32_t k = prev + 1; k <= lv; k++) level_off[k] = (uint32_t)i;
+    }
+    if (i == n - 1) level_off[lv + 1] = (uint32_t)n;
+}
+
+struct ChunkMode {
+    const uint32_t *level_off;
+    uint32_t *chunk_off;
+    uint32_t block;
+    __device__ uint64_t element(int64_t k) const
+    {
+        const uint32_t w = level_off[k + 1] - level_off[k];
+        return DualSeg::make(0, 0, 0, (w + block - 1) / block);
+    }
+    __device__ void output(int64_t k, uint64_t s) const
+    {
+        chunk_off[k + 1] = DualSeg::v2(s);
+        if (k == 0) chunk_off[0] = 0;
+    }
+};
+
+__global__ void chunk_level_kernel(const uint32_t *chunk_off, int64_t levels, uint32_t *chunk_level, int64_t cap,
+                                   const uint32_t *err)
+{
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (*err) return;
+    const uint32_t nchunks = chunk_off[levels];
+    if (c >= cap || c >= nchunks) return;
+    // largest k with chunk_off[k] <= c
+    int64_t lo = 0, hi = levels - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (chunk_off[mid] <= (uint32_t)c) lo = mid;
+        else hi = mid - 1;
+    }
+    chunk_level[c] = (uint32_t)lo;
+}
+
+// ---------------------------------------------------------------------------
+// a7: deterministic insert slots: exclusive counts in timestamp order
+// ---------------------------------------------------------------------------
+struct SlotMode {
+    const int32_t *type;
+    const int64_t *params;
+    int P;
+    int64_t n;
+    uint32_t *slot_a, *slot_b;
+    BulkCtl *ctl;
+    int which;   // 0: (call-forwarding inserts, orders) 1: (-, order lines)
+    __device__ uint32_t a(int64_t t) const
+    {
+        return which == 0 ? (type[t] == GPUTX_T_SUB_INSERT_CF) : 0u;
+    }
+    __device__ uint32_t bv(int64_t t) const
+    {
+        if (type[t] != GPUTX_T_OE_NEW_ORDER) return 0u;
+        if (which == 0) return 1u;
+        const int64_t c = params[t * P + 3];
+        return (c >= 1 && c <= OE_MAX_LINES) ? (uint32_t)c : 0u;
+    }
+    __device__ uint64_t element(int64_t t) const { return DualSeg::make(0, a(t), 0, bv(t)); }
+    __device__ void output(int64_t t, uint64_t s) const
+    {
+        const uint32_t ia = DualSeg::v1(s), ib = DualSeg::v2(s);
+        if (which == 0) {
+            slot_a[t] = ia - a(t);
+            slot_b[t] = ib - bv(t);
+            if (t == n - 1) { ctl->total.cf = ia; ctl->total.ord = ib; }
+        } else {
+            slot_b[t] = ib - bv(t);
+            if (t == n - 1) ctl->total.ol = ib;
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// PART: partition starts; TPL: counter reset
+// ---------------------------------------------------------------------------
+__global__ void part_heads_kernel(const uint32_t *skeys, int64_t n, uint32_t *part_start, BulkCtl *ctl)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n || ctl->err) return;
+    if (i == 0 || skeys[i] != skeys[i - 1]) part_start[atomicAdd(&ctl->npart, 1u)] = (uint32_t)i;
+}
+
+__global__ void tpl_reset_kernel(const uint32_t *skeys, int64_t m, uint32_t *done, uint32_t n_objects)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const uint32_t k = skeys[i];
+    if ((i == 0 || skeys[i - 1] != k) && k < n_objects) done[k] = 0;
+}
+
+template <class Mode>
+cudaError_t run_scan(gputx_bulk *b, const Mode &mode, int64_t count, int ctr_slot)
+{
+    if (count <= 0) return cudaSuccess;
+    const int64_t tiles = (count + SCAN_TILE - 1) / SCAN_TILE;
+    if (tiles > b->sc.scan_tiles) return cudaErrorInvalidValue;
+    cudaStream_t s = b->db->stream;
+    cudaError_t e = cudaMemsetAsync(b->sc.scan_status, 0, tiles * sizeof(uint64_t), s);
+    if (e) return e;
+    e = cudaMemsetAsync(b->sc.tile_ctr + ctr_slot, 0, sizeof(uint32_t), s);
+    if (e) return e;
+    dualseg_scan_kernel<Mode><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(
+        mode, count, b->sc.scan_status, b->sc.tile_ctr + ctr_slot, &b->ctl->err,
+        (uint64_t)b->db->cfg.spin_limit_ns);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+inline DevBulk dev_bulk(gputx_bulk *b, int mode)
+{
+    DevBulk d{};
+    d.n = b->n;
+    d.P = b->P;
+    d.R = b->R;
+    d.ts = b->ts;
+    d.type = b->type;
+    d.params = b->params;
+    d.status = b->status;
+    d.out = b->out;
+    d.err = &b->ctl->err;
+    d.base = &b->ctl->base;
+    d.slot_cf = b->sc.slot_cf;
+    d.slot_ord = b->sc.slot_ord;
+    d.slot_ol = b->sc.slot_ol;
+    d.conflict_mode = mode;
+    return d;
+}
+
+}  // namespace
+
+DevBulk make_dev_bulk(gputx_bulk *b, int mode) { return dev_bulk(b, mode); }
+
+cudaError_t launch_begin(gputx_bulk *b)
+{
+    const bool dc = (b->db->dev.registered & 1u) != 0;
+    begin_kernel<<<1, 1, 0, b->db->stream>>>(b->db->d_cursor, b->ctl, dc ? b->n : 0);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish(gputx_bulk *b)
+{
+    finish_kernel<<<1, 1, 0, b->db->stream>>>(b->db->d_cursor, b->ctl);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_extract(gputx_bulk *b, int mode, int part_size, uint32_t *pid_key, uint32_t *pid_val,
+                           bool write_ops)
+{
+    gputx_db *db = b->db;
+    cudaStream_t s = db->stream;
+    if (b->n == 0) return cudaSuccess;
+    ExtractArgs a{};
+    a.db = db->dev;
+    a.b = dev_bulk(b, mode);
+    a.ctl = b->ctl;
+    a.keys = b->sc.keys_a;
+    a.vals = b->sc.vals_a;
+    a.uniform_k = db->uniform_k;
+    a.mode = mode;
+    a.part_size = part_size < 1 ? 1 : part_size;
+    a.pid_key = pid_key;
+    a.pid_val = pid_val;
+    a.write_ops = write_ops;
+    if (!db->uniform_k && write_ops) {
+        // counts into level[] (free until the rank scan), then offsets
+        count_ops_kernel<<<grid_for(b->n), TB, 0, s>>>(db->dev, a.b, b->ctl, b->sc.level);
+        count_launches(1);
+        cudaError_t e = cudaGetLastError();
+        if (e) return e;
+        OffsetMode om{b->sc.level, b->sc.op_off, b->n};
+        e = run_scan(b, om, b->n, 0);
+        if (e) return e;
+        a.op_off = b->sc.op_off;
+    }
+    extract_kernel<<<grid_for(b->n), TB, 0, s>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort(gputx_bulk *b, uint32_t *&keys, uint32_t *&vals, uint32_t *&keys_alt, uint32_t *&vals_alt,
+                        int64_t count, int bits)
+{
+    if (count <= 1 || bits <= 0) return cudaSuccess;
+    cudaStream_t s = b->db->stream;
+    const int passes = (bits + 7) / 8;
+    const int64_t tiles = (count + SORT_TILE - 1) / SORT_TILE;
+    if (tiles > b->sc.sort_tiles || passes > 4) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(b->sc.sort_hist, 0, 4 * RADIX * sizeof(uint32_t), s);
+    if (e) return e;
+    e = cudaMemsetAsync(b->sc.sort_status, 0, (size_t)passes * tiles * RADIX * sizeof(uint32_t), s);
+    if (e) return e;
+    e = cudaMemsetAsync(b->sc.tile_ctr + 8, 0, 4 * sizeof(uint32_t), s);
+    if (e) return e;
+    static bool smem_set = false;
+    if (!smem_set) {
+        e = cudaFuncSetAttribute(radix_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SORT_SMEM);
+        if (e) return e;
+        smem_set = true;
+    }
+    int hist_blocks = b->db->num_sms * 4;
+    const int64_t need = (count + 255) / 256;
+    if (hist_blocks > need) hist_blocks = (int)need;
+    radix_hist_kernel<<<hist_blocks, 256, 0, s>>>(keys, count, passes, b->sc.sort_hist, &b->ctl->err);
+    count_launches(1);
+    radix_offsets_kernel<<<passes, RADIX, 0, s>>>(b->sc.sort_hist, b->sc.sort_offs);
+    count_launches(1);
+    for (int p = 0; p < passes; p++) {
+        radix_pass_kernel<<<(unsigned)tiles, SORT_THREADS, SORT_SMEM, s>>>(
+            keys, vals, keys_alt, vals_alt, count, 8 * p, b->sc.sort_offs + p * RADIX,
+            b->sc.sort_status + (size_t)p * tiles * RADIX, b->sc.tile_ctr + 8 + p, &b->ctl->err,
+            (uint64_t)b->db->cfg.spin_limit_ns);
+        count_launches(1);
+        e = cudaGetLastError();
+        if (e) return e;
+        uint32_t *t = keys; keys = keys_alt; keys_alt = t;
+        t = vals; vals = vals_alt; vals_alt = t;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_rank_scan(gputx_bulk *b, const uint32_t *sk, const uint32_t *sv, int64_t m, bool want_rid)
+{
+    cudaError_t e = cudaMemsetAsync(b->sc.level, 0, b->n * sizeof(uint32_t), b->db->stream);
+    if (e) return e;
+    RankMode rm{sk, sv, b->sc.level, want_rid ? b->sc.rid : nullptr};
+    return run_scan(b, rm, m, 1);
+}
+
+cudaError_t launch_ticket_scan(gputx_bulk *b, const uint32_t *sk, const uint32_t *sv, int64_t m)
+{
+    TicketMode tm{sk, sv, b->sc.lock_key, b->sc.lock_ticket, b->db->uniform_k ? nullptr : b->sc.op_off,
+                  b->db->uniform_k};
+    return run_scan(b, tm, m, 2);
+}
+
+cudaError_t launch_fixpoint_round(gputx_bulk *b, const uint32_t *sv, int64_t m)
+{
+    cudaStream_t s = b->db->stream;
+    if (m == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(b->sc.runmax, 0, m * sizeof(uint32_t), s);
+    if (e) return e;
+    e = cudaMemsetAsync(&b->ctl->changed, 0, sizeof(uint32_t), s);
+    if (e) return e;
+    runmax_kernel<<<grid_for(m), TB, 0, s>>>(sv, b->sc.rid, b->sc.level, b->sc.runmax, m, &b->ctl->err);
+    count_launches(1);
+    relax_kernel<<<grid_for(m), TB, 0, s>>>(sv, b->sc.rid, b->sc.runmax, b->sc.level, b->ctl, m);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_level_stats(gputx_bulk *b)
+{
+    if (b->n == 0) return cudaSuccess;
+    int blocks = b->db->num_sms * 2;
+    const int64_t need = (b->n + 255) / 256;
+    if (blocks > need) blocks = (int)need;
+    level_stats_kernel<<<blocks, 256, 0, b->db->stream>>>(b->sc.level, b->n, b->ctl);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_regroup_keys(gputx_bulk *b, uint32_t *keys, uint32_t *vals)
+{
+    if (b->n == 0) return cudaSuccess;
+    regroup_keys_kernel<<<grid_for(b->n), TB, 0, b->db->stream>>>(b->sc.level, b->type, b->n, b->db->tbits,
+                                                                   keys, vals);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_level_tables(gputx_bulk *b, const uint32_t *skeys, int64_t depth, int block)
+{
+    cudaStream_t s = b->db->stream;
+    if (b->n == 0) return cudaSuccess;
+    level_off_kernel<<<grid_for(b->n), TB, 0, s>>>(skeys, b->n, b->db->tbits, b->sc.level_off, &b->ctl->err);
+    count_launches(1);
+    const int64_t levels = depth + 1;
+    ChunkMode cm{b->sc.level_off, b->sc.chunk_off, (uint32_t)block};
+    cudaError_t e = run_scan(b, cm, levels, 3);
+    if (e) return e;
+    chunk_level_kernel<<<grid_for(b->sc.chunk_cap), TB, 0, s>>>(b->sc.chunk_off, levels, b->sc.chunk_level,
+                                                                b->sc.chunk_cap, &b->ctl->err);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_insert_slots(gputx_bulk *b)
+{
+    if (b->n == 0) return cudaSuccess;
+    const uint32_t reg = b->db->dev.registered;
+    const bool sub_ins = (reg >> GPUTX_T_SUB_INSERT_CF) & 1u;
+    const bool oe_no = (reg >> GPUTX_T_OE_NEW_ORDER) & 1u;
+    if (!sub_ins && !oe_no) return cudaSuccess;
+    SlotMode m0{b->type, b->params, b->P, b->n, b->sc.slot_cf, b->sc.slot_ord, b->ctl, 0};
+    cudaError_t e = run_scan(b, m0, b->n, 5);
+    if (e || !oe_no) return e;
+    SlotMode m1{b->type, b->params, b->P, b->n, nullptr, b->sc.slot_ol, b->ctl, 1};
+    return run_scan(b, m1, b->n, 6);
+}
+
+cudaError_t launch_part_heads(gputx_bulk *b, const uint32_t *skeys, int64_t n)
+{
+    if (n == 0) return cudaSuccess;
+    part_heads_kernel<<<grid_for(n), TB, 0, b->db->stream>>>(skeys, n, b->sc.part_start, b->ctl);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tpl_reset(gputx_bulk *b, const uint32_t *skeys, int64_t m)
+{
+    if (m == 0) return cudaSuccess;
+    tpl_reset_kernel<<<grid_for(m), TB, 0, b->db->stream>>>(skeys, m, b->db->d_done, b->db->dev.n_objects);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace gtx

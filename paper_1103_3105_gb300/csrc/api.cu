@@ -1,0 +1,1015 @@
+// api.cu -- the C ABI (include/gputx.h): database creation and loading, bulk
+// submission, strategy dispatch (Section 5 / Algorithm 1), synchronisation
+// and result read-back.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <unordered_set>
+#include <vector>
+
+#include "engine.h"
+
+using namespace gtx;
+
+namespace {
+
+constexpr int64_t HIST_HOLE = INT64_MIN;
+
+gputx_status fail(gputx_db *db, gputx_status st, const char *fmt, ...)
+    __attribute__((format(printf, 3, 4)));
+
+gputx_status fail(gputx_db *db, gputx_status st, const char *fmt, ...)
+{
+    if (db) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        db->last_error = buf;
+    }
+    return st;
+}
+
+gputx_status cuda_fail(gputx_db *db, cudaError_t e, const char *what)
+{
+    return fail(db, e == cudaErrorMemoryAllocation ? GPUTX_ENOMEM : GPUTX_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(db, e_, what); \
+    } while (0)
+
+template <class T> gputx_status dalloc(gputx_db *db, T **p, int64_t count, const char *what)
+{
+    *p = nullptr;
+    if (count <= 0) return GPUTX_OK;
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, (size_t)count * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(db, e, what);
+    db->allocs.push_back(q);
+    e = cudaMemsetAsync(q, 0, (size_t)count * sizeof(T), db->stream);
+    if (e != cudaSuccess) return cuda_fail(db, e, what);
+    *p = (T *)q;
+    return GPUTX_OK;
+}
+
+uint64_t next_pow2(uint64_t v)
+{
+    uint64_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// host replica of the device hash (MurmurHash3 64-bit finaliser) for bulk loads
+uint64_t hmix_host(unsigned long long k)
+{
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+gputx_status alloc_hash(gputx_db *db, HashIndex &h, int64_t rows, const char *what)
+{
+    const uint64_t cap = next_pow2((uint64_t)std::max<int64_t>(rows, 1) * 2);
+    gputx_status st = dalloc(db, &h.keys, (int64_t)cap, what);
+    if (st) return st;
+    st = dalloc(db, &h.rows, (int64_t)cap, what);
+    if (st) return st;
+    h.mask = cap - 1;
+    cudaError_t e = launch_fill_u64(h.keys, (int64_t)cap, HKEY_EMPTY, db->stream);
+    if (e) return cuda_fail(db, e, what);
+    return GPUTX_OK;
+}
+
+// builds a hash index for rows 0..n-1 with the given keys on the host and
+// uploads it; false on a duplicate key
+gputx_status upload_hash(gputx_db *db, const HashIndex &h, const std::vector<unsigned long long> &keys)
+{
+    const uint64_t cap = h.mask + 1;
+    if ((uint64_t)keys.size() * 2 > cap) return fail(db, GPUTX_ECAPACITY, "hash index too small");
+    std::vector<unsigned long long> hk(cap, HKEY_EMPTY);
+    std::vector<uint32_t> hr(cap, 0);
+    for (size_t r = 0; r < keys.size(); r++) {
+        uint64_t i = hmix_host(keys[r]) & h.mask;
+        while (hk[i] != HKEY_EMPTY) {
+            if (hk[i] == keys[r]) return fail(db, GPUTX_EINVAL, "duplicate key in loaded rows");
+            i = (i + 1) & h.mask;
+        }
+        hk[i] = keys[r];
+        hr[i] = (uint32_t)r;
+    }
+    CK(cudaMemcpy(h.keys, hk.data(), cap * sizeof(unsigned long long), cudaMemcpyHostToDevice), "hash upload");
+    CK(cudaMemcpy(h.rows, hr.data(), cap * sizeof(uint32_t), cudaMemcpyHostToDevice), "hash upload");
+    return GPUTX_OK;
+}
+
+int table_fields(int table)
+{
+    static const int f[GPUTX_NUM_TABLES] = {1, 1, 1, 5, 16, 6, 6, 5, 2, 3, 5, 1, 3, 5, 7};
+    return (table >= 0 && table < GPUTX_NUM_TABLES) ? f[table] : 0;
+}
+
+template <class T> gputx_status put_col(gputx_db *db, T *dst, const std::vector<T> &v)
+{
+    if (v.empty()) return GPUTX_OK;
+    CK(cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, db->stream), "load");
+    CK(cudaStreamSynchronize(db->stream), "load");
+    return GPUTX_OK;
+}
+
+template <class T> gputx_status get_col(gputx_db *db, std::vector<T> &v, const T *src, int64_t n)
+{
+    v.resize((size_t)std::max<int64_t>(n, 0));
+    if (n <= 0) return GPUTX_OK;
+    CK(cudaMemcpyAsync(v.data(), src, (size_t)n * sizeof(T), cudaMemcpyDeviceToHost, db->stream), "read");
+    CK(cudaStreamSynchronize(db->stream), "read");
+    return GPUTX_OK;
+}
+
+int type_schema(int t)
+{
+    if (t == GPUTX_T_DC_DEBIT_CREDIT) return 0;
+    if (t >= GPUTX_T_SUB_GET_SUBSCRIBER && t <= GPUTX_T_SUB_DELETE_CF) return 1;
+    if (t >= GPUTX_T_OE_NEW_ORDER && t <= GPUTX_T_OE_ORDER_STATUS) return 2;
+    return -1;
+}
+
+// operations per type: fixed count, or -1 when it depends on the parameters
+int type_ops(int t, int *maxk)
+{
+    switch (t) {
+    case GPUTX_T_DC_DEBIT_CREDIT: *maxk = 3; return 3;
+    case GPUTX_T_OE_NEW_ORDER: *maxk = 2 + 15; return -1;
+    case GPUTX_T_OE_PAYMENT: *maxk = 3; return 3;
+    case GPUTX_T_OE_ORDER_STATUS: *maxk = 2; return 2;
+    default: *maxk = 1; return 1;
+    }
+}
+
+struct Carver {
+    char *base;
+    size_t off = 0;
+    template <class T> T *take(int64_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T *p = (T *)(base ? base + off : nullptr);
+        off += (size_t)std::max<int64_t>(count, 0) * sizeof(T);
+        return p;
+    }
+};
+
+// lays out (or sizes, with base == nullptr) a bulk's arena
+size_t carve_bulk(gputx_bulk *b, char *base, bool device_inputs)
+{
+    gputx_db *db = b->db;
+    const int64_t n = b->n, m = n * std::max(db->kmax, 1);
+    const int64_t nn = std::max<int64_t>(n, 1), mm = std::max<int64_t>(m, 1);
+    Carver c{base};
+    if (!device_inputs) {
+        b->ts = c.take<int64_t>(nn);
+        b->type = c.take<int32_t>(nn);
+        b->params = c.take<int64_t>(nn * b->P);
+    }
+    b->status = c.take<int32_t>(nn);
+    b->out = c.take<int64_t>(nn * b->R);
+    b->ctl = c.take<BulkCtl>(1);
+    Scratch &s = b->sc;
+    s.m_cap = m;
+    s.keys_a = c.take<uint32_t>(mm);
+    s.vals_a = c.take<uint32_t>(mm);
+    s.keys_b = c.take<uint32_t>(mm);
+    s.vals_b = c.take<uint32_t>(mm);
+    s.op_off = c.take<uint32_t>(nn + 1);
+    s.level = c.take<uint32_t>(nn);
+    s.rid = db->need_fixpoint ? c.take<uint32_t>(mm) : nullptr;
+    s.runmax = db->need_fixpoint ? c.take<uint32_t>(mm) : nullptr;
+    s.lock_key = c.take<uint32_t>(mm);
+    s.lock_ticket = c.take<uint32_t>(mm);
+    s.level_off = c.take<uint32_t>(nn + 2);
+    s.chunk_off = c.take<uint32_t>(nn + 2);
+    s.chunk_cap = nn + nn / 32 + 2;
+    s.chunk_level = c.take<uint32_t>(s.chunk_cap);
+    s.done = c.take<uint32_t>(nn + 1);
+    s.part_start = c.take<uint32_t>(nn);
+    s.pid_key = c.take<uint32_t>(nn);
+    s.pid_val = c.take<uint32_t>(nn);
+    s.pid_key2 = c.take<uint32_t>(nn);
+    s.pid_val2 = c.take<uint32_t>(nn);
+    const bool slots = (db->dev.registered >> GPUTX_T_SUB_INSERT_CF & 1u) ||
+                       (db->dev.registered >> GPUTX_T_OE_NEW_ORDER & 1u);
+    s.slot_cf = slots ? c.take<uint32_t>(nn) : nullptr;
+    s.slot_ord = slots ? c.take<uint32_t>(nn) : nullptr;
+    s.slot_ol = slots ? c.take<uint32_t>(nn) : nullptr;
+    s.sort_hist = c.take<uint32_t>(4 * 256);
+    s.sort_offs = c.take<uint32_t>(4 * 256);
+    const int64_t big = std::max(mm, nn + 2);
+    s.sort_tiles = (big + 8191) / 8192;
+    s.sort_status = c.take<uint32_t>(4 * s.sort_tiles * 256);
+    s.tile_ctr = c.take<uint32_t>(16);
+    s.scan_tiles = (big + 2047) / 2048;
+    s.scan_status = c.take<uint64_t>(s.scan_tiles);
+    return c.off + 256;
+}
+
+gputx_status bulk_error(gputx_db *db, uint32_t err)
+{
+    if (err & ERR_INVAL) return fail(db, GPUTX_EINVAL, "invalid bulk: unknown or unregistered type, "
+                                                       "parameter out of range or timestamps not increasing");
+    if (err & ERR_TIMEOUT) return fail(db, GPUTX_ETIMEOUT, "a bounded device wait ran out");
+    if (err & ERR_CAPACITY) return fail(db, GPUTX_ECAPACITY, "an insert area or hash index is full");
+    if (err & ERR_BOUNDS) return fail(db, GPUTX_EBOUNDS, "device bounds check failed");
+    return GPUTX_OK;
+}
+
+gputx_status read_ctl(gputx_bulk *b)
+{
+    gputx_db *db = b->db;
+    CK(cudaMemcpyAsync(&b->host_ctl, b->ctl, sizeof(BulkCtl), cudaMemcpyDeviceToHost, db->stream), "sync");
+    CK(cudaStreamSynchronize(db->stream), "sync");
+    return GPUTX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *gputx_version(void) { return "gputx-gb300 0.1 (sm_103a)"; }
+
+const char *gputx_last_error(const gputx_db *db) { return db ? db->last_error.c_str() : "null database"; }
+
+int gputx_output_width(const gputx_db *db) { return db ? db->dev.out_width : 0; }
+
+void gputx_destroy_db(gputx_db *db)
+{
+    if (!db) return;
+    cudaStreamSynchronize(db->stream);
+    for (void *p : db->allocs) cudaFree(p);
+    if (db->own_stream) cudaStreamDestroy(db->stream);
+    delete db;
+}
+
+gputx_status gputx_create_db(const gputx_schema_desc *schema, const gputx_config *cfg, void *cuda_stream,
+                             gputx_db **out)
+{
+    if (!schema || !out) return GPUTX_EINVAL;
+    *out = nullptr;
+    gputx_db *db = new (std::nothrow) gputx_db();
+    if (!db) return GPUTX_ENOMEM;
+    db->schema = *schema;
+    if (cfg) db->cfg = *cfg;
+    gputx_config &c = db->cfg;
+    if (c.max_bulk <= 0) c.max_bulk = 1 << 22;
+    if (c.block_threads <= 0) c.block_threads = 256;
+    if (c.spin_limit_ns <= 0) c.spin_limit_ns = 2000000000LL;
+    if (c.kset_w0_min <= 0) c.kset_w0_min = 152 * 256;
+    if (c.part_c_max <= 0) c.part_c_max = 0;
+    if (c.part_d_min <= 0) c.part_d_min = 4096;
+    const gputx_schema_desc &s = db->schema;
+    auto bad = [&](const char *m) {
+        gputx_status st = fail(db, GPUTX_EINVAL, "%s", m);
+        std::string msg = db->last_error;
+        delete db;
+        (void)msg;
+        return st;
+    };
+    if (c.block_threads < 32 || c.block_threads > 1024 || c.block_threads % 32) return bad("block_threads");
+    if (c.max_bulk > (1 << 25)) return bad("max_bulk above 2^25");
+    if (s.dc_branches < 0 || s.dc_tellers < 0 || s.dc_accounts < 0 || s.sub_subscribers < 0 ||
+        s.oe_warehouses < 0 || s.oe_items < 0)
+        return bad("negative size");
+    if (s.dc_branches > 0) {
+        if (s.dc_tellers <= 0 || s.dc_accounts <= 0 || s.dc_tellers % s.dc_branches ||
+            s.dc_accounts % s.dc_tellers)
+            return bad("debit-credit: tellers must be a multiple of branches and accounts of tellers");
+    }
+    if (s.oe_warehouses > 0 && (s.oe_items <= 0 || s.oe_items >= (1 << 24) || s.oe_warehouses >= (1 << 16)))
+        return bad("order-entry sizes");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    db->device = dev;
+    cudaDeviceGetAttribute(&db->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cuda_stream) {
+        db->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&db->stream, cudaStreamNonBlocking) != cudaSuccess) return bad("stream");
+        db->own_stream = true;
+    }
+    // keep freed stream-ordered allocations for reuse by later bulks
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+
+    DevDB &d = db->dev;
+    // object ids: one range per (table, field group)
+    uint64_t o = 0;
+    const int64_t n_d = s.oe_warehouses * OE_DIST, n_c = n_d * OE_CUST;
+    d.o_acc = (uint32_t)o; o += s.dc_accounts;
+    d.o_tel = (uint32_t)o; o += s.dc_tellers;
+    d.o_br = (uint32_t)o; o += s.dc_branches;
+    d.o_sub = (uint32_t)o; o += s.sub_subscribers;
+    d.o_wytd = (uint32_t)o; o += s.oe_warehouses;
+    d.o_dytd = (uint32_t)o; o += n_d;
+    d.o_dnext = (uint32_t)o; o += n_d;
+    d.o_cpay = (uint32_t)o; o += n_c;
+    d.o_clast = (uint32_t)o; o += n_c;
+    d.o_stock = (uint32_t)o; o += s.oe_warehouses * s.oe_items;
+    if (o >= 0xffffffffull) {
+        gputx_destroy_db(db);
+        return GPUTX_EINVAL;
+    }
+    d.n_objects = (uint32_t)o;
+    db->obj_bits = std::max(1, bits_for(o ? o - 1 : 0));
+
+    gputx_status st = GPUTX_OK;
+#define TRY(x)                         \
+    do {                               \
+        st = (x);                      \
+        if (st) {                      \
+            std::string m = db->last_error; \
+            gputx_destroy_db(db);      \
+            (void)m;                   \
+            return st;                 \
+        }                              \
+    } while (0)
+    if (s.dc_branches > 0) {
+        d.n_br = s.dc_branches;
+        d.n_tel = s.dc_tellers;
+        d.n_acc = s.dc_accounts;
+        d.acc_per_tel = s.dc_accounts / s.dc_tellers;
+        d.acc_per_br = s.dc_accounts / s.dc_branches;
+        TRY(dalloc(db, &d.br_bal, d.n_br, "branch"));
+        TRY(dalloc(db, &d.tel_bal, d.n_tel, "teller"));
+        TRY(dalloc(db, &d.acc_bal, d.n_acc, "account"));
+        d.hist_cap = s.dc_history_capacity > 0 ? s.dc_history_capacity : 4 * c.max_bulk;
+        TRY(dalloc(db, &d.h_ts, d.hist_cap, "history"));
+        TRY(dalloc(db, &d.h_acc, d.hist_cap, "history"));
+        TRY(dalloc(db, &d.h_tel, d.hist_cap, "history"));
+        TRY(dalloc(db, &d.h_br, d.hist_cap, "history"));
+        TRY(dalloc(db, &d.h_delta, d.hist_cap, "history"));
+        if (launch_fill_i64(d.h_ts, d.hist_cap, HIST_HOLE, db->stream)) TRY(fail(db, GPUTX_ECUDA, "fill"));
+    }
+    if (s.sub_subscribers > 0) {
+        d.n_sub = s.sub_subscribers;
+        TRY(dalloc(db, &d.sub_rows, d.n_sub * SUB_FIELDS, "subscriber"));
+        const int64_t cap4 = 4 * d.n_sub;
+        d.child_cap = s.sub_child_capacity > 0 ? s.sub_child_capacity : 6 * d.n_sub;
+        TRY(dalloc(db, &d.ai_data, cap4 * 4, "access_info"));
+        TRY(dalloc(db, &d.ai_sid, cap4, "access_info"));
+        TRY(dalloc(db, &d.ai_type, cap4, "access_info"));
+        TRY(alloc_hash(db, d.ai_idx, cap4, "access_info index"));
+        TRY(dalloc(db, &d.sf_sid, cap4, "special_facility"));
+        TRY(dalloc(db, &d.sf_type, cap4, "special_facility"));
+        TRY(dalloc(db, &d.sf_active, cap4, "special_facility"));
+        TRY(dalloc(db, &d.sf_err, cap4, "special_facility"));
+        TRY(dalloc(db, &d.sf_data_a, cap4, "special_facility"));
+        TRY(dalloc(db, &d.sf_data_b, cap4, "special_facility"));
+        TRY(alloc_hash(db, d.sf_idx, cap4, "special_facility index"));
+        const int64_t cc = d.child_cap;
+        TRY(dalloc(db, &d.cf_sid, cc, "call_forwarding"));
+        TRY(dalloc(db, &d.cf_type, cc, "call_forwarding"));
+        TRY(dalloc(db, &d.cf_start, cc, "call_forwarding"));
+        TRY(dalloc(db, &d.cf_end, cc, "call_forwarding"));
+        TRY(dalloc(db, &d.cf_numberx, cc, "call_forwarding"));
+        TRY(dalloc(db, &d.cf_live, cc, "call_forwarding"));
+        TRY(alloc_hash(db, d.cf_idx, cc, "call_forwarding index"));
+    }
+    if (s.oe_warehouses > 0) {
+        d.n_wh = s.oe_warehouses;
+        d.n_items = s.oe_items;
+        TRY(dalloc(db, &d.w_tax, d.n_wh, "warehouse"));
+        TRY(dalloc(db, &d.w_ytd, d.n_wh, "warehouse"));
+        TRY(dalloc(db, &d.d_tax, n_d, "district"));
+        TRY(dalloc(db, &d.d_ytd, n_d, "district"));
+        TRY(dalloc(db, &d.d_next_o_id, n_d, "district"));
+        TRY(dalloc(db, &d.c_discount, n_c, "customer"));
+        TRY(dalloc(db, &d.c_balance, n_c, "customer"));
+        TRY(dalloc(db, &d.c_ytd, n_c, "customer"));
+        TRY(dalloc(db, &d.c_payment_cnt, n_c, "customer"));
+        TRY(dalloc(db, &d.c_last_o_id, n_c, "customer"));
+        TRY(dalloc(db, &d.i_price, d.n_items, "item"));
+        const int64_t ns = d.n_wh * d.n_items;
+        TRY(dalloc(db, &d.s_quantity, ns, "stock"));
+        TRY(dalloc(db, &d.s_order_cnt, ns, "stock"));
+        TRY(dalloc(db, &d.s_ytd, ns, "stock"));
+        d.ord_cap = s.oe_order_capacity > 0 ? s.oe_order_capacity : 2 * c.max_bulk;
+        d.ol_cap = s.oe_orderline_capacity > 0 ? s.oe_orderline_capacity : 16 * d.ord_cap;
+        TRY(dalloc(db, &d.o_w, d.ord_cap, "order"));
+        TRY(dalloc(db, &d.o_d, d.ord_cap, "order"));
+        TRY(dalloc(db, &d.o_c, d.ord_cap, "order"));
+        TRY(dalloc(db, &d.o_cnt, d.ord_cap, "order"));
+        TRY(dalloc(db, &d.o_id, d.ord_cap, "order"));
+        TRY(dalloc(db, &d.o_first, d.ord_cap, "order"));
+        TRY(dalloc(db, &d.o_live, d.ord_cap, "order"));
+        TRY(dalloc(db, &d.ol_item, d.ol_cap, "order_line"));
+        TRY(dalloc(db, &d.ol_sw, d.ol_cap, "order_line"));
+        TRY(dalloc(db, &d.ol_qty, d.ol_cap, "order_line"));
+        TRY(dalloc(db, &d.ol_amount, d.ol_cap, "order_line"));
+        TRY(alloc_hash(db, d.ord_idx, d.ord_cap, "order index"));
+    }
+    TRY(dalloc(db, &db->d_cursor, 1, "cursor"));
+    TRY(dalloc(db, &db->d_done, std::max<int64_t>(d.n_objects, 1), "lock counters"));
+#undef TRY
+    d.out_width = s.sub_subscribers > 0 ? 8 : s.oe_warehouses > 0 ? 4 : 1;
+    if (cudaStreamSynchronize(db->stream) != cudaSuccess) {
+        gputx_destroy_db(db);
+        return GPUTX_ECUDA;
+    }
+    *out = db;
+    return GPUTX_OK;
+}
+
+gputx_status gputx_register_types(gputx_db *db, const int32_t *type_ids, int n)
+{
+    if (!db || (n > 0 && !type_ids) || n < 0) return fail(db, GPUTX_EINVAL, "bad arguments");
+    uint32_t reg = db->dev.registered;
+    for (int i = 0; i < n; i++) {
+        const int t = type_ids[i];
+        const int sc = type_schema(t);
+        if (sc < 0) return fail(db, GPUTX_EINVAL, "unknown type id %d", t);
+        const bool have = (sc == 0 && db->dev.n_acc > 0) || (sc == 1 && db->dev.n_sub > 0) ||
+                          (sc == 2 && db->dev.n_wh > 0);
+        if (!have) return fail(db, GPUTX_EINVAL, "type %d needs a schema this database lacks", t);
+        reg |= 1u << t;
+    }
+    db->dev.registered = reg;
+    int kmax = 0, uniform = -2, ntypes = 0, maxid = 0;
+    bool fix = false;
+    for (int t = 0; t < GPUTX_NUM_TYPES; t++) {
+        if (!((reg >> t) & 1u)) continue;
+        ntypes++;
+        maxid = t;
+        int mk = 0;
+        const int k = type_ops(t, &mk);
+        kmax = std::max(kmax, mk);
+        if (uniform == -2) uniform = k;
+        else if (uniform != k) uniform = -1;
+        // one-pass ranks are exact when every transaction's items nest under
+        // one item it writes (debit-credit: account within teller within
+        // branch) or it touches one item (subscriber); order-entry's
+        // multi-item transactions need the refinement rounds
+        if (t >= GPUTX_T_OE_NEW_ORDER) fix = true;
+    }
+    db->kmax = kmax;
+    db->uniform_k = uniform > 0 ? uniform : 0;
+    db->need_fixpoint = fix;
+    db->tbits = ntypes > 1 ? bits_for((uint64_t)maxid) : 0;
+    return GPUTX_OK;
+}
+
+gputx_status gputx_load_table(gputx_db *db, int table, const int64_t *rows, size_t n_rows)
+{
+    if (!db || (!rows && n_rows)) return fail(db, GPUTX_EINVAL, "bad arguments");
+    DevDB &d = db->dev;
+    const int f = table_fields(table);
+    if (!f) return fail(db, GPUTX_EINVAL, "unknown table %d", table);
+    const int64_t n = (int64_t)n_rows;
+    auto col64 = [&](int j) {
+        std::vector<int64_t> v((size_t)n);
+        for (int64_t i = 0; i < n; i++) v[i] = rows[i * f + j];
+        return v;
+    };
+    auto col32 = [&](int j) {
+        std::vector<int32_t> v((size_t)n);
+        for (int64_t i = 0; i < n; i++) v[i] = (int32_t)rows[i * f + j];
+        return v;
+    };
+    auto need = [&](int64_t want, const char *what) -> gputx_status {
+        if (want <= 0) return fail(db, GPUTX_EINVAL, "%s: schema not created", what);
+        if (n != want) return fail(db, GPUTX_EINVAL, "%s: expected %lld rows, got %lld", what, (long long)want,
+                                   (long long)n);
+        return GPUTX_OK;
+    };
+    gputx_status st;
+    switch (table) {
+    case GPUTX_TBL_DC_BRANCH:
+        if ((st = need(d.n_br, "branch"))) return st;
+        return put_col(db, d.br_bal, col64(0));
+    case GPUTX_TBL_DC_TELLER:
+        if ((st = need(d.n_tel, "teller"))) return st;
+        return put_col(db, d.tel_bal, col64(0));
+    case GPUTX_TBL_DC_ACCOUNT:
+        if ((st = need(d.n_acc, "account"))) return st;
+        return put_col(db, d.acc_bal, col64(0));
+    case GPUTX_TBL_SUB_SUBSCRIBER: {
+        if ((st = need(d.n_sub, "subscriber"))) return st;
+        std::vector<int32_t> v((size_t)n * SUB_FIELDS);
+        for (int64_t i = 0; i < n * SUB_FIELDS; i++) v[i] = (int32_t)rows[i];
+        return put_col(db, d.sub_rows, v);
+    }
+    case GPUTX_TBL_SUB_ACCESS_INFO:
+    case GPUTX_TBL_SUB_SPECIAL_FACILITY:
+    case GPUTX_TBL_SUB_CALL_FORWARDING: {
+        if (d.n_sub <= 0) return fail(db, GPUTX_EINVAL, "subscriber schema not created");
+        InsertBase cur{};
+        CK(cudaMemcpy(&cur, db->d_cursor, sizeof cur, cudaMemcpyDeviceToHost), "cursor");
+        const bool is_cf = table == GPUTX_TBL_SUB_CALL_FORWARDING;
+        const int64_t cap = is_cf ? d.child_cap : 4 * d.n_sub;
+        if (n > cap) return fail(db, GPUTX_ECAPACITY, "too many child rows");
+        std::vector<unsigned long long> keys((size_t)n);
+        for (int64_t i = 0; i < n; i++) {
+            const int64_t *r = rows + i * f;
+            if (r[0] < 0 || r[0] >= d.n_sub || r[1] < 1 || r[1] > 4)
+                return fail(db, GPUTX_EINVAL, "child row %lld: key out of range", (long long)i);
+            if (is_cf && !(r[2] == 0 || r[2] == 8 || r[2] == 16))
+                return fail(db, GPUTX_EINVAL, "call_forwarding row %lld: start_time", (long long)i);
+            keys[i] = is_cf ? (unsigned long long)((r[0] * 4 + (r[1] - 1)) * 3 + r[2] / 8)
+                            : (unsigned long long)(r[0] * 4 + (r[1] - 1));
+        }
+        if (table == GPUTX_TBL_SUB_ACCESS_INFO) {
+            if ((st = upload_hash(db, d.ai_idx, keys))) return st;
+            std::vector<int32_t> data((size_t)n * 4);
+            for (int64_t i = 0; i < n; i++)
+                for (int j = 0; j < 4; j++) data[i * 4 + j] = (int32_t)rows[i * f + 2 + j];
+            if ((st = put_col(db, d.ai_data, data))) return st;
+            if ((st = put_col(db, d.ai_sid, col32(0)))) return st;
+            return put_col(db, d.ai_type, col32(1));
+        }
+        if (table == GPUTX_TBL_SUB_SPECIAL_FACILITY) {
+            if ((st = upload_hash(db, d.sf_idx, keys))) return st;
+            if ((st = put_col(db, d.sf_sid, col32(0)))) return st;
+            if ((st = put_col(db, d.sf_type, col32(1)))) return st;
+            if ((st = put_col(db, d.sf_active, col32(2)))) return st;
+            if ((st = put_col(db, d.sf_err, col32(3)))) return st;
+            if ((st = put_col(db, d.sf_data_a, col32(4)))) return st;
+            return put_col(db, d.sf_data_b, col32(5));
+        }
+        if (cur.cf != 0) return fail(db, GPUTX_ESTATE, "call_forwarding already holds rows");
+        if ((st = upload_hash(db, d.cf_idx, keys))) return st;
+        if ((st = put_col(db, d.cf_sid, col32(0)))) return st;
+        if ((st = put_col(db, d.cf_type, col32(1)))) return st;
+        if ((st = put_col(db, d.cf_start, col32(2)))) return st;
+        if ((st = put_col(db, d.cf_end, col32(3)))) return st;
+        if ((st = put_col(db, d.cf_numberx, col32(4)))) return st;
+        if ((st = put_col(db, d.cf_live, std::vector<uint8_t>((size_t)n, 1)))) return st;
+        cur.cf = n;
+        CK(cudaMemcpy(db->d_cursor, &cur, sizeof cur, cudaMemcpyHostToDevice), "cursor");
+        return GPUTX_OK;
+    }
+    case GPUTX_TBL_OE_WAREHOUSE:
+        if ((st = need(d.n_wh, "warehouse"))) return st;
+        if ((st = put_col(db, d.w_tax, col64(0)))) return st;
+        return put_col(db, d.w_ytd, col64(1));
+    case GPUTX_TBL_OE_DISTRICT:
+        if ((st = need(d.n_wh * OE_DIST, "district"))) return st;
+        if ((st = put_col(db, d.d_tax, col64(0)))) return st;
+        if ((st = put_col(db, d.d_ytd, col64(1)))) return st;
+        return put_col(db, d.d_next_o_id, col64(2));
+    case GPUTX_TBL_OE_CUSTOMER:
+        if ((st = need(d.n_wh * OE_DIST * OE_CUST, "customer"))) return st;
+        if ((st = put_col(db, d.c_discount, col64(0)))) return st;
+        if ((st = put_col(db, d.c_balance, col64(1)))) return st;
+        if ((st = put_col(db, d.c_ytd, col64(2)))) return st;
+        if ((st = put_col(db, d.c_payment_cnt, col64(3)))) return st;
+        return put_col(db, d.c_last_o_id, col64(4));
+    case GPUTX_TBL_OE_ITEM:
+        if ((st = need(d.n_items, "item"))) return st;
+        return put_col(db, d.i_price, col64(0));
+    case GPUTX_TBL_OE_STOCK:
+        if ((st = need(d.n_wh * d.n_items, "stock"))) return st;
+        if ((st = put_col(db, d.s_quantity, col32(0)))) return st;
+        if ((st = put_col(db, d.s_ytd, col64(1)))) return st;
+        return put_col(db, d.s_order_cnt, col32(2));
+    }
+    return fail(db, GPUTX_EINVAL, "table %d is read only", table);
+}
+
+gputx_status gputx_read_table(gputx_db *db, int table, int64_t *rows, size_t capacity_rows, size_t *n_rows)
+{
+    if (!db || !n_rows) return fail(db, GPUTX_EINVAL, "bad arguments");
+    const DevDB &d = db->dev;
+    const int f = table_fields(table);
+    if (!f) return fail(db, GPUTX_EINVAL, "unknown table %d", table);
+    CK(cudaStreamSynchronize(db->stream), "sync");
+    InsertBase cur{};
+    CK(cudaMemcpy(&cur, db->d_cursor, sizeof cur, cudaMemcpyDeviceToHost), "cursor");
+    std::vector<std::vector<int64_t>> cols;   // output columns
+    gputx_status st = GPUTX_OK;
+    auto add64 = [&](const int64_t *src, int64_t n) {
+        std::vector<int64_t> v;
+        if (!st) st = get_col(db, v, src, n);
+        cols.push_back(std::move(v));
+    };
+    auto add32 = [&](const int32_t *src, int64_t n) {
+        std::vector<int32_t> v;
+        if (!st) st = get_col(db, v, src, n);
+        cols.emplace_back(v.begin(), v.end());
+    };
+    std::vector<uint8_t> keep;   // live-row filter (empty = all)
+    switch (table) {
+    case GPUTX_TBL_DC_BRANCH: add64(d.br_bal, d.n_br); break;
+    case GPUTX_TBL_DC_TELLER: add64(d.tel_bal, d.n_tel); break;
+    case GPUTX_TBL_DC_ACCOUNT: add64(d.acc_bal, d.n_acc); break;
+    case GPUTX_TBL_DC_HISTORY: {
+        const int64_t n = std::min<int64_t>(cur.hist, d.hist_cap);
+        add64(d.h_ts, n); add64(d.h_acc, n); add64(d.h_tel, n); add64(d.h_br, n); add64(d.h_delta, n);
+        if (!st) {
+            keep.resize((size_t)n);
+            for (int64_t i = 0; i < n; i++) keep[i] = cols[0][i] != HIST_HOLE;
+        }
+        break;
+    }
+    case GPUTX_TBL_SUB_SUBSCRIBER: {
+        std::vector<int32_t> v;
+        st = get_col(db, v, d.sub_rows, d.n_sub * SUB_FIELDS);
+        if (st) return st;
+        const int64_t n = d.n_sub;
+        *n_rows = (size_t)n;
+        if (!rows) return GPUTX_OK;
+        if ((int64_t)capacity_rows < n) return fail(db, GPUTX_EINVAL, "capacity");
+        for (int64_t i = 0; i < n * SUB_FIELDS; i++) rows[i] = v[i];
+        return GPUTX_OK;
+    }
+    case GPUTX_TBL_SUB_ACCESS_INFO: {
+        // rows live = those indexed; read index to find them
+        std::vector<unsigned long long> hk;
+        std::vector<uint32_t> hr;
+        st = get_col(db, hk, d.ai_idx.keys, (int64_t)d.ai_idx.mask + 1);
+        if (!st) st = get_col(db, hr, d.ai_idx.rows, (int64_t)d.ai_idx.mask + 1);
+        if (st) return st;
+        std::vector<int32_t> data, sid, ty;
+        const int64_t cap = 4 * d.n_sub;
+        st = get_col(db, data, d.ai_data, cap * 4);
+        if (!st) st = get_col(db, sid, d.ai_sid, cap);
+        if (!st) st = get_col(db, ty, d.ai_type, cap);
+        if (st) return st;
+        std::vector<uint32_t> live;
+        for (size_t i = 0; i < hk.size(); i++)
+            if (hk[i] != HKEY_EMPTY && hk[i] != HKEY_TOMB) live.push_back(hr[i]);
+        std::sort(live.begin(), live.end());
+        *n_rows = live.size();
+        if (!rows) return GPUTX_OK;
+        if (capacity_rows < live.size()) return fail(db, GPUTX_EINVAL, "capacity");
+        for (size_t i = 0; i < live.size(); i++) {
+            const uint32_t r = live[i];
+            int64_t *o = rows + i * f;
+            o[0] = sid[r]; o[1] = ty[r];
+            for (int j = 0; j < 4; j++) o[2 + j] = data[(size_t)r * 4 + j];
+        }
+        return GPUTX_OK;
+    }
+    case GPUTX_TBL_SUB_SPECIAL_FACILITY: {
+        std::vector<unsigned long long> hk;
+        std::vector<uint32_t> hr;
+        st = get_col(db, hk, d.sf_idx.keys, (int64_t)d.sf_idx.mask + 1);
+        if (!st) st = get_col(db, hr, d.sf_idx.rows, (int64_t)d.sf_idx.mask + 1);
+        if (st) return st;
+        const int64_t cap = 4 * d.n_sub;
+        add32(d.sf_sid, cap); add32(d.sf_type, cap); add32(d.sf_active, cap);
+        add32(d.sf_err, cap); add32(d.sf_data_a, cap); add32(d.sf_data_b, cap);
+        if (st) return st;
+        keep.assign((size_t)cap, 0);
+        for (size_t i = 0; i < hk.size(); i++)
+            if (hk[i] != HKEY_EMPTY && hk[i] != HKEY_TOMB) keep[hr[i]] = 1;
+        break;
+    }
+    case GPUTX_TBL_SUB_CALL_FORWARDING: {
+        const int64_t n = std::min<int64_t>(cur.cf, d.child_cap);
+        add32(d.cf_sid, n); add32(d.cf_type, n); add32(d.cf_start, n); add32(d.cf_end, n);
+        add32(d.cf_numberx, n);
+        if (!st) st = get_col(db, keep, d.cf_live, n);
+        break;
+    }
+    case GPUTX_TBL_OE_WAREHOUSE: add64(d.w_tax, d.n_wh); add64(d.w_ytd, d.n_wh); break;
+    case GPUTX_TBL_OE_DISTRICT: {
+        const int64_t n = d.n_wh * OE_DIST;
+        add64(d.d_tax, n); add64(d.d_ytd, n); add64(d.d_next_o_id, n);
+        break;
+    }
+    case GPUTX_TBL_OE_CUSTOMER: {
+        const int64_t n = d.n_wh * OE_DIST * OE_CUST;
+        add64(d.c_discount, n); add64(d.c_balance, n); add64(d.c_ytd, n); add64(d.c_payment_cnt, n);
+        add64(d.c_last_o_id, n);
+        break;
+    }
+    case GPUTX_TBL_OE_ITEM: add64(d.i_price, d.n_items); break;
+    case GPUTX_TBL_OE_STOCK: {
+        const int64_t n = d.n_wh * d.n_items;
+        add32(d.s_quantity, n); add64(d.s_ytd, n); add32(d.s_order_cnt, n);
+        break;
+    }
+    case GPUTX_TBL_OE_ORDER:
+    case GPUTX_TBL_OE_ORDER_LINE: {
+        const int64_t n = std::min<int64_t>(cur.ord, d.ord_cap);
+        std::vector<int32_t> ow, od, oc, ocnt;
+        std::vector<int64_t> oid, ofirst;
+        std::vector<uint8_t> olive;
+        st = get_col(db, ow, d.o_w, n);
+        if (!st) st = get_col(db, od, d.o_d, n);
+        if (!st) st = get_col(db, oc, d.o_c, n);
+        if (!st) st = get_col(db, ocnt, d.o_cnt, n);
+        if (!st) st = get_col(db, oid, d.o_id, n);
+        if (!st) st = get_col(db, ofirst, d.o_first, n);
+        if (!st) st = get_col(db, olive, d.o_live, n);
+        if (st) return st;
+        if (table == GPUTX_TBL_OE_ORDER) {
+            cols = {std::vector<int64_t>(ow.begin(), ow.end()), std::vector<int64_t>(od.begin(), od.end()),
+                    oid, std::vector<int64_t>(oc.begin(), oc.end()),
+                    std::vector<int64_t>(ocnt.begin(), ocnt.end())};
+            keep = olive;
+            break;
+        }
+        const int64_t nl = std::min<int64_t>(cur.ol, d.ol_cap);
+        std::vector<int32_t> li, ls, lq;
+        std::vector<int64_t> la;
+        st = get_col(db, li, d.ol_item, nl);
+        if (!st) st = get_col(db, ls, d.ol_sw, nl);
+        if (!st) st = get_col(db, lq, d.ol_qty, nl);
+        if (!st) st = get_col(db, la, d.ol_amount, nl);
+        if (st) return st;
+        size_t total = 0;
+        for (int64_t i = 0; i < n; i++)
+            if (olive[i]) total += (size_t)ocnt[i];
+        *n_rows = total;
+        if (!rows) return GPUTX_OK;
+        if (capacity_rows < total) return fail(db, GPUTX_EINVAL, "capacity");
+        size_t r = 0;
+        for (int64_t i = 0; i < n; i++) {
+            if (!olive[i]) continue;
+            for (int j = 0; j < ocnt[i]; j++, r++) {
+                const int64_t l = ofirst[i] + j;
+                int64_t *o = rows + r * f;
+                o[0] = ow[i]; o[1] = od[i]; o[2] = oid[i];
+                o[3] = li[l]; o[4] = ls[l]; o[5] = lq[l]; o[6] = la[l];
+            }
+        }
+        return GPUTX_OK;
+    }
+    default:
+        return fail(db, GPUTX_EINVAL, "table %d", table);
+    }
+    if (st) return st;
+    if ((int)cols.size() != f) return fail(db, GPUTX_EINVAL, "table %d has no schema", table);
+    const int64_t n = cols.empty() ? 0 : (int64_t)cols[0].size();
+    size_t live = 0;
+    for (int64_t i = 0; i < n; i++) live += keep.empty() || keep[i];
+    *n_rows = live;
+    if (!rows) return GPUTX_OK;
+    if (capacity_rows < live) return fail(db, GPUTX_EINVAL, "capacity %zu < %zu rows", capacity_rows, live);
+    size_t r = 0;
+    for (int64_t i = 0; i < n; i++) {
+        if (!keep.empty() && !keep[i]) continue;
+        for (int j = 0; j < f; j++) rows[r * f + j] = cols[j][i];
+        r++;
+    }
+    return GPUTX_OK;
+}
+
+gputx_status gputx_submit_bulk(gputx_db *db, const int64_t *ts, const int32_t *type, const int64_t *params,
+                               int params_per_txn, size_t n, int mem, gputx_bulk **out)
+{
+    if (!db || !out) return fail(db, GPUTX_EINVAL, "bad arguments");
+    *out = nullptr;
+    if (n > 0 && (!ts || !type || !params)) return fail(db, GPUTX_EINVAL, "null bulk array");
+    if ((int64_t)n > db->cfg.max_bulk) return fail(db, GPUTX_EINVAL, "bulk of %zu above max_bulk", n);
+    if (params_per_txn < 1 || params_per_txn > 64) return fail(db, GPUTX_EINVAL, "params_per_txn");
+    if (mem != GPUTX_MEM_HOST && mem != GPUTX_MEM_DEVICE) return fail(db, GPUTX_EINVAL, "mem");
+    if (!db->dev.registered) return fail(db, GPUTX_ESTATE, "no registered types");
+    gputx_bulk *b = new (std::nothrow) gputx_bulk();
+    if (!b) return fail(db, GPUTX_ENOMEM, "host allocation");
+    b->db = db;
+    b->n = (int64_t)n;
+    b->P = params_per_txn;
+    b->R = db->dev.out_width;
+    const bool dev_in = mem == GPUTX_MEM_DEVICE;
+    b->arena_bytes = carve_bulk(b, nullptr, dev_in);
+    cudaError_t e = cudaMallocAsync(&b->arena, b->arena_bytes, db->stream);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(db, e, "bulk allocation");
+    }
+    carve_bulk(b, (char *)b->arena, dev_in);
+    if (dev_in) {
+        // referenced in place: the caller keeps them unchanged until the sync
+        b->ts = const_cast<int64_t *>(ts);
+        b->type = const_cast<int32_t *>(type);
+        b->params = const_cast<int64_t *>(params);
+    } else if (n > 0) {
+        e = cudaMemcpyAsync(b->ts, ts, n * sizeof(int64_t), cudaMemcpyHostToDevice, db->stream);
+        if (!e) e = cudaMemcpyAsync(b->type, type, n * sizeof(int32_t), cudaMemcpyHostToDevice, db->stream);
+        if (!e) e = cudaMemcpyAsync(b->params, params, n * params_per_txn * sizeof(int64_t),
+                                    cudaMemcpyHostToDevice, db->stream);
+    }
+    if (!e) e = cudaMemsetAsync(b->ctl, 0, sizeof(BulkCtl), db->stream);
+    if (!e && n > 0) e = cudaMemsetAsync(b->out, 0, n * b->R * sizeof(int64_t), db->stream);
+    if (!e && n > 0) e = cudaMemsetAsync(b->status, 0, n * sizeof(int32_t), db->stream);
+    if (!e) e = cudaEventCreate(&b->ev[7]);
+    if (e) {
+        cudaFreeAsync(b->arena, db->stream);
+        delete b;
+        return cuda_fail(db, e, "bulk upload");
+    }
+    *out = b;
+    return GPUTX_OK;
+}
+
+namespace {
+
+gputx_status run_kset_analysis(gputx_bulk *b, int mode, int part_size, uint32_t *&sk, uint32_t *&sv,
+                               uint32_t *&ak, uint32_t *&av, int64_t &m)
+{
+    gputx_db *db = b->db;
+    CK(cudaMemsetAsync(&b->ctl->cross, 0, 4, db->stream), "extract");
+    CK(launch_extract(b, mode, part_size, nullptr, nullptr, true), "extract");
+    m = b->n * db->uniform_k;
+    if (!db->uniform_k) {
+        uint32_t mm = 0;
+        CK(cudaMemcpyAsync(&mm, b->sc.op_off + b->n, sizeof mm, cudaMemcpyDeviceToHost, db->stream), "ops");
+        CK(cudaStreamSynchronize(db->stream), "ops");
+        m = mm;
+        if (m > b->sc.m_cap) m = b->sc.m_cap;
+    }
+    if (b->timing) cudaEventRecord(b->ev[1], db->stream);
+    sk = b->sc.keys_a; sv = b->sc.vals_a; ak = b->sc.keys_b; av = b->sc.vals_b;
+    CK(launch_sort(b, sk, sv, ak, av, m, db->obj_bits), "sort");
+    if (b->timing) cudaEventRecord(b->ev[2], db->stream);
+    return GPUTX_OK;
+}
+
+}  // namespace
+
+gputx_status gputx_execute(gputx_db *db, gputx_bulk *b, int strategy, const gputx_exec_opts *opts)
+{
+    if (!db || !b || b->db != db) return fail(db, GPUTX_EINVAL, "bad arguments");
+    if (b->executed) return fail(db, GPUTX_ESTATE, "bulk already executed");
+    if (strategy < GPUTX_KSET || strategy > GPUTX_AUTO) return fail(db, GPUTX_EINVAL, "strategy %d", strategy);
+    const int mode = opts ? opts->conflict_mode : GPUTX_CONFLICT_PAPER;
+    if (mode != GPUTX_CONFLICT_PAPER && mode != GPUTX_CONFLICT_ADD) return fail(db, GPUTX_EINVAL, "conflict mode");
+    int block = (opts && opts->block_threads) ? opts->block_threads : db->cfg.block_threads;
+    if (block < 32 || block > 1024 || block % 32) return fail(db, GPUTX_EINVAL, "block_threads");
+    int part_size = (opts && opts->part_size) ? opts->part_size : db->cfg.part_size;
+    if (part_size <= 0) part_size = (db->dev.n_sub > 0 && db->dev.n_acc == 0 && db->dev.n_wh == 0) ? 128 : 1;
+    b->executed = true;
+    b->timing = opts && opts->timing;
+    if (b->timing)
+        for (int i = 0; i < 7; i++)
+            if (!b->ev[i]) cudaEventCreate(&b->ev[i]);
+    cudaStream_t s = db->stream;
+    if (b->timing) cudaEventRecord(b->ev[0], s);
+    CK(launch_begin(b), "begin");
+    CK(launch_insert_slots(b), "insert slots");
+    const bool add = mode == GPUTX_CONFLICT_ADD;
+    gputx_status st = GPUTX_OK;
+    uint32_t *sk = nullptr, *sv = nullptr, *ak = nullptr, *av = nullptr;
+    int64_t m = 0;
+    int run = strategy;
+
+    if (strategy == GPUTX_KSET || strategy == GPUTX_AUTO) {
+        if ((st = run_kset_analysis(b, mode, part_size, sk, sv, ak, av, m))) return st;
+        CK(launch_rank_scan(b, sk, sv, m, db->need_fixpoint), "rank");
+        if (db->need_fixpoint) {
+            for (int round = 0; round < 1 << 20; round++) {
+                CK(launch_fixpoint_round(b, sv, m), "fixpoint");
+                uint32_t changed = 0, err = 0;
+                CK(cudaMemcpyAsync(&changed, &b->ctl->changed, 4, cudaMemcpyDeviceToHost, s), "fixpoint");
+                CK(cudaMemcpyAsync(&err, &b->ctl->err, 4, cudaMemcpyDeviceToHost, s), "fixpoint");
+                CK(cudaStreamSynchronize(s), "fixpoint");
+                b->fixpoint_rounds++;
+                if (!changed || err) break;
+            }
+        }
+        CK(launch_level_stats(b), "stats");
+        if ((st = read_ctl(b))) return st;
+        if (b->host_ctl.err) {
+            CK(cudaEventRecord(b->ev[7], s), "event");
+            return GPUTX_OK;     // reported by the sync
+        }
+        if (strategy == GPUTX_AUTO) {
+            // Algorithm 1 (Appendix D): wide 0-set -> K-SET; else few
+            // cross-partition transactions or a deep graph -> PART; else TPL
+            const int64_t w0 = b->host_ctl.w0, d = b->host_ctl.depth, c = b->host_ctl.cross;
+            if (w0 >= db->cfg.kset_w0_min) run = GPUTX_KSET;
+            else if (c <= db->cfg.part_c_max || d >= db->cfg.part_d_min) run = c ? GPUTX_TPL : GPUTX_PART;
+            else run = GPUTX_TPL;
+            // a PART pick with cross-partition transactions runs as TPL
+            // (Section 5.2); the sorted operations are reused for tickets
+            if (run == GPUTX_TPL && c && (c <= db->cfg.part_c_max || d >= db->cfg.part_d_min))
+                b->fallback = 1;
+        }
+    }
+    if (run == GPUTX_KSET) {
+        const int64_t depth = b->host_ctl.depth;
+        // regroup by (level, type): reuse the free op buffers
+        uint32_t *rk = ak, *rv = av, *rk2 = sk, *rv2 = sv;
+        CK(launch_regroup_keys(b, rk, rv), "regroup");
+        CK(launch_sort(b, rk, rv, rk2, rv2, b->n, bits_for((uint64_t)depth) + db->tbits), "regroup sort");
+        CK(launch_level_tables(b, rk, depth, block), "level tables");
+        if (b->timing) cudaEventRecord(b->ev[3], s);
+        CK(launch_kset(b, rv, b->sc.chunk_cap, block, add), "k-set execute");
+    } else if (run == GPUTX_PART) {
+        // partition ids by root key (Section 5.2 step 1), stable sort (step 2)
+        uint32_t *pk = b->sc.pid_key, *pv = b->sc.pid_val, *pk2 = b->sc.pid_key2, *pv2 = b->sc.pid_val2;
+        CK(cudaMemsetAsync(&b->ctl->cross, 0, 4, s), "part");
+        CK(launch_extract(b, mode, part_size, pk, pv, false), "extract");
+        if (b->timing) cudaEventRecord(b->ev[1], s);
+        if ((st = read_ctl(b))) return st;
+        if (b->host_ctl.err) {
+            CK(cudaEventRecord(b->ev[7], s), "event");
+            return GPUTX_OK;
+        }
+        if (b->host_ctl.cross > 0) {
+            // Section 5.2: cross-partition transactions run with TPL
+            b->fallback = 1;
+            run = GPUTX_TPL;
+            CK(cudaMemsetAsync(&b->ctl->cross, 0, 4, s), "part");
+        } else {
+            const int64_t roots = std::max<int64_t>({db->dev.n_br, db->dev.n_sub, db->dev.n_wh, 1});
+            const int bits = bits_for((uint64_t)((roots - 1) / part_size));
+            CK(launch_sort(b, pk, pv, pk2, pv2, b->n, bits), "partition sort");
+            if (b->timing) cudaEventRecord(b->ev[2], s);
+            CK(launch_part_heads(b, pk, b->n), "partition heads");
+            if (b->timing) cudaEventRecord(b->ev[3], s);
+            CK(launch_part(b, pk, pv, 128), "part execute");
+        }
+    }
+    if (run == GPUTX_TPL) {
+        if (!sk) {
+            if ((st = run_kset_analysis(b, mode, part_size, sk, sv, ak, av, m))) return st;
+        }
+        CK(launch_ticket_scan(b, sk, sv, m), "tickets");
+        if (b->timing) cudaEventRecord(b->ev[3], s);
+        CK(launch_tpl(b, block, add), "tpl execute");
+        if (b->timing) cudaEventRecord(b->ev[4], s);
+        CK(launch_tpl_reset(b, sk, m), "tpl reset");
+    }
+    if (b->timing && run != GPUTX_TPL) cudaEventRecord(b->ev[4], s);
+    CK(launch_finish(b), "finish");
+    CK(cudaEventRecord(b->ev[7], s), "event");
+    b->strategy_run = run;
+    return GPUTX_OK;
+}
+
+gputx_status gputx_sync_bulk(gputx_bulk *b, gputx_exec_stats *stats)
+{
+    if (!b) return GPUTX_EINVAL;
+    gputx_db *db = b->db;
+    if (!b->executed) return fail(db, GPUTX_ESTATE, "bulk not executed");
+    CK(cudaEventSynchronize(b->ev[7]), "sync");
+    CK(cudaMemcpy(&b->host_ctl, b->ctl, sizeof(BulkCtl), cudaMemcpyDeviceToHost), "sync");
+    b->synced = true;
+    if (stats) {
+        memset(stats, 0, sizeof *stats);
+        stats->strategy = b->strategy_run;
+        stats->fallback = b->fallback;
+        stats->n = b->n;
+        stats->n_ops = b->sc.m_cap;
+        stats->depth = b->host_ctl.depth;
+        stats->w0 = b->host_ctl.w0;
+        stats->cross = b->host_ctl.cross;
+        stats->fixpoint_rounds = b->fixpoint_rounds;
+        if (b->timing) {
+            float ms = 0;
+            if (!cudaEventElapsedTime(&ms, b->ev[0], b->ev[3])) stats->ms_analysis = ms;
+            if (!cudaEventElapsedTime(&ms, b->ev[1], b->ev[2])) stats->ms_sort = ms;
+            if (!cudaEventElapsedTime(&ms, b->ev[3], b->ev[4])) stats->ms_execute = ms;
+            if (!cudaEventElapsedTime(&ms, b->ev[0], b->ev[7])) stats->ms_total = ms;
+        }
+    }
+    return bulk_error(db, b->host_ctl.err);
+}
+
+gputx_status gputx_read_results(gputx_bulk *b, int32_t *status, int64_t *values, size_t n, int n_values)
+{
+    if (!b) return GPUTX_EINVAL;
+    gputx_db *db = b->db;
+    if ((int64_t)n != b->n) return fail(db, GPUTX_EINVAL, "n %zu != bulk size %lld", n, (long long)b->n);
+    if (values && n_values != b->R) return fail(db, GPUTX_EINVAL, "output width is %d", b->R);
+    gputx_status st = gputx_sync_bulk(b, nullptr);
+    if (st) return st;
+    if (n == 0) return GPUTX_OK;
+    if (status) CK(cudaMemcpyAsync(status, b->status, n * sizeof(int32_t), cudaMemcpyDeviceToHost, db->stream), "d2h");
+    if (values)
+        CK(cudaMemcpyAsync(values, b->out, n * b->R * sizeof(int64_t), cudaMemcpyDeviceToHost, db->stream), "d2h");
+    CK(cudaStreamSynchronize(db->stream), "d2h");
+    return GPUTX_OK;
+}
+
+gputx_status gputx_bulk_results_device(gputx_bulk *b, const int32_t **status, const int64_t **values)
+{
+    if (!b) return GPUTX_EINVAL;
+    if (status) *status = b->status;
+    if (values) *values = b->out;
+    return GPUTX_OK;
+}
+
+void gputx_free_bulk(gputx_bulk *b)
+{
+    if (!b) return;
+    gputx_db *db = b->db;
+    if (b->arena) cudaFreeAsync(b->arena, db->stream);
+    for (int i = 0; i < 8; i++)
+        if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+    delete b;
+}
+
+}  // extern "C"

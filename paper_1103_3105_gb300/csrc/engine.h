@@ -1,0 +1,136 @@
+// engine.h -- host-side state of a database and a bulk, and the launchers each
+// translation unit provides.  Internal to the library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace gtx {
+
+// Per-bulk control block in device memory (zeroed at submit).
+struct BulkCtl {
+    uint32_t err;          // ERR_* bits
+    uint32_t depth;        // d: largest level
+    uint32_t w0;           // 0-set size
+    uint32_t cross;        // cross-partition transactions
+    uint32_t changed;      // fixpoint: a level grew in the last round
+    uint32_t npart;        // PART: non-empty partitions
+    uint32_t claim;        // executors: next chunk to claim
+    uint32_t pad;
+    InsertBase base;       // where this bulk's inserts start (copied from the cursor)
+    InsertBase total;      // inserts this bulk reserves
+};
+
+// Scratch carved from one per-bulk allocation.
+struct Scratch {
+    uint32_t *keys_a, *vals_a, *keys_b, *vals_b;  // sort ping-pong, m entries each
+    uint32_t *op_off;      // n+1 exclusive op offsets (non-uniform op counts)
+    uint32_t *level;       // n
+    uint32_t *rid;         // m: global run id per sorted op (fixpoint)
+    uint32_t *runmax;      // m
+    uint32_t *lock_key;    // m: TPL per-op object, indexed by op slot
+    uint32_t *lock_ticket; // m
+    uint32_t *level_off;   // n+2
+    uint32_t *chunk_off;   // n+2
+    uint32_t *chunk_level; // n + n/min_block + 2
+    uint32_t *done;        // n+1 per-level completion counters
+    uint32_t *part_start;  // n
+    uint32_t *pid_key, *pid_val, *pid_key2, *pid_val2;  // PART sort, n each
+    uint32_t *slot_cf, *slot_ord, *slot_ol;   // n each
+    uint32_t *sort_hist;   // 4 x 256
+    uint32_t *sort_offs;   // 4 x 256
+    uint32_t *sort_status; // 4 x tiles x 256
+    uint32_t *tile_ctr;    // 16 counters
+    uint64_t *scan_status; // tiles
+    int64_t m_cap;         // op capacity
+    int64_t sort_tiles, scan_tiles, chunk_cap;
+};
+
+}  // namespace gtx
+
+struct gputx_db {
+    gtx::DevDB dev{};
+    gputx_schema_desc schema{};
+    gputx_config cfg{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int num_sms = 0;
+    std::string last_error;
+    std::vector<void *> allocs;
+    gtx::InsertBase *d_cursor = nullptr;   // device insert cursors
+    uint32_t *d_done = nullptr;            // TPL per-object counters, kept zero between bulks
+    int kmax = 0;                          // largest op count of a registered type
+    int uniform_k = 0;                     // every registered type has exactly this many ops (0 = no)
+    bool need_fixpoint = false;            // a registered type's ops may leave one-pass ranks inexact
+    int tbits = 0;                         // type bits in the level/type regroup key
+    int obj_bits = 1;                      // key bits of object ids
+};
+
+struct gputx_bulk {
+    gputx_db *db = nullptr;
+    int64_t n = 0;
+    int P = 0, R = 0;
+    void *arena = nullptr;
+    size_t arena_bytes = 0;
+    int64_t *ts = nullptr;
+    int32_t *type = nullptr;
+    int64_t *params = nullptr;
+    int32_t *status = nullptr;
+    int64_t *out = nullptr;
+    gtx::BulkCtl *ctl = nullptr;
+    gtx::Scratch sc{};
+    bool executed = false;
+    bool synced = false;
+    int strategy_run = -1;
+    int fallback = 0;
+    int64_t fixpoint_rounds = 0;
+    bool timing = false;
+    cudaEvent_t ev[8] = {};
+    gtx::BulkCtl host_ctl{};
+};
+
+namespace gtx {
+
+// analysis.cu
+DevBulk make_dev_bulk(gputx_bulk *b, int mode);
+cudaError_t launch_extract(gputx_bulk *b, int mode, int part_size, uint32_t *pid_key, uint32_t *pid_val,
+                           bool write_ops);
+cudaError_t launch_sort(gputx_bulk *b, uint32_t *&keys, uint32_t *&vals, uint32_t *&keys_alt,
+                        uint32_t *&vals_alt, int64_t count, int bits);
+cudaError_t launch_rank_scan(gputx_bulk *b, const uint32_t *sk, const uint32_t *sv, int64_t m, bool want_rid);
+cudaError_t launch_ticket_scan(gputx_bulk *b, const uint32_t *sk, const uint32_t *sv, int64_t m);
+cudaError_t launch_fixpoint_round(gputx_bulk *b, const uint32_t *sv, int64_t m);
+cudaError_t launch_level_stats(gputx_bulk *b);
+cudaError_t launch_regroup_keys(gputx_bulk *b, uint32_t *keys, uint32_t *vals);
+cudaError_t launch_level_tables(gputx_bulk *b, const uint32_t *skeys, int64_t depth, int block);
+cudaError_t launch_insert_slots(gputx_bulk *b);
+cudaError_t launch_part_heads(gputx_bulk *b, const uint32_t *skeys, int64_t n);
+cudaError_t launch_tpl_reset(gputx_bulk *b, const uint32_t *skeys, int64_t m);
+cudaError_t launch_begin(gputx_bulk *b);
+cudaError_t launch_finish(gputx_bulk *b);
+
+// exec.cu
+cudaError_t launch_kset(gputx_bulk *b, const uint32_t *order, int64_t nchunks, int block, bool atomic_add);
+cudaError_t launch_part(gputx_bulk *b, const uint32_t *pkeys, const uint32_t *pvals, int block);
+cudaError_t launch_tpl(gputx_bulk *b, int block, bool atomic_add);
+int exec_blocks_per_sm(int kind, int block);
+
+// tables.cu
+cudaError_t launch_fill_i64(int64_t *p, int64_t n, int64_t v, cudaStream_t s);
+cudaError_t launch_fill_u64(unsigned long long *p, int64_t n, unsigned long long v, cudaStream_t s);
+
+// kernels launched by this library since load (tracing)
+void count_launches(int k);
+
+inline int bits_for(uint64_t maxval)
+{
+    int b = 0;
+    while (b < 32 && (maxval >> b) != 0) b++;
+    return b;
+}
+
+}  // namespace gtx

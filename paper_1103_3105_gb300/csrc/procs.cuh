@@ -1,0 +1,459 @@
+// procs.cuh -- the registered stored procedures and their access sets.
+//
+// Section 3.2: every transaction type is a device function and one kernel
+// dispatches on the type with a switch.  Each procedure is written two-phase
+// (Appendix D): a read phase that may abort (status != 0, no writes) and a
+// write phase that never aborts, so no undo log is needed.
+//
+// access_set() declares the basic operations (Section 4.1) of a transaction
+// from its parameters alone, at field granularity (Section 3.2): a read or a
+// write on an item identified by a dense object id.  Items that are never
+// written (item prices, warehouse and district tax, customer discount) carry
+// no operation.  In GPUTX_CONFLICT_ADD mode, increments whose old value is
+// never read are class ADD.
+#pragma once
+#include "common.cuh"
+
+namespace gtx {
+
+// ---------------------------------------------------------------------------
+// validation of one signature (bulk contents are checked on the device)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool valid_txn(const DevDB &db, int32_t type, const int64_t *p, int P)
+{
+    if (type < 0 || type >= GPUTX_NUM_TYPES || !((db.registered >> type) & 1u)) return false;
+    switch (type) {
+    case GPUTX_T_DC_DEBIT_CREDIT:
+        return P >= 2 && p[0] >= 0 && p[0] < db.n_acc;
+    case GPUTX_T_SUB_GET_SUBSCRIBER:
+        return P >= 1 && p[0] >= 0 && p[0] < db.n_sub;
+    case GPUTX_T_SUB_GET_ACCESS:
+        return P >= 2 && p[0] >= 0 && p[0] < db.n_sub && p[1] >= 1 && p[1] <= 4;
+    case GPUTX_T_SUB_GET_NEW_DEST:
+        return P >= 4 && p[0] >= 0 && p[0] < db.n_sub && p[1] >= 1 && p[1] <= 4;
+    case GPUTX_T_SUB_UPDATE_LOCATION:
+        return P >= 2 && p[0] >= 0 && p[0] < db.n_sub;
+    case GPUTX_T_SUB_UPDATE_FACILITY:
+        return P >= 4 && p[0] >= 0 && p[0] < db.n_sub && p[1] >= 1 && p[1] <= 4;
+    case GPUTX_T_SUB_INSERT_CF:
+        return P >= 5 && p[0] >= 0 && p[0] < db.n_sub && p[1] >= 1 && p[1] <= 4 &&
+               (p[2] == 0 || p[2] == 8 || p[2] == 16);
+    case GPUTX_T_SUB_DELETE_CF:
+        return P >= 3 && p[0] >= 0 && p[0] < db.n_sub && p[1] >= 1 && p[1] <= 4 &&
+               (p[2] == 0 || p[2] == 8 || p[2] == 16);
+    case GPUTX_T_OE_NEW_ORDER: {
+        if (P < 4 || p[0] < 0 || p[0] >= db.n_wh || p[1] < 0 || p[1] >= OE_DIST || p[2] < 0 ||
+            p[2] >= OE_CUST || p[3] < 1 || p[3] > OE_MAX_LINES || P < 4 + p[3])
+            return false;
+        // items must be distinct; an item id of n_items or more is allowed
+        // (the order aborts in its read phase), a bad warehouse is not
+        for (int j = 0; j < (int)p[3]; j++) {
+            int64_t line = p[4 + j];
+            int64_t item = line & 0xFFFFFF, sw = (line >> 24) & 0xFFFF, qty = (line >> 40) & 0xFF;
+            if (line < 0 || sw >= db.n_wh || qty < 1) return false;
+            for (int k = 0; k < j; k++)
+                if ((p[4 + k] & 0xFFFFFF) == item) return false;
+        }
+        return true;
+    }
+    case GPUTX_T_OE_PAYMENT:
+        return P >= 4 && p[0] >= 0 && p[0] < db.n_wh && p[1] >= 0 && p[1] < OE_DIST &&
+               p[2] >= 0 && p[2] < OE_CUST;
+    case GPUTX_T_OE_ORDER_STATUS:
+        return P >= 3 && p[0] >= 0 && p[0] < db.n_wh && p[1] >= 0 && p[1] < OE_DIST &&
+               p[2] >= 0 && p[2] < OE_CUST;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// basic operations (Section 4.1): obj, class and root key of each
+// ---------------------------------------------------------------------------
+// Returns the number of operations written (<= MAX_OPS).  The root key is the
+// primary key of the schema's root relation (Section 5.1): the branch, the
+// subscriber, the warehouse.
+__device__ __forceinline__ int access_set(const DevDB &db, int32_t type, const int64_t *p, int mode,
+                                          uint32_t *obj, uint8_t *cls, uint32_t *root)
+{
+    const uint8_t blind = (mode == GPUTX_CONFLICT_ADD) ? CLS_A : CLS_W;
+    int k = 0;
+    switch (type) {
+    case GPUTX_T_DC_DEBIT_CREDIT: {
+        int64_t a = p[0];
+        uint32_t t = (uint32_t)(a / db.acc_per_tel), b = (uint32_t)(a / db.acc_per_br);
+        obj[0] = db.o_acc + (uint32_t)a; cls[0] = CLS_W; root[0] = b;
+        obj[1] = db.o_tel + t;           cls[1] = blind; root[1] = b;
+        obj[2] = db.o_br + b;            cls[2] = blind; root[2] = b;
+        return 3;
+    }
+    case GPUTX_T_SUB_GET_SUBSCRIBER:
+    case GPUTX_T_SUB_GET_ACCESS:
+    case GPUTX_T_SUB_GET_NEW_DEST:
+        obj[0] = db.o_sub + (uint32_t)p[0]; cls[0] = CLS_R; root[0] = (uint32_t)p[0];
+        return 1;
+    case GPUTX_T_SUB_UPDATE_LOCATION:
+    case GPUTX_T_SUB_UPDATE_FACILITY:
+    case GPUTX_T_SUB_INSERT_CF:
+    case GPUTX_T_SUB_DELETE_CF:
+        obj[0] = db.o_sub + (uint32_t)p[0]; cls[0] = CLS_W; root[0] = (uint32_t)p[0];
+        return 1;
+    case GPUTX_T_OE_NEW_ORDER: {
+        uint32_t w = (uint32_t)p[0], d = w * OE_DIST + (uint32_t)p[1];
+        uint32_t c = d * OE_CUST + (uint32_t)p[2];
+        obj[k] = db.o_dnext + d; cls[k] = CLS_W; root[k] = w; k++;
+        obj[k] = db.o_clast + c; cls[k] = CLS_W; root[k] = w; k++;
+        int cnt = (int)p[3];
+        for (int j = 0; j < cnt; j++) {
+            int64_t line = p[4 + j];
+            int64_t item = line & 0xFFFFFF, sw = (line >> 24) & 0xFFFF;
+            if (item >= db.n_items) continue;
+            obj[k] = db.o_stock + (uint32_t)(sw * db.n_items + item); cls[k] = CLS_W;
+            root[k] = (uint32_t)sw; k++;
+        }
+        return k;
+    }
+    case GPUTX_T_OE_PAYMENT: {
+        uint32_t w = (uint32_t)p[0], d = w * OE_DIST + (uint32_t)p[1];
+        uint32_t c = d * OE_CUST + (uint32_t)p[2];
+        obj[0] = db.o_wytd + w;  cls[0] = blind; root[0] = w;
+        obj[1] = db.o_dytd + d;  cls[1] = blind; root[1] = w;
+        obj[2] = db.o_cpay + c;  cls[2] = CLS_W; root[2] = w;
+        return 3;
+    }
+    case GPUTX_T_OE_ORDER_STATUS: {
+        uint32_t w = (uint32_t)p[0], d = w * OE_DIST + (uint32_t)p[1];
+        uint32_t c = d * OE_CUST + (uint32_t)p[2];
+        obj[0] = db.o_cpay + c;  cls[0] = CLS_R; root[0] = w;
+        obj[1] = db.o_clast + c; cls[1] = CLS_R; root[1] = w;
+        return 2;
+    }
+    }
+    return 0;
+}
+
+// number of operations without materialising them
+__device__ __forceinline__ int op_count(const DevDB &db, int32_t type, const int64_t *p)
+{
+    switch (type) {
+    case GPUTX_T_DC_DEBIT_CREDIT: return 3;
+    case GPUTX_T_OE_NEW_ORDER: {
+        int k = 2, cnt = (int)p[3];
+        for (int j = 0; j < cnt; j++) k += ((p[4 + j] & 0xFFFFFF) < db.n_items);
+        return k;
+    }
+    case GPUTX_T_OE_PAYMENT: return 3;
+    case GPUTX_T_OE_ORDER_STATUS: return 2;
+    default: return 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// hash index probes (linear probing on a multiplicative hash)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t hmix(unsigned long long k)
+{
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+// returns the row slot or -1
+__device__ __forceinline__ int64_t hash_find(const HashIndex &h, unsigned long long key)
+{
+    uint64_t i = hmix(key) & h.mask;
+    for (uint64_t probe = 0; probe <= h.mask; probe++, i = (i + 1) & h.mask) {
+        unsigned long long k = __ldcg(&h.keys[i]);
+        if (k == key) return (int64_t)__ldcg(&h.rows[i]);
+        if (k == HKEY_EMPTY) return -1;
+    }
+    return -1;
+}
+
+// Inserts key -> row.  The caller guarantees no concurrent operation on the
+// same key (its transactions conflict on the root item, so they never run at
+// the same time); other keys may be inserted concurrently, hence the CAS.
+// Reuses the first tombstone on the probe path.  Returns false when full.
+__device__ __forceinline__ bool hash_insert(const HashIndex &h, unsigned long long key, uint32_t row)
+{
+    for (int attempt = 0; attempt < 64; attempt++) {
+        uint64_t i = hmix(key) & h.mask;
+        int64_t tomb = -1;
+        uint64_t slot = ~0ull;
+        for (uint64_t probe = 0; probe <= h.mask; probe++, i = (i + 1) & h.mask) {
+            unsigned long long k = __ldcg(&h.keys[i]);
+            if (k == HKEY_TOMB) { if (tomb < 0) tomb = (int64_t)i; continue; }
+            if (k == HKEY_EMPTY) { slot = tomb >= 0 ? (uint64_t)tomb : i; break; }
+        }
+        if (slot == ~0ull) {
+            if (tomb < 0) return false;
+            slot = (uint64_t)tomb;
+        }
+        unsigned long long expect = __ldcg(&h.keys[slot]);
+        if (expect != HKEY_EMPTY && expect != HKEY_TOMB) continue;   // raced
+        if (atomicCAS(&h.keys[slot], expect, key) == expect) {
+            // readers of this key run in a later level / after this
+            // transaction's release, so the row may follow the key
+            __stcg(&h.rows[slot], row);
+            return true;
+        }
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool hash_erase(const HashIndex &h, unsigned long long key)
+{
+    uint64_t i = hmix(key) & h.mask;
+    for (uint64_t probe = 0; probe <= h.mask; probe++, i = (i + 1) & h.mask) {
+        unsigned long long k = __ldcg(&h.keys[i]);
+        if (k == key) { atomicExch(&h.keys[i], HKEY_TOMB); return true; }
+        if (k == HKEY_EMPTY) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ unsigned long long ai_key(int64_t s, int64_t t) { return (unsigned long long)(s * 4 + (t - 1)); }
+__device__ __forceinline__ unsigned long long sf_key(int64_t s, int64_t t) { return (unsigned long long)(s * 4 + (t - 1)); }
+__device__ __forceinline__ unsigned long long cf_key(int64_t s, int64_t t, int64_t st)
+{
+    return (unsigned long long)((s * 4 + (t - 1)) * 3 + st / 8);
+}
+__device__ __forceinline__ unsigned long long ord_key(int64_t dist, int64_t o_id)
+{
+    return ((unsigned long long)dist << 32) | (unsigned long long)(uint32_t)o_id;
+}
+
+__device__ __forceinline__ int64_t pack2(int32_t lo, int32_t hi)
+{
+    return (int64_t)((unsigned long long)(uint32_t)lo | ((unsigned long long)(uint32_t)hi << 32));
+}
+
+// ---------------------------------------------------------------------------
+// the combined procedure kernel body (Section 3.2's switch)
+// ---------------------------------------------------------------------------
+// t: transaction index in the bulk; pos: its position in this strategy's
+// processing order (history slot); atomic_add: execute ADD-class increments
+// with atomics (several transactions of one level may add to one item).
+__device__ __forceinline__ void exec_dc(const DevDB &db, const DevBulk &b, uint32_t t, uint32_t pos,
+                                        bool atomic_add)
+{
+    const int64_t *p = b.params + (int64_t)t * b.P;
+    const int64_t a = p[0], delta = p[1];
+    const int64_t tl = a / db.acc_per_tel, br = a / db.acc_per_br;
+    const int64_t slot = b.base->hist + pos;
+    if (slot >= db.hist_cap) {              // history full: not executed
+        set_err(b.err, ERR_CAPACITY);
+        b.status[t] = 3;
+        return;
+    }
+    // account: read-modify-write, its new value is the output
+    const int64_t na = wrap_add(ldg_cg(&db.acc_bal[a]), delta);
+    stg_cg(&db.acc_bal[a], na);
+    if (atomic_add) {
+        atomicAdd((unsigned long long *)&db.tel_bal[tl], (unsigned long long)delta);
+        atomicAdd((unsigned long long *)&db.br_bal[br], (unsigned long long)delta);
+    } else {
+        stg_cg(&db.tel_bal[tl], wrap_add(ldg_cg(&db.tel_bal[tl]), delta));
+        stg_cg(&db.br_bal[br], wrap_add(ldg_cg(&db.br_bal[br]), delta));
+    }
+    db.h_ts[slot] = b.ts[t];
+    db.h_acc[slot] = a;
+    db.h_tel[slot] = tl;
+    db.h_br[slot] = br;
+    db.h_delta[slot] = delta;
+    b.out[(int64_t)t * b.R] = na;
+    b.status[t] = 0;
+}
+
+// subscriber-location procedures (stand-ins shaped like TM-1, Appendix E)
+__device__ __forceinline__ void exec_sub(const DevDB &db, const DevBulk &b, uint32_t t, int32_t type)
+{
+    const int64_t *p = b.params + (int64_t)t * b.P;
+    int64_t *out = b.out + (int64_t)t * b.R;
+    const int64_t s = p[0];
+    int32_t *row = db.sub_rows + s * SUB_FIELDS;
+    int32_t st = 0;
+    switch (type) {
+    case GPUTX_T_SUB_GET_SUBSCRIBER: {
+        const int4 *r4 = reinterpret_cast<const int4 *>(row);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            int4 v = __ldcg(r4 + q);
+            out[2 * q] = pack2(v.x, v.y);
+            out[2 * q + 1] = pack2(v.z, v.w);
+        }
+        break;
+    }
+    case GPUTX_T_SUB_GET_ACCESS: {
+        int64_t r = hash_find(db.ai_idx, ai_key(s, p[1]));
+        if (r < 0) { st = 1; break; }
+        const int4 v = __ldcg(reinterpret_cast<const int4 *>(db.ai_data + r * 4));
+        out[0] = pack2(v.x, v.y);
+        out[1] = pack2(v.z, v.w);
+        break;
+    }
+    case GPUTX_T_SUB_GET_NEW_DEST: {
+        int64_t r = hash_find(db.sf_idx, sf_key(s, p[1]));
+        if (r < 0 || __ldcg(&db.sf_active[r]) != 1) { st = 1; break; }
+        int cnt = 0;
+        for (int k = 0; k < 3; k++) {
+            const int64_t stt = 8 * k;
+            if (stt > p[2]) continue;
+            int64_t c = hash_find(db.cf_idx, cf_key(s, p[1], stt));
+            if (c >= 0 && __ldcg(&db.cf_end[c]) > p[3]) out[1 + cnt++] = __ldcg(&db.cf_numberx[c]);
+        }
+        out[0] = cnt;
+        st = cnt ? 0 : 1;
+        break;
+    }
+    case GPUTX_T_SUB_UPDATE_LOCATION:
+        out[0] = ldg_cg(&row[15]);
+        stg_cg(&row[15], (int32_t)p[1]);
+        break;
+    case GPUTX_T_SUB_UPDATE_FACILITY: {
+        int64_t r = hash_find(db.sf_idx, sf_key(s, p[1]));
+        if (r < 0) { st = 1; break; }                  // read phase: abort
+        stg_cg(&row[0], (int32_t)p[2]);
+        stg_cg(&db.sf_data_a[r], (int32_t)p[3]);
+        break;
+    }
+    case GPUTX_T_SUB_INSERT_CF: {
+        if (hash_find(db.sf_idx, sf_key(s, p[1])) < 0) { st = 1; break; }
+        const unsigned long long key = cf_key(s, p[1], p[2]);
+        if (hash_find(db.cf_idx, key) >= 0) { st = 2; break; }
+        const int64_t slot = b.base->cf + b.slot_cf[t];
+        if (slot >= db.child_cap) { set_err(b.err, ERR_CAPACITY); st = 3; break; }
+        db.cf_sid[slot] = (int32_t)s;
+        db.cf_type[slot] = (int32_t)p[1];
+        db.cf_start[slot] = (int32_t)p[2];
+        stg_cg(&db.cf_end[slot], (int32_t)p[3]);
+        stg_cg(&db.cf_numberx[slot], (int32_t)p[4]);
+        stg_cg(&db.cf_live[slot], (uint8_t)1);
+        if (!hash_insert(db.cf_idx, key, (uint32_t)slot)) { set_err(b.err, ERR_CAPACITY); st = 3; }
+        break;
+    }
+    case GPUTX_T_SUB_DELETE_CF: {
+        const unsigned long long key = cf_key(s, p[1], p[2]);
+        int64_t r = hash_find(db.cf_idx, key);
+        if (r < 0) { st = 1; break; }
+        hash_erase(db.cf_idx, key);
+        stg_cg(&db.cf_live[r], (uint8_t)0);
+        break;
+    }
+    }
+    b.status[t] = st;
+}
+
+// order-entry procedures (stand-ins shaped like TPC-C, Appendix E)
+__device__ __forceinline__ void exec_oe(const DevDB &db, const DevBulk &b, uint32_t t, int32_t type,
+                                        bool atomic_add)
+{
+    const int64_t *p = b.params + (int64_t)t * b.P;
+    int64_t *out = b.out + (int64_t)t * b.R;
+    const int64_t w = p[0], d = w * OE_DIST + p[1], c = d * OE_CUST + p[2];
+    int32_t st = 0;
+    switch (type) {
+    case GPUTX_T_OE_NEW_ORDER: {
+        const int cnt = (int)p[3];
+        for (int j = 0; j < cnt; j++)                                  // read phase
+            if ((p[4 + j] & 0xFFFFFF) >= db.n_items) { st = 1; break; }
+        if (st) break;
+        const int64_t oslot = b.base->ord + b.slot_ord[t];
+        const int64_t lslot = b.base->ol + b.slot_ol[t];
+        if (oslot >= db.ord_cap || lslot + cnt > db.ol_cap) {
+            set_err(b.err, ERR_CAPACITY); st = 3; break;
+        }
+        const int64_t o_id = ldg_cg(&db.d_next_o_id[d]);
+        stg_cg(&db.d_next_o_id[d], o_id + 1);
+        int64_t total = 0;
+        for (int j = 0; j < cnt; j++) {
+            const int64_t line = p[4 + j];
+            const int64_t item = line & 0xFFFFFF, sw = (line >> 24) & 0xFFFF;
+            const int64_t qty = (line >> 40) & 0xFF;
+            const int64_t amount = qty * __ldg(&db.i_price[item]);
+            total += amount;
+            const int64_t s = sw * db.n_items + item;
+            int32_t q = ldg_cg(&db.s_quantity[s]);
+            q = (q >= qty + 10) ? (int32_t)(q - qty) : (int32_t)(q - qty + 91);
+            stg_cg(&db.s_quantity[s], q);
+            stg_cg(&db.s_ytd[s], ldg_cg(&db.s_ytd[s]) + qty);
+            stg_cg(&db.s_order_cnt[s], ldg_cg(&db.s_order_cnt[s]) + 1);
+            db.ol_item[lslot + j] = (int32_t)item;
+            db.ol_sw[lslot + j] = (int32_t)sw;
+            db.ol_qty[lslot + j] = (int32_t)qty;
+            stg_cg(&db.ol_amount[lslot + j], amount);
+        }
+        db.o_w[oslot] = (int32_t)w;
+        db.o_d[oslot] = (int32_t)p[1];
+        db.o_c[oslot] = (int32_t)p[2];
+        stg_cg(&db.o_cnt[oslot], (int32_t)cnt);
+        stg_cg(&db.o_id[oslot], o_id);
+        stg_cg(&db.o_first[oslot], lslot);
+        stg_cg(&db.o_live[oslot], (uint8_t)1);
+        if (!hash_insert(db.ord_idx, ord_key(d, o_id), (uint32_t)oslot)) {
+            set_err(b.err, ERR_CAPACITY); st = 3; break;
+        }
+        stg_cg(&db.c_last_o_id[c], o_id);
+        out[0] = o_id;
+        out[1] = total * (10000 - __ldg(&db.c_discount[c])) *
+                 (10000 + __ldg(&db.w_tax[w]) + __ldg(&db.d_tax[d])) / 100000000;
+        out[2] = cnt;
+        break;
+    }
+    case GPUTX_T_OE_PAYMENT: {
+        const int64_t amount = p[3];
+        if (atomic_add) {
+            atomicAdd((unsigned long long *)&db.w_ytd[w], (unsigned long long)amount);
+            atomicAdd((unsigned long long *)&db.d_ytd[d], (unsigned long long)amount);
+        } else {
+            stg_cg(&db.w_ytd[w], wrap_add(ldg_cg(&db.w_ytd[w]), amount));
+            stg_cg(&db.d_ytd[d], wrap_add(ldg_cg(&db.d_ytd[d]), amount));
+        }
+        const int64_t bal = wrap_add(ldg_cg(&db.c_balance[c]), -amount);
+        stg_cg(&db.c_balance[c], bal);
+        stg_cg(&db.c_ytd[c], wrap_add(ldg_cg(&db.c_ytd[c]), amount));
+        stg_cg(&db.c_payment_cnt[c], ldg_cg(&db.c_payment_cnt[c]) + 1);
+        out[0] = bal;
+        break;
+    }
+    case GPUTX_T_OE_ORDER_STATUS: {
+        const int64_t o = ldg_cg(&db.c_last_o_id[c]);
+        out[0] = ldg_cg(&db.c_balance[c]);
+        out[1] = o;
+        if (o == 0) { st = 1; break; }
+        const int64_t r = hash_find(db.ord_idx, ord_key(d, o));
+        if (r < 0) { set_err(b.err, ERR_BOUNDS); st = 1; break; }
+        const int cnt = ldg_cg(&db.o_cnt[r]);
+        const int64_t first = ldg_cg(&db.o_first[r]);
+        int64_t sum = 0;
+        for (int j = 0; j < cnt; j++) sum += ldg_cg(&db.ol_amount[first + j]);
+        out[2] = cnt;
+        out[3] = sum;
+        break;
+    }
+    }
+    b.status[t] = st;
+}
+
+__device__ __forceinline__ void exec_txn(const DevDB &db, const DevBulk &b, uint32_t t, uint32_t pos,
+                                         bool atomic_add)
+{
+    const int32_t type = b.type[t];
+    switch (type) {
+    case GPUTX_T_DC_DEBIT_CREDIT: exec_dc(db, b, t, pos, atomic_add); break;
+    case GPUTX_T_SUB_GET_SUBSCRIBER:
+    case GPUTX_T_SUB_GET_ACCESS:
+    case GPUTX_T_SUB_GET_NEW_DEST:
+    case GPUTX_T_SUB_UPDATE_LOCATION:
+    case GPUTX_T_SUB_UPDATE_FACILITY:
+    case GPUTX_T_SUB_INSERT_CF:
+    case GPUTX_T_SUB_DELETE_CF: exec_sub(db, b, t, type); break;
+    case GPUTX_T_OE_NEW_ORDER:
+    case GPUTX_T_OE_PAYMENT:
+    case GPUTX_T_OE_ORDER_STATUS: exec_oe(db, b, t, type, atomic_add); break;
+    }
+}
+
+}  // namespace gtx

@@ -111,12 +111,17 @@ def oracle_logical_state(db):
     compared as multisets keyed by their primary keys (physical row order is
     not part of the state)."""
     st = {}
-    for k in ("acc_bal", "tel_bal", "br_bal", "sub", "ai_present", "ai_data",
-              "sf_present", "sf_active", "sf_err", "sf_data_a", "sf_data_b",
-              "w_ytd", "d_ytd", "d_next_o_id", "c_balance", "c_ytd",
+    for k in ("acc_bal", "tel_bal", "br_bal", "sub", "ai_present",
+              "sf_present", "w_ytd", "d_ytd", "d_next_o_id", "c_balance", "c_ytd",
               "c_payment_cnt", "c_last_o_id", "s_quantity", "s_ytd", "s_order_cnt"):
         if k in db.a:
             st[k] = db.a[k].copy()
+    # child-row fields exist only where the row does
+    if "ai_data" in db.a:
+        st["ai_data"] = np.where(db.a["ai_present"].astype(bool)[:, :, None], db.a["ai_data"], 0)
+    for k in ("sf_active", "sf_err", "sf_data_a", "sf_data_b"):
+        if k in db.a:
+            st[k] = np.where(db.a["sf_present"].astype(bool), db.a[k], 0)
     if "cf_present" in db.a:
         p = db.a["cf_present"].astype(bool)
         st["cf_present"] = p.copy()
@@ -163,3 +168,65 @@ def state_diff(a, b):
         elif x != y:
             out.append(k)
     return out
+
+
+def gpu_logical_state(db, dc=False, sub=False, oe=False, n_sub=0, n_wh=0, n_items=0):
+    """The engine's database read back through gputx_read_table, in the same
+    logical form as ``oracle_logical_state``."""
+    import paper_1103_3105_gb300 as G
+    st = {}
+    if dc:
+        st["acc_bal"] = db.read(G.TBL_DC_ACCOUNT)[:, 0]
+        st["tel_bal"] = db.read(G.TBL_DC_TELLER)[:, 0]
+        st["br_bal"] = db.read(G.TBL_DC_BRANCH)[:, 0]
+        h = db.read(G.TBL_DC_HISTORY)
+        st["history"] = h[np.argsort(h[:, 0], kind="stable")]
+    if sub:
+        st["sub"] = db.read(G.TBL_SUB_SUBSCRIBER).astype(np.int32)
+        ai = db.read(G.TBL_SUB_ACCESS_INFO)
+        p = np.zeros((n_sub, 4), dtype=np.uint8)
+        d = np.zeros((n_sub, 4, 4), dtype=np.int32)
+        p[ai[:, 0], ai[:, 1] - 1] = 1
+        d[ai[:, 0], ai[:, 1] - 1] = ai[:, 2:6]
+        st["ai_present"], st["ai_data"] = p, d
+        sf = db.read(G.TBL_SUB_SPECIAL_FACILITY)
+        sp = np.zeros((n_sub, 4), dtype=np.uint8)
+        sp[sf[:, 0], sf[:, 1] - 1] = 1
+        st["sf_present"] = sp
+        for j, k in enumerate(("sf_active", "sf_err", "sf_data_a", "sf_data_b")):
+            a = np.zeros((n_sub, 4), dtype=np.int32)
+            a[sf[:, 0], sf[:, 1] - 1] = sf[:, 2 + j]
+            st[k] = a
+        cf = db.read(G.TBL_SUB_CALL_FORWARDING)
+        cp = np.zeros((n_sub, 4, 3), dtype=bool)
+        ce = np.zeros((n_sub, 4, 3), dtype=np.int32)
+        cn = np.zeros((n_sub, 4, 3), dtype=np.int32)
+        idx = (cf[:, 0], cf[:, 1] - 1, cf[:, 2] // 8)
+        assert not cp[idx].any() and len(set(zip(*[x.tolist() for x in idx]))) == len(cf), \
+            "duplicate live call_forwarding key"
+        cp[idx] = True
+        ce[idx] = cf[:, 3]
+        cn[idx] = cf[:, 4]
+        st["cf_present"], st["cf_end"], st["cf_numberx"] = cp, ce, cn
+    if oe:
+        w = db.read(G.TBL_OE_WAREHOUSE)
+        d = db.read(G.TBL_OE_DISTRICT)
+        c = db.read(G.TBL_OE_CUSTOMER)
+        s = db.read(G.TBL_OE_STOCK)
+        st["w_ytd"] = w[:, 1]
+        st["d_ytd"], st["d_next_o_id"] = d[:, 1], d[:, 2]
+        st["c_balance"], st["c_ytd"], st["c_payment_cnt"], st["c_last_o_id"] = c[:, 1], c[:, 2], c[:, 3], c[:, 4]
+        st["s_quantity"], st["s_ytd"], st["s_order_cnt"] = (s[:, 0].astype(np.int32), s[:, 1],
+                                                            s[:, 2].astype(np.int32))
+        orders = db.read(G.TBL_OE_ORDER)
+        lines = db.read(G.TBL_OE_ORDER_LINE)
+        by = {}
+        for l in lines:
+            by.setdefault((int(l[0]), int(l[1]), int(l[2])), []).append(
+                (int(l[3]), int(l[4]), int(l[5]), int(l[6])))
+        rows = []
+        for o in orders:
+            key = (int(o[0]), int(o[1]), int(o[2]))
+            rows.append(key + (int(o[3]), int(o[4]), tuple(sorted(by.get(key, [])))))
+        st["orders"] = sorted(rows)
+    return st

@@ -1,0 +1,50 @@
+"""The C ABI library loads without a GPU and exports every entry point that
+include/gputx.h declares; the Python binding names the same functions."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1103_3105_gb300 as G
+from paper_1103_3105_gb300 import _build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(gputx_\w+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return _build.build()
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    declared = _declared()
+    assert len(declared) >= 14
+    missing = [n for n in sorted(declared) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_abi(libpath):
+    assert set(G.EXPORTED) <= _declared()
+    assert _declared() <= set(G.EXPORTED) | {n for n in _declared() if n.startswith("gputx_")
+                                            and hasattr(G, n)}
+    assert G.gputx_version().startswith("gputx-gb300")
+
+
+def test_structs_match_header_sizes():
+    # the binding's ctypes mirrors must keep the header's field order and sizes
+    assert ctypes.sizeof(G.SchemaDesc) == 10 * 8
+    assert ctypes.sizeof(G.Config) == 8 + 4 + 4 + 8 * 4
+    assert ctypes.sizeof(G.ExecOpts) == 16
+    assert ctypes.sizeof(G.ExecStats) == 8 + 6 * 8 + 6 * 4

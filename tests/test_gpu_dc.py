@@ -1,0 +1,206 @@
+"""Debit-credit parity: the CUDA engine against the CPU oracle, bit for bit.
+
+All columns are int64, so the tolerance is zero: database state, per
+transaction status and output, and the structural statistics d and w0 must be
+identical to serial execution in timestamp order (Definition 1).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1103_3105_gb300 as G
+import workloads as W
+from tests._helpers import gpu_logical_state, oracle_logical_state, state_diff, states_equal
+
+pytestmark = pytest.mark.gpu
+
+STRATS = ["kset", "part", "tpl"]
+MODES = [G.CONFLICT_PAPER, G.CONFLICT_ADD]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def make_pair(B, T, A, cap, max_bulk=1 << 16, **kw):
+    tabs = W.dc_tables(B, T, A)
+    g = G.Database(dc=(B, T, A), history_capacity=cap, max_bulk=max_bulk, **kw)
+    g.register(G.DC_TYPES)
+    for t, rows in W.dc_rows(tabs).items():
+        g.load(t, rows)
+    o = oracle.OracleDB(dc=tabs, hist_cap=cap)
+    return g, o
+
+
+def run_both(g, o, bulk, strategy, mode, **kw):
+    b = g.submit_dict(bulk).execute(strategy, conflict_mode=mode, **kw)
+    stats = b.sync()
+    st, out = b.results()
+    b.free()
+    ost, oout = o.execute(bulk, R=1)
+    return stats, st, out, ost, oout
+
+
+def assert_same(g, o, st, out, ost, oout):
+    assert np.array_equal(st, ost)
+    assert np.array_equal(out, oout)
+    gs = gpu_logical_state(g, dc=True)
+    os_ = oracle_logical_state(o)
+    assert states_equal(gs, os_), state_diff(gs, os_)
+
+
+@pytest.mark.parametrize("strategy", STRATS)
+@pytest.mark.parametrize("mode", MODES)
+def test_config1_tiny_bank(strategy, mode):
+    """4 branches, 40 tellers, 4,000 accounts, 4,096 transactions."""
+    g, o = make_pair(4, 40, 4000, 8192)
+    bulk = W.dc_bulk(4096, 4000, 0.0, seed=W.seed_for(1))
+    stats, st, out, ost, oout = run_both(g, o, bulk, strategy, mode)
+    assert_same(g, o, st, out, ost, oout)
+    if strategy == "kset":
+        ob = oracle.OracleDB(dc=W.dc_tables(4, 40, 4000), hist_cap=8192)
+        obj, cls, root = ob.extract(bulk, mode, 3)
+        lv = oracle.levels(obj, cls, ob.num_objects())
+        d, w0, c = oracle.graph_stats(lv, root)
+        assert (stats["depth"], stats["w0"], stats["cross"]) == (d, w0, c)
+    g.close()
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 257, 8191, 8193, 20000])
+@pytest.mark.parametrize("strategy", STRATS)
+def test_ragged_sizes(n, strategy):
+    """Sizes around warp, CTA, scan-tile (2,048) and sort-tile (8,192) edges."""
+    g, o = make_pair(10, 100, 10000, 1 << 16)
+    bulk = W.dc_bulk(n, 10000, 0.5, seed=n)
+    for mode in MODES:
+        stats, st, out, ost, oout = run_both(g, o, bulk, strategy, mode)
+        assert_same(g, o, st, out, ost, oout)
+        bulk = W.dc_bulk(n, 10000, 0.5, seed=n + 1, ts0=int(bulk["ts"][-1]) + 1)
+    g.close()
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.5, 0.99])
+@pytest.mark.parametrize("strategy", STRATS)
+def test_skew(theta, strategy):
+    """Zipf-skewed accounts (hot rows give deep graphs and long partitions)."""
+    g, o = make_pair(100, 1000, 100000, 1 << 18)
+    for k in range(2):
+        bulk = W.dc_bulk(30000, 100000, theta, seed=int(theta * 100) + k, ts0=k * 30000)
+        stats, st, out, ost, oout = run_both(g, o, bulk, strategy, MODES[k])
+        assert_same(g, o, st, out, ost, oout)
+    g.close()
+
+
+def test_strategies_agree_across_a_sequence():
+    """Bulks run back to back with different strategies equal one serial run."""
+    g, o = make_pair(20, 200, 20000, 1 << 17)
+    ts0 = 0
+    for k, (s, m) in enumerate([("kset", 0), ("tpl", 1), ("part", 0), ("kset", 1), ("tpl", 0),
+                                ("auto", 0), ("auto", 1)]):
+        bulk = W.dc_bulk(5000 + 37 * k, 20000, 0.7, seed=50 + k, ts0=ts0)
+        ts0 += len(bulk["ts"])
+        stats, st, out, ost, oout = run_both(g, o, bulk, s, m)
+        assert np.array_equal(st, ost) and np.array_equal(out, oout), (s, m)
+    gs, os_ = gpu_logical_state(g, dc=True), oracle_logical_state(o)
+    assert states_equal(gs, os_), state_diff(gs, os_)
+    g.close()
+
+
+def test_empty_bulk():
+    g, o = make_pair(4, 40, 4000, 1024)
+    for s in STRATS:
+        b = g.submit(np.zeros(0, np.int64), np.zeros(0, np.int32), np.zeros((0, 2), np.int64))
+        b.execute(s)
+        st, out = b.results()
+        assert st.shape == (0,) and out.shape == (0, 1)
+        b.free()
+    assert len(g.read(G.TBL_DC_HISTORY)) == 0
+    g.close()
+
+
+@pytest.mark.parametrize("flaw", ["type", "account", "ts"])
+def test_invalid_bulk_is_rejected_and_leaves_state(flaw):
+    g, o = make_pair(4, 40, 4000, 8192)
+    good = W.dc_bulk(100, 4000, 0.0, seed=3)
+    run_both(g, o, good, "kset", 0)
+    bad = W.dc_bulk(100, 4000, 0.0, seed=4, ts0=100)
+    if flaw == "type":
+        bad["type"][50] = G.T_SUB_GET_SUBSCRIBER   # not registered
+    elif flaw == "account":
+        bad["params"][70, 0] = 4000
+    else:
+        bad["ts"][10] = bad["ts"][9]
+    before = gpu_logical_state(g, dc=True)
+    for s in STRATS:
+        b = g.submit_dict(bad).execute(s)
+        with pytest.raises(G.GputxError) as e:
+            b.sync()
+        assert e.value.status == G.EINVAL
+        b.free()
+    after = gpu_logical_state(g, dc=True)
+    assert states_equal(before, after), state_diff(before, after)
+    g.close()
+
+
+def test_device_resident_inputs():
+    torch = pytest.importorskip("torch")
+    g, o = make_pair(10, 100, 10000, 1 << 16)
+    bulk = W.dc_bulk(10000, 10000, 0.3, seed=9)
+    dev = {k: torch.from_numpy(bulk[k]).cuda() for k in ("ts", "type", "params")}
+    b = g.submit(dev["ts"], dev["type"], dev["params"]).execute("kset")
+    st, out = b.results()
+    b.free()
+    ost, oout = o.execute(bulk, 1)
+    assert np.array_equal(st, ost) and np.array_equal(out, oout)
+    g.close()
+
+
+def test_execute_twice_is_refused():
+    g, o = make_pair(4, 40, 4000, 8192)
+    b = g.submit_dict(W.dc_bulk(10, 4000, 0.0, seed=1)).execute("kset")
+    with pytest.raises(G.GputxError) as e:
+        b.execute("kset")
+    assert e.value.status == G.ESTATE
+    b.sync()
+    b.free()
+    g.close()
+
+
+def test_bounded_wait_reports_timeout():
+    """A 1 ns wait limit makes the level waits of a 1,000-deep K-SET run out:
+    the engine must report ETIMEOUT instead of hanging, and stay usable."""
+    g = G.Database(dc=(4, 40, 4000), history_capacity=1 << 16, max_bulk=1 << 14, spin_limit_ns=1)
+    g.register(G.DC_TYPES)
+    bulk = W.dc_bulk(4096, 4000, 0.0, seed=2)
+    b = g.submit_dict(bulk).execute("kset")
+    with pytest.raises(G.GputxError) as e:
+        b.sync()
+    assert e.value.status == G.ETIMEOUT
+    b.free()
+    g.close()
+    # the context still works
+    g2, o = make_pair(4, 40, 4000, 8192)
+    stats, st, out, ost, oout = run_both(g2, o, W.dc_bulk(500, 4000, 0.0, seed=3), "kset", 0)
+    assert np.array_equal(out, oout)
+    g2.close()
+
+
+@pytest.mark.parametrize("strategy,mode", [("kset", 0), ("kset", 1), ("tpl", 1), ("part", 0)])
+def test_full_size_config2(strategy, mode):
+    """The benchmark's workload: 1,000 branches, 10,000 tellers, 10,000,000
+    accounts, a bulk of 2^22 transactions, in the benchmark's launch shape.
+    The oracle runs the whole bulk serially, so every output is compared."""
+    A = 10_000_000
+    g, o = make_pair(1000, 10000, A, 1 << 22, max_bulk=1 << 22)
+    bulk = W.dc_bulk(1 << 22, A, 0.0, seed=W.seed_for(2, 22))
+    stats, st, out, ost, oout = run_both(g, o, bulk, strategy, mode)
+    assert np.array_equal(st, ost)
+    assert np.array_equal(out, oout)
+    assert np.array_equal(g.read(G.TBL_DC_ACCOUNT)[:, 0], o["acc_bal"])
+    assert np.array_equal(g.read(G.TBL_DC_BRANCH)[:, 0], o["br_bal"])
+    assert np.array_equal(g.read(G.TBL_DC_TELLER)[:, 0], o["tel_bal"])
+    h = g.read(G.TBL_DC_HISTORY)
+    assert np.array_equal(h[np.argsort(h[:, 0])], o.history())
+    g.close()

@@ -365,3 +365,60 @@ def oe_bulk(n: int, n_wh: int, n_items: int = 100_000, item_theta: float = 0.8,
         "params": params,
         "P": OE_PARAMS,
     }
+
+
+# ---------------------------------------------------------------------------
+# row formats of the engine's table loader (int64 fields per row)
+# ---------------------------------------------------------------------------
+def dc_rows(t: dict) -> dict:
+    """{table id: rows} for gputx_load_table (branch, teller, account)."""
+    return {0: t["branch_balance"].reshape(-1, 1), 1: t["teller_balance"].reshape(-1, 1),
+            2: t["account_balance"].reshape(-1, 1)}
+
+
+def sub_rows(t: dict) -> dict:
+    """{table id: rows}: subscriber (16 fields), access_info (s_id, ai_type,
+    data1..4), special_facility (s_id, sf_type, is_active, error_cntrl,
+    data_a, data_b), call_forwarding (s_id, sf_type, start_time, end_time,
+    numberx) -- child rows only where present."""
+    n = t["sub"].shape[0]
+    s_ai, a_ai = np.nonzero(t["ai_present"])
+    ai = np.column_stack([s_ai, a_ai + 1, t["ai_data"][s_ai, a_ai]]).astype(np.int64)
+    s_sf, a_sf = np.nonzero(t["sf_present"])
+    sf = np.column_stack([s_sf, a_sf + 1, t["sf_active"][s_sf, a_sf], t["sf_err"][s_sf, a_sf],
+                          t["sf_data_a"][s_sf, a_sf], t["sf_data_b"][s_sf, a_sf]]).astype(np.int64)
+    s_cf, a_cf, k_cf = np.nonzero(t["cf_present"])
+    cf = np.column_stack([s_cf, a_cf + 1, 8 * k_cf, t["cf_end"][s_cf, a_cf, k_cf],
+                          t["cf_numberx"][s_cf, a_cf, k_cf]]).astype(np.int64)
+    return {4: t["sub"].astype(np.int64).reshape(n, 16), 5: ai.reshape(-1, 6),
+            6: sf.reshape(-1, 6), 7: cf.reshape(-1, 5)}
+
+
+def oe_rows(t: dict) -> dict:
+    """{table id: rows}: warehouse (tax, ytd), district (tax, ytd,
+    next_o_id), customer (discount, balance, ytd_payment, payment_cnt,
+    last_o_id), item (price), stock (quantity, ytd, order_cnt)."""
+    return {
+        8: np.column_stack([t["w_tax"], t["w_ytd"]]),
+        9: np.column_stack([t["d_tax"], t["d_ytd"], t["d_next_o_id"]]),
+        10: np.column_stack([t["c_discount"], t["c_balance"], t["c_ytd"], t["c_payment_cnt"],
+                             t["c_last_o_id"]]),
+        11: t["i_price"].reshape(-1, 1),
+        12: np.column_stack([t["s_quantity"].astype(np.int64), t["s_ytd"],
+                             t["s_order_cnt"].astype(np.int64)]),
+    }
+
+
+def concat_bulks(parts, pick) -> dict:
+    """Interleave bulks of different schemas: transaction i comes from
+    parts[pick[i]] (its i-th transaction); parameters are zero-padded to the
+    widest schema."""
+    n = len(pick)
+    P = max(p["P"] for p in parts)
+    params = np.zeros((n, P), dtype=np.int64)
+    types = np.zeros(n, dtype=np.int32)
+    for k, p in enumerate(parts):
+        m = pick == k
+        params[m, : p["P"]] = p["params"][m]
+        types[m] = p["type"][m]
+    return {"ts": np.arange(n, dtype=np.int64), "type": types, "params": params, "P": P}
