@@ -136,7 +136,9 @@ def run_engine(args, rank, world, local_rank):
 
     n = 1 << args.bulk_log2
     K, Wm = args.steps, args.warmup
-    stream = torch.cuda.current_stream()
+    # the engine and every event/flush share one explicit stream
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
     cap = (2 * (K + Wm) + 8) * n
     db = G.Database(dc=(BRANCHES, TELLERS, ACCOUNTS), history_capacity=cap, max_bulk=n,
                     stream=stream.cuda_stream)

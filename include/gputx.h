@@ -148,6 +148,12 @@ typedef struct {
     int32_t block_threads;    /* 0 = database default */
     int32_t part_size;        /* 0 = database default */
     int32_t timing;           /* 1 = record per-phase CUDA events in stats */
+    int32_t kset_launch;      /* K-SET launch shape: 0 = per-level plan (wide
+                                 levels on the whole grid, runs of narrow levels
+                                 on one thread-block cluster), 1 = one persistent
+                                 launch with per-level counters (no host sync
+                                 after the analysis) */
+    int32_t narrow_max;       /* widest level run on one cluster; 0 = 16384 */
 } gputx_exec_opts;
 
 typedef struct gputx_db gputx_db;

@@ -79,7 +79,8 @@ class ExecStats(C.Structure):
 
 class ExecOpts(C.Structure):
     _fields_ = [("conflict_mode", C.c_int32), ("block_threads", C.c_int32),
-                ("part_size", C.c_int32), ("timing", C.c_int32)]
+                ("part_size", C.c_int32), ("timing", C.c_int32), ("kset_launch", C.c_int32),
+                ("narrow_max", C.c_int32)]
 
 
 _lib = None
@@ -224,9 +225,10 @@ class Bulk:
         self._keep = keep   # device inputs referenced in place stay alive
 
     def execute(self, strategy="kset", conflict_mode=CONFLICT_PAPER, block_threads=0, part_size=0,
-                timing=False):
+                timing=False, kset_launch=0, narrow_max=0):
         s = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
-        gputx_execute(self.db.h, self.h, s, ExecOpts(conflict_mode, block_threads, part_size, int(timing)))
+        gputx_execute(self.db.h, self.h, s, ExecOpts(conflict_mode, block_threads, part_size, int(timing),
+                                                     kset_launch, narrow_max))
         return self
 
     def sync(self) -> dict:

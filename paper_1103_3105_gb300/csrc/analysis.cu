@@ -78,7 +78,7 @@ __global__ void extract_kernel(ExtractArgs a)
     bool cross = false;
     if (t < a.b.n) {
         const int64_t *p = a.b.params + t * a.b.P;
-        const int64_t off = a.op_off ? (int64_t)a.op_off[t] : t * a.uniform_k;
+        const int64_t off = a.op_off ? (int64_t)a.op_off[t] : t * a.uniform_k;   // used when writing
         const bool ok = txn_valid(a.db, a.b, t);
         uint32_t obj[MAX_OPS], root[MAX_OPS];
         uint8_t cls[MAX_OPS];
@@ -88,7 +88,7 @@ __global__ void extract_kernel(ExtractArgs a)
         } else {
             set_err(&a.ctl->err, ERR_INVAL);
         }
-        if (a.op_off == nullptr) {
+        if (a.write_ops && a.op_off == nullptr) {
             // uniform layout: always fill K slots (dummy reads on object 0 for
             // an invalid transaction; the bulk will not execute)
             for (int j = k; j < a.uniform_k; j++) { obj[j] = 0; cls[j] = CLS_R; root[j] = 0; }
@@ -378,13 +378,43 @@ inline DevBulk dev_bulk(gputx_bulk *b, int mode)
     d.slot_cf = b->sc.slot_cf;
     d.slot_ord = b->sc.slot_ord;
     d.slot_ol = b->sc.slot_ol;
+    d.rec_params = b->sc.rec_params;
+    d.rec_ts = b->sc.rec_ts;
+    d.rec_type = b->sc.rec_type;
+    d.rec_t = b->sc.rec_t;
     d.conflict_mode = mode;
     return d;
+}
+
+// the bulk's signatures permuted into execution order: executors then read
+// them sequentially instead of chasing order[] into random rows
+__global__ void gather_kernel(DevBulk b, const uint32_t *order, int64_t *r_params, int64_t *r_ts,
+                              int32_t *r_type, uint32_t *r_t, const uint32_t *err)
+{
+    const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (pos >= b.n || *err) return;
+    const uint32_t t = order[pos];
+    r_t[pos] = t;
+    r_ts[pos] = b.ts[t];
+    r_type[pos] = b.type[t];
+    const int64_t *src = b.params + (int64_t)t * b.P;
+    int64_t *dst = r_params + pos * b.P;
+    for (int j = 0; j < b.P; j++) dst[j] = src[j];
 }
 
 }  // namespace
 
 DevBulk make_dev_bulk(gputx_bulk *b, int mode) { return dev_bulk(b, mode); }
+
+cudaError_t launch_gather(gputx_bulk *b, const uint32_t *order)
+{
+    if (b->n == 0) return cudaSuccess;
+    const DevBulk d = dev_bulk(b, 0);
+    gather_kernel<<<grid_for(b->n), TB, 0, b->db->stream>>>(d, order, b->sc.rec_params, b->sc.rec_ts,
+                                                             b->sc.rec_type, b->sc.rec_t, &b->ctl->err);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_begin(gputx_bulk *b)
 {
@@ -526,12 +556,13 @@ cudaError_t launch_regroup_keys(gputx_bulk *b, uint32_t *keys, uint32_t *vals)
     return cudaGetLastError();
 }
 
-cudaError_t launch_level_tables(gputx_bulk *b, const uint32_t *skeys, int64_t depth, int block)
+cudaError_t launch_level_tables(gputx_bulk *b, const uint32_t *skeys, int64_t depth, int block, bool chunks)
 {
     cudaStream_t s = b->db->stream;
     if (b->n == 0) return cudaSuccess;
     level_off_kernel<<<grid_for(b->n), TB, 0, s>>>(skeys, b->n, b->db->tbits, b->sc.level_off, &b->ctl->err);
     count_launches(1);
+    if (!chunks) return cudaGetLastError();
     const int64_t levels = depth + 1;
     ChunkMode cm{b->sc.level_off, b->sc.chunk_off, (uint32_t)block};
     cudaError_t e = run_scan(b, cm, levels, 3);

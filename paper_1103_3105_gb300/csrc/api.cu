@@ -204,6 +204,10 @@ size_t carve_bulk(gputx_bulk *b, char *base, bool device_inputs)
     s.pid_val = c.take<uint32_t>(nn);
     s.pid_key2 = c.take<uint32_t>(nn);
     s.pid_val2 = c.take<uint32_t>(nn);
+    s.rec_params = c.take<int64_t>(nn * b->P);
+    s.rec_ts = c.take<int64_t>(nn);
+    s.rec_type = c.take<int32_t>(nn);
+    s.rec_t = c.take<uint32_t>(nn);
     const bool slots = (db->dev.registered >> GPUTX_T_SUB_INSERT_CF & 1u) ||
                        (db->dev.registered >> GPUTX_T_OE_NEW_ORDER & 1u);
     s.slot_cf = slots ? c.take<uint32_t>(nn) : nullptr;
@@ -899,13 +903,30 @@ gputx_status gputx_execute(gputx_db *db, gputx_bulk *b, int strategy, const gput
     }
     if (run == GPUTX_KSET) {
         const int64_t depth = b->host_ctl.depth;
+        const bool persistent = opts && opts->kset_launch == 1;
         // regroup by (level, type): reuse the free op buffers
         uint32_t *rk = ak, *rv = av, *rk2 = sk, *rv2 = sv;
         CK(launch_regroup_keys(b, rk, rv), "regroup");
         CK(launch_sort(b, rk, rv, rk2, rv2, b->n, bits_for((uint64_t)depth) + db->tbits), "regroup sort");
-        CK(launch_level_tables(b, rk, depth, block), "level tables");
-        if (b->timing) cudaEventRecord(b->ev[3], s);
-        CK(launch_kset(b, rv, b->sc.chunk_cap, block, add), "k-set execute");
+        CK(launch_level_tables(b, rk, depth, block, persistent), "level tables");
+        if (persistent) {
+            CK(launch_gather(b, rv), "gather");
+            if (b->timing) cudaEventRecord(b->ev[3], s);
+            CK(launch_kset(b, rv, b->sc.chunk_cap, block, add), "k-set execute");
+        } else if (b->n > 0) {
+            // plan launches from the level widths
+            b->level_off_host.resize((size_t)depth + 2);
+            CK(cudaMemcpyAsync(b->level_off_host.data(), b->sc.level_off, (depth + 2) * sizeof(uint32_t),
+                               cudaMemcpyDeviceToHost, s), "level plan");
+            CK(cudaMemcpyAsync(&b->host_ctl.err, &b->ctl->err, 4, cudaMemcpyDeviceToHost, s), "level plan");
+            CK(cudaStreamSynchronize(s), "level plan");
+            if (!b->host_ctl.err) {
+                const int narrow = (opts && opts->narrow_max > 0) ? opts->narrow_max : 8192;
+                CK(launch_gather(b, rv), "gather");
+                if (b->timing) cudaEventRecord(b->ev[3], s);
+                CK(launch_kset_levels(b, b->level_off_host.data(), depth, narrow, add), "k-set execute");
+            }
+        }
     } else if (run == GPUTX_PART) {
         // partition ids by root key (Section 5.2 step 1), stable sort (step 2)
         uint32_t *pk = b->sc.pid_key, *pv = b->sc.pid_val, *pk2 = b->sc.pid_key2, *pv2 = b->sc.pid_val2;
@@ -928,8 +949,9 @@ gputx_status gputx_execute(gputx_db *db, gputx_bulk *b, int strategy, const gput
             CK(launch_sort(b, pk, pv, pk2, pv2, b->n, bits), "partition sort");
             if (b->timing) cudaEventRecord(b->ev[2], s);
             CK(launch_part_heads(b, pk, b->n), "partition heads");
+            CK(launch_gather(b, pv), "gather");
             if (b->timing) cudaEventRecord(b->ev[3], s);
-            CK(launch_part(b, pk, pv, 128), "part execute");
+            CK(launch_part(b, pk, 128), "part execute");
         }
     }
     if (run == GPUTX_TPL) {

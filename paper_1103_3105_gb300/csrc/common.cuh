@@ -111,6 +111,10 @@ struct DevBulk {
     const InsertBase *base;        // device: where this bulk's inserts start
     // per-transaction insert slots (exclusive prefix counts in ts order)
     const uint32_t *slot_cf, *slot_ord, *slot_ol;
+    // signatures gathered into this strategy's execution order
+    const int64_t *rec_params, *rec_ts;
+    const int32_t *rec_type;
+    const uint32_t *rec_t;
     int conflict_mode;
 };
 

@@ -39,6 +39,9 @@ struct Scratch {
     uint32_t *done;        // n+1 per-level completion counters
     uint32_t *part_start;  // n
     uint32_t *pid_key, *pid_val, *pid_key2, *pid_val2;  // PART sort, n each
+    int64_t *rec_params, *rec_ts;  // signatures gathered into execution order
+    int32_t *rec_type;
+    uint32_t *rec_t;
     uint32_t *slot_cf, *slot_ord, *slot_ol;   // n each
     uint32_t *sort_hist;   // 4 x 256
     uint32_t *sort_offs;   // 4 x 256
@@ -91,6 +94,7 @@ struct gputx_bulk {
     bool timing = false;
     cudaEvent_t ev[8] = {};
     gtx::BulkCtl host_ctl{};
+    std::vector<uint32_t> level_off_host;   // K-SET level boundaries read back for launch planning
 };
 
 namespace gtx {
@@ -106,16 +110,19 @@ cudaError_t launch_ticket_scan(gputx_bulk *b, const uint32_t *sk, const uint32_t
 cudaError_t launch_fixpoint_round(gputx_bulk *b, const uint32_t *sv, int64_t m);
 cudaError_t launch_level_stats(gputx_bulk *b);
 cudaError_t launch_regroup_keys(gputx_bulk *b, uint32_t *keys, uint32_t *vals);
-cudaError_t launch_level_tables(gputx_bulk *b, const uint32_t *skeys, int64_t depth, int block);
+cudaError_t launch_level_tables(gputx_bulk *b, const uint32_t *skeys, int64_t depth, int block, bool chunks);
 cudaError_t launch_insert_slots(gputx_bulk *b);
 cudaError_t launch_part_heads(gputx_bulk *b, const uint32_t *skeys, int64_t n);
 cudaError_t launch_tpl_reset(gputx_bulk *b, const uint32_t *skeys, int64_t m);
+cudaError_t launch_gather(gputx_bulk *b, const uint32_t *order);
 cudaError_t launch_begin(gputx_bulk *b);
 cudaError_t launch_finish(gputx_bulk *b);
 
 // exec.cu
 cudaError_t launch_kset(gputx_bulk *b, const uint32_t *order, int64_t nchunks, int block, bool atomic_add);
-cudaError_t launch_part(gputx_bulk *b, const uint32_t *pkeys, const uint32_t *pvals, int block);
+cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, int64_t depth, int narrow_max,
+                               bool atomic_add);
+cudaError_t launch_part(gputx_bulk *b, const uint32_t *pkeys, int block);
 cudaError_t launch_tpl(gputx_bulk *b, int block, bool atomic_add);
 int exec_blocks_per_sm(int kind, int block);
 

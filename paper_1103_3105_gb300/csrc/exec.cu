@@ -1,11 +1,18 @@
 // exec.cu -- the three bulk execution strategies (Section 5).
 //
-//   K-SET (Section 5.3)  a persistent grid walks the level-ordered bulk in
-//       chunks of one CTA; a chunk of level k starts once every transaction
-//       of level k-1 has finished (per-level completion counters), so the
-//       k-sets run in order with no conflict control inside a level
-//       (Property 1).  Chunks are claimed in increasing order, so every chunk
-//       a waiting CTA depends on is held by a running CTA: the waits end.
+//   K-SET (Section 5.3)  the k-sets run in order with no conflict control
+//       inside a level (Property 1).  Three launch shapes:
+//         wide level     one full-grid launch per level (kernel boundary =
+//                        the level barrier);
+//         narrow levels  one thread-block cluster (or one CTA) walks a run of
+//                        consecutive narrow levels, separated by cluster (or
+//                        CTA) barriers, loading the next level's signatures
+//                        and prefetching its rows into L2 before each barrier;
+//         persistent     a grid claims level-ordered chunks of one CTA; a
+//                        chunk of level k starts once every transaction of
+//                        level k-1 has finished (per-level counters).  Chunks
+//                        are claimed in increasing order, so every chunk a
+//                        waiting CTA depends on is held by a running CTA.
 //   PART (Section 5.2)   one thread per non-empty partition runs its
 //       transactions serially in timestamp order.
 //   TPL (Section 5.1)    ordered counter locks: an operation whose group has
@@ -15,8 +22,12 @@
 //       order, so the earliest unfinished one never waits: no deadlock.
 // Every wait is bounded by the configured limit; on expiry the kernel sets
 // ERR_TIMEOUT in the bulk's error word and returns.
+#include <cooperative_groups.h>
+
 #include "engine.h"
 #include "procs.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace gtx {
 
@@ -33,23 +44,95 @@ struct KsetArgs {
     bool atomic_add;
 };
 
-// waits until *p >= need; false on timeout
-__device__ __forceinline__ bool wait_at_least(const uint32_t *p, uint32_t need, uint64_t limit_ns)
+// waits until *p >= need; false on timeout.  The sleep between polls grows
+// with the number of releases still missing (each costs at least one
+// hand-off), so a waiter far back in a long chain polls rarely instead of
+// flooding L2 with acquire loads.
+// per_gap_ns = 0 keeps a short fixed poll (level counters, whose missing
+// releases arrive together).
+__device__ __forceinline__ bool wait_at_least(const uint32_t *p, uint32_t need, uint64_t limit_ns,
+                                              uint32_t per_gap_ns = 0)
 {
-    if (ld_acquire(p) >= need) return true;
+    uint32_t v = ld_acquire(p);
+    if (v >= need) return true;
     const uint64_t t0 = globaltimer();
     uint32_t spins = 0;
-    while (ld_acquire(p) < need) {
-        if (++spins > 32) __nanosleep(spins < 1024 ? 32 : 256);
-        if ((spins & 63) == 0 && globaltimer() - t0 > limit_ns) return false;
+    while (v < need) {
+        const uint32_t gap = need - v;
+        if (per_gap_ns && gap > 1) __nanosleep(gap > 64 ? 64 * per_gap_ns : per_gap_ns * gap);
+        else if (++spins > 64) __nanosleep(32);
+        if (globaltimer() - t0 > limit_ns) return false;
+        v = ld_acquire(p);
     }
     return true;
+}
+
+struct LevelArgs {
+    DevDB db;
+    DevBulk b;
+    const BulkCtl *ctl;
+    const uint32_t *level_off;
+    uint32_t k0, k1;     // levels [k0, k1)
+    bool atomic_add;
+};
+
+// one wide level [level_off[k0], level_off[k0+1]) over the whole grid
+__global__ void __launch_bounds__(256) kset_level_kernel(LevelArgs a)
+{
+    if (a.ctl->err) return;
+    const int64_t hb = a.ctl->base.hist;
+    const uint32_t lo = __ldg(&a.level_off[a.k0]), hi = __ldg(&a.level_off[a.k0 + 1]);
+    for (uint32_t pos = lo + blockIdx.x * blockDim.x + threadIdx.x; pos < hi; pos += gridDim.x * blockDim.x)
+        exec_txn(a.db, a.b, view_at(a.b, pos, hb), a.atomic_add);
+}
+
+// a run of narrow levels [k0, k1) on one thread-block cluster (CLUSTER) or
+// one CTA.  While level k executes, level k+1's records come into L1; after
+// it, level k+1's rows are prefetched into L2; then the barrier.
+template <bool CLUSTER>
+__global__ void __launch_bounds__(1024, 1) kset_narrow_kernel(LevelArgs a)
+{
+    if (a.ctl->err) return;   // set by an earlier launch only: uniform here
+    const int64_t hb = a.ctl->base.hist;
+    uint32_t nthreads = blockDim.x, rank = threadIdx.x;
+    if (CLUSTER) {
+        cg::cluster_group cl = cg::this_cluster();
+        nthreads = cl.num_threads();
+        rank = cl.thread_rank();
+    }
+    uint32_t lo = __ldg(&a.level_off[a.k0]);
+    uint32_t hi = __ldg(&a.level_off[a.k0 + 1]);
+    // this thread's first transaction of the current level, loaded ahead
+    TxnView v{};
+    if (lo + rank < hi) {
+        v = view_at(a.b, lo + rank, hb);
+        prefetch_txn(a.db, v);
+    }
+    for (uint32_t k = a.k0; k < a.k1; k++) {
+        const uint32_t nlo = hi;
+        const uint32_t nhi = (k + 1 < a.k1) ? __ldg(&a.level_off[k + 2]) : nlo;
+        // the next level's first signature for this thread: loads in flight
+        // while this level executes
+        TxnView nv{};
+        const bool has_next = nlo + rank < nhi;
+        if (has_next) nv = view_at(a.b, nlo + rank, hb);
+        if (lo + rank < hi) exec_txn(a.db, a.b, v, a.atomic_add);
+        for (uint32_t pos = lo + rank + nthreads; pos < hi; pos += nthreads)
+            exec_txn(a.db, a.b, view_at(a.b, pos, hb), a.atomic_add);
+        if (has_next) prefetch_txn(a.db, nv);     // rows into L2 before the barrier
+        if (CLUSTER) cg::this_cluster().sync();   // release/acquire at cluster scope
+        else __syncthreads();
+        lo = nlo;
+        hi = nhi;
+        v = nv;
+    }
 }
 
 __global__ void kset_kernel(KsetArgs a)
 {
     __shared__ uint32_t s_k, s_start, s_cnt, s_stop;
     const uint32_t nchunks = a.chunk_off[a.levels];
+    const int64_t hb = a.ctl->base.hist;
     while (true) {
         if (threadIdx.x == 0) {
             uint32_t stop = *(volatile uint32_t *)&a.ctl->err ? 1u : 0u;
@@ -59,10 +142,6 @@ __global__ void kset_kernel(KsetArgs a)
                 const uint32_t lo = a.level_off[k], hi = a.level_off[k + 1];
                 const uint32_t start = lo + (c - a.chunk_off[k]) * blockDim.x;
                 const uint32_t cnt = (hi - start) < blockDim.x ? (hi - start) : blockDim.x;
-                if (k > 0 && !wait_at_least(&a.done[k - 1], lo - a.level_off[k - 1], a.spin_limit_ns)) {
-                    set_err(&a.ctl->err, ERR_TIMEOUT);
-                    stop = 1;
-                }
                 s_k = k;
                 s_start = start;
                 s_cnt = cnt;
@@ -73,9 +152,24 @@ __global__ void kset_kernel(KsetArgs a)
         }
         __syncthreads();
         if (s_stop) break;
+        // signatures are immutable: load them and prefetch the rows while the
+        // previous level may still be running
+        TxnView v{};
         if (threadIdx.x < s_cnt) {
-            const uint32_t pos = s_start + threadIdx.x;
-            exec_txn(a.db, a.b, a.order[pos], pos, a.atomic_add);
+            v = view_at(a.b, s_start + threadIdx.x, hb);
+            prefetch_txn(a.db, v);
+        }
+        if (threadIdx.x == 0 && s_k > 0) {
+            const uint32_t k = s_k, lo = a.level_off[k];
+            if (!wait_at_least(&a.done[k - 1], lo - a.level_off[k - 1], a.spin_limit_ns)) {
+                set_err(&a.ctl->err, ERR_TIMEOUT);
+                s_stop = 1;
+            }
+        }
+        __syncthreads();
+        if (s_stop) break;
+        if (threadIdx.x < s_cnt) {
+            exec_txn(a.db, a.b, v, a.atomic_add);
             __threadfence();
         }
         __syncthreads();
@@ -83,15 +177,38 @@ __global__ void kset_kernel(KsetArgs a)
     }
 }
 
-__global__ void part_kernel(DevDB db, DevBulk b, const BulkCtl *ctl, const uint32_t *pkeys, const uint32_t *pvals,
+__global__ void part_kernel(DevDB db, DevBulk b, const BulkCtl *ctl, const uint32_t *pkeys,
                             const uint32_t *part_start)
 {
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= ctl->npart || ctl->err) return;
-    uint32_t i = part_start[p];
-    const uint32_t key = pkeys[i];
+    const int64_t hb = ctl->base.hist;
     const uint32_t n = (uint32_t)b.n;
-    for (; i < n && pkeys[i] == key; i++) exec_txn(db, b, pvals[i], i, false);
+    uint32_t i = part_start[p];
+    const uint32_t key = __ldg(&pkeys[i]);
+    // a two-deep pipeline along the partition's timestamp order: while
+    // transaction i executes, i+1's rows are already in L2 and i+2's record
+    // is loading; the partition's own order is the only dependency
+    TxnView v = view_at(b, i, hb);
+    prefetch_txn(db, v);
+    bool has1 = i + 1 < n && __ldg(&pkeys[i + 1]) == key;
+    TxnView v1{};
+    if (has1) {
+        v1 = view_at(b, i + 1, hb);
+        prefetch_txn(db, v1);
+    }
+    while (true) {
+        const bool has2 = has1 && i + 2 < n && __ldg(&pkeys[i + 2]) == key;
+        TxnView v2{};
+        if (has2) v2 = view_at(b, i + 2, hb);
+        exec_txn(db, b, v, false);
+        if (!has1) break;
+        if (has2) prefetch_txn(db, v2);
+        v = v1;
+        v1 = v2;
+        has1 = has2;
+        i++;
+    }
 }
 
 struct TplArgs {
@@ -109,6 +226,7 @@ __global__ void tpl_kernel(TplArgs a)
 {
     __shared__ uint32_t s_c, s_stop;
     const int64_t n = a.b.n;
+    const int64_t hb = a.ctl->base.hist;
     while (true) {
         if (threadIdx.x == 0) {
             s_stop = *(volatile uint32_t *)&a.ctl->err ? 1u : 0u;
@@ -121,15 +239,17 @@ __global__ void tpl_kernel(TplArgs a)
         if (t < n) {
             const int64_t off = a.op_off ? (int64_t)a.op_off[t] : t * a.uniform_k;
             const int cnt = a.op_off ? (int)(a.op_off[t + 1] - a.op_off[t]) : a.uniform_k;
+            const TxnView v = view_of(a.b, (uint32_t)t, hb);
+            prefetch_txn(a.db, v);
             bool ok = true;
             for (int j = 0; j < cnt && ok; j++) {
                 const uint32_t tk = a.lock_ticket[off + j];
-                if (tk && !wait_at_least(&a.done[a.lock_key[off + j]], tk, a.spin_limit_ns)) {
+                if (tk && !wait_at_least(&a.done[a.lock_key[off + j]], tk, a.spin_limit_ns, 250)) {
                     set_err(&a.ctl->err, ERR_TIMEOUT);
                     ok = false;
                 }
             }
-            if (ok) exec_txn(a.db, a.b, (uint32_t)t, (uint32_t)t, a.atomic_add);
+            if (ok) exec_txn(a.db, a.b, v, a.atomic_add);
             __threadfence();
             for (int j = 0; j < cnt; j++) red_release_add(&a.done[a.lock_key[off + j]], 1u);
         }
@@ -138,6 +258,33 @@ __global__ void tpl_kernel(TplArgs a)
 }
 
 }  // namespace
+
+// clusters of this size that fit the device at once (0 = none)
+int max_cluster_ok(int csize)
+{
+    static int cache[17] = {0};
+    static bool done[17] = {false};
+    if (csize < 1 || csize > 16) return 0;
+    if (done[csize]) return cache[csize];
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(csize, 1, 1);
+    cfg.blockDim = dim3(1024, 1, 1);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kset_narrow_kernel<true>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+    }
+    cache[csize] = n;
+    done[csize] = true;
+    return n;
+}
 
 int exec_blocks_per_sm(int kind, int block)
 {
@@ -174,13 +321,88 @@ cudaError_t launch_kset(gputx_bulk *b, const uint32_t *order, int64_t nchunks, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_part(gputx_bulk *b, const uint32_t *pkeys, const uint32_t *pvals, int block)
+cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, int64_t depth, int narrow_max,
+                               bool atomic_add)
+{
+    gputx_db *db = b->db;
+    if (b->n == 0) return cudaSuccess;
+    LevelArgs a{};
+    a.db = db->dev;
+    a.b = make_dev_bulk(b, atomic_add ? GPUTX_CONFLICT_ADD : GPUTX_CONFLICT_PAPER);
+    a.ctl = b->ctl;
+    a.level_off = b->sc.level_off;
+    a.atomic_add = atomic_add;
+    const int64_t levels = depth + 1;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(kset_narrow_kernel<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        attr_set = true;
+    }
+    int64_t k = 0;
+    while (k < levels) {
+        const uint32_t w = level_off_host[k + 1] - level_off_host[k];
+        if ((int64_t)w > narrow_max) {
+            a.k0 = (uint32_t)k;
+            a.k1 = (uint32_t)k + 1;
+            int64_t grid = ((int64_t)w + 255) / 256;
+            const int64_t cap = (int64_t)db->num_sms * 8;
+            if (grid > cap) grid = cap;
+            kset_level_kernel<<<(unsigned)grid, 256, 0, db->stream>>>(a);
+            count_launches(1);
+            k++;
+            continue;
+        }
+        // maximal run of narrow levels
+        int64_t e = k;
+        uint32_t wmax = 0;
+        while (e < levels) {
+            const uint32_t we = level_off_host[e + 1] - level_off_host[e];
+            if ((int64_t)we > narrow_max) break;
+            wmax = we > wmax ? we : wmax;
+            e++;
+        }
+        a.k0 = (uint32_t)k;
+        a.k1 = (uint32_t)e;
+        // spread a level over up to 16 SMs, about 64 transactions each, so
+        // no single SM's load/store pipeline carries a whole level
+        int csize = (int)((wmax + 63) / 64);
+        csize = csize < 1 ? 1 : (csize > 16 ? 16 : csize);
+        while (csize > 1 && max_cluster_ok(csize) == 0) csize >>= 1;
+        int threads = (int)((wmax + csize - 1) / csize);
+        threads = ((threads + 31) / 32) * 32;
+        threads = threads < 32 ? 32 : (threads > 1024 ? 1024 : threads);
+        if (csize <= 1) {
+            kset_narrow_kernel<false><<<1, threads, 0, db->stream>>>(a);
+        } else {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(csize, 1, 1);
+            cfg.blockDim = dim3(threads, 1, 1);
+            cfg.stream = db->stream;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = csize;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            cudaError_t e2 = cudaLaunchKernelEx(&cfg, kset_narrow_kernel<true>, a);
+            if (e2) return e2;
+        }
+        count_launches(1);
+        cudaError_t e3 = cudaGetLastError();
+        if (e3) return e3;
+        k = e;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_part(gputx_bulk *b, const uint32_t *pkeys, int block)
 {
     gputx_db *db = b->db;
     if (b->n == 0) return cudaSuccess;
     const DevBulk d = make_dev_bulk(b, GPUTX_CONFLICT_PAPER);
     const int64_t grid = (b->n + block - 1) / block;   // npart <= n, read on the device
-    part_kernel<<<(unsigned)grid, block, 0, db->stream>>>(db->dev, d, b->ctl, pkeys, pvals, b->sc.part_start);
+    part_kernel<<<(unsigned)grid, block, 0, db->stream>>>(db->dev, d, b->ctl, pkeys, b->sc.part_start);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -231,34 +231,139 @@ __device__ __forceinline__ int64_t pack2(int32_t lo, int32_t hi)
 }
 
 // ---------------------------------------------------------------------------
+// L2 prefetch of the rows a transaction will touch (a hint: it returns no
+// data, so it can run before the transaction is allowed to execute)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// A transaction as the executors see it: its signature (from the bulk, or
+// from the records gathered into execution order) and where its results go.
+struct TxnView {
+    const int64_t *p;     // parameter list
+    int64_t p0, p1;       // its first two entries, loaded with the view
+    int64_t ts;
+    int64_t hist_slot;    // history row of a debit-credit transaction
+    uint32_t t;           // index in the bulk: outputs, status, insert slots
+    int32_t type;
+};
+
+// signature at position pos of the gathered execution-order records; the
+// loads are issued here, so building a view early hides their latency
+__device__ __forceinline__ TxnView view_at(const DevBulk &b, uint32_t pos, int64_t hist_base)
+{
+    TxnView v;
+    v.p = b.rec_params + (int64_t)pos * b.P;
+    v.p0 = __ldg(&v.p[0]);
+    v.p1 = b.P > 1 ? __ldg(&v.p[1]) : 0;
+    v.ts = __ldg(&b.rec_ts[pos]);
+    v.type = __ldg(&b.rec_type[pos]);
+    v.t = __ldg(&b.rec_t[pos]);
+    v.hist_slot = hist_base + pos;
+    return v;
+}
+
+// signature of transaction t straight from the bulk (timestamp order)
+__device__ __forceinline__ TxnView view_of(const DevBulk &b, uint32_t t, int64_t hist_base)
+{
+    TxnView v;
+    v.p = b.params + (int64_t)t * b.P;
+    v.p0 = __ldg(&v.p[0]);
+    v.p1 = b.P > 1 ? __ldg(&v.p[1]) : 0;
+    v.ts = __ldg(&b.ts[t]);
+    v.type = __ldg(&b.type[t]);
+    v.t = t;
+    v.hist_slot = hist_base + t;
+    return v;
+}
+
+// L1 prefetch of the record lines at position pos (no data dependency)
+__device__ __forceinline__ void prefetch_record_l1(const DevBulk &b, uint32_t pos)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(b.rec_params + (int64_t)pos * b.P));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(b.rec_ts + pos));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(b.rec_type + pos));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(b.rec_t + pos));
+}
+
+__device__ __forceinline__ void prefetch_txn(const DevDB &db, const TxnView &v)
+{
+    const int64_t *p = v.p;
+    switch (v.type) {
+    case GPUTX_T_DC_DEBIT_CREDIT: {
+        const uint32_t a = (uint32_t)v.p0;
+        prefetch_l2(&db.acc_bal[a]);
+        prefetch_l2(&db.tel_bal[a / (uint32_t)db.acc_per_tel]);
+        prefetch_l2(&db.br_bal[a / (uint32_t)db.acc_per_br]);
+        break;
+    }
+    case GPUTX_T_SUB_GET_SUBSCRIBER:
+    case GPUTX_T_SUB_UPDATE_LOCATION:
+    case GPUTX_T_SUB_UPDATE_FACILITY:
+        prefetch_l2(db.sub_rows + v.p0 * SUB_FIELDS);
+        break;
+    case GPUTX_T_OE_PAYMENT: {
+        const int64_t w = __ldg(&p[0]), d = w * OE_DIST + __ldg(&p[1]), c = d * OE_CUST + __ldg(&p[2]);
+        prefetch_l2(&db.c_balance[c]);
+        prefetch_l2(&db.c_ytd[c]);
+        prefetch_l2(&db.c_payment_cnt[c]);
+        break;
+    }
+    case GPUTX_T_OE_NEW_ORDER: {
+        const int64_t w = __ldg(&p[0]), d = w * OE_DIST + __ldg(&p[1]);
+        prefetch_l2(&db.d_next_o_id[d]);
+        const int cnt = (int)__ldg(&p[3]);
+        for (int j = 0; j < cnt && j < OE_MAX_LINES; j++) {
+            const int64_t line = __ldg(&p[4 + j]);
+            const int64_t item = line & 0xFFFFFF, sw = (line >> 24) & 0xFFFF;
+            if (item < db.n_items) prefetch_l2(&db.s_quantity[sw * db.n_items + item]);
+        }
+        break;
+    }
+    default:
+        break;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // the combined procedure kernel body (Section 3.2's switch)
 // ---------------------------------------------------------------------------
-// t: transaction index in the bulk; pos: its position in this strategy's
-// processing order (history slot); atomic_add: execute ADD-class increments
-// with atomics (several transactions of one level may add to one item).
-__device__ __forceinline__ void exec_dc(const DevDB &db, const DevBulk &b, uint32_t t, uint32_t pos,
-                                        bool atomic_add)
+// atomic_add: execute ADD-class increments with atomics (several
+// transactions of one level may add to one item).
+__device__ __forceinline__ void exec_dc(const DevDB &db, const DevBulk &b, const TxnView &v, bool atomic_add)
 {
-    const int64_t *p = b.params + (int64_t)t * b.P;
-    const int64_t a = p[0], delta = p[1];
-    const int64_t tl = a / db.acc_per_tel, br = a / db.acc_per_br;
-    const int64_t slot = b.base->hist + pos;
+    const uint32_t t = v.t;
+    const int64_t a = v.p0, delta = v.p1;
+    // object ids fit 32 bits: 32-bit division is several times cheaper
+    const int64_t tl = (uint32_t)a / (uint32_t)db.acc_per_tel, br = (uint32_t)a / (uint32_t)db.acc_per_br;
+    const int64_t slot = v.hist_slot;
+    // every load before any store: the three rows are distinct cells but the
+    // compiler cannot prove it, so interleaving would serialise three L2
+    // round trips
+    const int64_t old_a = ldg_cg(&db.acc_bal[a]);
+    int64_t old_t = 0, old_b = 0;
+    if (!atomic_add) {
+        old_t = ldg_cg(&db.tel_bal[tl]);
+        old_b = ldg_cg(&db.br_bal[br]);
+    }
     if (slot >= db.hist_cap) {              // history full: not executed
         set_err(b.err, ERR_CAPACITY);
         b.status[t] = 3;
         return;
     }
     // account: read-modify-write, its new value is the output
-    const int64_t na = wrap_add(ldg_cg(&db.acc_bal[a]), delta);
+    const int64_t na = wrap_add(old_a, delta);
     stg_cg(&db.acc_bal[a], na);
     if (atomic_add) {
         atomicAdd((unsigned long long *)&db.tel_bal[tl], (unsigned long long)delta);
         atomicAdd((unsigned long long *)&db.br_bal[br], (unsigned long long)delta);
     } else {
-        stg_cg(&db.tel_bal[tl], wrap_add(ldg_cg(&db.tel_bal[tl]), delta));
-        stg_cg(&db.br_bal[br], wrap_add(ldg_cg(&db.br_bal[br]), delta));
+        stg_cg(&db.tel_bal[tl], wrap_add(old_t, delta));
+        stg_cg(&db.br_bal[br], wrap_add(old_b, delta));
     }
-    db.h_ts[slot] = b.ts[t];
+    db.h_ts[slot] = v.ts;
     db.h_acc[slot] = a;
     db.h_tel[slot] = tl;
     db.h_br[slot] = br;
@@ -268,9 +373,11 @@ __device__ __forceinline__ void exec_dc(const DevDB &db, const DevBulk &b, uint3
 }
 
 // subscriber-location procedures (stand-ins shaped like TM-1, Appendix E)
-__device__ __forceinline__ void exec_sub(const DevDB &db, const DevBulk &b, uint32_t t, int32_t type)
+__device__ __forceinline__ void exec_sub(const DevDB &db, const DevBulk &b, const TxnView &v)
 {
-    const int64_t *p = b.params + (int64_t)t * b.P;
+    const int64_t *p = v.p;
+    const uint32_t t = v.t;
+    const int32_t type = v.type;
     int64_t *out = b.out + (int64_t)t * b.R;
     const int64_t s = p[0];
     int32_t *row = db.sub_rows + s * SUB_FIELDS;
@@ -347,10 +454,11 @@ __device__ __forceinline__ void exec_sub(const DevDB &db, const DevBulk &b, uint
 }
 
 // order-entry procedures (stand-ins shaped like TPC-C, Appendix E)
-__device__ __forceinline__ void exec_oe(const DevDB &db, const DevBulk &b, uint32_t t, int32_t type,
-                                        bool atomic_add)
+__device__ __forceinline__ void exec_oe(const DevDB &db, const DevBulk &b, const TxnView &v, bool atomic_add)
 {
-    const int64_t *p = b.params + (int64_t)t * b.P;
+    const int64_t *p = v.p;
+    const uint32_t t = v.t;
+    const int32_t type = v.type;
     int64_t *out = b.out + (int64_t)t * b.R;
     const int64_t w = p[0], d = w * OE_DIST + p[1], c = d * OE_CUST + p[2];
     int32_t st = 0;
@@ -376,10 +484,12 @@ __device__ __forceinline__ void exec_oe(const DevDB &db, const DevBulk &b, uint3
             total += amount;
             const int64_t s = sw * db.n_items + item;
             int32_t q = ldg_cg(&db.s_quantity[s]);
+            const int64_t sy = ldg_cg(&db.s_ytd[s]);
+            const int32_t so = ldg_cg(&db.s_order_cnt[s]);
             q = (q >= qty + 10) ? (int32_t)(q - qty) : (int32_t)(q - qty + 91);
             stg_cg(&db.s_quantity[s], q);
-            stg_cg(&db.s_ytd[s], ldg_cg(&db.s_ytd[s]) + qty);
-            stg_cg(&db.s_order_cnt[s], ldg_cg(&db.s_order_cnt[s]) + 1);
+            stg_cg(&db.s_ytd[s], sy + qty);
+            stg_cg(&db.s_order_cnt[s], so + 1);
             db.ol_item[lslot + j] = (int32_t)item;
             db.ol_sw[lslot + j] = (int32_t)sw;
             db.ol_qty[lslot + j] = (int32_t)qty;
@@ -404,17 +514,25 @@ __device__ __forceinline__ void exec_oe(const DevDB &db, const DevBulk &b, uint3
     }
     case GPUTX_T_OE_PAYMENT: {
         const int64_t amount = p[3];
+        // loads first (see exec_dc), then the stores
+        int64_t wy = 0, dy = 0;
+        if (!atomic_add) {
+            wy = ldg_cg(&db.w_ytd[w]);
+            dy = ldg_cg(&db.d_ytd[d]);
+        }
+        const int64_t cb = ldg_cg(&db.c_balance[c]), cy = ldg_cg(&db.c_ytd[c]);
+        const int64_t cn = ldg_cg(&db.c_payment_cnt[c]);
         if (atomic_add) {
             atomicAdd((unsigned long long *)&db.w_ytd[w], (unsigned long long)amount);
             atomicAdd((unsigned long long *)&db.d_ytd[d], (unsigned long long)amount);
         } else {
-            stg_cg(&db.w_ytd[w], wrap_add(ldg_cg(&db.w_ytd[w]), amount));
-            stg_cg(&db.d_ytd[d], wrap_add(ldg_cg(&db.d_ytd[d]), amount));
+            stg_cg(&db.w_ytd[w], wrap_add(wy, amount));
+            stg_cg(&db.d_ytd[d], wrap_add(dy, amount));
         }
-        const int64_t bal = wrap_add(ldg_cg(&db.c_balance[c]), -amount);
+        const int64_t bal = wrap_add(cb, -amount);
         stg_cg(&db.c_balance[c], bal);
-        stg_cg(&db.c_ytd[c], wrap_add(ldg_cg(&db.c_ytd[c]), amount));
-        stg_cg(&db.c_payment_cnt[c], ldg_cg(&db.c_payment_cnt[c]) + 1);
+        stg_cg(&db.c_ytd[c], wrap_add(cy, amount));
+        stg_cg(&db.c_payment_cnt[c], cn + 1);
         out[0] = bal;
         break;
     }
@@ -437,22 +555,20 @@ __device__ __forceinline__ void exec_oe(const DevDB &db, const DevBulk &b, uint3
     b.status[t] = st;
 }
 
-__device__ __forceinline__ void exec_txn(const DevDB &db, const DevBulk &b, uint32_t t, uint32_t pos,
-                                         bool atomic_add)
+__device__ __forceinline__ void exec_txn(const DevDB &db, const DevBulk &b, const TxnView &v, bool atomic_add)
 {
-    const int32_t type = b.type[t];
-    switch (type) {
-    case GPUTX_T_DC_DEBIT_CREDIT: exec_dc(db, b, t, pos, atomic_add); break;
+    switch (v.type) {
+    case GPUTX_T_DC_DEBIT_CREDIT: exec_dc(db, b, v, atomic_add); break;
     case GPUTX_T_SUB_GET_SUBSCRIBER:
     case GPUTX_T_SUB_GET_ACCESS:
     case GPUTX_T_SUB_GET_NEW_DEST:
     case GPUTX_T_SUB_UPDATE_LOCATION:
     case GPUTX_T_SUB_UPDATE_FACILITY:
     case GPUTX_T_SUB_INSERT_CF:
-    case GPUTX_T_SUB_DELETE_CF: exec_sub(db, b, t, type); break;
+    case GPUTX_T_SUB_DELETE_CF: exec_sub(db, b, v); break;
     case GPUTX_T_OE_NEW_ORDER:
     case GPUTX_T_OE_PAYMENT:
-    case GPUTX_T_OE_ORDER_STATUS: exec_oe(db, b, t, type, atomic_add); break;
+    case GPUTX_T_OE_ORDER_STATUS: exec_oe(db, b, v, atomic_add); break;
     }
 }
 

@@ -133,13 +133,18 @@ def oracle_logical_state(db):
     if "ord" in db.a:
         orders = db.orders()
         ol = db.order_lines()
-        rows = []
-        for r, o in enumerate(orders):
-            lines = ol[o[5]: o[5] + o[4]]
-            lines = sorted((int(x[1]), int(x[2]), int(x[3]), int(x[4])) for x in lines)
-            rows.append((int(o[0]), int(o[1]), int(o[2]), int(o[3]), int(o[4]), tuple(lines)))
-        st["orders"] = sorted(rows)
+        st["orders"] = _sorted_rows(orders[:, :5])
+        keys = orders[ol[:, 0].astype(np.int64), :3] if len(ol) else np.zeros((0, 3), np.int64)
+        st["order_lines"] = _sorted_rows(np.column_stack([keys, ol[:, 1:5]]).reshape(-1, 7))
     return st
+
+
+def _sorted_rows(a):
+    """Rows of a 2-D int array in lexicographic order (a canonical multiset)."""
+    a = np.asarray(a, dtype=np.int64)
+    if len(a) == 0:
+        return a.reshape(0, a.shape[1] if a.ndim == 2 else 0)
+    return a[np.lexsort(a.T[::-1])]
 
 
 def states_equal(a, b):
@@ -218,15 +223,6 @@ def gpu_logical_state(db, dc=False, sub=False, oe=False, n_sub=0, n_wh=0, n_item
         st["c_balance"], st["c_ytd"], st["c_payment_cnt"], st["c_last_o_id"] = c[:, 1], c[:, 2], c[:, 3], c[:, 4]
         st["s_quantity"], st["s_ytd"], st["s_order_cnt"] = (s[:, 0].astype(np.int32), s[:, 1],
                                                             s[:, 2].astype(np.int32))
-        orders = db.read(G.TBL_OE_ORDER)
-        lines = db.read(G.TBL_OE_ORDER_LINE)
-        by = {}
-        for l in lines:
-            by.setdefault((int(l[0]), int(l[1]), int(l[2])), []).append(
-                (int(l[3]), int(l[4]), int(l[5]), int(l[6])))
-        rows = []
-        for o in orders:
-            key = (int(o[0]), int(o[1]), int(o[2]))
-            rows.append(key + (int(o[3]), int(o[4]), tuple(sorted(by.get(key, [])))))
-        st["orders"] = sorted(rows)
+        st["orders"] = _sorted_rows(db.read(G.TBL_OE_ORDER))
+        st["order_lines"] = _sorted_rows(db.read(G.TBL_OE_ORDER_LINE))
     return st

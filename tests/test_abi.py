@@ -46,5 +46,5 @@ def test_structs_match_header_sizes():
     # the binding's ctypes mirrors must keep the header's field order and sizes
     assert ctypes.sizeof(G.SchemaDesc) == 10 * 8
     assert ctypes.sizeof(G.Config) == 8 + 4 + 4 + 8 * 4
-    assert ctypes.sizeof(G.ExecOpts) == 16
+    assert ctypes.sizeof(G.ExecOpts) == 24
     assert ctypes.sizeof(G.ExecStats) == 8 + 6 * 8 + 6 * 4
