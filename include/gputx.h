@@ -241,6 +241,40 @@ const char *gputx_version(void);
  * databases together (for tracing and launch accounting). */
 unsigned long long gputx_launch_count(void);
 
+/* Allocation-free K-SET execution of one bulk.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory,
+ * such as a process whose device memory is all reserved up front by another
+ * allocator (a serving stack or a host framework that must account for every
+ * byte), or a latency-critical path where a cudaMalloc could block on a
+ * device-wide synchronisation or fail under memory pressure.
+ *
+ * ts[n], type[n], params[n x params_per_txn] are DEVICE arrays; status[n]
+ * (int32) and values[n x gputx_output_width(db)] (int64) are DEVICE arrays
+ * the caller owns and the call fills.  The bulk runs with K-SET (one
+ * persistent launch per level run) under conflict_mode on the database's
+ * stream, and the call returns after it finished.  Results and the database
+ * are the same as gputx_submit_bulk + gputx_execute(GPUTX_KSET) +
+ * gputx_read_results would produce.
+ *
+ * Working memory comes from one file-scope device array of
+ * GPUTX_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds
+ * until the process exits; the call allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library routine).  A bulk whose working set does
+ * not fit returns EINVAL before any work is enqueued (for debit-credit
+ * about 300,000 transactions fit; multi-item order-entry bulks fewer).
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  Every
+ * call shares the one array and each clears what must start at zero, so
+ * calls that overlap on the GPU (two databases on different streams, or two
+ * host threads) race: serialise them.
+ * Errors: EINVAL (null pointer, bad width, unregistered type found on the
+ * device, bulk too large), ETIMEOUT/ECAPACITY/EBOUNDS as for gputx_sync_bulk,
+ * ECUDA when the device address cannot be obtained. */
+#define GPUTX_NOALLOC_SCRATCH_BYTES (48u << 20)
+gputx_status gputx_execute_kset_noalloc(gputx_db *db, const int64_t *ts, const int32_t *type,
+                                        const int64_t *params, int params_per_txn, size_t n,
+                                        int conflict_mode, int32_t *status, int64_t *values);
+
 #ifdef __cplusplus
 }
 #endif

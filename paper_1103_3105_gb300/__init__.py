@@ -42,7 +42,8 @@ TABLE_FIELDS = (1, 1, 1, 5, 16, 6, 6, 5, 2, 3, 5, 1, 3, 5, 7)
 EXPORTED = ("gputx_create_db", "gputx_destroy_db", "gputx_last_error", "gputx_register_types",
             "gputx_load_table", "gputx_read_table", "gputx_submit_bulk", "gputx_execute",
             "gputx_sync_bulk", "gputx_read_results", "gputx_bulk_results_device",
-            "gputx_output_width", "gputx_free_bulk", "gputx_version", "gputx_launch_count")
+            "gputx_output_width", "gputx_free_bulk", "gputx_version", "gputx_launch_count",
+            "gputx_execute_kset_noalloc")
 
 
 class GputxError(RuntimeError):
@@ -110,6 +111,7 @@ def lib():
             "gputx_free_bulk": ([p], None),
             "gputx_version": ([], C.c_char_p),
             "gputx_launch_count": ([], C.c_ulonglong),
+            "gputx_execute_kset_noalloc": ([p, p, p, p, C.c_int, sz, C.c_int, p, p], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -216,6 +218,16 @@ def gputx_output_width(db) -> int:
 
 def gputx_free_bulk(bulk):
     lib().gputx_free_bulk(bulk)
+
+
+NOALLOC_SCRATCH_BYTES = 48 << 20
+
+
+def gputx_execute_kset_noalloc(db, ts, type_, params, params_per_txn: int, n: int, conflict_mode: int,
+                               status, values):
+    """All arrays are CUDA tensors (or device addresses); see gputx.h."""
+    _check(db, lib().gputx_execute_kset_noalloc(db, _ptr(ts), _ptr(type_), _ptr(params), params_per_txn,
+                                                n, conflict_mode, _ptr(status), _ptr(values)))
 
 
 # --- conveniences --------------------------------------------------------------

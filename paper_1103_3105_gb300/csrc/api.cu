@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <unordered_set>
 #include <vector>
@@ -1034,4 +1035,117 @@ void gputx_free_bulk(gputx_bulk *b)
     delete b;
 }
 
+// ---------------------------------------------------------------------------
+// allocation-free K-SET execution (see gputx_execute_kset_noalloc)
+// ---------------------------------------------------------------------------
 }  // extern "C"
+
+namespace {
+
+// The working memory of gputx_execute_kset_noalloc: one array per device,
+// resident for the life of the process.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GPUTX_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevices] = {};
+
+// device address of the scratch array for the current device (set-up once per
+// device, with that device current)
+gputx_status noalloc_scratch(gputx_db *db, void **out)
+{
+    int dev = 0;
+    CK(cudaGetDevice(&dev), "get device");
+    if (dev < 0 || dev >= kMaxDevices) return fail(db, GPUTX_ECUDA, "device index %d", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(db, e ? e : cudaErrorInvalidSymbol, "scratch address");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return GPUTX_OK;
+}
+
+}  // namespace
+
+extern "C" gputx_status gputx_execute_kset_noalloc(gputx_db *db, const int64_t *ts, const int32_t *type,
+                                                   const int64_t *params, int params_per_txn, size_t n,
+                                                   int conflict_mode, int32_t *status, int64_t *values)
+{
+    if (!db) return GPUTX_EINVAL;
+    if (n > 0 && (!ts || !type || !params || !status || !values)) return fail(db, GPUTX_EINVAL, "null array");
+    if (params_per_txn < 1 || params_per_txn > 64) return fail(db, GPUTX_EINVAL, "params_per_txn");
+    if ((int64_t)n > db->cfg.max_bulk) return fail(db, GPUTX_EINVAL, "bulk above max_bulk");
+    if (conflict_mode != GPUTX_CONFLICT_PAPER && conflict_mode != GPUTX_CONFLICT_ADD)
+        return fail(db, GPUTX_EINVAL, "conflict mode");
+    if (!db->dev.registered) return fail(db, GPUTX_ESTATE, "no registered types");
+    void *scratch = nullptr;
+    gputx_status st = noalloc_scratch(db, &scratch);
+    if (st) return st;
+
+    // a bulk whose arrays all live in the scratch array (inputs and outputs
+    // stay in the caller's buffers)
+    gputx_bulk b;
+    b.db = db;
+    b.n = (int64_t)n;
+    b.P = params_per_txn;
+    b.R = db->dev.out_width;
+    const size_t need = carve_bulk(&b, nullptr, true);
+    if (need > GPUTX_NOALLOC_SCRATCH_BYTES)
+        return fail(db, GPUTX_EINVAL, "bulk needs %zu bytes of working memory, the no-allocation area has %u",
+                    need, (unsigned)GPUTX_NOALLOC_SCRATCH_BYTES);
+    carve_bulk(&b, (char *)scratch, true);
+    b.ts = const_cast<int64_t *>(ts);
+    b.type = const_cast<int32_t *>(type);
+    b.params = const_cast<int64_t *>(params);
+    b.status = status;
+    b.out = values;
+    cudaStream_t s = db->stream;
+    // the array keeps the previous call's contents: clear what starts at zero
+    CK(cudaMemsetAsync(b.ctl, 0, sizeof(BulkCtl), s), "clear");
+    if (n > 0) {
+        CK(cudaMemsetAsync(values, 0, n * b.R * sizeof(int64_t), s), "clear");
+        CK(cudaMemsetAsync(status, 0, n * sizeof(int32_t), s), "clear");
+    }
+    const bool add = conflict_mode == GPUTX_CONFLICT_ADD;
+    const int block = db->cfg.block_threads;
+    CK(launch_begin(&b), "begin");
+    CK(launch_insert_slots(&b), "insert slots");
+    CK(cudaMemsetAsync(&b.ctl->cross, 0, 4, s), "extract");
+    CK(launch_extract(&b, conflict_mode, 1, nullptr, nullptr, true), "extract");
+    int64_t m = b.n * db->uniform_k;
+    if (!db->uniform_k) {
+        uint32_t mm = 0;
+        CK(cudaMemcpyAsync(&mm, b.sc.op_off + b.n, sizeof mm, cudaMemcpyDeviceToHost, s), "ops");
+        CK(cudaStreamSynchronize(s), "ops");
+        m = mm > (uint32_t)b.sc.m_cap ? b.sc.m_cap : mm;
+    }
+    uint32_t *sk = b.sc.keys_a, *sv = b.sc.vals_a, *ak = b.sc.keys_b, *av = b.sc.vals_b;
+    CK(launch_sort(&b, sk, sv, ak, av, m, db->obj_bits), "sort");
+    CK(launch_rank_scan(&b, sk, sv, m, db->need_fixpoint), "rank");
+    if (db->need_fixpoint) {
+        for (int round = 0; round < 1 << 20; round++) {
+            CK(launch_fixpoint_round(&b, sv, m), "fixpoint");
+            uint32_t changed = 0, err = 0;
+            CK(cudaMemcpyAsync(&changed, &b.ctl->changed, 4, cudaMemcpyDeviceToHost, s), "fixpoint");
+            CK(cudaMemcpyAsync(&err, &b.ctl->err, 4, cudaMemcpyDeviceToHost, s), "fixpoint");
+            CK(cudaStreamSynchronize(s), "fixpoint");
+            if (!changed || err) break;
+        }
+    }
+    CK(launch_level_stats(&b), "stats");
+    if ((st = read_ctl(&b))) return st;
+    if (b.host_ctl.err) return bulk_error(db, b.host_ctl.err);
+    const int64_t depth = b.host_ctl.depth;
+    uint32_t *rk = ak, *rv = av, *rk2 = sk, *rv2 = sv;
+    CK(launch_regroup_keys(&b, rk, rv), "regroup");
+    CK(launch_sort(&b, rk, rv, rk2, rv2, b.n, bits_for((uint64_t)depth) + db->tbits), "regroup sort");
+    CK(launch_level_tables(&b, rk, depth, block, true), "level tables");
+    CK(launch_gather(&b, rv), "gather");
+    CK(launch_kset(&b, rv, b.sc.chunk_cap, block, add), "k-set execute");
+    CK(launch_finish(&b), "finish");
+    if ((st = read_ctl(&b))) return st;
+    return bulk_error(db, b.host_ctl.err);
+}
