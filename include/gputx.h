@@ -275,6 +275,77 @@ gputx_status gputx_execute_kset_noalloc(gputx_db *db, const int64_t *ts, const i
                                         const int64_t *params, int params_per_txn, size_t n,
                                         int conflict_mode, int32_t *status, int64_t *values);
 
+/* ------------------------------------------------------------------------ */
+/* Serving: a transaction pool and bulk generator over one database          */
+/* ------------------------------------------------------------------------ */
+/* Section 3.2: submitted transactions wait in a pool; the system periodically
+ * generates a bulk from it and returns the results.  Here a worker thread
+ * closes a bulk when its oldest transaction has waited deadline_us or max_bulk
+ * transactions are pending, and keeps up to max_inflight bulks on the GPU:
+ * the analysis of a new bulk overlaps the execution of earlier ones, and bulks
+ * apply in id order.  Every submitted transaction gets the next id, which is
+ * its timestamp, so the served stream equals serial execution in id order.
+ * While a server runs, only the server may submit or execute bulks on its
+ * database. */
+typedef struct gputx_server gputx_server;
+
+typedef struct {
+    int64_t deadline_us;      /* bulk closes when its oldest transaction waited
+                                 this long (default 1000) */
+    int64_t max_bulk;         /* ... or holds this many (default: db max_bulk) */
+    int32_t max_inflight;     /* bulks on the device at once, 1..8 (default 2);
+                                 1 = one bulk at a time, no overlap */
+    int32_t strategy;         /* gputx_strategy of every bulk (default K-SET) */
+    int32_t conflict_mode;    /* gputx_conflict_mode */
+    int32_t params_per_txn;   /* parameter row width of submissions (default 2) */
+    int64_t queue_capacity;   /* pending + in-flight transactions admitted
+                                 (default 2^30) */
+    int64_t min_free_bytes;   /* refuse submissions while free device memory is
+                                 below this (0 = no check) */
+} gputx_serve_config;
+
+typedef struct {
+    int64_t submitted, completed, bulks, max_bulk_seen, refused;
+    double p50_us, p99_us, mean_us;   /* arrival -> result available on the host */
+    double txn_per_s;                 /* completed / (last completion - first arrival) */
+} gputx_serve_stats;
+
+/* Monotonic clock (ns) that arrival times passed to gputx_server_submit use. */
+int64_t gputx_clock_ns(void);
+
+/* Starts a server on a database with registered types.  ESTATE if none are
+ * registered, EINVAL on a bad strategy, ENOMEM if its pinned staging buffers
+ * cannot be allocated. */
+gputx_status gputx_server_create(gputx_db *db, const gputx_serve_config *cfg, gputx_server **out);
+
+/* Adds n transactions (host arrays: type[n], params[n x params_per_txn]) to
+ * the pool; arrival_ns[n] (gputx_clock_ns timebase) or NULL for now.  *first_id
+ * receives the id (timestamp) of the first; the rest follow consecutively.
+ * Admission: ENOMEM, with nothing added, when the pool would exceed
+ * queue_capacity, an insert area (history, call forwarding, orders, order
+ * lines) could not hold the inserts already admitted plus these, or free
+ * device memory is below min_free_bytes.  A device error of an earlier bulk
+ * is returned here too. */
+gputx_status gputx_server_submit(gputx_server *s, const int32_t *type, const int64_t *params, size_t n,
+                                 const int64_t *arrival_ns, int64_t *first_id);
+
+/* Copies the results of ids [first_id, first_id + n) that have completed
+ * into status[n] / values[n x output width] / complete_ns[n] (any may be
+ * NULL); entries of unfinished ids are left as they are.  *n_done counts the
+ * finished ones.  EINVAL for ids never submitted. */
+gputx_status gputx_server_results(gputx_server *s, int64_t first_id, size_t n, int32_t *status, int64_t *values,
+                                  int64_t *complete_ns, size_t *n_done);
+
+/* Waits until every submitted transaction completed (closing the last bulk
+ * without waiting for its deadline); returns the first device error. */
+gputx_status gputx_server_drain(gputx_server *s);
+
+gputx_status gputx_server_stats(gputx_server *s, gputx_serve_stats *stats);
+const char *gputx_server_last_error(const gputx_server *s);
+
+/* Stops the worker after the pending transactions complete, frees buffers. */
+void gputx_server_destroy(gputx_server *s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,7 +43,9 @@ EXPORTED = ("gputx_create_db", "gputx_destroy_db", "gputx_last_error", "gputx_re
             "gputx_load_table", "gputx_read_table", "gputx_submit_bulk", "gputx_execute",
             "gputx_sync_bulk", "gputx_read_results", "gputx_bulk_results_device",
             "gputx_output_width", "gputx_free_bulk", "gputx_version", "gputx_launch_count",
-            "gputx_execute_kset_noalloc")
+            "gputx_execute_kset_noalloc", "gputx_clock_ns", "gputx_server_create", "gputx_server_submit",
+            "gputx_server_results", "gputx_server_drain", "gputx_server_stats",
+            "gputx_server_last_error", "gputx_server_destroy")
 
 
 class GputxError(RuntimeError):
@@ -73,6 +75,21 @@ class ExecStats(C.Structure):
                 ("cross", C.c_int64), ("fixpoint_rounds", C.c_int64),
                 ("ms_h2d", C.c_float), ("ms_analysis", C.c_float), ("ms_sort", C.c_float),
                 ("ms_execute", C.c_float), ("ms_d2h", C.c_float), ("ms_total", C.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServeConfig(C.Structure):
+    _fields_ = [("deadline_us", C.c_int64), ("max_bulk", C.c_int64), ("max_inflight", C.c_int32),
+                ("strategy", C.c_int32), ("conflict_mode", C.c_int32), ("params_per_txn", C.c_int32),
+                ("queue_capacity", C.c_int64), ("min_free_bytes", C.c_int64)]
+
+
+class ServeStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("bulks", C.c_int64),
+                ("max_bulk_seen", C.c_int64), ("refused", C.c_int64), ("p50_us", C.c_double),
+                ("p99_us", C.c_double), ("mean_us", C.c_double), ("txn_per_s", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -112,6 +129,14 @@ def lib():
             "gputx_version": ([], C.c_char_p),
             "gputx_launch_count": ([], C.c_ulonglong),
             "gputx_execute_kset_noalloc": ([p, p, p, p, C.c_int, sz, C.c_int, p, p], C.c_int),
+            "gputx_clock_ns": ([], C.c_int64),
+            "gputx_server_create": ([p, C.POINTER(ServeConfig), C.POINTER(p)], C.c_int),
+            "gputx_server_submit": ([p, p, p, sz, p, C.POINTER(C.c_int64)], C.c_int),
+            "gputx_server_results": ([p, C.c_int64, sz, p, p, p, C.POINTER(sz)], C.c_int),
+            "gputx_server_drain": ([p], C.c_int),
+            "gputx_server_stats": ([p, C.POINTER(ServeStats)], C.c_int),
+            "gputx_server_last_error": ([p], C.c_char_p),
+            "gputx_server_destroy": ([p], None),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -312,6 +337,93 @@ class Database:
     def close(self):
         if self.h:
             gputx_destroy_db(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --- serving -------------------------------------------------------------------
+def gputx_clock_ns() -> int:
+    return int(lib().gputx_clock_ns())
+
+
+def _scheck(srv, st):
+    if st != OK:
+        raise GputxError(st, lib().gputx_server_last_error(srv).decode() if srv else "")
+
+
+def gputx_server_create(db, cfg: ServeConfig):
+    out = C.c_void_p()
+    st = lib().gputx_server_create(db, C.byref(cfg), C.byref(out))
+    if st != OK:
+        raise GputxError(st, "server_create")
+    return out
+
+
+def gputx_server_submit(srv, type_, params, arrival_ns=None) -> int:
+    type_ = np.ascontiguousarray(type_, dtype=np.int32)
+    params = np.ascontiguousarray(params, dtype=np.int64)
+    arr = None if arrival_ns is None else np.ascontiguousarray(arrival_ns, dtype=np.int64)
+    first = C.c_int64()
+    _scheck(srv, lib().gputx_server_submit(srv, _ptr(type_), _ptr(params), len(type_), _ptr(arr),
+                                           C.byref(first)))
+    return first.value
+
+
+def gputx_server_results(srv, first_id: int, n: int, width: int):
+    st = np.zeros(n, dtype=np.int32)
+    vals = np.zeros((n, width), dtype=np.int64)
+    done_ns = np.zeros(n, dtype=np.int64)
+    nd = C.c_size_t()
+    _scheck(srv, lib().gputx_server_results(srv, first_id, n, _ptr(st), _ptr(vals), _ptr(done_ns),
+                                            C.byref(nd)))
+    return st, vals, done_ns, nd.value
+
+
+def gputx_server_drain(srv):
+    _scheck(srv, lib().gputx_server_drain(srv))
+
+
+def gputx_server_stats(srv) -> dict:
+    st = ServeStats()
+    _scheck(srv, lib().gputx_server_stats(srv, C.byref(st)))
+    return st.as_dict()
+
+
+def gputx_server_destroy(srv):
+    lib().gputx_server_destroy(srv)
+
+
+class Server:
+    """Transaction pool + bulk generator over a Database (see gputx.h)."""
+
+    def __init__(self, db: Database, deadline_us=1000, max_bulk=0, max_inflight=2, strategy="kset",
+                 conflict_mode=CONFLICT_PAPER, params_per_txn=2, queue_capacity=0, min_free_bytes=0):
+        s = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
+        cfg = ServeConfig(deadline_us, max_bulk, max_inflight, s, conflict_mode, params_per_txn,
+                          queue_capacity, min_free_bytes)
+        self.db = db
+        self.h = gputx_server_create(db.h, cfg)
+
+    def submit(self, type_, params, arrival_ns=None) -> int:
+        return gputx_server_submit(self.h, type_, params, arrival_ns)
+
+    def results(self, first_id, n):
+        return gputx_server_results(self.h, first_id, n, self.db.width)
+
+    def drain(self):
+        gputx_server_drain(self.h)
+
+    def stats(self) -> dict:
+        return gputx_server_stats(self.h)
+
+    def close(self):
+        if self.h:
+            gputx_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

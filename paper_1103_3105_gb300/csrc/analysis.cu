@@ -350,7 +350,7 @@ cudaError_t run_scan(gputx_bulk *b, const Mode &mode, int64_t count, int ctr_slo
     if (count <= 0) return cudaSuccess;
     const int64_t tiles = (count + SCAN_TILE - 1) / SCAN_TILE;
     if (tiles > b->sc.scan_tiles) return cudaErrorInvalidValue;
-    cudaStream_t s = b->db->stream;
+    cudaStream_t s = b->stream;
     cudaError_t e = cudaMemsetAsync(b->sc.scan_status, 0, tiles * sizeof(uint64_t), s);
     if (e) return e;
     e = cudaMemsetAsync(b->sc.tile_ctr + ctr_slot, 0, sizeof(uint32_t), s);
@@ -410,7 +410,7 @@ cudaError_t launch_gather(gputx_bulk *b, const uint32_t *order)
 {
     if (b->n == 0) return cudaSuccess;
     const DevBulk d = dev_bulk(b, 0);
-    gather_kernel<<<grid_for(b->n), TB, 0, b->db->stream>>>(d, order, b->sc.rec_params, b->sc.rec_ts,
+    gather_kernel<<<grid_for(b->n), TB, 0, b->stream>>>(d, order, b->sc.rec_params, b->sc.rec_ts,
                                                              b->sc.rec_type, b->sc.rec_t, &b->ctl->err);
     count_launches(1);
     return cudaGetLastError();
@@ -419,14 +419,14 @@ cudaError_t launch_gather(gputx_bulk *b, const uint32_t *order)
 cudaError_t launch_begin(gputx_bulk *b)
 {
     const bool dc = (b->db->dev.registered & 1u) != 0;
-    begin_kernel<<<1, 1, 0, b->db->stream>>>(b->db->d_cursor, b->ctl, dc ? b->n : 0);
+    begin_kernel<<<1, 1, 0, b->stream>>>(b->db->d_cursor, b->ctl, dc ? b->n : 0);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_finish(gputx_bulk *b)
 {
-    finish_kernel<<<1, 1, 0, b->db->stream>>>(b->db->d_cursor, b->ctl);
+    finish_kernel<<<1, 1, 0, b->stream>>>(b->db->d_cursor, b->ctl);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -435,7 +435,7 @@ cudaError_t launch_extract(gputx_bulk *b, int mode, int part_size, uint32_t *pid
                            bool write_ops)
 {
     gputx_db *db = b->db;
-    cudaStream_t s = db->stream;
+    cudaStream_t s = b->stream;
     if (b->n == 0) return cudaSuccess;
     ExtractArgs a{};
     a.db = db->dev;
@@ -469,7 +469,7 @@ cudaError_t launch_sort(gputx_bulk *b, uint32_t *&keys, uint32_t *&vals, uint32_
                         int64_t count, int bits)
 {
     if (count <= 1 || bits <= 0) return cudaSuccess;
-    cudaStream_t s = b->db->stream;
+    cudaStream_t s = b->stream;
     const int passes = (bits + 7) / 8;
     const int64_t tiles = (count + SORT_TILE - 1) / SORT_TILE;
     if (tiles > b->sc.sort_tiles || passes > 4) return cudaErrorInvalidValue;
@@ -508,7 +508,7 @@ cudaError_t launch_sort(gputx_bulk *b, uint32_t *&keys, uint32_t *&vals, uint32_
 
 cudaError_t launch_rank_scan(gputx_bulk *b, const uint32_t *sk, const uint32_t *sv, int64_t m, bool want_rid)
 {
-    cudaError_t e = cudaMemsetAsync(b->sc.level, 0, b->n * sizeof(uint32_t), b->db->stream);
+    cudaError_t e = cudaMemsetAsync(b->sc.level, 0, b->n * sizeof(uint32_t), b->stream);
     if (e) return e;
     RankMode rm{sk, sv, b->sc.level, want_rid ? b->sc.rid : nullptr};
     return run_scan(b, rm, m, 1);
@@ -523,7 +523,7 @@ cudaError_t launch_ticket_scan(gputx_bulk *b, const uint32_t *sk, const uint32_t
 
 cudaError_t launch_fixpoint_round(gputx_bulk *b, const uint32_t *sv, int64_t m)
 {
-    cudaStream_t s = b->db->stream;
+    cudaStream_t s = b->stream;
     if (m == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(b->sc.runmax, 0, m * sizeof(uint32_t), s);
     if (e) return e;
@@ -542,7 +542,7 @@ cudaError_t launch_level_stats(gputx_bulk *b)
     int blocks = b->db->num_sms * 2;
     const int64_t need = (b->n + 255) / 256;
     if (blocks > need) blocks = (int)need;
-    level_stats_kernel<<<blocks, 256, 0, b->db->stream>>>(b->sc.level, b->n, b->ctl);
+    level_stats_kernel<<<blocks, 256, 0, b->stream>>>(b->sc.level, b->n, b->ctl);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -550,7 +550,7 @@ cudaError_t launch_level_stats(gputx_bulk *b)
 cudaError_t launch_regroup_keys(gputx_bulk *b, uint32_t *keys, uint32_t *vals)
 {
     if (b->n == 0) return cudaSuccess;
-    regroup_keys_kernel<<<grid_for(b->n), TB, 0, b->db->stream>>>(b->sc.level, b->type, b->n, b->db->tbits,
+    regroup_keys_kernel<<<grid_for(b->n), TB, 0, b->stream>>>(b->sc.level, b->type, b->n, b->db->tbits,
                                                                    keys, vals);
     count_launches(1);
     return cudaGetLastError();
@@ -558,7 +558,7 @@ cudaError_t launch_regroup_keys(gputx_bulk *b, uint32_t *keys, uint32_t *vals)
 
 cudaError_t launch_level_tables(gputx_bulk *b, const uint32_t *skeys, int64_t depth, int block, bool chunks)
 {
-    cudaStream_t s = b->db->stream;
+    cudaStream_t s = b->stream;
     if (b->n == 0) return cudaSuccess;
     level_off_kernel<<<grid_for(b->n), TB, 0, s>>>(skeys, b->n, b->db->tbits, b->sc.level_off, &b->ctl->err);
     count_launches(1);
@@ -590,7 +590,7 @@ cudaError_t launch_insert_slots(gputx_bulk *b)
 cudaError_t launch_part_heads(gputx_bulk *b, const uint32_t *skeys, int64_t n)
 {
     if (n == 0) return cudaSuccess;
-    part_heads_kernel<<<grid_for(n), TB, 0, b->db->stream>>>(skeys, n, b->sc.part_start, b->ctl);
+    part_heads_kernel<<<grid_for(n), TB, 0, b->stream>>>(skeys, n, b->sc.part_start, b->ctl);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -598,7 +598,7 @@ cudaError_t launch_part_heads(gputx_bulk *b, const uint32_t *skeys, int64_t n)
 cudaError_t launch_tpl_reset(gputx_bulk *b, const uint32_t *skeys, int64_t m)
 {
     if (m == 0) return cudaSuccess;
-    tpl_reset_kernel<<<grid_for(m), TB, 0, b->db->stream>>>(skeys, m, b->db->d_done, b->db->dev.n_objects);
+    tpl_reset_kernel<<<grid_for(m), TB, 0, b->stream>>>(skeys, m, b->db->d_done, b->db->dev.n_objects);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -238,8 +238,8 @@ gputx_status bulk_error(gputx_db *db, uint32_t err)
 gputx_status read_ctl(gputx_bulk *b)
 {
     gputx_db *db = b->db;
-    CK(cudaMemcpyAsync(&b->host_ctl, b->ctl, sizeof(BulkCtl), cudaMemcpyDeviceToHost, db->stream), "sync");
-    CK(cudaStreamSynchronize(db->stream), "sync");
+    CK(cudaMemcpyAsync(&b->host_ctl, b->ctl, sizeof(BulkCtl), cudaMemcpyDeviceToHost, b->stream), "sync");
+    CK(cudaStreamSynchronize(b->stream), "sync");
     return GPUTX_OK;
 }
 
@@ -256,7 +256,14 @@ int gputx_output_width(const gputx_db *db) { return db ? db->dev.out_width : 0; 
 void gputx_destroy_db(gputx_db *db)
 {
     if (!db) return;
+    if (db->last_done) cudaStreamWaitEvent(db->stream, db->last_done, 0);
     cudaStreamSynchronize(db->stream);
+    for (cudaStream_t ps : db->pool)
+        if (ps) {
+            cudaStreamSynchronize(ps);
+            cudaStreamDestroy(ps);
+        }
+    if (db->last_done) cudaEventDestroy(db->last_done);
     for (void *p : db->allocs) cudaFree(p);
     if (db->own_stream) cudaStreamDestroy(db->stream);
     delete db;
@@ -307,6 +314,15 @@ gputx_status gputx_create_db(const gputx_schema_desc *schema, const gputx_config
     } else {
         if (cudaStreamCreateWithFlags(&db->stream, cudaStreamNonBlocking) != cudaSuccess) return bad("stream");
         db->own_stream = true;
+    }
+    for (int i = 0; i < gputx_db::kPool; i++)
+        if (cudaStreamCreateWithFlags(&db->pool[i], cudaStreamNonBlocking) != cudaSuccess) {
+            gputx_destroy_db(db);
+            return GPUTX_ECUDA;
+        }
+    if (cudaEventCreateWithFlags(&db->last_done, cudaEventDisableTiming) != cudaSuccess) {
+        gputx_destroy_db(db);
+        return GPUTX_ECUDA;
     }
     // keep freed stream-ordered allocations for reuse by later bulks
     cudaMemPool_t pool;
@@ -595,6 +611,7 @@ gputx_status gputx_read_table(gputx_db *db, int table, int64_t *rows, size_t cap
     const DevDB &d = db->dev;
     const int f = table_fields(table);
     if (!f) return fail(db, GPUTX_EINVAL, "unknown table %d", table);
+    CK(cudaStreamWaitEvent(db->stream, db->last_done, 0), "sync");
     CK(cudaStreamSynchronize(db->stream), "sync");
     InsertBase cur{};
     CK(cudaMemcpy(&cur, db->d_cursor, sizeof cur, cudaMemcpyDeviceToHost), "cursor");
@@ -786,10 +803,23 @@ gputx_status gputx_submit_bulk(gputx_db *db, const int64_t *ts, const int32_t *t
     b->n = (int64_t)n;
     b->P = params_per_txn;
     b->R = db->dev.out_width;
+    b->stream = db->pool[db->next_pool];
+    db->next_pool = (db->next_pool + 1) % gputx_db::kPool;
+    // the bulk's stream starts after what the caller queued on the database
+    // stream (device inputs may be produced there)
+    cudaError_t e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+    if (!e) e = cudaEventRecord(b->ev_in, db->stream);
+    if (!e) e = cudaStreamWaitEvent(b->stream, b->ev_in, 0);
+    if (e) {
+        if (b->ev_in) cudaEventDestroy(b->ev_in);
+        delete b;
+        return cuda_fail(db, e, "bulk stream");
+    }
     const bool dev_in = mem == GPUTX_MEM_DEVICE;
     b->arena_bytes = carve_bulk(b, nullptr, dev_in);
-    cudaError_t e = cudaMallocAsync(&b->arena, b->arena_bytes, db->stream);
+    e = cudaMallocAsync(&b->arena, b->arena_bytes, b->stream);
     if (e != cudaSuccess) {
+        cudaEventDestroy(b->ev_in);
         delete b;
         return cuda_fail(db, e, "bulk allocation");
     }
@@ -800,17 +830,18 @@ gputx_status gputx_submit_bulk(gputx_db *db, const int64_t *ts, const int32_t *t
         b->type = const_cast<int32_t *>(type);
         b->params = const_cast<int64_t *>(params);
     } else if (n > 0) {
-        e = cudaMemcpyAsync(b->ts, ts, n * sizeof(int64_t), cudaMemcpyHostToDevice, db->stream);
-        if (!e) e = cudaMemcpyAsync(b->type, type, n * sizeof(int32_t), cudaMemcpyHostToDevice, db->stream);
+        e = cudaMemcpyAsync(b->ts, ts, n * sizeof(int64_t), cudaMemcpyHostToDevice, b->stream);
+        if (!e) e = cudaMemcpyAsync(b->type, type, n * sizeof(int32_t), cudaMemcpyHostToDevice, b->stream);
         if (!e) e = cudaMemcpyAsync(b->params, params, n * params_per_txn * sizeof(int64_t),
-                                    cudaMemcpyHostToDevice, db->stream);
+                                    cudaMemcpyHostToDevice, b->stream);
     }
-    if (!e) e = cudaMemsetAsync(b->ctl, 0, sizeof(BulkCtl), db->stream);
-    if (!e && n > 0) e = cudaMemsetAsync(b->out, 0, n * b->R * sizeof(int64_t), db->stream);
-    if (!e && n > 0) e = cudaMemsetAsync(b->status, 0, n * sizeof(int32_t), db->stream);
+    if (!e) e = cudaMemsetAsync(b->ctl, 0, sizeof(BulkCtl), b->stream);
+    if (!e && n > 0) e = cudaMemsetAsync(b->out, 0, n * b->R * sizeof(int64_t), b->stream);
+    if (!e && n > 0) e = cudaMemsetAsync(b->status, 0, n * sizeof(int32_t), b->stream);
     if (!e) e = cudaEventCreate(&b->ev[7]);
     if (e) {
-        cudaFreeAsync(b->arena, db->stream);
+        cudaFreeAsync(b->arena, b->stream);
+        cudaEventDestroy(b->ev_in);
         delete b;
         return cuda_fail(db, e, "bulk upload");
     }
@@ -824,21 +855,41 @@ gputx_status run_kset_analysis(gputx_bulk *b, int mode, int part_size, uint32_t 
                                uint32_t *&ak, uint32_t *&av, int64_t &m)
 {
     gputx_db *db = b->db;
-    CK(cudaMemsetAsync(&b->ctl->cross, 0, 4, db->stream), "extract");
+    CK(cudaMemsetAsync(&b->ctl->cross, 0, 4, b->stream), "extract");
     CK(launch_extract(b, mode, part_size, nullptr, nullptr, true), "extract");
     m = b->n * db->uniform_k;
     if (!db->uniform_k) {
         uint32_t mm = 0;
-        CK(cudaMemcpyAsync(&mm, b->sc.op_off + b->n, sizeof mm, cudaMemcpyDeviceToHost, db->stream), "ops");
-        CK(cudaStreamSynchronize(db->stream), "ops");
+        CK(cudaMemcpyAsync(&mm, b->sc.op_off + b->n, sizeof mm, cudaMemcpyDeviceToHost, b->stream), "ops");
+        CK(cudaStreamSynchronize(b->stream), "ops");
         m = mm;
         if (m > b->sc.m_cap) m = b->sc.m_cap;
     }
-    if (b->timing) cudaEventRecord(b->ev[1], db->stream);
+    if (b->timing) cudaEventRecord(b->ev[1], b->stream);
     sk = b->sc.keys_a; sv = b->sc.vals_a; ak = b->sc.keys_b; av = b->sc.vals_b;
     CK(launch_sort(b, sk, sv, ak, av, m, db->obj_bits), "sort");
-    if (b->timing) cudaEventRecord(b->ev[2], db->stream);
+    if (b->timing) cudaEventRecord(b->ev[2], b->stream);
     return GPUTX_OK;
+}
+
+// The database-touching tail of a bulk starts after the previous bulk's tail
+// (bulks apply in gputx_execute order); the analysis before it overlaps.
+cudaError_t begin_tail(gputx_bulk *b)
+{
+    cudaError_t e = cudaStreamWaitEvent(b->stream, b->db->last_done, 0);
+    if (e) return e;
+    return launch_begin(b);
+}
+
+cudaError_t end_tail(gputx_bulk *b)
+{
+    gputx_db *db = b->db;
+    cudaError_t e = launch_finish(b);
+    if (!e) e = cudaEventRecord(db->last_done, b->stream);
+    if (!e) e = cudaEventRecord(b->ev[7], b->stream);
+    // callers that order work on the database stream see the bulk as done
+    if (!e) e = cudaStreamWaitEvent(db->stream, db->last_done, 0);
+    return e;
 }
 
 }  // namespace
@@ -859,9 +910,8 @@ gputx_status gputx_execute(gputx_db *db, gputx_bulk *b, int strategy, const gput
     if (b->timing)
         for (int i = 0; i < 7; i++)
             if (!b->ev[i]) cudaEventCreate(&b->ev[i]);
-    cudaStream_t s = db->stream;
+    cudaStream_t s = b->stream;
     if (b->timing) cudaEventRecord(b->ev[0], s);
-    CK(launch_begin(b), "begin");
     CK(launch_insert_slots(b), "insert slots");
     const bool add = mode == GPUTX_CONFLICT_ADD;
     gputx_status st = GPUTX_OK;
@@ -912,6 +962,7 @@ gputx_status gputx_execute(gputx_db *db, gputx_bulk *b, int strategy, const gput
         CK(launch_level_tables(b, rk, depth, block, persistent), "level tables");
         if (persistent) {
             CK(launch_gather(b, rv), "gather");
+            CK(begin_tail(b), "order");
             if (b->timing) cudaEventRecord(b->ev[3], s);
             CK(launch_kset(b, rv, b->sc.chunk_cap, block, add), "k-set execute");
         } else if (b->n > 0) {
@@ -924,9 +975,12 @@ gputx_status gputx_execute(gputx_db *db, gputx_bulk *b, int strategy, const gput
             if (!b->host_ctl.err) {
                 const int narrow = (opts && opts->narrow_max > 0) ? opts->narrow_max : 8192;
                 CK(launch_gather(b, rv), "gather");
+                CK(begin_tail(b), "order");
                 if (b->timing) cudaEventRecord(b->ev[3], s);
                 CK(launch_kset_levels(b, b->level_off_host.data(), depth, narrow, add), "k-set execute");
             }
+        } else {
+            CK(begin_tail(b), "order");   // empty bulk
         }
     } else if (run == GPUTX_PART) {
         // partition ids by root key (Section 5.2 step 1), stable sort (step 2)
@@ -951,6 +1005,7 @@ gputx_status gputx_execute(gputx_db *db, gputx_bulk *b, int strategy, const gput
             if (b->timing) cudaEventRecord(b->ev[2], s);
             CK(launch_part_heads(b, pk, b->n), "partition heads");
             CK(launch_gather(b, pv), "gather");
+            CK(begin_tail(b), "order");
             if (b->timing) cudaEventRecord(b->ev[3], s);
             CK(launch_part(b, pk, 128), "part execute");
         }
@@ -960,14 +1015,14 @@ gputx_status gputx_execute(gputx_db *db, gputx_bulk *b, int strategy, const gput
             if ((st = run_kset_analysis(b, mode, part_size, sk, sv, ak, av, m))) return st;
         }
         CK(launch_ticket_scan(b, sk, sv, m), "tickets");
+        CK(begin_tail(b), "order");
         if (b->timing) cudaEventRecord(b->ev[3], s);
         CK(launch_tpl(b, block, add), "tpl execute");
         if (b->timing) cudaEventRecord(b->ev[4], s);
         CK(launch_tpl_reset(b, sk, m), "tpl reset");
     }
     if (b->timing && run != GPUTX_TPL) cudaEventRecord(b->ev[4], s);
-    CK(launch_finish(b), "finish");
-    CK(cudaEventRecord(b->ev[7], s), "event");
+    CK(end_tail(b), "finish");
     b->strategy_run = run;
     return GPUTX_OK;
 }
@@ -1010,10 +1065,10 @@ gputx_status gputx_read_results(gputx_bulk *b, int32_t *status, int64_t *values,
     gputx_status st = gputx_sync_bulk(b, nullptr);
     if (st) return st;
     if (n == 0) return GPUTX_OK;
-    if (status) CK(cudaMemcpyAsync(status, b->status, n * sizeof(int32_t), cudaMemcpyDeviceToHost, db->stream), "d2h");
+    if (status) CK(cudaMemcpyAsync(status, b->status, n * sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream), "d2h");
     if (values)
-        CK(cudaMemcpyAsync(values, b->out, n * b->R * sizeof(int64_t), cudaMemcpyDeviceToHost, db->stream), "d2h");
-    CK(cudaStreamSynchronize(db->stream), "d2h");
+        CK(cudaMemcpyAsync(values, b->out, n * b->R * sizeof(int64_t), cudaMemcpyDeviceToHost, b->stream), "d2h");
+    CK(cudaStreamSynchronize(b->stream), "d2h");
     return GPUTX_OK;
 }
 
@@ -1028,10 +1083,10 @@ gputx_status gputx_bulk_results_device(gputx_bulk *b, const int32_t **status, co
 void gputx_free_bulk(gputx_bulk *b)
 {
     if (!b) return;
-    gputx_db *db = b->db;
-    if (b->arena) cudaFreeAsync(b->arena, db->stream);
+    if (b->arena) cudaFreeAsync(b->arena, b->stream);
     for (int i = 0; i < 8; i++)
         if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
     delete b;
 }
 
@@ -1097,6 +1152,7 @@ extern "C" gputx_status gputx_execute_kset_noalloc(gputx_db *db, const int64_t *
         return fail(db, GPUTX_EINVAL, "bulk needs %zu bytes of working memory, the no-allocation area has %u",
                     need, (unsigned)GPUTX_NOALLOC_SCRATCH_BYTES);
     carve_bulk(&b, (char *)scratch, true);
+    b.stream = db->stream;
     b.ts = const_cast<int64_t *>(ts);
     b.type = const_cast<int32_t *>(type);
     b.params = const_cast<int64_t *>(params);
@@ -1111,6 +1167,7 @@ extern "C" gputx_status gputx_execute_kset_noalloc(gputx_db *db, const int64_t *
     }
     const bool add = conflict_mode == GPUTX_CONFLICT_ADD;
     const int block = db->cfg.block_threads;
+    CK(cudaStreamWaitEvent(s, db->last_done, 0), "order");
     CK(launch_begin(&b), "begin");
     CK(launch_insert_slots(&b), "insert slots");
     CK(cudaMemsetAsync(&b.ctl->cross, 0, 4, s), "extract");
@@ -1146,6 +1203,7 @@ extern "C" gputx_status gputx_execute_kset_noalloc(gputx_db *db, const int64_t *
     CK(launch_gather(&b, rv), "gather");
     CK(launch_kset(&b, rv, b.sc.chunk_cap, block, add), "k-set execute");
     CK(launch_finish(&b), "finish");
+    CK(cudaEventRecord(db->last_done, s), "order");
     if ((st = read_ctl(&b))) return st;
     return bulk_error(db, b.host_ctl.err);
 }

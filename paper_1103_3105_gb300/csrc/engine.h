@@ -71,10 +71,19 @@ struct gputx_db {
     bool need_fixpoint = false;            // a registered type's ops may leave one-pass ranks inexact
     int tbits = 0;                         // type bits in the level/type regroup key
     int obj_bits = 1;                      // key bits of object ids
+    // Each bulk runs on a stream of this pool, so the analysis of one bulk
+    // overlaps the execution of the one before; `last_done` orders the
+    // database-touching tail of every bulk after that of its predecessor.
+    static constexpr int kPool = 4;
+    cudaStream_t pool[kPool] = {};
+    int next_pool = 0;
+    cudaEvent_t last_done = nullptr;
 };
 
 struct gputx_bulk {
     gputx_db *db = nullptr;
+    cudaStream_t stream = nullptr;          // this bulk's stream (from the database's pool)
+    cudaEvent_t ev_in = nullptr;            // inputs ready on the database stream
     int64_t n = 0;
     int P = 0, R = 0;
     void *arena = nullptr;

@@ -310,13 +310,13 @@ cudaError_t launch_kset(gputx_bulk *b, const uint32_t *order, int64_t nchunks, i
     a.levels = (int64_t)b->host_ctl.depth + 1;
     a.spin_limit_ns = (uint64_t)db->cfg.spin_limit_ns;
     a.atomic_add = atomic_add;
-    cudaError_t e = cudaMemsetAsync(b->sc.done, 0, (size_t)a.levels * sizeof(uint32_t), db->stream);
+    cudaError_t e = cudaMemsetAsync(b->sc.done, 0, (size_t)a.levels * sizeof(uint32_t), b->stream);
     if (e) return e;
-    e = cudaMemsetAsync(&b->ctl->claim, 0, sizeof(uint32_t), db->stream);
+    e = cudaMemsetAsync(&b->ctl->claim, 0, sizeof(uint32_t), b->stream);
     if (e) return e;
     int64_t grid = (int64_t)db->num_sms * exec_blocks_per_sm(0, block);
     if (grid > nchunks) grid = nchunks;
-    kset_kernel<<<(unsigned)grid, block, 0, db->stream>>>(a);
+    kset_kernel<<<(unsigned)grid, block, 0, b->stream>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -347,7 +347,7 @@ cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, in
             int64_t grid = ((int64_t)w + 255) / 256;
             const int64_t cap = (int64_t)db->num_sms * 8;
             if (grid > cap) grid = cap;
-            kset_level_kernel<<<(unsigned)grid, 256, 0, db->stream>>>(a);
+            kset_level_kernel<<<(unsigned)grid, 256, 0, b->stream>>>(a);
             count_launches(1);
             k++;
             continue;
@@ -372,12 +372,12 @@ cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, in
         threads = ((threads + 31) / 32) * 32;
         threads = threads < 32 ? 32 : (threads > 1024 ? 1024 : threads);
         if (csize <= 1) {
-            kset_narrow_kernel<false><<<1, threads, 0, db->stream>>>(a);
+            kset_narrow_kernel<false><<<1, threads, 0, b->stream>>>(a);
         } else {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(csize, 1, 1);
             cfg.blockDim = dim3(threads, 1, 1);
-            cfg.stream = db->stream;
+            cfg.stream = b->stream;
             cudaLaunchAttribute attr[1];
             attr[0].id = cudaLaunchAttributeClusterDimension;
             attr[0].val.clusterDim.x = csize;
@@ -402,7 +402,7 @@ cudaError_t launch_part(gputx_bulk *b, const uint32_t *pkeys, int block)
     if (b->n == 0) return cudaSuccess;
     const DevBulk d = make_dev_bulk(b, GPUTX_CONFLICT_PAPER);
     const int64_t grid = (b->n + block - 1) / block;   // npart <= n, read on the device
-    part_kernel<<<(unsigned)grid, block, 0, db->stream>>>(db->dev, d, b->ctl, pkeys, b->sc.part_start);
+    part_kernel<<<(unsigned)grid, block, 0, b->stream>>>(db->dev, d, b->ctl, pkeys, b->sc.part_start);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -422,12 +422,12 @@ cudaError_t launch_tpl(gputx_bulk *b, int block, bool atomic_add)
     a.uniform_k = db->uniform_k;
     a.spin_limit_ns = (uint64_t)db->cfg.spin_limit_ns;
     a.atomic_add = atomic_add;
-    cudaError_t e = cudaMemsetAsync(&b->ctl->claim, 0, sizeof(uint32_t), db->stream);
+    cudaError_t e = cudaMemsetAsync(&b->ctl->claim, 0, sizeof(uint32_t), b->stream);
     if (e) return e;
     int64_t grid = (int64_t)db->num_sms * exec_blocks_per_sm(1, block);
     const int64_t chunks = (b->n + block - 1) / block;
     if (grid > chunks) grid = chunks;
-    tpl_kernel<<<(unsigned)grid, block, 0, db->stream>>>(a);
+    tpl_kernel<<<(unsigned)grid, block, 0, b->stream>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }

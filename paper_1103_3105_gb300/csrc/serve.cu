@@ -1,0 +1,457 @@
+// serve.cu -- a serving loop over the bulk engine (Section 3.2's transaction
+// pool and bulk generator, Section 6.3's response time vs throughput).
+//
+// Clients submit transactions into a pool; the pool assigns each one the next
+// id, which is its timestamp (Section 3.2).  A worker thread closes a bulk
+// when the oldest pending transaction has waited `deadline_us` or `max_bulk`
+// are pending, and hands it to gputx_execute.  Up to `max_inflight` bulks are
+// on the device at once: the analysis of a new bulk runs while earlier bulks
+// execute, and the database applies bulks in id order, so the served stream
+// equals serial execution in id order (Definition 1 over the whole stream).
+// Admission refuses work the pool, the insert areas or free device memory
+// cannot hold.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "engine.h"
+
+namespace {
+
+int64_t now_ns()
+{
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+// latency histogram: 1 us bins up to 1 s, then one overflow bin
+struct LatencyHist {
+    static constexpr int kBins = 1000000;
+    std::vector<uint64_t> bins = std::vector<uint64_t>(kBins + 1, 0);
+    uint64_t count = 0;
+    double sum_us = 0;
+    void add(int64_t ns)
+    {
+        int64_t us = ns / 1000;
+        if (us < 0) us = 0;
+        bins[us < kBins ? us : kBins]++;
+        count++;
+        sum_us += (double)ns / 1000.0;
+    }
+    double quantile(double q) const
+    {
+        if (!count) return 0;
+        const uint64_t target = (uint64_t)(q * (double)(count - 1)) + 1;
+        uint64_t acc = 0;
+        for (int i = 0; i <= kBins; i++) {
+            acc += bins[i];
+            if (acc >= target) return (double)i + 0.5;
+        }
+        return (double)kBins;
+    }
+};
+
+struct Slot {
+    gputx_bulk *bulk = nullptr;
+    int64_t first_id = 0;
+    int64_t n = 0;
+    int32_t *h_type = nullptr;
+    int64_t *h_ts = nullptr, *h_params = nullptr, *h_values = nullptr;
+    int32_t *h_status = nullptr;
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+    int64_t inserts[4] = {0, 0, 0, 0};   // hist, cf, ord, ol reserved by this bulk
+};
+
+}  // namespace
+
+struct gputx_server {
+    gputx_db *db = nullptr;
+    gputx_serve_config cfg{};
+    std::mutex mu;
+    std::condition_variable cv;
+    std::thread worker;
+    bool stop = false;
+    bool flush = false;               // drain: close bulks without waiting for deadlines
+    gputx_status worker_status = GPUTX_OK;
+    std::string worker_error;
+    // the pool: pending transactions, ids next_consume .. next_id-1
+    std::vector<int32_t> p_type;
+    std::vector<int64_t> p_params;
+    std::vector<int64_t> p_arrival;
+    int64_t pool_base = 0;            // id of p_*[0]
+    int64_t next_consume = 0;         // first id not yet in a bulk
+    int64_t next_id = 0;              // next id to assign
+    int64_t inflight_txns = 0;
+    // insert accounting (rows reserved by pending + in-flight work, and used)
+    int64_t ins_reserved[4] = {0, 0, 0, 0};
+    int64_t ins_used[4] = {0, 0, 0, 0};
+    int64_t ins_cap[4] = {0, 0, 0, 0};
+    // results, indexed by id
+    std::vector<int32_t> r_status;
+    std::vector<int64_t> r_values;
+    std::vector<int64_t> r_complete;
+    std::vector<uint8_t> r_done;
+    int64_t completed = 0, bulks = 0, max_bulk_seen = 0, refused = 0;
+    int64_t first_arrival = -1, last_complete = 0;
+    LatencyHist hist;
+    std::vector<Slot> slots;
+    std::deque<int> order;            // in-flight slots in execution order
+    int R = 1, P = 1;
+};
+
+namespace {
+
+// rows of each append area one transaction takes (history rows are taken per
+// bulk position when the debit-credit schema exists)
+void insert_need(const gputx_server *s, int32_t type, const int64_t *p, int64_t need[4])
+{
+    need[0] = (s->db->dev.registered & 1u) ? 1 : 0;
+    need[1] = type == GPUTX_T_SUB_INSERT_CF ? 1 : 0;
+    need[2] = type == GPUTX_T_OE_NEW_ORDER ? 1 : 0;
+    need[3] = type == GPUTX_T_OE_NEW_ORDER ? (p[3] > 0 && p[3] <= 15 ? p[3] : 0) : 0;
+}
+
+gputx_status set_worker_error(gputx_server *s, gputx_status st, const char *what)
+{
+    s->worker_status = st;
+    s->worker_error = std::string(what) + ": " + gputx_last_error(s->db);
+    return st;
+}
+
+// reaps finished bulks in order (lock held)
+void reap(gputx_server *s, bool block)
+{
+    while (!s->order.empty()) {
+        Slot &sl = s->slots[s->order.front()];
+        if (block) {
+            s->mu.unlock();
+            cudaEventSynchronize(sl.done);
+            s->mu.lock();
+        } else if (cudaEventQuery(sl.done) == cudaErrorNotReady) {
+            return;
+        }
+        const int64_t t = now_ns();
+        if (sl.bulk) {
+            gputx_status st = gputx_sync_bulk(sl.bulk, nullptr);
+            if (st != GPUTX_OK) set_worker_error(s, st, "bulk");
+        }
+        for (int64_t i = 0; i < sl.n; i++) {
+            const int64_t id = sl.first_id + i;
+            s->r_status[id] = sl.h_status[i];
+            std::memcpy(&s->r_values[id * s->R], sl.h_values + i * s->R, sizeof(int64_t) * s->R);
+            s->r_complete[id] = t;
+            s->r_done[id] = 1;
+            s->hist.add(t - s->p_arrival[id - s->pool_base]);
+        }
+        s->completed += sl.n;
+        s->last_complete = t;
+        s->inflight_txns -= sl.n;
+        for (int k = 0; k < 4; k++) {
+            s->ins_reserved[k] -= sl.inserts[k];
+            s->ins_used[k] += sl.inserts[k];
+        }
+        if (sl.bulk) gputx_free_bulk(sl.bulk);
+        sl.bulk = nullptr;
+        sl.busy = false;
+        s->order.pop_front();
+        s->cv.notify_all();
+    }
+    // drop the pool's prefix no bulk still needs (arrivals of finished ids)
+    const int64_t keep_from = s->order.empty() ? s->next_consume : s->slots[s->order.front()].first_id;
+    const int64_t drop = keep_from - s->pool_base;
+    if (drop > (1 << 20) && drop * 2 > (int64_t)s->p_type.size()) {
+        s->p_type.erase(s->p_type.begin(), s->p_type.begin() + drop);
+        s->p_params.erase(s->p_params.begin(), s->p_params.begin() + drop * s->P);
+        s->p_arrival.erase(s->p_arrival.begin(), s->p_arrival.begin() + drop);
+        s->pool_base = keep_from;
+    }
+}
+
+// cuts the next bulk [next_consume, next_consume + n) and launches it (lock
+// held on entry and exit; released while the engine works)
+void launch(gputx_server *s, int slot_idx, int64_t n)
+{
+    Slot &sl = s->slots[slot_idx];
+    sl.first_id = s->next_consume;
+    sl.n = n;
+    sl.busy = true;
+    const int64_t off = s->next_consume - s->pool_base;
+    std::memcpy(sl.h_type, &s->p_type[off], sizeof(int32_t) * n);
+    std::memcpy(sl.h_params, &s->p_params[off * s->P], sizeof(int64_t) * n * s->P);
+    for (int k = 0; k < 4; k++) sl.inserts[k] = 0;
+    for (int64_t i = 0; i < n; i++) {
+        sl.h_ts[i] = sl.first_id + i;
+        int64_t need[4];
+        insert_need(s, sl.h_type[i], sl.h_params + i * s->P, need);
+        for (int k = 0; k < 4; k++) sl.inserts[k] += need[k];
+    }
+    s->next_consume += n;
+    s->inflight_txns += n;
+    s->bulks++;
+    s->max_bulk_seen = std::max(s->max_bulk_seen, n);
+    s->order.push_back(slot_idx);
+    s->mu.unlock();
+    gputx_bulk *b = nullptr;
+    gputx_status st = gputx_submit_bulk(s->db, sl.h_ts, sl.h_type, sl.h_params, s->P, (size_t)n,
+                                        GPUTX_MEM_HOST, &b);
+    if (st == GPUTX_OK) {
+        gputx_exec_opts o{};
+        o.conflict_mode = s->cfg.conflict_mode;
+        st = gputx_execute(s->db, b, s->cfg.strategy, &o);
+    }
+    if (st == GPUTX_OK) {
+        // results come back asynchronously into this slot's pinned buffers
+        const int32_t *ds = nullptr;
+        const int64_t *dv = nullptr;
+        gputx_bulk_results_device(b, &ds, &dv);
+        cudaMemcpyAsync(sl.h_status, ds, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, b->stream);
+        cudaMemcpyAsync(sl.h_values, dv, sizeof(int64_t) * n * s->R, cudaMemcpyDeviceToHost, b->stream);
+        cudaEventRecord(sl.done, b->stream);
+    }
+    s->mu.lock();
+    sl.bulk = b;
+    if (st != GPUTX_OK) {
+        set_worker_error(s, st, "launch");
+        if (!b) cudaEventRecord(sl.done, s->db->stream);
+        else cudaEventRecord(sl.done, b->stream);
+        if (!b) {
+            // nothing on the device: complete the bulk with its error status
+            for (int64_t i = 0; i < n; i++) sl.h_status[i] = -(int32_t)st;
+            std::memset(sl.h_values, 0, sizeof(int64_t) * n * s->R);
+        }
+    }
+}
+
+void worker_main(gputx_server *s)
+{
+    int dev = s->db->device;
+    cudaSetDevice(dev);
+    std::unique_lock<std::mutex> lk(s->mu);
+    const int64_t deadline = s->cfg.deadline_us * 1000;
+    while (true) {
+        reap(s, false);
+        const int64_t pending = s->next_id - s->next_consume;
+        if (s->stop && pending == 0 && s->order.empty()) break;
+        int free_slot = -1;
+        for (int i = 0; i < (int)s->slots.size(); i++)
+            if (!s->slots[i].busy) { free_slot = i; break; }
+        bool ready = false;
+        if (pending > 0) {
+            const int64_t oldest = s->p_arrival[s->next_consume - s->pool_base];
+            ready = pending >= s->cfg.max_bulk || now_ns() - oldest >= deadline || s->stop || s->flush;
+        }
+        if (ready && free_slot >= 0) {
+            launch(s, free_slot, std::min<int64_t>(pending, s->cfg.max_bulk));
+            continue;
+        }
+        if (ready && free_slot < 0) {
+            reap(s, true);   // every slot busy: wait for the oldest bulk
+            continue;
+        }
+        // sleep until the oldest pending transaction reaches its deadline, a
+        // submit arrives, or a bulk may have finished
+        int64_t wait_ns = 200000;
+        if (pending > 0) {
+            const int64_t oldest = s->p_arrival[s->next_consume - s->pool_base];
+            wait_ns = std::max<int64_t>(0, oldest + deadline - now_ns());
+        }
+        if (!s->order.empty()) wait_ns = std::min<int64_t>(wait_ns, 20000);
+        if (wait_ns > 0) s->cv.wait_for(lk, std::chrono::nanoseconds(wait_ns));
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t gputx_clock_ns(void) { return now_ns(); }
+
+gputx_status gputx_server_create(gputx_db *db, const gputx_serve_config *cfg, gputx_server **out)
+{
+    if (!db || !out) return GPUTX_EINVAL;
+    *out = nullptr;
+    if (!db->dev.registered) return GPUTX_ESTATE;
+    gputx_server *s = new (std::nothrow) gputx_server();
+    if (!s) return GPUTX_ENOMEM;
+    s->db = db;
+    if (cfg) s->cfg = *cfg;
+    gputx_serve_config &c = s->cfg;
+    if (c.deadline_us <= 0) c.deadline_us = 1000;
+    if (c.max_bulk <= 0 || c.max_bulk > db->cfg.max_bulk) c.max_bulk = db->cfg.max_bulk;
+    if (c.max_inflight <= 0) c.max_inflight = 2;
+    if (c.max_inflight > 8) c.max_inflight = 8;
+    if (c.params_per_txn <= 0) c.params_per_txn = 2;
+    if (c.queue_capacity <= 0) c.queue_capacity = 1ll << 30;
+    if (c.strategy < GPUTX_KSET || c.strategy > GPUTX_AUTO) {
+        delete s;
+        return GPUTX_EINVAL;
+    }
+    s->P = c.params_per_txn;
+    s->R = db->dev.out_width;
+    s->ins_cap[0] = db->dev.hist_cap;
+    s->ins_cap[1] = db->dev.child_cap;
+    s->ins_cap[2] = db->dev.ord_cap;
+    s->ins_cap[3] = db->dev.ol_cap;
+    // rows already used by earlier bulks of this database
+    gtx::InsertBase cur{};
+    cudaStreamWaitEvent(db->stream, db->last_done, 0);
+    if (cudaMemcpyAsync(&cur, db->d_cursor, sizeof cur, cudaMemcpyDeviceToHost, db->stream) != cudaSuccess ||
+        cudaStreamSynchronize(db->stream) != cudaSuccess) {
+        delete s;
+        return GPUTX_ECUDA;
+    }
+    s->ins_used[0] = cur.hist;
+    s->ins_used[1] = cur.cf;
+    s->ins_used[2] = cur.ord;
+    s->ins_used[3] = cur.ol;
+    s->slots.resize(c.max_inflight);
+    for (Slot &sl : s->slots) {
+        const int64_t n = c.max_bulk;
+        bool ok = cudaHostAlloc((void **)&sl.h_type, sizeof(int32_t) * n, cudaHostAllocDefault) == cudaSuccess &&
+                  cudaHostAlloc((void **)&sl.h_ts, sizeof(int64_t) * n, cudaHostAllocDefault) == cudaSuccess &&
+                  cudaHostAlloc((void **)&sl.h_params, sizeof(int64_t) * n * s->P, cudaHostAllocDefault) ==
+                      cudaSuccess &&
+                  cudaHostAlloc((void **)&sl.h_status, sizeof(int32_t) * n, cudaHostAllocDefault) == cudaSuccess &&
+                  cudaHostAlloc((void **)&sl.h_values, sizeof(int64_t) * n * s->R, cudaHostAllocDefault) ==
+                      cudaSuccess &&
+                  cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            gputx_server_destroy(s);
+            return GPUTX_ENOMEM;
+        }
+    }
+    s->worker = std::thread(worker_main, s);
+    *out = s;
+    return GPUTX_OK;
+}
+
+gputx_status gputx_server_submit(gputx_server *s, const int32_t *type, const int64_t *params, size_t n,
+                                 const int64_t *arrival_ns, int64_t *first_id)
+{
+    if (!s || (n && (!type || !params))) return GPUTX_EINVAL;
+    const int64_t t = now_ns();
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->worker_status != GPUTX_OK) return s->worker_status;
+    // admission: the pool, the insert areas and free device memory
+    const int64_t queued = s->next_id - s->next_consume + s->inflight_txns;
+    if (queued + (int64_t)n > s->cfg.queue_capacity) {
+        s->refused += (int64_t)n;
+        return GPUTX_ENOMEM;
+    }
+    int64_t need[4] = {0, 0, 0, 0};
+    for (size_t i = 0; i < n; i++) {
+        int64_t q[4];
+        insert_need(s, type[i], params + i * s->P, q);
+        for (int k = 0; k < 4; k++) need[k] += q[k];
+    }
+    for (int k = 0; k < 4; k++)
+        if (need[k] && s->ins_used[k] + s->ins_reserved[k] + need[k] > s->ins_cap[k]) {
+            s->refused += (int64_t)n;
+            return GPUTX_ENOMEM;
+        }
+    if (s->cfg.min_free_bytes > 0) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && (int64_t)fr < s->cfg.min_free_bytes) {
+            s->refused += (int64_t)n;
+            return GPUTX_ENOMEM;
+        }
+    }
+    for (int k = 0; k < 4; k++) s->ins_reserved[k] += need[k];
+    const int64_t id0 = s->next_id;
+    s->p_type.insert(s->p_type.end(), type, type + n);
+    s->p_params.insert(s->p_params.end(), params, params + n * s->P);
+    for (size_t i = 0; i < n; i++) s->p_arrival.push_back(arrival_ns ? arrival_ns[i] : t);
+    if (s->first_arrival < 0 && n) s->first_arrival = arrival_ns ? arrival_ns[0] : t;
+    s->next_id += (int64_t)n;
+    s->r_status.resize(s->next_id, 0);
+    s->r_values.resize(s->next_id * s->R, 0);
+    s->r_complete.resize(s->next_id, 0);
+    s->r_done.resize(s->next_id, 0);
+    if (first_id) *first_id = id0;
+    s->cv.notify_all();
+    return GPUTX_OK;
+}
+
+gputx_status gputx_server_results(gputx_server *s, int64_t first_id, size_t n, int32_t *status, int64_t *values,
+                                  int64_t *complete_ns, size_t *n_done)
+{
+    if (!s || first_id < 0) return GPUTX_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (first_id + (int64_t)n > s->next_id) return GPUTX_EINVAL;
+    size_t done = 0;
+    for (size_t i = 0; i < n; i++) {
+        const int64_t id = first_id + (int64_t)i;
+        if (!s->r_done[id]) continue;
+        done++;
+        if (status) status[i] = s->r_status[id];
+        if (values) std::memcpy(values + i * s->R, &s->r_values[id * s->R], sizeof(int64_t) * s->R);
+        if (complete_ns) complete_ns[i] = s->r_complete[id];
+    }
+    if (n_done) *n_done = done;
+    return GPUTX_OK;
+}
+
+gputx_status gputx_server_drain(gputx_server *s)
+{
+    if (!s) return GPUTX_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    s->cv.notify_all();
+    s->flush = true;   // the pending tail goes out without waiting for its deadline
+    s->cv.notify_all();
+    while (s->completed < s->next_id && s->worker_status == GPUTX_OK) s->cv.wait_for(lk, std::chrono::milliseconds(1));
+    s->flush = false;
+    return s->worker_status;
+}
+
+gputx_status gputx_server_stats(gputx_server *s, gputx_serve_stats *st)
+{
+    if (!s || !st) return GPUTX_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    std::memset(st, 0, sizeof *st);
+    st->submitted = s->next_id;
+    st->completed = s->completed;
+    st->bulks = s->bulks;
+    st->max_bulk_seen = s->max_bulk_seen;
+    st->refused = s->refused;
+    st->p50_us = s->hist.quantile(0.50);
+    st->p99_us = s->hist.quantile(0.99);
+    st->mean_us = s->hist.count ? s->hist.sum_us / (double)s->hist.count : 0;
+    if (s->completed && s->last_complete > s->first_arrival)
+        st->txn_per_s = (double)s->completed / ((double)(s->last_complete - s->first_arrival) * 1e-9);
+    return GPUTX_OK;
+}
+
+const char *gputx_server_last_error(const gputx_server *s)
+{
+    return s ? s->worker_error.c_str() : "null server";
+}
+
+void gputx_server_destroy(gputx_server *s)
+{
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        s->cv.notify_all();
+    }
+    if (s->worker.joinable()) s->worker.join();
+    for (Slot &sl : s->slots) {
+        if (sl.bulk) gputx_free_bulk(sl.bulk);
+        if (sl.h_type) cudaFreeHost(sl.h_type);
+        if (sl.h_ts) cudaFreeHost(sl.h_ts);
+        if (sl.h_params) cudaFreeHost(sl.h_params);
+        if (sl.h_status) cudaFreeHost(sl.h_status);
+        if (sl.h_values) cudaFreeHost(sl.h_values);
+        if (sl.done) cudaEventDestroy(sl.done);
+    }
+    delete s;
+}
+
+}  // extern "C"

@@ -204,3 +204,25 @@ def test_full_size_config2(strategy, mode):
     h = g.read(G.TBL_DC_HISTORY)
     assert np.array_equal(h[np.argsort(h[:, 0])], o.history())
     g.close()
+
+
+@pytest.mark.parametrize("strategy,mode", [("kset", 0), ("kset", 1), ("tpl", 0), ("part", 0)])
+def test_back_to_back_bulks_without_sync(strategy, mode):
+    """Bulks executed one after another without waiting: each bulk's analysis
+    overlaps the previous bulk's execution on the device, yet they apply in
+    call order."""
+    g, o = make_pair(20, 200, 20000, 1 << 18)
+    bulks, handles, ts0 = [], [], 0
+    for k in range(6):
+        bulk = W.dc_bulk(7000 + 911 * k, 20000, 0.8, seed=300 + k, ts0=ts0)
+        ts0 += len(bulk["ts"])
+        bulks.append(bulk)
+        handles.append(g.submit_dict(bulk).execute(strategy, conflict_mode=mode))
+    for bulk, h in zip(bulks, handles):
+        st, out = h.results()
+        h.free()
+        ost, oout = o.execute(bulk, R=1)
+        assert np.array_equal(st, ost) and np.array_equal(out, oout)
+    gs, os_ = gpu_logical_state(g, dc=True), oracle_logical_state(o)
+    assert states_equal(gs, os_), state_diff(gs, os_)
+    g.close()
