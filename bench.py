@@ -217,10 +217,13 @@ def run_engine(args, rank, world, local_rank):
         e2e_total = float(t.item())
     e2e_value = n * K * world / e2e_total
 
-    sweep = None
-    if args.sweep and rank == 0:
+    sweep = serving = None
+    if rank == 0:
         db.close()
-        sweep = run_sweep(args, G, torch, dev, stream, flush)
+        if args.sweep:
+            sweep = run_sweep(args, G, torch, dev, stream, flush)
+        if args.serve:
+            serving = run_serving(args, G, torch, stream)
 
     if rank != 0:
         if dist:
@@ -266,6 +269,8 @@ def run_engine(args, rank, world, local_rank):
         line["cpu_baseline"] = cpu_baseline(args, bulks)
     if sweep is not None:
         line["sweep"] = sweep
+    if serving is not None:
+        line["serving"] = serving
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -315,6 +320,50 @@ def run_sweep(args, G, torch, dev, stream, flush):
                     rec.update({"ms": ms, "txn_per_s": n / (ms / 1e3), "depth": st["depth"],
                                 "w0": st["w0"], "exec_ms": st["ms_execute"], "sort_ms": st["ms_sort"]})
                     out.append(rec)
+    db.close()
+    return out
+
+
+def run_serving(args, G, torch, stream):
+    """Open-loop Poisson arrivals through the server: continuous batching
+    (several bulks in flight) against the plain per-bulk path (one bulk at a
+    time, closed every deadline).  Latency = result on the host - arrival."""
+    out = []
+    rates = [float(r) for r in args.serve_rates.split(",")]
+    deadlines = [int(d) for d in args.serve_deadlines_us.split(",")]
+    total = int(sum(rates) * args.serve_seconds * len(deadlines) * 2) + (1 << 22)
+    db = G.Database(dc=(BRANCHES, TELLERS, ACCOUNTS), history_capacity=total, max_bulk=1 << 20,
+                    stream=stream.cuda_stream)
+    db.register(G.DC_TYPES)
+    rng = np.random.default_rng(W.seed_for(5))
+    for rate in rates:
+        n = int(rate * args.serve_seconds)
+        bulk = W.dc_bulk(n, ACCOUNTS, args.theta, seed=W.seed_for(5, int(rate // 1e6)))
+        gaps = rng.exponential(1e9 / rate, size=n)
+        offs = np.cumsum(gaps).astype(np.int64)
+        for deadline in deadlines:
+            for label, inflight in (("continuous", 3), ("plain", 1)):
+                srv = G.Server(db, deadline_us=deadline, max_bulk=1 << 20, max_inflight=inflight,
+                               strategy=args.serve_strategy,
+                               conflict_mode=G.CONFLICT_ADD if args.mode == "add" else G.CONFLICT_PAPER)
+                t0 = G.gputx_clock_ns() + 2_000_000
+                arrivals = t0 + offs
+                i = 0
+                while i < n:
+                    now = G.gputx_clock_ns()
+                    j = int(np.searchsorted(arrivals, now, side="right"))
+                    if j > i:
+                        srv.submit(bulk["type"][i:j], bulk["params"][i:j], arrivals[i:j])
+                        i = j
+                    else:
+                        time.sleep(20e-6)
+                srv.drain()
+                st = srv.stats()
+                srv.close()
+                out.append({"offered_txn_per_s": rate, "deadline_us": deadline, "mode": label,
+                            "max_inflight": inflight, "txn": n, "p50_us": st["p50_us"], "p99_us": st["p99_us"],
+                            "mean_us": st["mean_us"], "txn_per_s": st["txn_per_s"], "bulks": st["bulks"],
+                            "max_bulk": st["max_bulk_seen"]})
     db.close()
     return out
 
@@ -392,6 +441,12 @@ def main():
     ap.add_argument("--cpu-baseline", dest="cpu_baseline", action="store_true", default=True)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-budget-s", type=float, default=10.0)
+    ap.add_argument("--serve", dest="serve", action="store_true", default=True)
+    ap.add_argument("--no-serve", dest="serve", action="store_false")
+    ap.add_argument("--serve-rates", default="1e6,5e6,20e6,50e6")
+    ap.add_argument("--serve-deadlines-us", default="1000,10000")
+    ap.add_argument("--serve-seconds", type=float, default=0.5)
+    ap.add_argument("--serve-strategy", default="kset", choices=["kset", "part", "tpl", "auto"])
     args = ap.parse_args()
     rank, world = env_int("RANK", 0), env_int("WORLD_SIZE", 1)
     local_rank = env_int("LOCAL_RANK", 0)
