@@ -276,6 +276,57 @@ gputx_status gputx_execute_kset_noalloc(gputx_db *db, const int64_t *ts, const i
                                         int conflict_mode, int32_t *status, int64_t *values);
 
 /* ------------------------------------------------------------------------ */
+/* Batched execution through captured CUDA graphs, with an online autotuner   */
+/* ------------------------------------------------------------------------ */
+/* A stream of transactions (uneven sizes, mixed types) runs as consecutive
+ * bulks of one size.  For each (bulk size, strategy, block shape) a
+ * fixed-capacity bulk's whole pipeline -- extraction, grouping sort, ranks,
+ * refinement rounds on the device, regrouping and one persistent K-SET launch
+ * (or the TPL kernel) -- is captured once in a CUDA graph and replayed for
+ * every bulk of that shape, shorter bulks padded with inactive transactions.
+ * With tune = 1 the stream's own first bulks run under different
+ * configurations, seeded by Algorithm 1 (Appendix D) on the first bulk's
+ * depth, 0-set and cross-partition count, and the fastest per transaction is
+ * kept.  Every transaction executes exactly once, in timestamp order, so
+ * tuning never changes results.  History rows are consumed per live
+ * transaction. */
+typedef struct gputx_batcher gputx_batcher;
+
+typedef struct {
+    int32_t tune;             /* 1 = choose strategy, bulk size, block shape */
+    int32_t strategy;         /* GPUTX_KSET or GPUTX_TPL when not tuning */
+    int32_t block_threads;    /* when not tuning (default 256) */
+    int32_t conflict_mode;    /* gputx_conflict_mode */
+    int64_t bulk_size;        /* transactions per bulk when not tuning (default 2^16) */
+    int64_t bulk_size_max;    /* largest bulk the tuner may pick (default: db max_bulk) */
+    int32_t params_per_txn;   /* parameter row width (default 2) */
+    int32_t reserved;
+} gputx_batch_config;
+
+typedef struct {
+    int32_t tuned;            /* 1 once the tuner settled */
+    int32_t strategy, block_threads, n_measured;
+    int64_t bulk_size, bulks_run;
+    int32_t measured_strategy[16], measured_block[16];
+    int64_t measured_bulk[16];
+    double measured_ns_per_txn[16];
+} gputx_batch_choice;
+
+/* ESTATE without registered types. */
+gputx_status gputx_batcher_create(gputx_db *db, const gputx_batch_config *cfg, gputx_batcher **out);
+
+/* Executes n transactions (host arrays, ts strictly increasing) and writes
+ * their results (host arrays status[n], values[n x output width]); returns
+ * after the last bulk finished.  Device errors as for gputx_sync_bulk. */
+gputx_status gputx_batcher_run(gputx_batcher *bt, const int64_t *ts, const int32_t *type, const int64_t *params,
+                               size_t n, int32_t *status, int64_t *values);
+
+/* The configuration in use and the tuner's measurements. */
+gputx_status gputx_batcher_choice(const gputx_batcher *bt, gputx_batch_choice *out);
+
+void gputx_batcher_destroy(gputx_batcher *bt);
+
+/* ------------------------------------------------------------------------ */
 /* Serving: a transaction pool and bulk generator over one database          */
 /* ------------------------------------------------------------------------ */
 /* Section 3.2: submitted transactions wait in a pool; the system periodically

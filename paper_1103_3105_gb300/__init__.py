@@ -45,7 +45,8 @@ EXPORTED = ("gputx_create_db", "gputx_destroy_db", "gputx_last_error", "gputx_re
             "gputx_output_width", "gputx_free_bulk", "gputx_version", "gputx_launch_count",
             "gputx_execute_kset_noalloc", "gputx_clock_ns", "gputx_server_create", "gputx_server_submit",
             "gputx_server_results", "gputx_server_drain", "gputx_server_stats",
-            "gputx_server_last_error", "gputx_server_destroy")
+            "gputx_server_last_error", "gputx_server_destroy", "gputx_batcher_create",
+            "gputx_batcher_run", "gputx_batcher_choice", "gputx_batcher_destroy")
 
 
 class GputxError(RuntimeError):
@@ -95,6 +96,27 @@ class ServeStats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BatchConfig(C.Structure):
+    _fields_ = [("tune", C.c_int32), ("strategy", C.c_int32), ("block_threads", C.c_int32),
+                ("conflict_mode", C.c_int32), ("bulk_size", C.c_int64), ("bulk_size_max", C.c_int64),
+                ("params_per_txn", C.c_int32), ("reserved", C.c_int32)]
+
+
+class BatchChoice(C.Structure):
+    _fields_ = [("tuned", C.c_int32), ("strategy", C.c_int32), ("block_threads", C.c_int32),
+                ("n_measured", C.c_int32), ("bulk_size", C.c_int64), ("bulks_run", C.c_int64),
+                ("measured_strategy", C.c_int32 * 16), ("measured_block", C.c_int32 * 16),
+                ("measured_bulk", C.c_int64 * 16), ("measured_ns_per_txn", C.c_double * 16)]
+
+    def as_dict(self):
+        k = self.n_measured
+        return {"tuned": bool(self.tuned), "strategy": self.strategy, "block_threads": self.block_threads,
+                "bulk_size": self.bulk_size, "bulks_run": self.bulks_run,
+                "measured": [{"strategy": self.measured_strategy[i], "block": self.measured_block[i],
+                              "bulk": self.measured_bulk[i], "ns_per_txn": self.measured_ns_per_txn[i]}
+                             for i in range(k)]}
+
+
 class ExecOpts(C.Structure):
     _fields_ = [("conflict_mode", C.c_int32), ("block_threads", C.c_int32),
                 ("part_size", C.c_int32), ("timing", C.c_int32), ("kset_launch", C.c_int32),
@@ -137,6 +159,10 @@ def lib():
             "gputx_server_stats": ([p, C.POINTER(ServeStats)], C.c_int),
             "gputx_server_last_error": ([p], C.c_char_p),
             "gputx_server_destroy": ([p], None),
+            "gputx_batcher_create": ([p, C.POINTER(BatchConfig), C.POINTER(p)], C.c_int),
+            "gputx_batcher_run": ([p, p, p, p, sz, p, p], C.c_int),
+            "gputx_batcher_choice": ([p, C.POINTER(BatchChoice)], C.c_int),
+            "gputx_batcher_destroy": ([p], None),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -424,6 +450,63 @@ class Server:
     def close(self):
         if self.h:
             gputx_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --- batched execution through captured graphs -----------------------------------
+def gputx_batcher_create(db, cfg: BatchConfig):
+    out = C.c_void_p()
+    _check(db, lib().gputx_batcher_create(db, C.byref(cfg), C.byref(out)))
+    return out
+
+
+def gputx_batcher_run(db, bt, ts, type_, params, status, values):
+    _check(db, lib().gputx_batcher_run(bt, _ptr(ts), _ptr(type_), _ptr(params), len(ts), _ptr(status),
+                                       _ptr(values)))
+
+
+def gputx_batcher_choice(bt) -> dict:
+    c = BatchChoice()
+    lib().gputx_batcher_choice(bt, C.byref(c))
+    return c.as_dict()
+
+
+def gputx_batcher_destroy(bt):
+    lib().gputx_batcher_destroy(bt)
+
+
+class Batcher:
+    """Consecutive graph-captured bulks with an optional online autotuner."""
+
+    def __init__(self, db: Database, tune=True, strategy="kset", block_threads=256,
+                 conflict_mode=CONFLICT_PAPER, bulk_size=0, bulk_size_max=0, params_per_txn=2):
+        s = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
+        cfg = BatchConfig(int(tune), s, block_threads, conflict_mode, bulk_size, bulk_size_max,
+                          params_per_txn, 0)
+        self.db = db
+        self.h = gputx_batcher_create(db.h, cfg)
+
+    def run(self, ts, type_, params):
+        ts = np.ascontiguousarray(ts, dtype=np.int64)
+        type_ = np.ascontiguousarray(type_, dtype=np.int32)
+        params = np.ascontiguousarray(params, dtype=np.int64)
+        st = np.zeros(len(ts), dtype=np.int32)
+        vals = np.zeros((len(ts), self.db.width), dtype=np.int64)
+        gputx_batcher_run(self.db.h, self.h, ts, type_, params, st, vals)
+        return st, vals
+
+    def choice(self) -> dict:
+        return gputx_batcher_choice(self.h)
+
+    def close(self):
+        if self.h:
+            gputx_batcher_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -2,6 +2,7 @@
 // 1-2, Appendix D): basic-operation extraction, grouping by data item with a
 // radix sort, per-group ranks, transaction depths (k-set levels), regrouping
 // by (level, type), insert slots, partition ids.
+#include <cooperative_groups.h>
 #include <cstdio>
 
 #include "engine.h"
@@ -23,10 +24,10 @@ inline unsigned grid_for(int64_t n, int block = TB)
 // ---------------------------------------------------------------------------
 // bulk begin / finish: insert bases from the device cursors
 // ---------------------------------------------------------------------------
-__global__ void begin_kernel(const InsertBase *cursor, BulkCtl *ctl, int64_t hist_rows)
+__global__ void begin_kernel(const InsertBase *cursor, BulkCtl *ctl, int64_t hist_rows, bool live_rows)
 {
     ctl->base = *cursor;
-    ctl->total.hist = hist_rows;
+    ctl->total.hist = live_rows ? (int64_t)ctl->n_live : hist_rows;
 }
 
 __global__ void finish_kernel(InsertBase *cursor, const BulkCtl *ctl)
@@ -52,7 +53,14 @@ struct ExtractArgs {
     int part_size;
     uint32_t *pid_key, *pid_val;   // PART: partition id and txn per transaction (or null)
     bool write_ops;
+    bool sentinel_fill;            // fill unused slots with padding operations
+    uint32_t sentinel_key;         // object id above every real one
 };
+
+__device__ __forceinline__ bool txn_padding(const DevBulk &b, int64_t t)
+{
+    return b.n_live && t >= (int64_t)*b.n_live;
+}
 
 __device__ __forceinline__ bool txn_valid(const DevDB &db, const DevBulk &b, int64_t t)
 {
@@ -79,16 +87,24 @@ __global__ void extract_kernel(ExtractArgs a)
     if (t < a.b.n) {
         const int64_t *p = a.b.params + t * a.b.P;
         const int64_t off = a.op_off ? (int64_t)a.op_off[t] : t * a.uniform_k;   // used when writing
-        const bool ok = txn_valid(a.db, a.b, t);
+        const bool pad = txn_padding(a.b, t);
+        const bool ok = pad || txn_valid(a.db, a.b, t);
         uint32_t obj[MAX_OPS], root[MAX_OPS];
         uint8_t cls[MAX_OPS];
         int k = 0;
-        if (ok) {
+        if (ok && !pad) {
             k = access_set(a.db, a.b.type[t], p, a.mode, obj, cls, root);
-        } else {
+        } else if (!ok) {
             set_err(&a.ctl->err, ERR_INVAL);
         }
-        if (a.write_ops && a.op_off == nullptr) {
+        if (a.write_ops && a.sentinel_fill) {
+            // padding operations after the real ones: they sort past every
+            // real group and every consumer skips their payload
+            for (int j = k; j < a.uniform_k; j++) {
+                a.keys[off + j] = a.sentinel_key;
+                a.vals[off + j] = OP_SENTINEL;
+            }
+        } else if (a.write_ops && a.op_off == nullptr) {
             // uniform layout: always fill K slots (dummy reads on object 0 for
             // an invalid transaction; the bulk will not execute)
             for (int j = k; j < a.uniform_k; j++) { obj[j] = 0; cls[j] = CLS_R; root[j] = 0; }
@@ -147,6 +163,7 @@ struct RankMode {
     }
     __device__ void output(int64_t i, uint64_t s) const
     {
+        if (sv[i] == OP_SENTINEL) return;
         const uint32_t rank = DualSeg::v1(s);
         const uint32_t txn = sv[i] >> 7;
         atomicMax(&level[txn], rank);
@@ -175,6 +192,7 @@ struct TicketMode {
     __device__ void output(int64_t i, uint64_t s) const
     {
         const uint32_t v = sv[i];
+        if (v == OP_SENTINEL) return;
         const uint32_t txn = v >> 7, j = (v >> 2) & 31u;
         const int64_t slot = (op_off ? (int64_t)op_off[txn] : (int64_t)txn * uniform_k) + j;
         lock_key[slot] = sk[i];
@@ -191,7 +209,7 @@ __global__ void runmax_kernel(const uint32_t *sv, const uint32_t *rid, const uin
                               int64_t m, const uint32_t *err)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= m || *err) return;
+    if (i >= m || *err || sv[i] == OP_SENTINEL) return;
     atomicMax(&runmax[rid[i] & 0x7fffffffu], level[sv[i] >> 7]);
 }
 
@@ -200,7 +218,7 @@ __global__ void relax_kernel(const uint32_t *sv, const uint32_t *rid, const uint
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     bool grew = false;
-    if (i < m && !ctl->err) {
+    if (i < m && !ctl->err && sv[i] != OP_SENTINEL) {
         const uint32_t r = rid[i];
         if (!(r & 0x80000000u)) {
             const uint32_t cand = runmax[(r & 0x7fffffffu) - 1u] + 1u;
@@ -208,6 +226,46 @@ __global__ void relax_kernel(const uint32_t *sv, const uint32_t *rid, const uint
         }
     }
     if (__any_sync(0xffffffffu, grew) && (threadIdx.x & 31) == 0) ctl->changed = 1;
+}
+
+// All refinement rounds in one cooperative launch (no host round trips): a
+// grid barrier separates clearing run maxima, gathering them, and relaxing
+// depths.  Round r reports growth in changed_r[r % 3]; the flag of round r+1
+// is cleared during round r, after every thread has read it two rounds ago.
+__global__ void __launch_bounds__(256) fixpoint_coop_kernel(const uint32_t *sv, const uint32_t *rid,
+                                                           uint32_t *runmax, uint32_t *level, BulkCtl *ctl,
+                                                           int64_t m, uint32_t max_rounds)
+{
+    cooperative_groups::grid_group g = cooperative_groups::this_grid();
+    if (ctl->err) return;   // set before this launch only: every block returns
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    uint32_t r = 0;
+    bool grew_any = true;
+    for (; r < max_rounds && grew_any; r++) {
+        for (int64_t i = i0; i < m; i += stride) runmax[i] = 0;
+        if (i0 == 0) ctl->changed_r[(r + 1) % 3] = 0;
+        g.sync();
+        for (int64_t i = i0; i < m; i += stride) {
+            const uint32_t v = sv[i];
+            if (v != OP_SENTINEL) atomicMax(&runmax[rid[i] & 0x7fffffffu], level[v >> 7]);
+        }
+        g.sync();
+        bool grew = false;
+        for (int64_t i = i0; i < m; i += stride) {
+            const uint32_t v = sv[i], rr = rid[i];
+            if (v == OP_SENTINEL || (rr & 0x80000000u)) continue;
+            const uint32_t cand = runmax[(rr & 0x7fffffffu) - 1u] + 1u;
+            grew |= atomicMax(&level[v >> 7], cand) < cand;
+        }
+        if (__any_sync(0xffffffffu, grew) && (threadIdx.x & 31) == 0) atomicOr(&ctl->changed_r[r % 3], 1u);
+        g.sync();
+        grew_any = *(volatile uint32_t *)&ctl->changed_r[r % 3] != 0;
+    }
+    if (i0 == 0) {
+        ctl->rounds = r;
+        if (grew_any) set_err(&ctl->err, ERR_TIMEOUT);   // no fixpoint within the bound
+    }
 }
 
 // d and w0 (Appendix D structural parameters)
@@ -233,11 +291,16 @@ __global__ void level_stats_kernel(const uint32_t *level, int64_t n, BulkCtl *ct
 // a6: regroup by (level, type) -- Appendix D's grouping by type, per level
 // ---------------------------------------------------------------------------
 __global__ void regroup_keys_kernel(const uint32_t *level, const int32_t *type, int64_t n, int tbits,
-                                    uint32_t *keys, uint32_t *vals)
+                                    uint32_t *keys, uint32_t *vals, const uint32_t *n_live)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n) return;
-    keys[t] = (level[t] << tbits) | (tbits ? (uint32_t)type[t] : 0u);
+    if (n_live && t >= (int64_t)*n_live) {
+        keys[t] = (uint32_t)n << tbits;   // padding: past every real level
+    } else {
+        const int32_t ty = type[t];
+        keys[t] = (level[t] << tbits) | (tbits && ty > 0 ? (uint32_t)ty : 0u);
+    }
     vals[t] = (uint32_t)t;
 }
 
@@ -260,8 +323,10 @@ struct ChunkMode {
     const uint32_t *level_off;
     uint32_t *chunk_off;
     uint32_t block;
+    const BulkCtl *ctl;   // levels = depth + 1, read on the device
     __device__ uint64_t element(int64_t k) const
     {
+        if (k > (int64_t)ctl->depth) return 0;
         const uint32_t w = level_off[k + 1] - level_off[k];
         return DualSeg::make(0, 0, 0, (w + block - 1) / block);
     }
@@ -272,11 +337,12 @@ struct ChunkMode {
     }
 };
 
-__global__ void chunk_level_kernel(const uint32_t *chunk_off, int64_t levels, uint32_t *chunk_level, int64_t cap,
-                                   const uint32_t *err)
+__global__ void chunk_level_kernel(const uint32_t *chunk_off, const BulkCtl *ctl, uint32_t *chunk_level,
+                                   int64_t cap, const uint32_t *err)
 {
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (*err) return;
+    const int64_t levels = (int64_t)ctl->depth + 1;
     const uint32_t nchunks = chunk_off[levels];
     if (c >= cap || c >= nchunks) return;
     // largest k with chunk_off[k] <= c
@@ -382,6 +448,7 @@ inline DevBulk dev_bulk(gputx_bulk *b, int mode)
     d.rec_ts = b->sc.rec_ts;
     d.rec_type = b->sc.rec_type;
     d.rec_t = b->sc.rec_t;
+    d.n_live = b->graph ? &b->ctl->n_live : nullptr;
     d.conflict_mode = mode;
     return d;
 }
@@ -419,7 +486,7 @@ cudaError_t launch_gather(gputx_bulk *b, const uint32_t *order)
 cudaError_t launch_begin(gputx_bulk *b)
 {
     const bool dc = (b->db->dev.registered & 1u) != 0;
-    begin_kernel<<<1, 1, 0, b->stream>>>(b->db->d_cursor, b->ctl, dc ? b->n : 0);
+    begin_kernel<<<1, 1, 0, b->stream>>>(b->db->d_cursor, b->ctl, dc ? b->n : 0, dc && b->graph);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -449,7 +516,10 @@ cudaError_t launch_extract(gputx_bulk *b, int mode, int part_size, uint32_t *pid
     a.pid_key = pid_key;
     a.pid_val = pid_val;
     a.write_ops = write_ops;
-    if (!db->uniform_k && write_ops) {
+    a.sentinel_fill = b->graph;
+    a.sentinel_key = db->dev.n_objects;
+    if (b->graph) a.uniform_k = db->kmax;
+    if (!db->uniform_k && write_ops && !b->graph) {
         // counts into level[] (free until the rank scan), then offsets
         count_ops_kernel<<<grid_for(b->n), TB, 0, s>>>(db->dev, a.b, b->ctl, b->sc.level);
         count_launches(1);
@@ -516,8 +586,9 @@ cudaError_t launch_rank_scan(gputx_bulk *b, const uint32_t *sk, const uint32_t *
 
 cudaError_t launch_ticket_scan(gputx_bulk *b, const uint32_t *sk, const uint32_t *sv, int64_t m)
 {
-    TicketMode tm{sk, sv, b->sc.lock_key, b->sc.lock_ticket, b->db->uniform_k ? nullptr : b->sc.op_off,
-                  b->db->uniform_k};
+    const bool fixed = b->db->uniform_k || b->graph;
+    TicketMode tm{sk, sv, b->sc.lock_key, b->sc.lock_ticket, fixed ? nullptr : b->sc.op_off,
+                  b->graph ? b->db->kmax : b->db->uniform_k};
     return run_scan(b, tm, m, 2);
 }
 
@@ -536,6 +607,33 @@ cudaError_t launch_fixpoint_round(gputx_bulk *b, const uint32_t *sv, int64_t m)
     return cudaGetLastError();
 }
 
+cudaError_t launch_fixpoint_device(gputx_bulk *b, const uint32_t *sv, int64_t m)
+{
+    if (m == 0) return cudaSuccess;
+    static int blocks_per_sm = 0;
+    if (!blocks_per_sm) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, fixpoint_coop_kernel, 256, 0);
+        if (blocks_per_sm < 1) blocks_per_sm = 1;
+    }
+    int64_t grid = (int64_t)b->db->num_sms * blocks_per_sm;
+    const int64_t need = (m + 255) / 256;
+    if (grid > need) grid = need;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.stream = b->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const uint32_t max_rounds = (uint32_t)(b->n + 2 > 0xffffffffll ? 0xffffffffll : b->n + 2);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, fixpoint_coop_kernel, sv, (const uint32_t *)b->sc.rid, b->sc.runmax,
+                                       b->sc.level, b->ctl, m, max_rounds);
+    count_launches(1);
+    return e;
+}
+
 cudaError_t launch_level_stats(gputx_bulk *b)
 {
     if (b->n == 0) return cudaSuccess;
@@ -551,7 +649,7 @@ cudaError_t launch_regroup_keys(gputx_bulk *b, uint32_t *keys, uint32_t *vals)
 {
     if (b->n == 0) return cudaSuccess;
     regroup_keys_kernel<<<grid_for(b->n), TB, 0, b->stream>>>(b->sc.level, b->type, b->n, b->db->tbits,
-                                                                   keys, vals);
+                                                               keys, vals, b->graph ? &b->ctl->n_live : nullptr);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -563,11 +661,12 @@ cudaError_t launch_level_tables(gputx_bulk *b, const uint32_t *skeys, int64_t de
     level_off_kernel<<<grid_for(b->n), TB, 0, s>>>(skeys, b->n, b->db->tbits, b->sc.level_off, &b->ctl->err);
     count_launches(1);
     if (!chunks) return cudaGetLastError();
-    const int64_t levels = depth + 1;
-    ChunkMode cm{b->sc.level_off, b->sc.chunk_off, (uint32_t)block};
+    // graph bulks do not know their depth on the host: scan every possible level
+    const int64_t levels = b->graph ? b->n : depth + 1;
+    ChunkMode cm{b->sc.level_off, b->sc.chunk_off, (uint32_t)block, b->ctl};
     cudaError_t e = run_scan(b, cm, levels, 3);
     if (e) return e;
-    chunk_level_kernel<<<grid_for(b->sc.chunk_cap), TB, 0, s>>>(b->sc.chunk_off, levels, b->sc.chunk_level,
+    chunk_level_kernel<<<grid_for(b->sc.chunk_cap), TB, 0, s>>>(b->sc.chunk_off, b->ctl, b->sc.chunk_level,
                                                                 b->sc.chunk_cap, &b->ctl->err);
     count_launches(1);
     return cudaGetLastError();

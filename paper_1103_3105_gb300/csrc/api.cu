@@ -245,6 +245,8 @@ gputx_status read_ctl(gputx_bulk *b)
 
 }  // namespace
 
+size_t gtx_carve_bulk(gputx_bulk *b, char *base, bool device_inputs) { return carve_bulk(b, base, device_inputs); }
+
 extern "C" {
 
 const char *gputx_version(void) { return "gputx-gb300 0.1 (sm_103a)"; }
@@ -350,7 +352,7 @@ gputx_status gputx_create_db(const gputx_schema_desc *schema, const gputx_config
         return GPUTX_EINVAL;
     }
     d.n_objects = (uint32_t)o;
-    db->obj_bits = std::max(1, bits_for(o ? o - 1 : 0));
+    db->obj_bits = std::max(1, bits_for(o));   // covers the padding key o as well
 
     gputx_status st = GPUTX_OK;
 #define TRY(x)                         \
@@ -922,17 +924,7 @@ gputx_status gputx_execute(gputx_db *db, gputx_bulk *b, int strategy, const gput
     if (strategy == GPUTX_KSET || strategy == GPUTX_AUTO) {
         if ((st = run_kset_analysis(b, mode, part_size, sk, sv, ak, av, m))) return st;
         CK(launch_rank_scan(b, sk, sv, m, db->need_fixpoint), "rank");
-        if (db->need_fixpoint) {
-            for (int round = 0; round < 1 << 20; round++) {
-                CK(launch_fixpoint_round(b, sv, m), "fixpoint");
-                uint32_t changed = 0, err = 0;
-                CK(cudaMemcpyAsync(&changed, &b->ctl->changed, 4, cudaMemcpyDeviceToHost, s), "fixpoint");
-                CK(cudaMemcpyAsync(&err, &b->ctl->err, 4, cudaMemcpyDeviceToHost, s), "fixpoint");
-                CK(cudaStreamSynchronize(s), "fixpoint");
-                b->fixpoint_rounds++;
-                if (!changed || err) break;
-            }
-        }
+        if (db->need_fixpoint) CK(launch_fixpoint_device(b, sv, m), "fixpoint");
         CK(launch_level_stats(b), "stats");
         if ((st = read_ctl(b))) return st;
         if (b->host_ctl.err) {
@@ -1044,7 +1036,7 @@ gputx_status gputx_sync_bulk(gputx_bulk *b, gputx_exec_stats *stats)
         stats->depth = b->host_ctl.depth;
         stats->w0 = b->host_ctl.w0;
         stats->cross = b->host_ctl.cross;
-        stats->fixpoint_rounds = b->fixpoint_rounds;
+        stats->fixpoint_rounds = b->host_ctl.rounds;
         if (b->timing) {
             float ms = 0;
             if (!cudaEventElapsedTime(&ms, b->ev[0], b->ev[3])) stats->ms_analysis = ms;
@@ -1182,16 +1174,7 @@ extern "C" gputx_status gputx_execute_kset_noalloc(gputx_db *db, const int64_t *
     uint32_t *sk = b.sc.keys_a, *sv = b.sc.vals_a, *ak = b.sc.keys_b, *av = b.sc.vals_b;
     CK(launch_sort(&b, sk, sv, ak, av, m, db->obj_bits), "sort");
     CK(launch_rank_scan(&b, sk, sv, m, db->need_fixpoint), "rank");
-    if (db->need_fixpoint) {
-        for (int round = 0; round < 1 << 20; round++) {
-            CK(launch_fixpoint_round(&b, sv, m), "fixpoint");
-            uint32_t changed = 0, err = 0;
-            CK(cudaMemcpyAsync(&changed, &b.ctl->changed, 4, cudaMemcpyDeviceToHost, s), "fixpoint");
-            CK(cudaMemcpyAsync(&err, &b.ctl->err, 4, cudaMemcpyDeviceToHost, s), "fixpoint");
-            CK(cudaStreamSynchronize(s), "fixpoint");
-            if (!changed || err) break;
-        }
-    }
+    if (db->need_fixpoint) CK(launch_fixpoint_device(&b, sv, m), "fixpoint");
     CK(launch_level_stats(&b), "stats");
     if ((st = read_ctl(&b))) return st;
     if (b.host_ctl.err) return bulk_error(db, b.host_ctl.err);

@@ -115,8 +115,13 @@ struct DevBulk {
     const int64_t *rec_params, *rec_ts;
     const int32_t *rec_type;
     const uint32_t *rec_t;
+    // fixed-capacity (graph) bulks: transactions at t >= *n_live are padding
+    // (no operations, never executed); null = every transaction is live
+    const uint32_t *n_live;
     int conflict_mode;
 };
+
+constexpr uint32_t OP_SENTINEL = 0xffffffffu;   // payload of a padding operation
 
 // ---------------------------------------------------------------------------
 // memory-model helpers

@@ -19,9 +19,11 @@ struct BulkCtl {
     uint32_t changed;      // fixpoint: a level grew in the last round
     uint32_t npart;        // PART: non-empty partitions
     uint32_t claim;        // executors: next chunk to claim
-    uint32_t pad;
+    uint32_t n_live;       // fixed-capacity bulks: live transactions (the rest pad)
     InsertBase base;       // where this bulk's inserts start (copied from the cursor)
     InsertBase total;      // inserts this bulk reserves
+    uint32_t changed_r[3]; // refinement rounds run on the device: rotating per-round flags
+    uint32_t rounds;       // refinement rounds taken
 };
 
 // Scratch carved from one per-bulk allocation.
@@ -97,6 +99,8 @@ struct gputx_bulk {
     gtx::Scratch sc{};
     bool executed = false;
     bool synced = false;
+    bool graph = false;    // fixed capacity, padded with inactive transactions,
+                           // no host synchronisation (capturable in a CUDA graph)
     int strategy_run = -1;
     int fallback = 0;
     int64_t fixpoint_rounds = 0;
@@ -117,6 +121,7 @@ cudaError_t launch_sort(gputx_bulk *b, uint32_t *&keys, uint32_t *&vals, uint32_
 cudaError_t launch_rank_scan(gputx_bulk *b, const uint32_t *sk, const uint32_t *sv, int64_t m, bool want_rid);
 cudaError_t launch_ticket_scan(gputx_bulk *b, const uint32_t *sk, const uint32_t *sv, int64_t m);
 cudaError_t launch_fixpoint_round(gputx_bulk *b, const uint32_t *sv, int64_t m);
+cudaError_t launch_fixpoint_device(gputx_bulk *b, const uint32_t *sv, int64_t m);
 cudaError_t launch_level_stats(gputx_bulk *b);
 cudaError_t launch_regroup_keys(gputx_bulk *b, uint32_t *keys, uint32_t *vals);
 cudaError_t launch_level_tables(gputx_bulk *b, const uint32_t *skeys, int64_t depth, int block, bool chunks);

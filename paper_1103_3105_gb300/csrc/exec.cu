@@ -131,7 +131,8 @@ __global__ void __launch_bounds__(1024, 1) kset_narrow_kernel(LevelArgs a)
 __global__ void kset_kernel(KsetArgs a)
 {
     __shared__ uint32_t s_k, s_start, s_cnt, s_stop;
-    const uint32_t nchunks = a.chunk_off[a.levels];
+    const int64_t levels = (int64_t)a.ctl->depth + 1;   // from the analysis, on the device
+    const uint32_t nchunks = a.chunk_off[levels];
     const int64_t hb = a.ctl->base.hist;
     while (true) {
         if (threadIdx.x == 0) {
@@ -220,6 +221,8 @@ struct TplArgs {
     int uniform_k;
     uint64_t spin_limit_ns;
     bool atomic_add;
+    bool graph;          // fixed-capacity bulk: K slots per transaction, only the
+                         // first op_count are real; padding transactions skipped
 };
 
 __global__ void tpl_kernel(TplArgs a)
@@ -236,9 +239,11 @@ __global__ void tpl_kernel(TplArgs a)
         const int64_t start = (int64_t)s_c * blockDim.x;
         if (s_stop || start >= n) break;
         const int64_t t = start + threadIdx.x;
-        if (t < n) {
+        if (t < n && !(a.b.n_live && t >= (int64_t)*a.b.n_live)) {
             const int64_t off = a.op_off ? (int64_t)a.op_off[t] : t * a.uniform_k;
-            const int cnt = a.op_off ? (int)(a.op_off[t + 1] - a.op_off[t]) : a.uniform_k;
+            const int cnt = a.op_off ? (int)(a.op_off[t + 1] - a.op_off[t])
+                                     : (a.graph ? op_count(a.db, a.b.type[t], a.b.params + t * a.b.P)
+                                                : a.uniform_k);
             const TxnView v = view_of(a.b, (uint32_t)t, hb);
             prefetch_txn(a.db, v);
             bool ok = true;
@@ -307,10 +312,10 @@ cudaError_t launch_kset(gputx_bulk *b, const uint32_t *order, int64_t nchunks, i
     a.chunk_off = b->sc.chunk_off;
     a.chunk_level = b->sc.chunk_level;
     a.done = b->sc.done;
-    a.levels = (int64_t)b->host_ctl.depth + 1;
+    a.levels = 0;
     a.spin_limit_ns = (uint64_t)db->cfg.spin_limit_ns;
     a.atomic_add = atomic_add;
-    cudaError_t e = cudaMemsetAsync(b->sc.done, 0, (size_t)a.levels * sizeof(uint32_t), b->stream);
+    cudaError_t e = cudaMemsetAsync(b->sc.done, 0, (size_t)(b->n + 1) * sizeof(uint32_t), b->stream);
     if (e) return e;
     e = cudaMemsetAsync(&b->ctl->claim, 0, sizeof(uint32_t), b->stream);
     if (e) return e;
@@ -417,9 +422,10 @@ cudaError_t launch_tpl(gputx_bulk *b, int block, bool atomic_add)
     a.ctl = b->ctl;
     a.lock_key = b->sc.lock_key;
     a.lock_ticket = b->sc.lock_ticket;
-    a.op_off = db->uniform_k ? nullptr : b->sc.op_off;
+    a.op_off = (db->uniform_k || b->graph) ? nullptr : b->sc.op_off;
     a.done = db->d_done;
-    a.uniform_k = db->uniform_k;
+    a.uniform_k = b->graph ? db->kmax : db->uniform_k;
+    a.graph = b->graph;
     a.spin_limit_ns = (uint64_t)db->cfg.spin_limit_ns;
     a.atomic_add = atomic_add;
     cudaError_t e = cudaMemsetAsync(&b->ctl->claim, 0, sizeof(uint32_t), b->stream);
