@@ -105,6 +105,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def replica_throughput(units_local: float, seconds_local: float, dist=None, device=None) -> float:
+    """Whole-job throughput of independent replicas (the path does not shard:
+    every rank runs its own database and bulks, no data-path collective).
+    Units add up over ranks; time is the slowest rank's (max over ranks)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return units_local / seconds_local
+    import torch
+    t = torch.tensor([seconds_local, units_local], dtype=torch.float64, device=device)
+    secs = t[:1].clone()
+    units = t[1:].clone()
+    dist.all_reduce(secs, op=dist.ReduceOp.MAX)
+    dist.all_reduce(units, op=dist.ReduceOp.SUM)
+    return float(units.item()) / float(secs.item())
+
+
 def measured_peak_hbm():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -181,11 +196,8 @@ def run_engine(args, rank, world, local_rank):
     launches = G.gputx_launch_count() - launches0
     # count only the engine's kernels: the L2 flushes are torch's
     total_ms = sum(times)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = n * K * world / (total_ms / 1e3)
+    value = replica_throughput(n * K, total_ms / 1e3, dist, dev)
+    total_ms = n * K * world / value * 1e3   # the slowest rank's time
 
     # end to end through the public API with host buffers: H2D + D2H inside
     pinned = []
@@ -210,20 +222,17 @@ def run_engine(args, rank, world, local_rank):
         b.results(st_h.numpy(), out_h.numpy())
         e2e_times.append(time.perf_counter() - t0)
         b.free()
-    e2e_total = sum(e2e_times)
-    if dist:
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = n * K * world / e2e_total
+    e2e_value = replica_throughput(n * K, sum(e2e_times), dist, dev)
 
-    sweep = serving = None
+    sweep = serving = batched = None
     if rank == 0:
         db.close()
         if args.sweep:
             sweep = run_sweep(args, G, torch, dev, stream, flush)
         if args.serve:
             serving = run_serving(args, G, torch, stream)
+        if args.batched:
+            batched = run_batched(args, G, torch, stream)
 
     if rank != 0:
         if dist:
@@ -271,6 +280,8 @@ def run_engine(args, rank, world, local_rank):
         line["sweep"] = sweep
     if serving is not None:
         line["serving"] = serving
+    if batched is not None:
+        line["batched"] = batched
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -368,6 +379,60 @@ def run_serving(args, G, torch, stream):
     return out
 
 
+def run_batched(args, G, torch, stream):
+    """Order-entry stream of uneven bulks (64 warehouses x 10 districts x
+    3,000 customers, 100,000 items): the graph batcher with its autotuner
+    against the plain per-bulk K-SET path.  Host arrays in and out (H2D and
+    D2H inside the timing) for both."""
+    n_wh, n_items = 64, 100_000
+    init = W.oe_tables(n_wh, n_items=n_items, seed=W.seed_for(4))
+    rng = np.random.default_rng(W.seed_for(4, 1))
+    sizes, total = [], 0
+    while total < args.batch_txns:
+        k = int(2 ** rng.uniform(10, 21))
+        sizes.append(k)
+        total += k
+    stream_bulk = W.oe_bulk(total, n_wh, n_items=n_items, seed=W.seed_for(4, 2))
+    out = {"workload": f"order-entry {n_wh} warehouses, {n_items} items, {len(sizes)} bulks of "
+                       f"2^10..2^21 transactions, {total} in all", "txn": total}
+    for label in ("plain_kset", "batched_tuned"):
+        cap = 2 * total + (1 << 22)
+        db = G.Database(oe=(n_wh, n_items), order_capacity=cap, orderline_capacity=cap * 15,
+                        max_bulk=1 << 21, stream=stream.cuda_stream)
+        db.register(G.OE_TYPES)
+        for t, rows in W.oe_rows(init).items():
+            db.load(t, rows)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if label == "plain_kset":
+            i = 0
+            for k in sizes:
+                b = db.submit(stream_bulk["ts"][i:i + k], stream_bulk["type"][i:i + k],
+                              stream_bulk["params"][i:i + k])
+                b.execute("kset", conflict_mode=G.CONFLICT_ADD if args.mode == "add" else G.CONFLICT_PAPER)
+                b.results()
+                b.free()
+                i += k
+            choice = None
+        else:
+            bt = G.Batcher(db, tune=True, params_per_txn=W.OE_PARAMS, bulk_size_max=1 << 21,
+                           conflict_mode=G.CONFLICT_ADD if args.mode == "add" else G.CONFLICT_PAPER)
+            bt.run(stream_bulk["ts"], stream_bulk["type"], stream_bulk["params"])
+            choice = bt.choice()
+            bt.close()
+        dt = time.perf_counter() - t0
+        out[label] = {"txn_per_s": total / dt, "seconds": dt}
+        if choice is not None:
+            names = {G.KSET: "kset", G.TPL: "tpl"}
+            out[label]["choice"] = {"strategy": names.get(choice["strategy"]), "bulk": choice["bulk_size"],
+                                    "block": choice["block_threads"],
+                                    "measured": [{"strategy": names.get(m["strategy"]), "bulk": m["bulk"],
+                                                  "block": m["block"], "ns_per_txn": m["ns_per_txn"]}
+                                                 for m in choice["measured"]]}
+        db.close()
+    return out
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline leg and reference arm)
 # ---------------------------------------------------------------------------
@@ -447,6 +512,9 @@ def main():
     ap.add_argument("--serve-deadlines-us", default="1000,10000")
     ap.add_argument("--serve-seconds", type=float, default=0.5)
     ap.add_argument("--serve-strategy", default="kset", choices=["kset", "part", "tpl", "auto"])
+    ap.add_argument("--batched", dest="batched", action="store_true", default=True)
+    ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--batch-txns", type=int, default=3_000_000)
     args = ap.parse_args()
     rank, world = env_int("RANK", 0), env_int("WORLD_SIZE", 1)
     local_rank = env_int("LOCAL_RANK", 0)
