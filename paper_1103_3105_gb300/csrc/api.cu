@@ -999,7 +999,7 @@ gputx_status gputx_execute(gputx_db *db, gputx_bulk *b, int strategy, const gput
             CK(launch_gather(b, pv), "gather");
             CK(begin_tail(b), "order");
             if (b->timing) cudaEventRecord(b->ev[3], s);
-            CK(launch_part(b, pk, 128), "part execute");
+            CK(launch_part(b, pk, 128, (roots + part_size - 1) / part_size), "part execute");
         }
     }
     if (run == GPUTX_TPL) {

@@ -136,7 +136,7 @@ cudaError_t launch_finish(gputx_bulk *b);
 cudaError_t launch_kset(gputx_bulk *b, const uint32_t *order, int64_t nchunks, int block, bool atomic_add);
 cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, int64_t depth, int narrow_max,
                                bool atomic_add);
-cudaError_t launch_part(gputx_bulk *b, const uint32_t *pkeys, int block);
+cudaError_t launch_part(gputx_bulk *b, const uint32_t *pkeys, int block, int64_t max_parts);
 cudaError_t launch_tpl(gputx_bulk *b, int block, bool atomic_add);
 int exec_blocks_per_sm(int kind, int block);
 

@@ -22,6 +22,7 @@
 //       order, so the earliest unfinished one never waits: no deadlock.
 // Every wait is bounded by the configured limit; on expiry the kernel sets
 // ERR_TIMEOUT in the bulk's error word and returns.
+#include <algorithm>
 #include <cooperative_groups.h>
 
 #include "engine.h"
@@ -89,8 +90,8 @@ __global__ void __launch_bounds__(256) kset_level_kernel(LevelArgs a)
 // a run of narrow levels [k0, k1) on one thread-block cluster (CLUSTER) or
 // one CTA.  While level k executes, level k+1's records come into L1; after
 // it, level k+1's rows are prefetched into L2; then the barrier.
-template <bool CLUSTER>
-__global__ void __launch_bounds__(1024, 1) kset_narrow_kernel(LevelArgs a)
+template <bool CLUSTER, int MAXT>
+__global__ void __launch_bounds__(MAXT) kset_narrow_kernel(LevelArgs a)
 {
     if (a.ctl->err) return;   // set by an earlier launch only: uniform here
     const int64_t hb = a.ctl->base.hist;
@@ -181,7 +182,14 @@ __global__ void kset_kernel(KsetArgs a)
 __global__ void part_kernel(DevDB db, DevBulk b, const BulkCtl *ctl, const uint32_t *pkeys,
                             const uint32_t *part_start)
 {
+    extern __shared__ unsigned long long part_smem[];
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    // the partition's cells stay with this thread for the whole launch: a
+    // write-through cache in shared memory serves its repeated reads
+    CachedCells cells;
+    cells.tag = part_smem + threadIdx.x * CachedCells::kSlots;
+    cells.val = (int64_t *)(part_smem + (blockDim.x + threadIdx.x) * CachedCells::kSlots);
+    for (int i = 0; i < CachedCells::kSlots; i++) cells.tag[i] = 0;
     if (p >= ctl->npart || ctl->err) return;
     const int64_t hb = ctl->base.hist;
     const uint32_t n = (uint32_t)b.n;
@@ -202,7 +210,7 @@ __global__ void part_kernel(DevDB db, DevBulk b, const BulkCtl *ctl, const uint3
         const bool has2 = has1 && i + 2 < n && __ldg(&pkeys[i + 2]) == key;
         TxnView v2{};
         if (has2) v2 = view_at(b, i + 2, hb);
-        exec_txn(db, b, v, false);
+        exec_txn(db, b, v, false, cells);
         if (!has1) break;
         if (has2) prefetch_txn(db, v2);
         v = v1;
@@ -282,7 +290,7 @@ int max_cluster_ok(int csize)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, kset_narrow_kernel<true>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, kset_narrow_kernel<true, 1024>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         n = 0;
     }
@@ -340,7 +348,9 @@ cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, in
     const int64_t levels = depth + 1;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(kset_narrow_kernel<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(kset_narrow_kernel<true, 256>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(kset_narrow_kernel<true, 512>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(kset_narrow_kernel<true, 1024>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         attr_set = true;
     }
     int64_t k = 0;
@@ -377,7 +387,8 @@ cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, in
         threads = ((threads + 31) / 32) * 32;
         threads = threads < 32 ? 32 : (threads > 1024 ? 1024 : threads);
         if (csize <= 1) {
-            kset_narrow_kernel<false><<<1, threads, 0, b->stream>>>(a);
+            if (threads <= 256) kset_narrow_kernel<false, 256><<<1, threads, 0, b->stream>>>(a);
+            else kset_narrow_kernel<false, 1024><<<1, threads, 0, b->stream>>>(a);
         } else {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(csize, 1, 1);
@@ -390,7 +401,11 @@ cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, in
             attr[0].val.clusterDim.z = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            cudaError_t e2 = cudaLaunchKernelEx(&cfg, kset_narrow_kernel<true>, a);
+            // up to 256 threads a CTA: more registers per thread for the
+            // loads in flight
+            cudaError_t e2 = threads <= 256   ? cudaLaunchKernelEx(&cfg, kset_narrow_kernel<true, 256>, a)
+                             : threads <= 512 ? cudaLaunchKernelEx(&cfg, kset_narrow_kernel<true, 512>, a)
+                                              : cudaLaunchKernelEx(&cfg, kset_narrow_kernel<true, 1024>, a);
             if (e2) return e2;
         }
         count_launches(1);
@@ -401,13 +416,20 @@ cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_part(gputx_bulk *b, const uint32_t *pkeys, int block)
+cudaError_t launch_part(gputx_bulk *b, const uint32_t *pkeys, int block, int64_t max_parts)
 {
     gputx_db *db = b->db;
     if (b->n == 0) return cudaSuccess;
     const DevBulk d = make_dev_bulk(b, GPUTX_CONFLICT_PAPER);
-    const int64_t grid = (b->n + block - 1) / block;   // npart <= n, read on the device
-    part_kernel<<<(unsigned)grid, block, 0, b->stream>>>(db->dev, d, b->ctl, pkeys, b->sc.part_start);
+    // few partitions per SM: their scattered stores share one load/store
+    // pipeline, so spread the expected partitions over every SM
+    const int64_t parts = std::max<int64_t>(1, std::min<int64_t>(b->n, max_parts));
+    int threads = (int)((parts + db->num_sms - 1) / db->num_sms);
+    threads = ((threads + 7) / 8) * 8;
+    threads = threads < 8 ? 8 : (threads > block ? block : threads);
+    const int64_t grid = (b->n + threads - 1) / threads;   // npart <= n, read on the device
+    const size_t smem = (size_t)threads * 2 * CachedCells::kSlots * sizeof(unsigned long long);
+    part_kernel<<<(unsigned)grid, threads, smem, b->stream>>>(db->dev, d, b->ctl, pkeys, b->sc.part_start);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -330,9 +330,50 @@ __device__ __forceinline__ void prefetch_txn(const DevDB &db, const TxnView &v)
 // ---------------------------------------------------------------------------
 // the combined procedure kernel body (Section 3.2's switch)
 // ---------------------------------------------------------------------------
+// How procedures read and write mutable int64 cells.
+//   GlobalCells  L2 is the coherence point (ld.cg / st.cg); any strategy.
+//   CachedCells  write-through cache of recently touched cells in this
+//                thread's shared memory.  Only for a thread that owns its
+//                cells for the whole launch -- PART, whose partition is
+//                touched by no other thread -- where a cell written by one
+//                transaction and read by the next stays on chip instead of
+//                making an L2 round trip.
+struct GlobalCells {
+    __device__ __forceinline__ int64_t ld(const int64_t *p) const { return __ldcg(p); }
+    __device__ __forceinline__ void st(int64_t *p, int64_t v) const { __stcg(p, v); }
+};
+
+struct CachedCells {
+    static constexpr int kSlots = 16;
+    unsigned long long *tag;   // kSlots entries of this thread (shared memory)
+    int64_t *val;
+    __device__ __forceinline__ int slot(const int64_t *p) const
+    {
+        return (int)((((unsigned long long)p >> 3) * 0x9E3779B97F4A7C15ull) >> 60);
+    }
+    __device__ __forceinline__ int64_t ld(const int64_t *p)
+    {
+        const int i = slot(p);
+        if (tag[i] == (unsigned long long)p) return val[i];
+        const int64_t x = __ldcg(p);
+        tag[i] = (unsigned long long)p;
+        val[i] = x;
+        return x;
+    }
+    __device__ __forceinline__ void st(int64_t *p, int64_t x)
+    {
+        __stcg(p, x);
+        const int i = slot(p);
+        tag[i] = (unsigned long long)p;
+        val[i] = x;
+    }
+};
+
 // atomic_add: execute ADD-class increments with atomics (several
 // transactions of one level may add to one item).
-__device__ __forceinline__ void exec_dc(const DevDB &db, const DevBulk &b, const TxnView &v, bool atomic_add)
+template <class Cells>
+__device__ __forceinline__ void exec_dc(const DevDB &db, const DevBulk &b, const TxnView &v, bool atomic_add,
+                                        Cells &cells)
 {
     const uint32_t t = v.t;
     const int64_t a = v.p0, delta = v.p1;
@@ -342,11 +383,11 @@ __device__ __forceinline__ void exec_dc(const DevDB &db, const DevBulk &b, const
     // every load before any store: the three rows are distinct cells but the
     // compiler cannot prove it, so interleaving would serialise three L2
     // round trips
-    const int64_t old_a = ldg_cg(&db.acc_bal[a]);
+    const int64_t old_a = cells.ld(&db.acc_bal[a]);
     int64_t old_t = 0, old_b = 0;
     if (!atomic_add) {
-        old_t = ldg_cg(&db.tel_bal[tl]);
-        old_b = ldg_cg(&db.br_bal[br]);
+        old_t = cells.ld(&db.tel_bal[tl]);
+        old_b = cells.ld(&db.br_bal[br]);
     }
     if (slot >= db.hist_cap) {              // history full: not executed
         set_err(b.err, ERR_CAPACITY);
@@ -355,13 +396,13 @@ __device__ __forceinline__ void exec_dc(const DevDB &db, const DevBulk &b, const
     }
     // account: read-modify-write, its new value is the output
     const int64_t na = wrap_add(old_a, delta);
-    stg_cg(&db.acc_bal[a], na);
+    cells.st(&db.acc_bal[a], na);
     if (atomic_add) {
         atomicAdd((unsigned long long *)&db.tel_bal[tl], (unsigned long long)delta);
         atomicAdd((unsigned long long *)&db.br_bal[br], (unsigned long long)delta);
     } else {
-        stg_cg(&db.tel_bal[tl], wrap_add(old_t, delta));
-        stg_cg(&db.br_bal[br], wrap_add(old_b, delta));
+        cells.st(&db.tel_bal[tl], wrap_add(old_t, delta));
+        cells.st(&db.br_bal[br], wrap_add(old_b, delta));
     }
     db.h_ts[slot] = v.ts;
     db.h_acc[slot] = a;
@@ -454,7 +495,9 @@ __device__ __forceinline__ void exec_sub(const DevDB &db, const DevBulk &b, cons
 }
 
 // order-entry procedures (stand-ins shaped like TPC-C, Appendix E)
-__device__ __forceinline__ void exec_oe(const DevDB &db, const DevBulk &b, const TxnView &v, bool atomic_add)
+template <class Cells>
+__device__ __forceinline__ void exec_oe(const DevDB &db, const DevBulk &b, const TxnView &v, bool atomic_add,
+                                        Cells &cells)
 {
     const int64_t *p = v.p;
     const uint32_t t = v.t;
@@ -473,8 +516,8 @@ __device__ __forceinline__ void exec_oe(const DevDB &db, const DevBulk &b, const
         if (oslot >= db.ord_cap || lslot + cnt > db.ol_cap) {
             set_err(b.err, ERR_CAPACITY); st = 3; break;
         }
-        const int64_t o_id = ldg_cg(&db.d_next_o_id[d]);
-        stg_cg(&db.d_next_o_id[d], o_id + 1);
+        const int64_t o_id = cells.ld(&db.d_next_o_id[d]);
+        cells.st(&db.d_next_o_id[d], o_id + 1);
         int64_t total = 0;
         for (int j = 0; j < cnt; j++) {
             const int64_t line = p[4 + j];
@@ -484,11 +527,11 @@ __device__ __forceinline__ void exec_oe(const DevDB &db, const DevBulk &b, const
             total += amount;
             const int64_t s = sw * db.n_items + item;
             int32_t q = ldg_cg(&db.s_quantity[s]);
-            const int64_t sy = ldg_cg(&db.s_ytd[s]);
+            const int64_t sy = cells.ld(&db.s_ytd[s]);
             const int32_t so = ldg_cg(&db.s_order_cnt[s]);
             q = (q >= qty + 10) ? (int32_t)(q - qty) : (int32_t)(q - qty + 91);
             stg_cg(&db.s_quantity[s], q);
-            stg_cg(&db.s_ytd[s], sy + qty);
+            cells.st(&db.s_ytd[s], sy + qty);
             stg_cg(&db.s_order_cnt[s], so + 1);
             db.ol_item[lslot + j] = (int32_t)item;
             db.ol_sw[lslot + j] = (int32_t)sw;
@@ -505,7 +548,7 @@ __device__ __forceinline__ void exec_oe(const DevDB &db, const DevBulk &b, const
         if (!hash_insert(db.ord_idx, ord_key(d, o_id), (uint32_t)oslot)) {
             set_err(b.err, ERR_CAPACITY); st = 3; break;
         }
-        stg_cg(&db.c_last_o_id[c], o_id);
+        cells.st(&db.c_last_o_id[c], o_id);
         out[0] = o_id;
         out[1] = total * (10000 - __ldg(&db.c_discount[c])) *
                  (10000 + __ldg(&db.w_tax[w]) + __ldg(&db.d_tax[d])) / 100000000;
@@ -517,28 +560,28 @@ __device__ __forceinline__ void exec_oe(const DevDB &db, const DevBulk &b, const
         // loads first (see exec_dc), then the stores
         int64_t wy = 0, dy = 0;
         if (!atomic_add) {
-            wy = ldg_cg(&db.w_ytd[w]);
-            dy = ldg_cg(&db.d_ytd[d]);
+            wy = cells.ld(&db.w_ytd[w]);
+            dy = cells.ld(&db.d_ytd[d]);
         }
-        const int64_t cb = ldg_cg(&db.c_balance[c]), cy = ldg_cg(&db.c_ytd[c]);
-        const int64_t cn = ldg_cg(&db.c_payment_cnt[c]);
+        const int64_t cb = cells.ld(&db.c_balance[c]), cy = cells.ld(&db.c_ytd[c]);
+        const int64_t cn = cells.ld(&db.c_payment_cnt[c]);
         if (atomic_add) {
             atomicAdd((unsigned long long *)&db.w_ytd[w], (unsigned long long)amount);
             atomicAdd((unsigned long long *)&db.d_ytd[d], (unsigned long long)amount);
         } else {
-            stg_cg(&db.w_ytd[w], wrap_add(wy, amount));
-            stg_cg(&db.d_ytd[d], wrap_add(dy, amount));
+            cells.st(&db.w_ytd[w], wrap_add(wy, amount));
+            cells.st(&db.d_ytd[d], wrap_add(dy, amount));
         }
         const int64_t bal = wrap_add(cb, -amount);
-        stg_cg(&db.c_balance[c], bal);
-        stg_cg(&db.c_ytd[c], wrap_add(cy, amount));
-        stg_cg(&db.c_payment_cnt[c], cn + 1);
+        cells.st(&db.c_balance[c], bal);
+        cells.st(&db.c_ytd[c], wrap_add(cy, amount));
+        cells.st(&db.c_payment_cnt[c], cn + 1);
         out[0] = bal;
         break;
     }
     case GPUTX_T_OE_ORDER_STATUS: {
-        const int64_t o = ldg_cg(&db.c_last_o_id[c]);
-        out[0] = ldg_cg(&db.c_balance[c]);
+        const int64_t o = cells.ld(&db.c_last_o_id[c]);
+        out[0] = cells.ld(&db.c_balance[c]);
         out[1] = o;
         if (o == 0) { st = 1; break; }
         const int64_t r = hash_find(db.ord_idx, ord_key(d, o));
@@ -555,10 +598,12 @@ __device__ __forceinline__ void exec_oe(const DevDB &db, const DevBulk &b, const
     b.status[t] = st;
 }
 
-__device__ __forceinline__ void exec_txn(const DevDB &db, const DevBulk &b, const TxnView &v, bool atomic_add)
+template <class Cells>
+__device__ __forceinline__ void exec_txn(const DevDB &db, const DevBulk &b, const TxnView &v, bool atomic_add,
+                                         Cells &cells)
 {
     switch (v.type) {
-    case GPUTX_T_DC_DEBIT_CREDIT: exec_dc(db, b, v, atomic_add); break;
+    case GPUTX_T_DC_DEBIT_CREDIT: exec_dc(db, b, v, atomic_add, cells); break;
     case GPUTX_T_SUB_GET_SUBSCRIBER:
     case GPUTX_T_SUB_GET_ACCESS:
     case GPUTX_T_SUB_GET_NEW_DEST:
@@ -568,8 +613,14 @@ __device__ __forceinline__ void exec_txn(const DevDB &db, const DevBulk &b, cons
     case GPUTX_T_SUB_DELETE_CF: exec_sub(db, b, v); break;
     case GPUTX_T_OE_NEW_ORDER:
     case GPUTX_T_OE_PAYMENT:
-    case GPUTX_T_OE_ORDER_STATUS: exec_oe(db, b, v, atomic_add); break;
+    case GPUTX_T_OE_ORDER_STATUS: exec_oe(db, b, v, atomic_add, cells); break;
     }
+}
+
+__device__ __forceinline__ void exec_txn(const DevDB &db, const DevBulk &b, const TxnView &v, bool atomic_add)
+{
+    GlobalCells g;
+    exec_txn(db, b, v, atomic_add, g);
 }
 
 }  // namespace gtx
