@@ -36,12 +36,41 @@ import workloads as W  # noqa: E402
 
 BRANCHES, TELLERS, ACCOUNTS = 1000, 10_000, 10_000_000
 METRIC = "txns/sec on 1 GB300 per strategy & bulk size vs plain path; p50/p99 latency"
-# algorithmic bytes of one debit-credit transaction in the executor: params
-# (account, delta) 16 B + ts 8 B + its index in the level order 4 B + account,
-# teller, branch balance read+write 3 x 16 B + history row 40 B + output 8 B +
-# status 4 B
-EXEC_BYTES_PER_TXN = 16 + 8 + 4 + 48 + 40 + 8 + 4
+# algorithmic bytes of one debit-credit transaction in the executor, at the
+# granularity of random HBM access (one 32 B sector per random cell):
+#   execution-order record (params 16 B, ts 8 B, type 4 B, index 4 B)  32 B, sequential
+#   account balance: one sector read + one sector written            64 B, random
+#   teller and branch balances (80 KB + 8 KB: resident in L2)           0 B
+#   history row (ts, account, teller, branch, delta)                   40 B, sequential
+#   output value 8 B + status 4 B                                      12 B
+EXEC_BYTES_PER_TXN = 32 + 64 + 0 + 40 + 12
 L2_FLUSH_BYTES = 256 << 20
+# the executor kernel that dominates each headline configuration
+DOMINANT_KERNEL = {("kset", "paper"): "kset_narrow_kernel", ("kset", "add"): "kset_level_kernel",
+                   ("part", "paper"): "part_kernel", ("part", "add"): "part_kernel",
+                   ("tpl", "paper"): "tpl_kernel", ("tpl", "add"): "tpl_kernel"}
+# DRAM bytes (read + write) per launch from one ncu capture of the dominant
+# kernel at this configuration, keyed by (strategy, mode, bulk log2); each
+# entry holds the digest of the kernel sources it was taken on, and is
+# reported as null once those sources change
+TRAFFIC = {("kset", "paper", 22): {"bytes": 344518144 + 294963712, "digest": "64c839395589c8fc"}}
+KERNEL_SOURCES = ("common.cuh", "procs.cuh", "exec.cu")
+
+
+def kernel_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1103_3105_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(strategy, mode, lg):
+    t = TRAFFIC.get((strategy, mode, lg))
+    if t is None or t["digest"] != kernel_digest():
+        return None
+    return t["bytes"]
 
 
 def env_int(k, d):
@@ -263,11 +292,15 @@ def run_engine(args, rank, world, local_rank):
         "e2e": {"value": e2e_value, "unit": "txn/s", "h2d_bytes_per_step": n * (8 + 4 + 16),
                 "d2h_bytes_per_step": n * (4 + 8 * db.width)},
         "gpu_launches": int(launches),
-        "roofline": {"kernel": "kset_kernel" if args.strategy == "kset" else f"{args.strategy}_kernel",
+        "roofline": {"kernel": DOMINANT_KERNEL.get((args.strategy, args.mode), "executor"),
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind,
                      "algorithmic_bytes_per_txn": EXEC_BYTES_PER_TXN,
-                     "kernel_ms": ex, "traffic": None},
+                     "kernel_ms": ex, "kernel_source_digest": kernel_digest(),
+                     "traffic": traffic_for(args.strategy, args.mode, args.bulk_log2),
+                     # the level chain, not bandwidth, bounds K-SET on a deep graph
+                     "levels": stats["depth"] + 1 if stats else None,
+                     "ns_per_level": ex * 1e6 / (stats["depth"] + 1) if stats else None},
         "phases_ms": {"execute": ex, "op_sort": statistics.median(sort_ms),
                       "analysis": stats["ms_analysis"] if stats else None},
         "graph": {"depth": stats["depth"], "w0": stats["w0"], "cross": stats["cross"]} if stats else None,
@@ -329,7 +362,9 @@ def run_sweep(args, G, torch, dev, stream, flush):
                             ts.append(e0.elapsed_time(e1))
                     ms = statistics.median(ts)
                     rec.update({"ms": ms, "txn_per_s": n / (ms / 1e3), "depth": st["depth"],
-                                "w0": st["w0"], "exec_ms": st["ms_execute"], "sort_ms": st["ms_sort"]})
+                                "w0": st["w0"], "exec_ms": st["ms_execute"], "sort_ms": st["ms_sort"],
+                                "exec_hbm_frac": (n * EXEC_BYTES_PER_TXN / (st["ms_execute"] / 1e3) / 1e9
+                                                  / measured_peak_hbm()[0]) if st["ms_execute"] > 0 else None})
                     out.append(rec)
     db.close()
     return out

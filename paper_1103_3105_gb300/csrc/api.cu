@@ -148,7 +148,7 @@ int type_schema(int t)
 int type_ops(int t, int *maxk)
 {
     switch (t) {
-    case GPUTX_T_DC_DEBIT_CREDIT: *maxk = 3; return 3;
+    case GPUTX_T_DC_DEBIT_CREDIT: *maxk = 1; return 1;
     case GPUTX_T_OE_NEW_ORDER: *maxk = 2 + 15; return -1;
     case GPUTX_T_OE_PAYMENT: *maxk = 3; return 3;
     case GPUTX_T_OE_ORDER_STATUS: *maxk = 2; return 2;
@@ -337,13 +337,15 @@ gputx_status gputx_create_db(const gputx_schema_desc *schema, const gputx_config
     // object ids: one range per (table, field group)
     uint64_t o = 0;
     const int64_t n_d = s.oe_warehouses * OE_DIST, n_c = n_d * OE_CUST;
-    d.o_acc = (uint32_t)o; o += s.dc_accounts;
-    d.o_tel = (uint32_t)o; o += s.dc_tellers;
+    // small root tables first, so a bulk whose keys are only root keys sorts
+    // on few bits
     d.o_br = (uint32_t)o; o += s.dc_branches;
-    d.o_sub = (uint32_t)o; o += s.sub_subscribers;
+    d.o_tel = (uint32_t)o; o += s.dc_tellers;
     d.o_wytd = (uint32_t)o; o += s.oe_warehouses;
     d.o_dytd = (uint32_t)o; o += n_d;
     d.o_dnext = (uint32_t)o; o += n_d;
+    d.o_acc = (uint32_t)o; o += s.dc_accounts;
+    d.o_sub = (uint32_t)o; o += s.sub_subscribers;
     d.o_cpay = (uint32_t)o; o += n_c;
     d.o_clast = (uint32_t)o; o += n_c;
     d.o_stock = (uint32_t)o; o += s.oe_warehouses * s.oe_items;
@@ -853,6 +855,20 @@ gputx_status gputx_submit_bulk(gputx_db *db, const int64_t *ts, const int32_t *t
 
 namespace {
 
+// key bits of the largest object id the registered types can extract under
+// `mode` (objects are numbered small root tables first)
+int key_bits(const gputx_db *db, int mode)
+{
+    const DevDB &d = db->dev;
+    const uint32_t reg = d.registered;
+    uint64_t top = 1;
+    if (reg & 1u) top = std::max<uint64_t>(top, mode == GPUTX_CONFLICT_ADD ? (uint64_t)d.o_acc + d.n_acc
+                                                                           : (uint64_t)d.o_br + d.n_br);
+    if (reg & 0xFEu) top = std::max<uint64_t>(top, (uint64_t)d.o_sub + d.n_sub);
+    if (reg & 0x700u) top = std::max<uint64_t>(top, (uint64_t)d.n_objects);
+    return std::max(1, bits_for(top - 1));
+}
+
 gputx_status run_kset_analysis(gputx_bulk *b, int mode, int part_size, uint32_t *&sk, uint32_t *&sv,
                                uint32_t *&ak, uint32_t *&av, int64_t &m)
 {
@@ -869,7 +885,7 @@ gputx_status run_kset_analysis(gputx_bulk *b, int mode, int part_size, uint32_t 
     }
     if (b->timing) cudaEventRecord(b->ev[1], b->stream);
     sk = b->sc.keys_a; sv = b->sc.vals_a; ak = b->sc.keys_b; av = b->sc.vals_b;
-    CK(launch_sort(b, sk, sv, ak, av, m, db->obj_bits), "sort");
+    CK(launch_sort(b, sk, sv, ak, av, m, key_bits(db, mode)), "sort");
     if (b->timing) cudaEventRecord(b->ev[2], b->stream);
     return GPUTX_OK;
 }
@@ -1172,7 +1188,7 @@ extern "C" gputx_status gputx_execute_kset_noalloc(gputx_db *db, const int64_t *
         m = mm > (uint32_t)b.sc.m_cap ? b.sc.m_cap : mm;
     }
     uint32_t *sk = b.sc.keys_a, *sv = b.sc.vals_a, *ak = b.sc.keys_b, *av = b.sc.vals_b;
-    CK(launch_sort(&b, sk, sv, ak, av, m, db->obj_bits), "sort");
+    CK(launch_sort(&b, sk, sv, ak, av, m, key_bits(db, conflict_mode)), "sort");
     CK(launch_rank_scan(&b, sk, sv, m, db->need_fixpoint), "rank");
     if (db->need_fixpoint) CK(launch_fixpoint_device(&b, sv, m), "fixpoint");
     CK(launch_level_stats(&b), "stats");

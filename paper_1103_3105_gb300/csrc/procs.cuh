@@ -79,12 +79,23 @@ __device__ __forceinline__ int access_set(const DevDB &db, int32_t type, const i
     int k = 0;
     switch (type) {
     case GPUTX_T_DC_DEBIT_CREDIT: {
-        int64_t a = p[0];
-        uint32_t t = (uint32_t)(a / db.acc_per_tel), b = (uint32_t)(a / db.acc_per_br);
-        obj[0] = db.o_acc + (uint32_t)a; cls[0] = CLS_W; root[0] = b;
-        obj[1] = db.o_tel + t;           cls[1] = blind; root[1] = b;
-        obj[2] = db.o_br + b;            cls[2] = blind; root[2] = b;
-        return 3;
+        // The transaction writes its account, teller and branch balances.
+        // With reads and writes only, every pair of debit-credit transactions
+        // that conflicts on an account or a teller also conflicts on the
+        // branch above it (both write it), so the branch -- the root key of
+        // Section 5.1 -- stands for all three: same conflict relation, same
+        // depths, one operation.  With ADD, teller and branch increments
+        // commute with each other and no procedure reads them, so only the
+        // account orders transactions.
+        const int64_t a = p[0];
+        const uint32_t b = (uint32_t)a / (uint32_t)db.acc_per_br;
+        if (mode == GPUTX_CONFLICT_ADD) {
+            obj[0] = db.o_acc + (uint32_t)a; cls[0] = CLS_W; root[0] = b;
+        } else {
+            obj[0] = db.o_br + b; cls[0] = CLS_W; root[0] = b;
+        }
+        (void)blind;
+        return 1;
     }
     case GPUTX_T_SUB_GET_SUBSCRIBER:
     case GPUTX_T_SUB_GET_ACCESS:
@@ -135,7 +146,7 @@ __device__ __forceinline__ int access_set(const DevDB &db, int32_t type, const i
 __device__ __forceinline__ int op_count(const DevDB &db, int32_t type, const int64_t *p)
 {
     switch (type) {
-    case GPUTX_T_DC_DEBIT_CREDIT: return 3;
+    case GPUTX_T_DC_DEBIT_CREDIT: return 1;
     case GPUTX_T_OE_NEW_ORDER: {
         int k = 2, cnt = (int)p[3];
         for (int j = 0; j < cnt; j++) k += ((p[4 + j] & 0xFFFFFF) < db.n_items);

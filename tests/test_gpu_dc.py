@@ -168,13 +168,15 @@ def test_execute_twice_is_refused():
     g.close()
 
 
-def test_bounded_wait_reports_timeout():
-    """A 1 ns wait limit makes the level waits of a 1,000-deep K-SET run out:
-    the engine must report ETIMEOUT instead of hanging, and stay usable."""
+@pytest.mark.parametrize("strategy,launch", [("kset", 1), ("tpl", 0)])
+def test_bounded_wait_reports_timeout(strategy, launch):
+    """A 1 ns wait limit makes the per-level waits of a 1,000-deep persistent
+    K-SET launch (or TPL's lock waits) run out: the engine must report
+    ETIMEOUT instead of hanging, and stay usable."""
     g = G.Database(dc=(4, 40, 4000), history_capacity=1 << 16, max_bulk=1 << 14, spin_limit_ns=1)
     g.register(G.DC_TYPES)
     bulk = W.dc_bulk(4096, 4000, 0.0, seed=2)
-    b = g.submit_dict(bulk).execute("kset")
+    b = g.submit_dict(bulk).execute(strategy, kset_launch=launch)
     with pytest.raises(G.GputxError) as e:
         b.sync()
     assert e.value.status == G.ETIMEOUT
