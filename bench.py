@@ -47,8 +47,9 @@ EXEC_BYTES_PER_TXN = 32 + 64 + 0 + 40 + 12
 L2_FLUSH_BYTES = 256 << 20
 # the executor kernel that dominates each headline configuration
 DOMINANT_KERNEL = {("kset", "paper"): "kset_narrow_kernel", ("kset", "add"): "kset_level_kernel",
-                   ("part", "paper"): "part_kernel", ("part", "add"): "part_kernel",
-                   ("tpl", "paper"): "tpl_kernel", ("tpl", "add"): "tpl_kernel"}
+                   ("part", "paper"): "part_dc_kernel", ("part", "add"): "part_dc_kernel",
+                   ("tpl", "paper"): "tpl_kernel", ("tpl", "add"): "tpl_kernel",
+                   ("scan", "paper"): "seg64_scan_kernel", ("scan", "add"): "seg64_scan_kernel"}
 # DRAM bytes (read + write) per launch from one ncu capture of the dominant
 # kernel at this configuration, keyed by (strategy, mode, bulk log2); each
 # entry holds the digest of the kernel sources it was taken on, and is
@@ -328,7 +329,7 @@ def run_sweep(args, G, torch, dev, stream, flush):
     out = []
     sizes = [14, 16, 18, 20, 22]
     # history rows for every bulk the sweep can run
-    rows = 3 * 5 * 3 * sum(1 << lg for lg in sizes)
+    rows = 3 * 6 * 3 * sum(1 << lg for lg in sizes)
     db = G.Database(dc=(BRANCHES, TELLERS, ACCOUNTS), history_capacity=rows, max_bulk=1 << 22,
                     stream=stream.cuda_stream)
     db.register(G.DC_TYPES)
@@ -337,10 +338,10 @@ def run_sweep(args, G, torch, dev, stream, flush):
         dbig = {k: torch.from_numpy(big[k]).to(dev) for k in ("ts", "type", "params")}
         for lg in sizes:
             n = 1 << lg
-            for strategy in ("kset", "part", "tpl"):
+            for strategy in ("kset", "part", "tpl", "scan"):
                 for mode_name, mode in (("paper", G.CONFLICT_PAPER), ("add", G.CONFLICT_ADD)):
-                    if strategy == "part" and mode_name == "add":
-                        continue   # PART runs partitions serially: the model does not change it
+                    if strategy in ("part", "scan") and mode_name == "add":
+                        continue   # PART runs partitions serially, SCAN always sums: the model changes neither
                     rec = {"theta": theta, "bulk": n, "strategy": strategy, "mode": mode_name}
                     if time.perf_counter() - t_start > args.sweep_budget_s:
                         rec["skipped"] = "time budget"
@@ -371,27 +372,46 @@ def run_sweep(args, G, torch, dev, stream, flush):
 
 
 def run_serving(args, G, torch, stream):
-    """Open-loop Poisson arrivals through the server: continuous batching
-    (several bulks in flight) against the plain per-bulk path (one bulk at a
-    time, closed every deadline).  Latency = result on the host - arrival."""
+    """The served mix: debit-credit and subscriber schemas loaded together in a
+    device-resident database of about 20 GB, open-loop Poisson arrivals of a
+    50/50 mix of the two schemas' transactions.  Three serving modes:
+    continuous batching (several bulks in flight), the plain per-bulk path
+    (one bulk at a time, closed every deadline) and incremental 0-set
+    execution.  Latency = result on the host - arrival."""
     out = []
     rates = [float(r) for r in args.serve_rates.split(",")]
     deadlines = [int(d) for d in args.serve_deadlines_us.split(",")]
-    total = int(sum(rates) * args.serve_seconds * len(deadlines) * 2) + (1 << 22)
-    db = G.Database(dc=(BRANCHES, TELLERS, ACCOUNTS), history_capacity=total, max_bulk=1 << 20,
-                    stream=stream.cuda_stream)
-    db.register(G.DC_TYPES)
+    n_sub = args.serve_subscribers
+    total = int(sum(rates) * args.serve_seconds * len(deadlines) * 3) + (1 << 22)
+    free0 = torch.cuda.mem_get_info()[0]
+    # history rows fill the database to the configured size (at least what
+    # every served transaction needs)
+    hist_rows = max(total, int(args.serve_db_gb * 1e9 / 40))
+    db = G.Database(dc=(BRANCHES, TELLERS, ACCOUNTS), sub=n_sub, history_capacity=hist_rows,
+                    sub_child_capacity=6 * n_sub, max_bulk=1 << 20, stream=stream.cuda_stream)
+    db.register(G.DC_TYPES + G.SUB_TYPES)
+    for t, r in W.sub_rows(W.sub_tables(n_sub, seed=W.seed_for(5, 1))).items():
+        db.load(t, r)
+    torch.cuda.synchronize()
+    db_bytes = free0 - torch.cuda.mem_get_info()[0]
     rng = np.random.default_rng(W.seed_for(5))
+    mode = G.CONFLICT_ADD if args.mode == "add" else G.CONFLICT_PAPER
     for rate in rates:
         n = int(rate * args.serve_seconds)
-        bulk = W.dc_bulk(n, ACCOUNTS, args.theta, seed=W.seed_for(5, int(rate // 1e6)))
+        parts = [W.dc_bulk(n, ACCOUNTS, args.theta, seed=W.seed_for(5, int(rate // 1e6))),
+                 W.sub_bulk(n, n_sub, args.theta, seed=W.seed_for(5, 50 + int(rate // 1e6)))]
+        bulk = W.concat_bulks(parts, rng.integers(0, 2, size=n))
         gaps = rng.exponential(1e9 / rate, size=n)
         offs = np.cumsum(gaps).astype(np.int64)
         for deadline in deadlines:
-            for label, inflight in (("continuous", 3), ("plain", 1)):
+            for label, inflight, zero in (("continuous", 3, False), ("plain", 1, False), ("zero_set", 1, True)):
+                if zero and rate > args.serve_zero_set_max_rate:
+                    out.append({"offered_txn_per_s": rate, "deadline_us": deadline, "mode": label,
+                                "skipped": "rate above --serve-zero-set-max-rate"})
+                    continue
                 srv = G.Server(db, deadline_us=deadline, max_bulk=1 << 20, max_inflight=inflight,
-                               strategy=args.serve_strategy,
-                               conflict_mode=G.CONFLICT_ADD if args.mode == "add" else G.CONFLICT_PAPER)
+                               strategy=args.serve_strategy, conflict_mode=mode, params_per_txn=bulk["P"],
+                               zero_set=zero)
                 t0 = G.gputx_clock_ns() + 2_000_000
                 arrivals = t0 + offs
                 i = 0
@@ -411,7 +431,8 @@ def run_serving(args, G, torch, stream):
                             "mean_us": st["mean_us"], "txn_per_s": st["txn_per_s"], "bulks": st["bulks"],
                             "max_bulk": st["max_bulk_seen"]})
     db.close()
-    return out
+    return {"db_bytes": int(db_bytes), "subscribers": n_sub, "accounts": ACCOUNTS, "history_rows": hist_rows,
+            "mix": "50% debit-credit, 50% subscriber (30/25/25/8/8/2/2)", "runs": out}
 
 
 def run_batched(args, G, torch, stream):
@@ -531,7 +552,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gputx", choices=["gputx", "reference"])
-    ap.add_argument("--strategy", default="kset", choices=["kset", "part", "tpl", "auto"])
+    ap.add_argument("--strategy", default="kset", choices=["kset", "part", "tpl", "auto", "scan"])
     ap.add_argument("--mode", default="paper", choices=["paper", "add"])
     ap.add_argument("--theta", type=float, default=0.0)
     ap.add_argument("--bulk-log2", type=int, default=22)
@@ -547,6 +568,9 @@ def main():
     ap.add_argument("--serve-deadlines-us", default="1000,10000")
     ap.add_argument("--serve-seconds", type=float, default=0.5)
     ap.add_argument("--serve-strategy", default="kset", choices=["kset", "part", "tpl", "auto"])
+    ap.add_argument("--serve-subscribers", type=int, default=2_000_000)
+    ap.add_argument("--serve-db-gb", type=float, default=20.0)
+    ap.add_argument("--serve-zero-set-max-rate", type=float, default=5e6)
     ap.add_argument("--batched", dest="batched", action="store_true", default=True)
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--batch-txns", type=int, default=3_000_000)

@@ -52,7 +52,18 @@ typedef enum {
     GPUTX_KSET = 0,       /* Section 5.3: k-sets level by level */
     GPUTX_PART = 1,       /* Section 5.2: one thread per partition */
     GPUTX_TPL = 2,        /* Section 5.1: ordered counter locks */
-    GPUTX_AUTO = 3        /* Algorithm 1 over the measured d, w0, c */
+    GPUTX_AUTO = 3,       /* Algorithm 1 over the measured d, w0, c */
+    /* Debit-credit bulks only (every registered type is
+     * GPUTX_T_DC_DEBIT_CREDIT, else EINVAL): the blind-increment refinement
+     * (GPUTX_CONFLICT_ADD) carried to the end.  Operations are grouped by
+     * account with the stable sort of Section 4.2. Each output is then the
+     * account's balance before the bulk plus a segmented prefix sum of the
+     * deltas in timestamp order. Teller and branch balances receive wrapping
+     * sums. History rows take slots base + t (timestamp order).  The work
+     * does not depend on the depth of the dependency graph; the results are
+     * those of Definition 1.  If the bulk's history rows do not all fit, the
+     * bulk fails with ECAPACITY and writes nothing. */
+    GPUTX_SCAN = 4
 } gputx_strategy;
 
 typedef enum {
@@ -353,6 +364,14 @@ typedef struct {
                                  (default 2^30) */
     int64_t min_free_bytes;   /* refuse submissions while free device memory is
                                  below this (0 = no check) */
+    int32_t zero_set;         /* 1: incremental 0-set execution (Section 5.3):
+                                 arrivals join a device-resident pool
+                                 (gputx_pool, capacity 2 x max_bulk) and
+                                 every step executes the pool's 0-set, so a
+                                 long dependency chain never holds back the
+                                 transactions that do not depend on it;
+                                 strategy and max_inflight are unused */
+    int32_t reserved;         /* zero */
 } gputx_serve_config;
 
 typedef struct {
@@ -396,6 +415,54 @@ const char *gputx_server_last_error(const gputx_server *s);
 
 /* Stops the worker after the pending transactions complete, frees buffers. */
 void gputx_server_destroy(gputx_server *s);
+
+/* ---------------------------------------------------------------------------
+ * Incremental 0-set execution (Section 5.3).  A device-resident pool of
+ * pending transactions keeps their basic operations sorted by item.  New
+ * transactions' operations are sorted and merged into that array.  Each step
+ * executes the pool's 0-set as one bulk and removes it, so the former 1-set
+ * becomes the next 0-set.  The 0-set holds the sources of the T-dependency
+ * graph (Section 4.1): transactions with no earlier conflicting pending
+ * operation, so each commutes with every earlier transaction still pending.  The results of all steps therefore
+ * equal serial execution of the whole stream in timestamp order
+ * (Definition 1).  A step always executes the oldest pending transaction, so
+ * a pool with pending work always makes progress.
+ * ------------------------------------------------------------------------- */
+typedef struct gputx_pool gputx_pool;
+
+typedef struct {
+    int64_t capacity;       /* ring slots: the timestamp span pending at once
+                               (oldest pending to newest added), >= 1 */
+    int32_t params_per_txn; /* P of every added transaction */
+    int32_t conflict_mode;  /* gputx_conflict_mode of the 0-set */
+    int64_t reserved[2];    /* zero */
+} gputx_pool_config;
+
+/* The pool's device memory is about capacity x (56 + 8 P + 40 K) bytes, where
+ * K is the largest number of basic operations of a registered type. */
+gputx_status gputx_pool_create(gputx_db *db, const gputx_pool_config *cfg, gputx_pool **out);
+
+/* Appends n transactions from host arrays (ts[n], type[n], params[n x P]);
+ * timestamps continue the stream strictly increasing.  Returns ECAPACITY when
+ * the pending span would exceed the capacity and EINVAL for an invalid
+ * signature or timestamp.  In both cases nothing is added. */
+gputx_status gputx_pool_add(gputx_pool *p, const int64_t *ts, const int32_t *type, const int64_t *params,
+                            size_t n);
+
+/* Executes the pool's current 0-set; *executed = its size (0 only when the
+ * pool is empty).  Synchronous: the results are ready on return. */
+gputx_status gputx_pool_step(gputx_pool *p, size_t *executed);
+
+/* The last step's transactions in timestamp order: ts[k], status[k],
+ * values[k x R] (R = gputx_output_width).  *n = how many; capacity too small
+ * -> EINVAL. */
+gputx_status gputx_pool_results(const gputx_pool *p, int64_t *ts, int32_t *status, int64_t *values,
+                                size_t capacity, size_t *n);
+
+/* Transactions added and not yet executed. */
+size_t gputx_pool_pending(const gputx_pool *p);
+
+void gputx_pool_destroy(gputx_pool *p);
 
 #ifdef __cplusplus
 }

@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import weakref
 
 import numpy as np
 
@@ -20,8 +21,8 @@ LIB_PATH = os.path.join(_HERE, "libgputx.so")
 # --- constants mirrored from include/gputx.h --------------------------------
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBOUNDS, ESTATE, ECAPACITY = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ETIMEOUT", "EBOUNDS", "ESTATE", "ECAPACITY"]
-KSET, PART, TPL, AUTO = range(4)
-STRATEGIES = {"kset": KSET, "part": PART, "tpl": TPL, "auto": AUTO}
+KSET, PART, TPL, AUTO, SCAN = range(5)
+STRATEGIES = {"kset": KSET, "part": PART, "tpl": TPL, "auto": AUTO, "scan": SCAN}
 CONFLICT_PAPER, CONFLICT_ADD = 0, 1
 MEM_HOST, MEM_DEVICE = 0, 1
 
@@ -46,7 +47,9 @@ EXPORTED = ("gputx_create_db", "gputx_destroy_db", "gputx_last_error", "gputx_re
             "gputx_execute_kset_noalloc", "gputx_clock_ns", "gputx_server_create", "gputx_server_submit",
             "gputx_server_results", "gputx_server_drain", "gputx_server_stats",
             "gputx_server_last_error", "gputx_server_destroy", "gputx_batcher_create",
-            "gputx_batcher_run", "gputx_batcher_choice", "gputx_batcher_destroy")
+            "gputx_batcher_run", "gputx_batcher_choice", "gputx_batcher_destroy",
+            "gputx_pool_create", "gputx_pool_add", "gputx_pool_step", "gputx_pool_results",
+            "gputx_pool_pending", "gputx_pool_destroy")
 
 
 class GputxError(RuntimeError):
@@ -84,7 +87,8 @@ class ExecStats(C.Structure):
 class ServeConfig(C.Structure):
     _fields_ = [("deadline_us", C.c_int64), ("max_bulk", C.c_int64), ("max_inflight", C.c_int32),
                 ("strategy", C.c_int32), ("conflict_mode", C.c_int32), ("params_per_txn", C.c_int32),
-                ("queue_capacity", C.c_int64), ("min_free_bytes", C.c_int64)]
+                ("queue_capacity", C.c_int64), ("min_free_bytes", C.c_int64), ("zero_set", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class ServeStats(C.Structure):
@@ -115,6 +119,11 @@ class BatchChoice(C.Structure):
                 "measured": [{"strategy": self.measured_strategy[i], "block": self.measured_block[i],
                               "bulk": self.measured_bulk[i], "ns_per_txn": self.measured_ns_per_txn[i]}
                              for i in range(k)]}
+
+
+class PoolConfig(C.Structure):
+    _fields_ = [("capacity", C.c_int64), ("params_per_txn", C.c_int32), ("conflict_mode", C.c_int32),
+                ("reserved", C.c_int64 * 2)]
 
 
 class ExecOpts(C.Structure):
@@ -163,6 +172,12 @@ def lib():
             "gputx_batcher_run": ([p, p, p, p, sz, p, p], C.c_int),
             "gputx_batcher_choice": ([p, C.POINTER(BatchChoice)], C.c_int),
             "gputx_batcher_destroy": ([p], None),
+            "gputx_pool_create": ([p, C.POINTER(PoolConfig), C.POINTER(p)], C.c_int),
+            "gputx_pool_add": ([p, p, p, p, sz], C.c_int),
+            "gputx_pool_step": ([p, C.POINTER(sz)], C.c_int),
+            "gputx_pool_results": ([p, p, p, p, sz, C.POINTER(sz)], C.c_int),
+            "gputx_pool_pending": ([p], sz),
+            "gputx_pool_destroy": ([p], None),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -334,6 +349,11 @@ class Database:
                      alg1.get("kset_w0_min", 0), alg1.get("part_c_max", 0), alg1.get("part_d_min", 0))
         self.h = gputx_create_db(sch, cfg, stream)
         self.width = gputx_output_width(self.h)
+        # servers, batchers and pools over this database: closed before it
+        self._dependents = weakref.WeakSet()
+
+    def _adopt(self, obj):
+        self._dependents.add(obj)
 
     def register(self, types):
         gputx_register_types(self.h, list(types))
@@ -362,6 +382,8 @@ class Database:
 
     def close(self):
         if self.h:
+            for d in list(self._dependents):
+                d.close()
             gputx_destroy_db(self.h)
             self.h = None
 
@@ -428,12 +450,14 @@ class Server:
     """Transaction pool + bulk generator over a Database (see gputx.h)."""
 
     def __init__(self, db: Database, deadline_us=1000, max_bulk=0, max_inflight=2, strategy="kset",
-                 conflict_mode=CONFLICT_PAPER, params_per_txn=2, queue_capacity=0, min_free_bytes=0):
+                 conflict_mode=CONFLICT_PAPER, params_per_txn=2, queue_capacity=0, min_free_bytes=0,
+                 zero_set=False):
         s = STRATEGIES[strategy] if isinstance(strategy, str) else int(strategy)
         cfg = ServeConfig(deadline_us, max_bulk, max_inflight, s, conflict_mode, params_per_txn,
-                          queue_capacity, min_free_bytes)
+                          queue_capacity, min_free_bytes, int(bool(zero_set)), 0)
         self.db = db
         self.h = gputx_server_create(db.h, cfg)
+        db._adopt(self)
 
     def submit(self, type_, params, arrival_ns=None) -> int:
         return gputx_server_submit(self.h, type_, params, arrival_ns)
@@ -491,6 +515,7 @@ class Batcher:
                           params_per_txn, 0)
         self.db = db
         self.h = gputx_batcher_create(db.h, cfg)
+        db._adopt(self)
 
     def run(self, ts, type_, params):
         ts = np.ascontiguousarray(ts, dtype=np.int64)
@@ -507,6 +532,78 @@ class Batcher:
     def close(self):
         if self.h:
             gputx_batcher_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --- incremental 0-set execution (Section 5.3) -------------------------------
+def gputx_pool_create(db, cfg: PoolConfig):
+    out = C.c_void_p()
+    _check(db, lib().gputx_pool_create(db, C.byref(cfg), C.byref(out)))
+    return out
+
+
+def gputx_pool_add(db, pool, ts, type_, params):
+    ts = np.ascontiguousarray(ts, dtype=np.int64)
+    type_ = np.ascontiguousarray(type_, dtype=np.int32)
+    params = np.ascontiguousarray(params, dtype=np.int64)
+    _check(db, lib().gputx_pool_add(pool, _ptr(ts), _ptr(type_), _ptr(params), len(ts)))
+
+
+def gputx_pool_step(db, pool) -> int:
+    n = C.c_size_t()
+    _check(db, lib().gputx_pool_step(pool, C.byref(n)))
+    return n.value
+
+
+def gputx_pool_results(db, pool, width: int):
+    n = C.c_size_t()
+    _check(db, lib().gputx_pool_results(pool, None, None, None, 0, C.byref(n)))
+    ts = np.zeros(n.value, dtype=np.int64)
+    st = np.zeros(n.value, dtype=np.int32)
+    vals = np.zeros((n.value, width), dtype=np.int64)
+    _check(db, lib().gputx_pool_results(pool, _ptr(ts), _ptr(st), _ptr(vals), n.value, C.byref(n)))
+    return ts, st, vals
+
+
+def gputx_pool_pending(pool) -> int:
+    return int(lib().gputx_pool_pending(pool))
+
+
+def gputx_pool_destroy(pool):
+    lib().gputx_pool_destroy(pool)
+
+
+class Pool:
+    """Device-resident transaction pool executed 0-set by 0-set (gputx.h)."""
+
+    def __init__(self, db: Database, capacity: int, params_per_txn: int = 2, conflict_mode=CONFLICT_PAPER):
+        self.db = db
+        self.h = gputx_pool_create(db.h, PoolConfig(capacity, params_per_txn, conflict_mode))
+        db._adopt(self)
+
+    def add(self, ts, type_, params):
+        gputx_pool_add(self.db.h, self.h, ts, type_, params)
+
+    def step(self) -> int:
+        return gputx_pool_step(self.db.h, self.h)
+
+    def results(self):
+        """(ts, status, values) of the last step, in timestamp order."""
+        return gputx_pool_results(self.db.h, self.h, self.db.width)
+
+    @property
+    def pending(self) -> int:
+        return gputx_pool_pending(self.h)
+
+    def close(self):
+        if self.h:
+            gputx_pool_destroy(self.h)
             self.h = None
 
     def __del__(self):

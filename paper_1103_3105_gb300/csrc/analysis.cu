@@ -395,11 +395,42 @@ struct SlotMode {
 // ---------------------------------------------------------------------------
 // PART: partition starts; TPL: counter reset
 // ---------------------------------------------------------------------------
-__global__ void part_heads_kernel(const uint32_t *skeys, int64_t n, uint32_t *part_start, BulkCtl *ctl)
+// partition heads in sorted order: part_start[p] = first position of the
+// p-th partition, part_start[npart] = n (a compaction by prefix count)
+struct HeadMode {
+    const uint32_t *skeys;
+    uint32_t *part_start;
+    BulkCtl *ctl;
+    int64_t n;
+    __device__ bool head(int64_t i) const { return i == 0 || skeys[i] != skeys[i - 1]; }
+    __device__ uint64_t element(int64_t i) const { return DualSeg::make(0, 0, 0, head(i) ? 1u : 0u); }
+    __device__ void output(int64_t i, uint64_t s) const
+    {
+        const uint32_t c = DualSeg::v2(s);
+        if (head(i)) part_start[c - 1] = (uint32_t)i;
+        if (i == n - 1) {
+            part_start[c] = (uint32_t)n;
+            ctl->npart = c;
+        }
+    }
+};
+
+// PART records of a debit-credit bulk, packed in partition order (32 B: two
+// 16-byte loads), with the teller index precomputed
+__global__ void gather_dc_kernel(DevDB db, DevBulk b, const uint32_t *order, DcRecord *rec, const uint32_t *err)
 {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n || ctl->err) return;
-    if (i == 0 || skeys[i] != skeys[i - 1]) part_start[atomicAdd(&ctl->npart, 1u)] = (uint32_t)i;
+    const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (pos >= b.n || *err) return;
+    const uint32_t t = order[pos];
+    const uint32_t a = (uint32_t)b.params[(int64_t)t * b.P];
+    DcRecord r;
+    r.delta = b.params[(int64_t)t * b.P + 1];
+    r.ts = b.ts[t];
+    r.a = a;
+    r.t = t;
+    r.tl = db.div_tel.div(a);
+    r.pad = 0;
+    rec[pos] = r;
 }
 
 __global__ void tpl_reset_kernel(const uint32_t *skeys, int64_t m, uint32_t *done, uint32_t n_objects)
@@ -469,9 +500,153 @@ __global__ void gather_kernel(DevBulk b, const uint32_t *order, int64_t *r_param
     for (int j = 0; j < b.P; j++) dst[j] = src[j];
 }
 
+// ---------------------------------------------------------------------------
+// SCAN executor for bulks of debit-credit transactions (blind increments,
+// the ADD refinement taken to its end).  Under Definition 1 the output of
+// transaction t is its account's balance before the bulk plus the deltas of
+// the bulk's transactions on that account up to and including t, in
+// timestamp order: a segmented prefix sum over the operations grouped by
+// account (the stable grouping sort keeps timestamp order inside a group).
+// Teller and branch balances only receive sums, and wrapping addition is
+// associative and commutative, so atomic adds give the serial result.
+// ---------------------------------------------------------------------------
+struct ScanExecMode {
+    const uint32_t *sk, *sv;     // operations grouped by account object id
+    const int64_t *params;
+    int64_t *acc_bal, *out;
+    int32_t *status;
+    int64_t m;
+    int P, R;
+    uint32_t o_acc;
+    __device__ Seg64 element(int64_t i) const
+    {
+        const uint32_t k = sk[i], t = sv[i] >> 7;
+        const bool head = i == 0 || sk[i - 1] != k;
+        const uint64_t d = (uint64_t)__ldg(&params[(int64_t)t * P + 1]);
+        // the balance before the bulk matters only at the first operation on
+        // the account; loading it for every operation keeps the loads free of
+        // branches, so the tile's loads all overlap
+        const uint64_t bal = (uint64_t)__ldcg(&acc_bal[k - o_acc]);
+        return Seg64::make(head ? 1u : 0u, head ? bal + d : d);
+    }
+    __device__ void output(int64_t i, const Seg64 &s) const
+    {
+        const uint32_t k = sk[i], t = sv[i] >> 7;
+        out[(int64_t)t * R] = (int64_t)s.v;
+        // last operation on the account: its balance after the bulk (every
+        // tile reading this account's balance published its aggregate
+        // before this tile finished its look-back)
+        if (i == m - 1 || sk[i + 1] != k) __stcg(&acc_bal[k - o_acc], (int64_t)s.v);
+    }
+};
+
+// the whole bulk's history rows fit, or nothing of it runs
+__global__ void scan_capacity_kernel(BulkCtl *ctl, int64_t n, int64_t hist_cap)
+{
+    if (ctl->base.hist + n > hist_cap) set_err(&ctl->err, ERR_CAPACITY);
+}
+
+// history rows in timestamp order (slot = base + t) and the teller and branch
+// sums; reads the signatures sequentially.  With `local` the sums gather in
+// shared memory first (one slot per teller and branch) and each block adds
+// its non-zero sums once: the same-address atomics on the few branch rows
+// would otherwise serialise in L2.
+__global__ void scan_dc_rows_kernel(DevDB db, DevBulk b, const BulkCtl *ctl, bool local)
+{
+    extern __shared__ unsigned long long sums[];   // [n_tel] tellers, then [n_br] branches
+    const bool stop = ctl->err != 0;               // uniform: set before this launch
+    if (stop) return;
+    const uint32_t n_tel = (uint32_t)db.n_tel, n_br = (uint32_t)db.n_br;
+    if (local) {
+        for (uint32_t i = threadIdx.x; i < n_tel + n_br; i += blockDim.x) sums[i] = 0;
+        __syncthreads();
+    }
+    const int64_t hb = ctl->base.hist;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < b.n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t a = (uint32_t)b.params[t * b.P];
+        const int64_t d = b.params[t * b.P + 1];
+        const uint32_t tl = db.div_tel.div(a), br = db.div_br.div(a);
+        const int64_t slot = hb + t;
+        db.h_ts[slot] = b.ts[t];
+        db.h_acc[slot] = a;
+        db.h_tel[slot] = tl;
+        db.h_br[slot] = br;
+        db.h_delta[slot] = d;
+        b.status[t] = 0;   // here, in timestamp order, rather than scattered by the scan
+        if (local) {
+            atomicAdd(&sums[tl], (unsigned long long)d);
+            atomicAdd(&sums[n_tel + br], (unsigned long long)d);
+        } else {
+            atomicAdd((unsigned long long *)&db.tel_bal[tl], (unsigned long long)d);
+            atomicAdd((unsigned long long *)&db.br_bal[br], (unsigned long long)d);
+        }
+    }
+    if (local) {
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < n_tel + n_br; i += blockDim.x) {
+            const unsigned long long v = sums[i];
+            if (!v) continue;
+            unsigned long long *dst = i < n_tel ? (unsigned long long *)&db.tel_bal[i]
+                                                : (unsigned long long *)&db.br_bal[i - n_tel];
+            atomicAdd(dst, v);
+        }
+    }
+}
+
 }  // namespace
 
 DevBulk make_dev_bulk(gputx_bulk *b, int mode) { return dev_bulk(b, mode); }
+
+cudaError_t launch_scan_exec(gputx_bulk *b, const uint32_t *sk, const uint32_t *sv, int64_t m)
+{
+    gputx_db *db = b->db;
+    cudaStream_t s = b->stream;
+    scan_capacity_kernel<<<1, 1, 0, s>>>(b->ctl, b->n, db->dev.hist_cap);
+    count_launches(1);
+    if (m > 0) {
+        const int64_t tiles = (m + SCAN_TILE - 1) / SCAN_TILE;
+        if (tiles > b->sc.scan_tiles) return cudaErrorInvalidValue;
+        ScanExecMode mode;
+        mode.sk = sk;
+        mode.sv = sv;
+        mode.params = b->params;
+        mode.acc_bal = db->dev.acc_bal;
+        mode.out = b->out;
+        mode.status = b->status;
+        mode.m = m;
+        mode.P = b->P;
+        mode.R = b->R;
+        mode.o_acc = db->dev.o_acc;
+        Seg64Status st;
+        st.word = (uint32_t *)b->sc.scan_status;
+        st.agg = b->sc.scan_vals;
+        st.inc = b->sc.scan_vals + tiles;
+        cudaError_t e = cudaMemsetAsync(st.word, 0, tiles * sizeof(uint32_t), s);
+        if (!e) e = cudaMemsetAsync(b->sc.tile_ctr + 12, 0, sizeof(uint32_t), s);
+        if (e) return e;
+        seg64_scan_kernel<ScanExecMode><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(
+            mode, m, st, b->sc.tile_ctr + 12, &b->ctl->err, (uint64_t)db->cfg.spin_limit_ns);
+        count_launches(1);
+    }
+    if (b->n > 0) {
+        // teller and branch sums in shared memory when they fit, one block per SM
+        const size_t smem = (size_t)(db->dev.n_tel + db->dev.n_br) * sizeof(unsigned long long);
+        const bool local = smem <= (200u << 10);
+        const int threads = 1024;
+        int64_t grid = (b->n + threads - 1) / threads;
+        if (grid > (int64_t)db->num_sms) grid = db->num_sms;
+        if (local && smem > (48u << 10)) {
+            const cudaError_t e = cudaFuncSetAttribute(scan_dc_rows_kernel,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e) return e;
+        }
+        scan_dc_rows_kernel<<<(unsigned)grid, threads, local ? smem : 0, s>>>(
+            db->dev, dev_bulk(b, GPUTX_CONFLICT_ADD), b->ctl, local);
+        count_launches(1);
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_gather(gputx_bulk *b, const uint32_t *order)
 {
@@ -479,6 +654,16 @@ cudaError_t launch_gather(gputx_bulk *b, const uint32_t *order)
     const DevBulk d = dev_bulk(b, 0);
     gather_kernel<<<grid_for(b->n), TB, 0, b->stream>>>(d, order, b->sc.rec_params, b->sc.rec_ts,
                                                              b->sc.rec_type, b->sc.rec_t, &b->ctl->err);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_dc(gputx_bulk *b, const uint32_t *order)
+{
+    if (b->n == 0) return cudaSuccess;
+    if (!b->sc.rec_dc) return cudaErrorInvalidValue;
+    gather_dc_kernel<<<grid_for(b->n), TB, 0, b->stream>>>(b->db->dev, dev_bulk(b, 0), order, b->sc.rec_dc,
+                                                                &b->ctl->err);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -688,10 +873,13 @@ cudaError_t launch_insert_slots(gputx_bulk *b)
 
 cudaError_t launch_part_heads(gputx_bulk *b, const uint32_t *skeys, int64_t n)
 {
-    if (n == 0) return cudaSuccess;
-    part_heads_kernel<<<grid_for(n), TB, 0, b->stream>>>(skeys, n, b->sc.part_start, b->ctl);
-    count_launches(1);
-    return cudaGetLastError();
+    if (n <= 0) return cudaSuccess;
+    HeadMode hm;
+    hm.skeys = skeys;
+    hm.part_start = b->sc.part_start;
+    hm.ctl = b->ctl;
+    hm.n = n;
+    return run_scan(b, hm, n, 4);
 }
 
 cudaError_t launch_tpl_reset(gputx_bulk *b, const uint32_t *skeys, int64_t m)

@@ -200,7 +200,7 @@ size_t carve_bulk(gputx_bulk *b, char *base, bool device_inputs)
     s.chunk_cap = nn + nn / 32 + 2;
     s.chunk_level = c.take<uint32_t>(s.chunk_cap);
     s.done = c.take<uint32_t>(nn + 1);
-    s.part_start = c.take<uint32_t>(nn);
+    s.part_start = c.take<uint32_t>(nn + 1);
     s.pid_key = c.take<uint32_t>(nn);
     s.pid_val = c.take<uint32_t>(nn);
     s.pid_key2 = c.take<uint32_t>(nn);
@@ -222,6 +222,8 @@ size_t carve_bulk(gputx_bulk *b, char *base, bool device_inputs)
     s.tile_ctr = c.take<uint32_t>(16);
     s.scan_tiles = (big + 2047) / 2048;
     s.scan_status = c.take<uint64_t>(s.scan_tiles);
+    s.scan_vals = c.take<uint64_t>(2 * s.scan_tiles);
+    s.rec_dc = db->dev.registered == (1u << GPUTX_T_DC_DEBIT_CREDIT) ? c.take<DcRecord>(nn) : nullptr;
     return c.off + 256;
 }
 
@@ -373,6 +375,8 @@ gputx_status gputx_create_db(const gputx_schema_desc *schema, const gputx_config
         d.n_acc = s.dc_accounts;
         d.acc_per_tel = s.dc_accounts / s.dc_tellers;
         d.acc_per_br = s.dc_accounts / s.dc_branches;
+        d.div_tel = FastDiv::make((uint32_t)d.acc_per_tel);
+        d.div_br = FastDiv::make((uint32_t)d.acc_per_br);
         TRY(dalloc(db, &d.br_bal, d.n_br, "branch"));
         TRY(dalloc(db, &d.tel_bal, d.n_tel, "teller"));
         TRY(dalloc(db, &d.acc_bal, d.n_acc, "account"));
@@ -916,7 +920,9 @@ gputx_status gputx_execute(gputx_db *db, gputx_bulk *b, int strategy, const gput
 {
     if (!db || !b || b->db != db) return fail(db, GPUTX_EINVAL, "bad arguments");
     if (b->executed) return fail(db, GPUTX_ESTATE, "bulk already executed");
-    if (strategy < GPUTX_KSET || strategy > GPUTX_AUTO) return fail(db, GPUTX_EINVAL, "strategy %d", strategy);
+    if (strategy < GPUTX_KSET || strategy > GPUTX_SCAN) return fail(db, GPUTX_EINVAL, "strategy %d", strategy);
+    if (strategy == GPUTX_SCAN && db->dev.registered != (1u << GPUTX_T_DC_DEBIT_CREDIT))
+        return fail(db, GPUTX_EINVAL, "SCAN needs a database whose only registered type is debit-credit");
     const int mode = opts ? opts->conflict_mode : GPUTX_CONFLICT_PAPER;
     if (mode != GPUTX_CONFLICT_PAPER && mode != GPUTX_CONFLICT_ADD) return fail(db, GPUTX_EINVAL, "conflict mode");
     int block = (opts && opts->block_threads) ? opts->block_threads : db->cfg.block_threads;
@@ -1012,11 +1018,18 @@ gputx_status gputx_execute(gputx_db *db, gputx_bulk *b, int strategy, const gput
             CK(launch_sort(b, pk, pv, pk2, pv2, b->n, bits), "partition sort");
             if (b->timing) cudaEventRecord(b->ev[2], s);
             CK(launch_part_heads(b, pk, b->n), "partition heads");
-            CK(launch_gather(b, pv), "gather");
+            if (part_dc_applies(db, part_size)) CK(launch_gather_dc(b, pv), "gather");
+            else CK(launch_gather(b, pv), "gather");
             CK(begin_tail(b), "order");
             if (b->timing) cudaEventRecord(b->ev[3], s);
-            CK(launch_part(b, pk, 128, (roots + part_size - 1) / part_size), "part execute");
+            CK(launch_part(b, pk, 128, (roots + part_size - 1) / part_size, part_size), "part execute");
         }
+    }
+    if (run == GPUTX_SCAN) {
+        if ((st = run_kset_analysis(b, GPUTX_CONFLICT_ADD, part_size, sk, sv, ak, av, m))) return st;
+        CK(begin_tail(b), "order");
+        if (b->timing) cudaEventRecord(b->ev[3], s);
+        CK(launch_scan_exec(b, sk, sv, m), "scan execute");
     }
     if (run == GPUTX_TPL) {
         if (!sk) {

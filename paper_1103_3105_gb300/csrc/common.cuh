@@ -13,6 +13,7 @@
 // Every item that can conflict (Section 4.1) has a dense 32-bit object id:
 // one contiguous range per (table, field group).
 #pragma once
+#include "fastdiv.h"
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -53,6 +54,7 @@ struct DevDB {
 
     // debit-credit
     int64_t n_br, n_tel, n_acc, acc_per_tel, acc_per_br;
+    FastDiv div_tel, div_br;   // account -> teller, account -> branch
     int64_t *br_bal, *tel_bal, *acc_bal;
     int64_t hist_cap;
     int64_t *h_ts, *h_acc, *h_tel, *h_br, *h_delta;
@@ -92,6 +94,13 @@ struct DevDB {
     // which types are enabled (bit per type id)
     uint32_t registered;
     int out_width;
+};
+
+// a debit-credit transaction packed for the PART executor (32 B, 16-byte
+// aligned: two vector loads)
+struct __align__(16) DcRecord {
+    int64_t delta, ts;
+    uint32_t a, t, tl, pad;
 };
 
 // insert bases of one bulk: where its new rows start in each append area

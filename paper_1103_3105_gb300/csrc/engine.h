@@ -50,6 +50,8 @@ struct Scratch {
     uint32_t *sort_status; // 4 x tiles x 256
     uint32_t *tile_ctr;    // 16 counters
     uint64_t *scan_status; // tiles
+    uint64_t *scan_vals;   // 2 x tiles: per-tile values of 64-bit scans
+    DcRecord *rec_dc;      // n packed debit-credit records (debit-credit-only databases)
     int64_t m_cap;         // op capacity
     int64_t sort_tiles, scan_tiles, chunk_cap;
 };
@@ -129,6 +131,8 @@ cudaError_t launch_insert_slots(gputx_bulk *b);
 cudaError_t launch_part_heads(gputx_bulk *b, const uint32_t *skeys, int64_t n);
 cudaError_t launch_tpl_reset(gputx_bulk *b, const uint32_t *skeys, int64_t m);
 cudaError_t launch_gather(gputx_bulk *b, const uint32_t *order);
+cudaError_t launch_gather_dc(gputx_bulk *b, const uint32_t *order);
+bool part_dc_applies(const gputx_db *db, int part_size);
 cudaError_t launch_begin(gputx_bulk *b);
 cudaError_t launch_finish(gputx_bulk *b);
 
@@ -136,8 +140,12 @@ cudaError_t launch_finish(gputx_bulk *b);
 cudaError_t launch_kset(gputx_bulk *b, const uint32_t *order, int64_t nchunks, int block, bool atomic_add);
 cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, int64_t depth, int narrow_max,
                                bool atomic_add);
-cudaError_t launch_part(gputx_bulk *b, const uint32_t *pkeys, int block, int64_t max_parts);
+cudaError_t launch_part(gputx_bulk *b, const uint32_t *pkeys, int block, int64_t max_parts, int part_size);
 cudaError_t launch_tpl(gputx_bulk *b, int block, bool atomic_add);
+// a conflict-free bulk (a 0-set) in one launch
+cudaError_t launch_independent(gputx_bulk *b, bool atomic_add);
+// SCAN: segmented prefix sums over operations grouped by account
+cudaError_t launch_scan_exec(gputx_bulk *b, const uint32_t *sk, const uint32_t *sv, int64_t m);
 int exec_blocks_per_sm(int kind, int block);
 
 // tables.cu

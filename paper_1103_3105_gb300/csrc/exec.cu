@@ -77,6 +77,16 @@ struct LevelArgs {
     bool atomic_add;
 };
 
+// a bulk known to hold no two conflicting transactions (a 0-set): every
+// transaction at once, straight from the bulk's signatures (timestamp order)
+__global__ void __launch_bounds__(256) independent_kernel(DevDB db, DevBulk b, const BulkCtl *ctl, bool atomic_add)
+{
+    if (ctl->err) return;
+    const int64_t hb = ctl->base.hist;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < b.n; t += (int64_t)gridDim.x * blockDim.x)
+        exec_txn(db, b, view_of(b, (uint32_t)t, hb), atomic_add);
+}
+
 // one wide level [level_off[k0], level_off[k0+1]) over the whole grid
 __global__ void __launch_bounds__(256) kset_level_kernel(LevelArgs a)
 {
@@ -91,7 +101,7 @@ __global__ void __launch_bounds__(256) kset_level_kernel(LevelArgs a)
 // one CTA.  While level k executes, level k+1's records come into L1; after
 // it, level k+1's rows are prefetched into L2; then the barrier.
 template <bool CLUSTER, int MAXT>
-__global__ void __launch_bounds__(MAXT) kset_narrow_kernel(LevelArgs a)
+__global__ void __launch_bounds__(MAXT, 1) kset_narrow_kernel(LevelArgs a)
 {
     if (a.ctl->err) return;   // set by an earlier launch only: uniform here
     const int64_t hb = a.ctl->base.hist;
@@ -218,6 +228,97 @@ __global__ void part_kernel(DevDB db, DevBulk b, const BulkCtl *ctl, const uint3
         has1 = has2;
         i++;
     }
+}
+
+// PART for bulks of debit-credit transactions only, one partition per
+// branch (Section 5.2 with the branch as partition key).  No transaction of
+// another partition touches this branch, its tellers or its accounts, so:
+//   - the branch balance lives in a register and the branch's tellers in
+//     shared memory for the whole partition, and are written back once;
+//   - the partition runs in batches of G transactions.  A batch issues all
+//     its record and account loads at once (one memory round trip, the
+//     accounts already prefetched into L2 by the batch before), then executes
+//     its transactions one by one in timestamp order.  An account loaded for
+//     the batch may have been written by an earlier transaction of the same
+//     batch: that transaction's new balance is forwarded instead (compared in
+//     registers); writes of earlier batches precede the loads in program
+//     order, so the loaded values include them.
+// The result equals running the partition's transactions one by one.
+constexpr int kPartDcTellers = 32;   // tellers per branch held in shared memory
+
+template <int G>
+__global__ void __launch_bounds__(128) part_dc_kernel(DevDB db, DevBulk b, const BulkCtl *ctl,
+                                                      const DcRecord *rec, const uint32_t *pkeys,
+                                                      const uint32_t *part_start)
+{
+    extern __shared__ unsigned long long part_smem[];
+    const uint32_t nt = blockDim.x, x = threadIdx.x;
+    int64_t *tel = (int64_t *)part_smem;   // teller k of thread x at [k * nt + x]
+    const uint32_t p = blockIdx.x * nt + x;
+    if (p >= ctl->npart || ctl->err) return;   // no block barrier below
+    const int64_t hb = ctl->base.hist;
+    const uint32_t lo = part_start[p], hi = part_start[p + 1];
+    const uint32_t br = __ldg(&pkeys[lo]);     // partition key = branch
+    const uint32_t tpb = (uint32_t)(db.acc_per_br / db.acc_per_tel);
+    const uint32_t tel0 = br * tpb;
+    int64_t bbal = __ldcg(&db.br_bal[br]);
+    for (uint32_t k = 0; k < tpb; k++) tel[k * nt + x] = __ldcg(&db.tel_bal[tel0 + k]);
+    // the first batch's accounts into L2
+    for (uint32_t k = 0; k < G && lo + k < hi; k++) prefetch_l2(&db.acc_bal[__ldg(&rec[lo + k].a)]);
+    for (uint32_t base = lo; base < hi; base += G) {
+        const uint32_t cnt = min((uint32_t)G, hi - base);
+        DcRecord r[G];
+        uint32_t an[G];
+        int64_t v[G];
+#pragma unroll
+        for (int k = 0; k < G; k++) {
+            if (k < (int)cnt) r[k] = rec[base + k];
+            else r[k] = DcRecord{0, 0, 0, 0, 0, 0};
+        }
+#pragma unroll
+        for (int k = 0; k < G; k++) an[k] = (base + G + k < hi) ? __ldg(&rec[base + G + k].a) : 0xffffffffu;
+#pragma unroll
+        for (int k = 0; k < G; k++) v[k] = (k < (int)cnt) ? __ldcg(&db.acc_bal[r[k].a]) : 0;
+        // the next batch's accounts into L2, the records after it into L1
+#pragma unroll
+        for (int k = 0; k < G; k++)
+            if (an[k] != 0xffffffffu) prefetch_l2(&db.acc_bal[an[k]]);
+#pragma unroll
+        for (int k = 0; k < G; k += 4)
+            if (base + 2 * G + k < hi) asm volatile("prefetch.global.L1 [%0];" ::"l"(rec + base + 2 * G + k));
+#pragma unroll
+        for (int k = 0; k < G; k++) {
+            if (k >= (int)cnt) break;
+            // the newest balance: forwarded from an earlier transaction of
+            // this batch on the same account, else the loaded value
+            int64_t old = v[k];
+#pragma unroll
+            for (int j = 0; j < k; j++)
+                if (r[j].a == r[k].a) old = v[j];
+            const int64_t slot = hb + base + k;
+            if (slot >= db.hist_cap) {          // history full: not executed
+                set_err(b.err, ERR_CAPACITY);
+                b.status[r[k].t] = 3;
+                v[k] = old;                     // later forwards see the unchanged balance
+                continue;
+            }
+            const int64_t na = wrap_add(old, r[k].delta);
+            v[k] = na;                          // from here on: this transaction's new balance
+            __stcg(&db.acc_bal[r[k].a], na);
+            int64_t *tc = &tel[(r[k].tl - tel0) * nt + x];
+            *tc = wrap_add(*tc, r[k].delta);
+            bbal = wrap_add(bbal, r[k].delta);
+            db.h_ts[slot] = r[k].ts;
+            db.h_acc[slot] = r[k].a;
+            db.h_tel[slot] = r[k].tl;
+            db.h_br[slot] = br;
+            db.h_delta[slot] = r[k].delta;
+            b.out[(int64_t)r[k].t * b.R] = na;
+            b.status[r[k].t] = 0;
+        }
+    }
+    __stcg(&db.br_bal[br], bbal);
+    for (uint32_t k = 0; k < tpb; k++) __stcg(&db.tel_bal[tel0 + k], tel[k * nt + x]);
 }
 
 struct TplArgs {
@@ -416,20 +517,50 @@ cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_part(gputx_bulk *b, const uint32_t *pkeys, int block, int64_t max_parts)
+bool part_dc_applies(const gputx_db *db, int part_size)
+{
+    const DevDB &d = db->dev;
+    return d.registered == (1u << GPUTX_T_DC_DEBIT_CREDIT) && part_size == 1 && d.n_br > 0 &&
+           d.acc_per_br / d.acc_per_tel <= kPartDcTellers;
+}
+
+cudaError_t launch_part(gputx_bulk *b, const uint32_t *pkeys, int block, int64_t max_parts, int part_size)
 {
     gputx_db *db = b->db;
     if (b->n == 0) return cudaSuccess;
     const DevBulk d = make_dev_bulk(b, GPUTX_CONFLICT_PAPER);
     // few partitions per SM: their scattered stores share one load/store
-    // pipeline, so spread the expected partitions over every SM
+    // pipeline, so spread the possible partitions over every SM
     const int64_t parts = std::max<int64_t>(1, std::min<int64_t>(b->n, max_parts));
     int threads = (int)((parts + db->num_sms - 1) / db->num_sms);
     threads = ((threads + 7) / 8) * 8;
     threads = threads < 8 ? 8 : (threads > block ? block : threads);
-    const int64_t grid = (b->n + threads - 1) / threads;   // npart <= n, read on the device
-    const size_t smem = (size_t)threads * 2 * CachedCells::kSlots * sizeof(unsigned long long);
-    part_kernel<<<(unsigned)grid, threads, smem, b->stream>>>(db->dev, d, b->ctl, pkeys, b->sc.part_start);
+    const int64_t grid = (parts + threads - 1) / threads;   // npart <= parts, read on the device
+    if (part_dc_applies(db, part_size)) {
+        const size_t smem = (size_t)threads * kPartDcTellers * 8;
+        if (smem > (48u << 10)) {
+            const cudaError_t e = cudaFuncSetAttribute(part_dc_kernel<16>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e) return e;
+        }
+        part_dc_kernel<16><<<(unsigned)grid, threads, smem, b->stream>>>(db->dev, d, b->ctl, b->sc.rec_dc, pkeys,
+                                                                       b->sc.part_start);
+    } else {
+        const size_t smem = (size_t)threads * 2 * CachedCells::kSlots * sizeof(unsigned long long);
+        part_kernel<<<(unsigned)grid, threads, smem, b->stream>>>(db->dev, d, b->ctl, pkeys, b->sc.part_start);
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_independent(gputx_bulk *b, bool atomic_add)
+{
+    gputx_db *db = b->db;
+    if (b->n == 0) return cudaSuccess;
+    int64_t grid = (b->n + 255) / 256;
+    if (grid > (int64_t)db->num_sms * 8) grid = (int64_t)db->num_sms * 8;
+    independent_kernel<<<(unsigned)grid, 256, 0, b->stream>>>(
+        db->dev, make_dev_bulk(b, atomic_add ? GPUTX_CONFLICT_ADD : GPUTX_CONFLICT_PAPER), b->ctl, atomic_add);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -88,7 +88,7 @@ __device__ __forceinline__ int access_set(const DevDB &db, int32_t type, const i
         // commute with each other and no procedure reads them, so only the
         // account orders transactions.
         const int64_t a = p[0];
-        const uint32_t b = (uint32_t)a / (uint32_t)db.acc_per_br;
+        const uint32_t b = db.div_br.div((uint32_t)a);
         if (mode == GPUTX_CONFLICT_ADD) {
             obj[0] = db.o_acc + (uint32_t)a; cls[0] = CLS_W; root[0] = b;
         } else {
@@ -306,8 +306,8 @@ __device__ __forceinline__ void prefetch_txn(const DevDB &db, const TxnView &v)
     case GPUTX_T_DC_DEBIT_CREDIT: {
         const uint32_t a = (uint32_t)v.p0;
         prefetch_l2(&db.acc_bal[a]);
-        prefetch_l2(&db.tel_bal[a / (uint32_t)db.acc_per_tel]);
-        prefetch_l2(&db.br_bal[a / (uint32_t)db.acc_per_br]);
+        prefetch_l2(&db.tel_bal[db.div_tel.div(a)]);
+        prefetch_l2(&db.br_bal[db.div_br.div(a)]);
         break;
     }
     case GPUTX_T_SUB_GET_SUBSCRIBER:
@@ -380,16 +380,26 @@ struct CachedCells {
     }
 };
 
+// A debit-credit transaction in two parts.  dc_state updates the three
+// balances -- the only cells later transactions of the bulk read -- and
+// returns what dc_finish writes: the history row and the outputs, which no
+// transaction of the bulk reads.  An executor may therefore publish the
+// state part (a barrier's release) before writing the rest.
+struct DcOut {
+    int64_t slot, ts, delta, na, a, tl, br;
+    uint32_t t;
+};
+
 // atomic_add: execute ADD-class increments with atomics (several
-// transactions of one level may add to one item).
+// transactions of one level may add to one item).  False when the history
+// is full (the transaction is not executed; status 3).
 template <class Cells>
-__device__ __forceinline__ void exec_dc(const DevDB &db, const DevBulk &b, const TxnView &v, bool atomic_add,
-                                        Cells &cells)
+__device__ __forceinline__ bool dc_state(const DevDB &db, const DevBulk &b, const TxnView &v, bool atomic_add,
+                                         Cells &cells, DcOut &o)
 {
     const uint32_t t = v.t;
     const int64_t a = v.p0, delta = v.p1;
-    // object ids fit 32 bits: 32-bit division is several times cheaper
-    const int64_t tl = (uint32_t)a / (uint32_t)db.acc_per_tel, br = (uint32_t)a / (uint32_t)db.acc_per_br;
+    const int64_t tl = db.div_tel.div((uint32_t)a), br = db.div_br.div((uint32_t)a);
     const int64_t slot = v.hist_slot;
     // every load before any store: the three rows are distinct cells but the
     // compiler cannot prove it, so interleaving would serialise three L2
@@ -403,7 +413,7 @@ __device__ __forceinline__ void exec_dc(const DevDB &db, const DevBulk &b, const
     if (slot >= db.hist_cap) {              // history full: not executed
         set_err(b.err, ERR_CAPACITY);
         b.status[t] = 3;
-        return;
+        return false;
     }
     // account: read-modify-write, its new value is the output
     const int64_t na = wrap_add(old_a, delta);
@@ -415,13 +425,34 @@ __device__ __forceinline__ void exec_dc(const DevDB &db, const DevBulk &b, const
         cells.st(&db.tel_bal[tl], wrap_add(old_t, delta));
         cells.st(&db.br_bal[br], wrap_add(old_b, delta));
     }
-    db.h_ts[slot] = v.ts;
-    db.h_acc[slot] = a;
-    db.h_tel[slot] = tl;
-    db.h_br[slot] = br;
-    db.h_delta[slot] = delta;
-    b.out[(int64_t)t * b.R] = na;
-    b.status[t] = 0;
+    o.slot = slot;
+    o.ts = v.ts;
+    o.delta = delta;
+    o.na = na;
+    o.a = a;
+    o.tl = tl;
+    o.br = br;
+    o.t = t;
+    return true;
+}
+
+__device__ __forceinline__ void dc_finish(const DevDB &db, const DevBulk &b, const DcOut &o)
+{
+    db.h_ts[o.slot] = o.ts;
+    db.h_acc[o.slot] = o.a;
+    db.h_tel[o.slot] = o.tl;
+    db.h_br[o.slot] = o.br;
+    db.h_delta[o.slot] = o.delta;
+    b.out[(int64_t)o.t * b.R] = o.na;
+    b.status[o.t] = 0;
+}
+
+template <class Cells>
+__device__ __forceinline__ void exec_dc(const DevDB &db, const DevBulk &b, const TxnView &v, bool atomic_add,
+                                        Cells &cells)
+{
+    DcOut o;
+    if (dc_state(db, b, v, atomic_add, cells, o)) dc_finish(db, b, o);
 }
 
 // subscriber-location procedures (stand-ins shaped like TM-1, Appendix E)

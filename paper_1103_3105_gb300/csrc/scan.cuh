@@ -184,8 +184,184 @@ dualseg_scan_kernel(Mode mode, int64_t count, uint64_t *status, uint32_t *tile_c
 }
 
 // ===========================================================================
+// segmented 64-bit sums (wrapping): the scan state of the SCAN executor
+// ===========================================================================
+// (f, v): f set = a segment starts in this span, v = sum since the last
+// start (or since the beginning).  A 64-bit sum and its flag do not fit one
+// status word, so a tile publishes its value first and then, with release
+// semantics, a 32-bit status word; readers acquire the status word before
+// reading the value.  Aggregate and inclusive values have separate slots, so
+// a value a reader may still fetch is never overwritten.
+struct Seg64 {
+    uint32_t f;
+    uint64_t v;
+    __device__ __forceinline__ static Seg64 make(uint32_t f, uint64_t v) { return Seg64{f, v}; }
+    __device__ __forceinline__ static Seg64 identity() { return Seg64{0u, 0ull}; }
+    // a precedes b
+    __device__ __forceinline__ static Seg64 combine(const Seg64 &a, const Seg64 &b)
+    {
+        return Seg64{a.f | b.f, b.f ? b.v : a.v + b.v};
+    }
+};
+
+__device__ __forceinline__ uint32_t ld_acquire_gpu_u32(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu_u32(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ Seg64 shfl_down_seg(const Seg64 &x, int off)
+{
+    return Seg64{__shfl_down_sync(0xffffffffu, x.f, off), __shfl_down_sync(0xffffffffu, x.v, off)};
+}
+__device__ __forceinline__ Seg64 shfl_up_seg(const Seg64 &x, int off)
+{
+    return Seg64{__shfl_up_sync(0xffffffffu, x.f, off), __shfl_up_sync(0xffffffffu, x.v, off)};
+}
+__device__ __forceinline__ Seg64 shfl_seg(const Seg64 &x, int lane)
+{
+    return Seg64{__shfl_sync(0xffffffffu, x.f, lane), __shfl_sync(0xffffffffu, x.v, lane)};
+}
+
+struct Seg64Status {
+    uint32_t *word;      // per tile: state (LB_*) | f << 2
+    uint64_t *agg, *inc; // per tile values
+};
+
+// Look-back by warp 0 of a tile; returns the exclusive prefix of `tile`.
+__device__ __forceinline__ Seg64 lookback_seg64(const Seg64Status &st, uint32_t tile, const Seg64 &tile_agg,
+                                                uint32_t *err, uint64_t spin_limit_ns)
+{
+    const int lane = threadIdx.x & 31;
+    if (tile == 0) {
+        if (lane == 0) {
+            st.inc[0] = tile_agg.v;
+            st_release_gpu_u32(&st.word[0], (uint32_t)LB_INC | (tile_agg.f << 2));
+        }
+        return Seg64::identity();
+    }
+    if (lane == 0) {
+        st.agg[tile] = tile_agg.v;
+        st_release_gpu_u32(&st.word[tile], (uint32_t)LB_AGG | (tile_agg.f << 2));
+    }
+    Seg64 running = Seg64::identity();
+    int64_t window_end = (int64_t)tile - 1;
+    const uint64_t t0 = globaltimer();
+    while (true) {
+        const int64_t t = window_end - lane;
+        uint32_t w = (uint32_t)LB_INC;
+        Seg64 x = Seg64::identity();
+        if (t >= 0) {
+            while (true) {
+                w = ld_acquire_gpu_u32(&st.word[t]);
+                if ((w & 3u) != (uint32_t)LB_INVALID) break;
+                if (globaltimer() - t0 > spin_limit_ns) {
+                    set_err(err, ERR_TIMEOUT);
+                    w = (uint32_t)LB_INC;   // give up: fold nothing more
+                    break;
+                }
+            }
+            if ((w & 3u) == (uint32_t)LB_INC) x = Seg64{(w >> 2) & 1u, ld_volatile_u64(&st.inc[t])};
+            else if ((w & 3u) == (uint32_t)LB_AGG) x = Seg64{(w >> 2) & 1u, ld_volatile_u64(&st.agg[t])};
+        }
+        const uint32_t inc_mask = __ballot_sync(0xffffffffu, (w & 3u) == (uint32_t)LB_INC);
+        const int stop = inc_mask ? __ffs(inc_mask) - 1 : 31;
+        Seg64 v = (lane <= stop) ? x : Seg64::identity();
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const Seg64 other = shfl_down_seg(v, off);
+            if (lane + off < 32) v = Seg64::combine(other, v);
+        }
+        v = shfl_seg(v, 0);
+        running = Seg64::combine(v, running);
+        if (inc_mask) break;
+        window_end -= 32;
+    }
+    if (lane == 0) {
+        const Seg64 incl = Seg64::combine(running, tile_agg);
+        st.inc[tile] = incl.v;
+        st_release_gpu_u32(&st.word[tile], (uint32_t)LB_INC | (incl.f << 2));
+    }
+    return running;
+}
+
+// Single-pass scan of a Seg64 state over [0, count).  Mode provides
+// `Seg64 element(int64_t i)` and `void output(int64_t i, const Seg64 &incl)`;
+// thread t owns SCAN_ITEMS consecutive elements.
+template <class Mode>
+__global__ void __launch_bounds__(SCAN_THREADS)
+seg64_scan_kernel(Mode mode, int64_t count, Seg64Status st, uint32_t *tile_ctr, uint32_t *err,
+                  uint64_t spin_limit_ns)
+{
+    __shared__ uint32_t s_tile, s_abort;
+    __shared__ Seg64 s_warp[SCAN_THREADS / 32];
+    __shared__ Seg64 s_prefix;
+    if (threadIdx.x == 0) {
+        s_abort = *(volatile uint32_t *)err;
+        if (!s_abort) s_tile = atomicAdd(tile_ctr, 1u);
+    }
+    __syncthreads();
+    if (s_abort) return;
+    const uint32_t tile = s_tile;
+    const int64_t base = (int64_t)tile * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    Seg64 incl[SCAN_ITEMS];
+    // every element's loads first (independent), then the combine chain
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; j++) {
+        const int64_t i = base + j;
+        incl[j] = (i < count) ? mode.element(i) : Seg64::identity();
+    }
+    Seg64 acc = incl[0];
+#pragma unroll
+    for (int j = 1; j < SCAN_ITEMS; j++) {
+        acc = Seg64::combine(acc, incl[j]);
+        incl[j] = acc;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    Seg64 x = acc;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const Seg64 o = shfl_up_seg(x, off);
+        if (lane >= off) x = Seg64::combine(o, x);
+    }
+    if (lane == 31) s_warp[warp] = x;
+    Seg64 thread_excl = shfl_up_seg(x, 1);
+    if (lane == 0) thread_excl = Seg64::identity();
+    __syncthreads();
+    if (warp == 0) {
+        Seg64 w = (lane < SCAN_THREADS / 32) ? s_warp[lane] : Seg64::identity();
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const Seg64 o = shfl_up_seg(w, off);
+            if (lane >= off) w = Seg64::combine(o, w);
+        }
+        const Seg64 tile_agg = shfl_seg(w, SCAN_THREADS / 32 - 1);
+        Seg64 wexcl = shfl_up_seg(w, 1);
+        if (lane == 0) wexcl = Seg64::identity();
+        if (lane < SCAN_THREADS / 32) s_warp[lane] = wexcl;
+        const Seg64 pre = lookback_seg64(st, tile, tile_agg, err, spin_limit_ns);
+        if (lane == 0) s_prefix = pre;
+    }
+    __syncthreads();
+    const Seg64 prefix = Seg64::combine(Seg64::combine(s_prefix, s_warp[warp]), thread_excl);
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; j++) {
+        const int64_t i = base + j;
+        if (i < count) mode.output(i, Seg64::combine(prefix, incl[j]));
+    }
+}
+
+// ===========================================================================
 // onesweep LSD radix sort of (u32 key, u32 value) pairs, 8-bit digits
 // ===========================================================================
+// (internal linkage: each translation unit that includes this header gets
+// its own copy of these kernels)
+namespace {
 constexpr int SORT_THREADS = 512;
 constexpr int SORT_ITEMS = 16;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
@@ -355,5 +531,7 @@ radix_pass_kernel(const uint32_t *__restrict__ kin, const uint32_t *__restrict__
         vout[g] = s_vals[i];
     }
 }
+
+}  // namespace
 
 }  // namespace gtx

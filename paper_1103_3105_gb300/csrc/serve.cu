@@ -104,6 +104,9 @@ struct gputx_server {
     std::vector<Slot> slots;
     std::deque<int> order;            // in-flight slots in execution order
     int R = 1, P = 1;
+    // incremental 0-set mode: the device pool, and the oldest id not yet done
+    gputx_pool *zpool = nullptr;
+    int64_t oldest_open = 0;
 };
 
 namespace {
@@ -267,6 +270,105 @@ void worker_main(gputx_server *s)
     }
 }
 
+// Incremental 0-set serving (Section 5.3): arrivals join the device pool as
+// they come (at once while the pool holds work, else when the oldest waited
+// deadline_us or max_bulk are waiting), and every step executes the pool's
+// current 0-set.  Results complete per transaction.
+void worker_zero_set(gputx_server *s)
+{
+    cudaSetDevice(s->db->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    const int64_t deadline = s->cfg.deadline_us * 1000;
+    std::vector<int64_t> a_ts, r_ts, r_vals;
+    std::vector<int32_t> a_type, r_st;
+    std::vector<int64_t> a_params;
+    while (s->worker_status == GPUTX_OK) {
+        const int64_t queued = s->next_id - s->next_consume;
+        const size_t in_pool = gputx_pool_pending(s->zpool);
+        if (s->stop && queued == 0 && in_pool == 0) break;
+        bool take = false;
+        if (queued > 0) {
+            const int64_t oldest = s->p_arrival[s->next_consume - s->pool_base];
+            take = in_pool > 0 || queued >= s->cfg.max_bulk || now_ns() - oldest >= deadline || s->stop || s->flush;
+        }
+        if (take) {
+            // as many as the pool's capacity takes (halving on ECAPACITY)
+            int64_t n = std::min<int64_t>(queued, s->cfg.max_bulk);
+            const int64_t off = s->next_consume - s->pool_base;
+            a_ts.resize(n);
+            a_type.assign(s->p_type.begin() + off, s->p_type.begin() + off + n);
+            a_params.assign(s->p_params.begin() + off * s->P, s->p_params.begin() + (off + n) * s->P);
+            for (int64_t i = 0; i < n; i++) a_ts[i] = s->next_consume + i;
+            lk.unlock();
+            gputx_status st = GPUTX_ECAPACITY;
+            while (n > 0 && (st = gputx_pool_add(s->zpool, a_ts.data(), a_type.data(), a_params.data(), (size_t)n)) ==
+                                GPUTX_ECAPACITY)
+                n /= 2;
+            lk.lock();
+            if (st == GPUTX_OK) {
+                s->next_consume += n;
+                s->inflight_txns += n;
+            } else if (st != GPUTX_ECAPACITY) {
+                set_worker_error(s, st, "pool add");
+                break;
+            }
+        }
+        if (gputx_pool_pending(s->zpool) > 0) {
+            lk.unlock();
+            size_t k = 0, got = 0;
+            gputx_status st = gputx_pool_step(s->zpool, &k);
+            if (st == GPUTX_OK && k) {
+                r_ts.resize(k);
+                r_st.resize(k);
+                r_vals.resize(k * s->R);
+                st = gputx_pool_results(s->zpool, r_ts.data(), r_st.data(), r_vals.data(), k, &got);
+            }
+            const int64_t t = now_ns();
+            lk.lock();
+            if (st != GPUTX_OK) {
+                set_worker_error(s, st, "pool step");
+                break;
+            }
+            for (size_t i = 0; i < got; i++) {
+                const int64_t id = r_ts[i];
+                s->r_status[id] = r_st[i];
+                std::memcpy(&s->r_values[id * s->R], &r_vals[i * s->R], sizeof(int64_t) * s->R);
+                s->r_complete[id] = t;
+                s->r_done[id] = 1;
+                s->hist.add(t - s->p_arrival[id - s->pool_base]);
+                int64_t need[4];
+                insert_need(s, s->p_type[id - s->pool_base], &s->p_params[(id - s->pool_base) * s->P], need);
+                for (int q = 0; q < 4; q++) {
+                    s->ins_reserved[q] -= need[q];
+                    s->ins_used[q] += need[q];
+                }
+            }
+            s->completed += (int64_t)got;
+            s->inflight_txns -= (int64_t)got;
+            s->last_complete = t;
+            s->bulks++;
+            s->max_bulk_seen = std::max<int64_t>(s->max_bulk_seen, (int64_t)got);
+            while (s->oldest_open < s->next_id && s->r_done[s->oldest_open]) s->oldest_open++;
+            const int64_t drop = std::min(s->oldest_open, s->next_consume) - s->pool_base;
+            if (drop > (1 << 20) && drop * 2 > (int64_t)s->p_type.size()) {
+                s->p_type.erase(s->p_type.begin(), s->p_type.begin() + drop);
+                s->p_params.erase(s->p_params.begin(), s->p_params.begin() + drop * s->P);
+                s->p_arrival.erase(s->p_arrival.begin(), s->p_arrival.begin() + drop);
+                s->pool_base += drop;
+            }
+            s->cv.notify_all();
+            continue;
+        }
+        int64_t wait_ns = 200000;
+        if (queued > 0) {
+            const int64_t oldest = s->p_arrival[s->next_consume - s->pool_base];
+            wait_ns = std::max<int64_t>(0, oldest + deadline - now_ns());
+        }
+        if (wait_ns > 0) s->cv.wait_for(lk, std::chrono::nanoseconds(wait_ns));
+    }
+    s->cv.notify_all();
+}
+
 }  // namespace
 
 extern "C" {
@@ -289,7 +391,7 @@ gputx_status gputx_server_create(gputx_db *db, const gputx_serve_config *cfg, gp
     if (c.max_inflight > 8) c.max_inflight = 8;
     if (c.params_per_txn <= 0) c.params_per_txn = 2;
     if (c.queue_capacity <= 0) c.queue_capacity = 1ll << 30;
-    if (c.strategy < GPUTX_KSET || c.strategy > GPUTX_AUTO) {
+    if (c.strategy < GPUTX_KSET || c.strategy > GPUTX_SCAN) {
         delete s;
         return GPUTX_EINVAL;
     }
@@ -311,6 +413,20 @@ gputx_status gputx_server_create(gputx_db *db, const gputx_serve_config *cfg, gp
     s->ins_used[1] = cur.cf;
     s->ins_used[2] = cur.ord;
     s->ins_used[3] = cur.ol;
+    if (c.zero_set) {
+        gputx_pool_config pc{};
+        pc.capacity = std::min<int64_t>(1 << 25, std::max<int64_t>(2 * c.max_bulk, 1 << 12));
+        pc.params_per_txn = c.params_per_txn;
+        pc.conflict_mode = c.conflict_mode;
+        const gputx_status pst = gputx_pool_create(db, &pc, &s->zpool);
+        if (pst != GPUTX_OK) {
+            delete s;
+            return pst;
+        }
+        s->worker = std::thread(worker_zero_set, s);
+        *out = s;
+        return GPUTX_OK;
+    }
     s->slots.resize(c.max_inflight);
     for (Slot &sl : s->slots) {
         const int64_t n = c.max_bulk;
@@ -442,6 +558,7 @@ void gputx_server_destroy(gputx_server *s)
         s->cv.notify_all();
     }
     if (s->worker.joinable()) s->worker.join();
+    if (s->zpool) gputx_pool_destroy(s->zpool);
     for (Slot &sl : s->slots) {
         if (sl.bulk) gputx_free_bulk(sl.bulk);
         if (sl.h_type) cudaFreeHost(sl.h_type);

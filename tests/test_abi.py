@@ -48,7 +48,8 @@ def test_structs_match_header_sizes():
     assert ctypes.sizeof(G.Config) == 8 + 4 + 4 + 8 * 4
     assert ctypes.sizeof(G.ExecOpts) == 24
     assert ctypes.sizeof(G.ExecStats) == 8 + 6 * 8 + 6 * 4
-    assert ctypes.sizeof(G.ServeConfig) == 8 * 2 + 4 * 4 + 8 * 2
+    assert ctypes.sizeof(G.ServeConfig) == 8 * 2 + 4 * 4 + 8 * 2 + 4 * 2
     assert ctypes.sizeof(G.ServeStats) == 5 * 8 + 4 * 8
     assert ctypes.sizeof(G.BatchConfig) == 4 * 4 + 2 * 8 + 2 * 4
+    assert ctypes.sizeof(G.PoolConfig) == 8 + 2 * 4 + 2 * 8
     assert ctypes.sizeof(G.BatchChoice) == 4 * 4 + 2 * 8 + 16 * 4 * 2 + 16 * 8 * 2

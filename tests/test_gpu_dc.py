@@ -14,7 +14,7 @@ from tests._helpers import gpu_logical_state, oracle_logical_state, state_diff, 
 
 pytestmark = pytest.mark.gpu
 
-STRATS = ["kset", "part", "tpl"]
+STRATS = ["kset", "part", "tpl", "scan"]
 MODES = [G.CONFLICT_PAPER, G.CONFLICT_ADD]
 
 
@@ -93,12 +93,30 @@ def test_skew(theta, strategy):
     g.close()
 
 
+@pytest.mark.parametrize("B,T,A", [(4, 40, 160), (8, 8, 64), (3, 96, 960), (2, 66, 660)])
+def test_part_dense_repeats(B, T, A):
+    """PART with few accounts per branch: an account recurs within a few
+    transactions of its partition (the early account loads must see the
+    writes in between), and many accounts share a slot of the recent-write
+    table.  Covers 1, 10 and 32 tellers per branch (shared-memory tellers)
+    and 33 (the general partition runner)."""
+    g, o = make_pair(B, T, A, 1 << 17)
+    ts0 = 0
+    for k, theta in enumerate([0.0, 0.9]):
+        bulk = W.dc_bulk(20_000 + 13 * k, A, theta, seed=300 + k, ts0=ts0)
+        ts0 += len(bulk["ts"])
+        stats, st, out, ost, oout = run_both(g, o, bulk, "part", 0)
+        assert stats["strategy"] == G.PART
+        assert_same(g, o, st, out, ost, oout)
+    g.close()
+
+
 def test_strategies_agree_across_a_sequence():
     """Bulks run back to back with different strategies equal one serial run."""
     g, o = make_pair(20, 200, 20000, 1 << 17)
     ts0 = 0
     for k, (s, m) in enumerate([("kset", 0), ("tpl", 1), ("part", 0), ("kset", 1), ("tpl", 0),
-                                ("auto", 0), ("auto", 1)]):
+                                ("auto", 0), ("scan", 0), ("auto", 1), ("scan", 1)]):
         bulk = W.dc_bulk(5000 + 37 * k, 20000, 0.7, seed=50 + k, ts0=ts0)
         ts0 += len(bulk["ts"])
         stats, st, out, ost, oout = run_both(g, o, bulk, s, m)
@@ -189,7 +207,7 @@ def test_bounded_wait_reports_timeout(strategy, launch):
     g2.close()
 
 
-@pytest.mark.parametrize("strategy,mode", [("kset", 0), ("kset", 1), ("tpl", 1), ("part", 0)])
+@pytest.mark.parametrize("strategy,mode", [("kset", 0), ("kset", 1), ("tpl", 1), ("part", 0), ("scan", 0)])
 def test_full_size_config2(strategy, mode):
     """The benchmark's workload: 1,000 branches, 10,000 tellers, 10,000,000
     accounts, a bulk of 2^22 transactions, in the benchmark's launch shape.
@@ -208,7 +226,7 @@ def test_full_size_config2(strategy, mode):
     g.close()
 
 
-@pytest.mark.parametrize("strategy,mode", [("kset", 0), ("kset", 1), ("tpl", 0), ("part", 0)])
+@pytest.mark.parametrize("strategy,mode", [("kset", 0), ("kset", 1), ("tpl", 0), ("part", 0), ("scan", 0)])
 def test_back_to_back_bulks_without_sync(strategy, mode):
     """Bulks executed one after another without waiting: each bulk's analysis
     overlaps the previous bulk's execution on the device, yet they apply in
@@ -227,4 +245,46 @@ def test_back_to_back_bulks_without_sync(strategy, mode):
         assert np.array_equal(st, ost) and np.array_equal(out, oout)
     gs, os_ = gpu_logical_state(g, dc=True), oracle_logical_state(o)
     assert states_equal(gs, os_), state_diff(gs, os_)
+    g.close()
+
+
+def test_scan_full_size_hot_accounts():
+    """SCAN at the benchmark's size with Zipf 0.99 accounts: a dependency
+    graph over 200,000 levels deep, executed as prefix sums."""
+    A = 10_000_000
+    g, o = make_pair(1000, 10000, A, 1 << 22, max_bulk=1 << 22)
+    bulk = W.dc_bulk(1 << 22, A, 0.99, seed=W.seed_for(2, 99))
+    stats, st, out, ost, oout = run_both(g, o, bulk, "scan", 0)
+    assert np.array_equal(st, ost) and np.array_equal(out, oout)
+    assert np.array_equal(g.read(G.TBL_DC_ACCOUNT)[:, 0], o["acc_bal"])
+    assert np.array_equal(g.read(G.TBL_DC_BRANCH)[:, 0], o["br_bal"])
+    assert np.array_equal(g.read(G.TBL_DC_TELLER)[:, 0], o["tel_bal"])
+    h = g.read(G.TBL_DC_HISTORY)
+    assert np.array_equal(h[np.argsort(h[:, 0])], o.history())
+    g.close()
+
+
+def test_scan_history_full_writes_nothing():
+    """SCAN runs a bulk whole or not at all: history rows that do not fit
+    fail the bulk with ECAPACITY and leave the database as it was."""
+    g, o = make_pair(4, 40, 4000, 150)
+    run_both(g, o, W.dc_bulk(100, 4000, 0.0, seed=5), "scan", 0)
+    before = gpu_logical_state(g, dc=True)
+    b = g.submit_dict(W.dc_bulk(100, 4000, 0.0, seed=6, ts0=100)).execute("scan")
+    with pytest.raises(G.GputxError) as e:
+        b.sync()
+    assert e.value.status == G.ECAPACITY
+    b.free()
+    assert states_equal(before, gpu_logical_state(g, dc=True))
+    g.close()
+
+
+def test_scan_needs_debit_credit_only():
+    g = G.Database(dc=(4, 40, 4000), sub=100, history_capacity=1024, sub_child_capacity=1024, max_bulk=1024)
+    g.register(G.DC_TYPES + G.SUB_TYPES)
+    b = g.submit_dict(W.dc_bulk(10, 4000, 0.0, seed=1))
+    with pytest.raises(G.GputxError) as e:
+        b.execute("scan")
+    assert e.value.status == G.EINVAL
+    b.free()
     g.close()

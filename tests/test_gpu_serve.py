@@ -45,7 +45,7 @@ def trickle(srv, bulk, rng, max_chunk=3000, pause_s=0.0002):
 
 
 @pytest.mark.parametrize("strategy,mode,inflight", [("kset", 0, 3), ("kset", 1, 1), ("tpl", 1, 2),
-                                                    ("part", 0, 2), ("auto", 0, 3)])
+                                                    ("part", 0, 2), ("auto", 0, 3), ("scan", 0, 3)])
 def test_served_stream_equals_serial_execution(strategy, mode, inflight):
     A = 10_000
     g = dc_db(A=A)
@@ -61,6 +61,29 @@ def test_served_stream_equals_serial_execution(strategy, mode, inflight):
     srv.close()
     assert nd == 60_000 and stats["completed"] == 60_000
     assert stats["bulks"] > 1 and 0 < stats["p50_us"] <= stats["p99_us"]
+    ost, oout = o.execute(bulk, R=1)
+    assert np.array_equal(st, ost) and np.array_equal(vals, oout)
+    gs, os_ = gpu_logical_state(g, dc=True), oracle_logical_state(o)
+    assert states_equal(gs, os_), state_diff(gs, os_)
+    g.close()
+
+
+@pytest.mark.parametrize("theta,mode", [(0.0, 0), (0.99, 0), (0.99, 1)])
+def test_zero_set_serving_equals_serial_execution(theta, mode):
+    """Incremental 0-set serving (Section 5.3): arrivals join the device pool
+    and each step runs its 0-set; results complete out of id order, yet the
+    stream equals serial execution in id order."""
+    A = 10_000
+    g = dc_db(A=A)
+    o = oracle.OracleDB(dc=W.dc_tables(10, 100, A), hist_cap=1 << 20)
+    srv = G.Server(g, deadline_us=300, max_bulk=4096, zero_set=True, conflict_mode=mode)
+    bulk = W.dc_bulk(30_000, A, theta, seed=33 + mode)
+    trickle(srv, bulk, np.random.default_rng(2))
+    srv.drain()
+    st, vals, done_ns, nd = srv.results(0, 30_000)
+    stats = srv.stats()
+    srv.close()
+    assert nd == 30_000 and stats["completed"] == 30_000 and stats["bulks"] > 1
     ost, oout = o.execute(bulk, R=1)
     assert np.array_equal(st, ost) and np.array_equal(vals, oout)
     gs, os_ = gpu_logical_state(g, dc=True), oracle_logical_state(o)
