@@ -63,7 +63,20 @@ typedef enum {
      * does not depend on the depth of the dependency graph; the results are
      * those of Definition 1.  If the bulk's history rows do not all fit, the
      * bulk fails with ECAPACITY and writes nothing. */
-    GPUTX_SCAN = 4
+    GPUTX_SCAN = 4,
+    /* Appendix G, timestamp constraint relaxed: the results equal serial
+     * execution in SOME order (serializability), the one gputx_bulk_order
+     * reports, instead of timestamp order.
+     * PART_RELAXED groups transactions by partition with per-partition
+     * counters and a prefix sum (no sort); each partition runs in counter
+     * order.  A bulk with a cross-partition transaction runs as TPL_RELAXED.
+     * TPL_RELAXED: every transaction takes a spin lock on each of its items in
+     * increasing item order (no deadlock), executes, takes a commit ticket
+     * while holding the locks and releases them; the ticket order is the
+     * serial order.  With GPUTX_CONFLICT_ADD, ADD-class items are updated with
+     * atomics instead of locked.  Waits are bounded (ETIMEOUT). */
+    GPUTX_PART_RELAXED = 5,
+    GPUTX_TPL_RELAXED = 6
 } gputx_strategy;
 
 typedef enum {
@@ -233,6 +246,13 @@ gputx_status gputx_sync_bulk(gputx_bulk *bulk, gputx_exec_stats *stats);
  * width (gputx_output_width). */
 gputx_status gputx_read_results(gputx_bulk *bulk, int32_t *status, int64_t *values, size_t n,
                                 int n_values);
+
+/* After a sync: order[k] = the index (0..n-1) of the transaction at position
+ * k of a serial order whose execution gives exactly this bulk's results.  For
+ * the timestamp-order strategies that is 0, 1, ..., n-1 (Definition 1); for
+ * the relaxed strategies it is the order they executed in.  EINVAL if n
+ * differs from the bulk size or the bulk has not been executed. */
+gputx_status gputx_bulk_order(gputx_bulk *bulk, uint32_t *order, size_t n);
 
 /* Device pointers of the result arrays (status int32[n], values int64[n x
  * width]) for callers that keep results on the device. */

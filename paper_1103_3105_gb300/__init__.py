@@ -21,8 +21,9 @@ LIB_PATH = os.path.join(_HERE, "libgputx.so")
 # --- constants mirrored from include/gputx.h --------------------------------
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBOUNDS, ESTATE, ECAPACITY = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ETIMEOUT", "EBOUNDS", "ESTATE", "ECAPACITY"]
-KSET, PART, TPL, AUTO, SCAN = range(5)
-STRATEGIES = {"kset": KSET, "part": PART, "tpl": TPL, "auto": AUTO, "scan": SCAN}
+KSET, PART, TPL, AUTO, SCAN, PART_RELAXED, TPL_RELAXED = range(7)
+STRATEGIES = {"kset": KSET, "part": PART, "tpl": TPL, "auto": AUTO, "scan": SCAN,
+              "part_relaxed": PART_RELAXED, "tpl_relaxed": TPL_RELAXED}
 CONFLICT_PAPER, CONFLICT_ADD = 0, 1
 MEM_HOST, MEM_DEVICE = 0, 1
 
@@ -49,7 +50,7 @@ EXPORTED = ("gputx_create_db", "gputx_destroy_db", "gputx_last_error", "gputx_re
             "gputx_server_last_error", "gputx_server_destroy", "gputx_batcher_create",
             "gputx_batcher_run", "gputx_batcher_choice", "gputx_batcher_destroy",
             "gputx_pool_create", "gputx_pool_add", "gputx_pool_step", "gputx_pool_results",
-            "gputx_pool_pending", "gputx_pool_destroy")
+            "gputx_pool_pending", "gputx_pool_destroy", "gputx_bulk_order")
 
 
 class GputxError(RuntimeError):
@@ -155,6 +156,7 @@ def lib():
             "gputx_sync_bulk": ([p, C.POINTER(ExecStats)], C.c_int),
             "gputx_read_results": ([p, p, p, sz, C.c_int], C.c_int),
             "gputx_bulk_results_device": ([p, C.POINTER(p), C.POINTER(p)], C.c_int),
+            "gputx_bulk_order": ([p, p, sz], C.c_int),
             "gputx_output_width": ([p], C.c_int),
             "gputx_free_bulk": ([p], None),
             "gputx_version": ([], C.c_char_p),
@@ -272,6 +274,12 @@ def gputx_read_results(db, bulk, n: int, width: int, status=None, values=None):
     return status, values
 
 
+def gputx_bulk_order(db, bulk, n: int) -> np.ndarray:
+    order = np.zeros(n, dtype=np.uint32)
+    _check(db, lib().gputx_bulk_order(bulk, _ptr(order), n))
+    return order
+
+
 def gputx_bulk_results_device(bulk):
     s, v = C.c_void_p(), C.c_void_p()
     lib().gputx_bulk_results_device(bulk, C.byref(s), C.byref(v))
@@ -314,6 +322,11 @@ class Bulk:
 
     def results(self, status=None, values=None):
         return gputx_read_results(self.db.h, self.h, self.n, self.db.width, status, values)
+
+    def order(self) -> np.ndarray:
+        """A serial order with this bulk's results (timestamp order unless a
+        relaxed strategy ran)."""
+        return gputx_bulk_order(self.db.h, self.h, self.n)
 
     def free(self):
         if self.h:

@@ -501,6 +501,53 @@ __global__ void gather_kernel(DevBulk b, const uint32_t *order, int64_t *r_param
 }
 
 // ---------------------------------------------------------------------------
+// relaxed timestamps (Appendix G): validation and counter-based grouping
+// ---------------------------------------------------------------------------
+__global__ void validate_kernel(DevDB db, DevBulk b, BulkCtl *ctl)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < b.n && !txn_valid(db, b, t)) set_err(&ctl->err, ERR_INVAL);
+}
+
+// each transaction takes the next counter value of its partition as its
+// position in the partition (the order of the atomics is the relaxation)
+__global__ void part_count_kernel(DevDB db, DevBulk b, BulkCtl *ctl, int mode, int part_size, uint32_t *cnt,
+                                  uint32_t *pid_of, uint32_t *key_of)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool cross = false;
+    if (t < b.n) {
+        uint32_t pid = 0, key = 0;
+        if (txn_valid(db, b, t)) {
+            uint32_t obj[MAX_OPS], root[MAX_OPS];
+            uint8_t cls[MAX_OPS];
+            const int k = access_set(db, b.type[t], b.params + t * b.P, mode, obj, cls, root);
+            pid = k ? root[0] / (uint32_t)part_size : 0;
+            for (int j = 1; j < k; j++) cross |= (root[j] / (uint32_t)part_size) != pid;
+            key = atomicAdd(&cnt[pid], 1u);
+        } else {
+            set_err(&ctl->err, ERR_INVAL);
+        }
+        pid_of[t] = pid;
+        key_of[t] = key;
+    }
+    const uint32_t cross_mask = __ballot_sync(0xffffffffu, cross);
+    if ((threadIdx.x & 31) == 0 && cross_mask) atomicAdd(&ctl->cross, (uint32_t)__popc(cross_mask));
+}
+
+// position = start of the partition (prefix sum of the counters) + counter value
+__global__ void part_scatter_kernel(int64_t n, const uint32_t *off, const uint32_t *pid_of, const uint32_t *key_of,
+                                    uint32_t *pkeys, uint32_t *order, const uint32_t *err)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n || *err) return;
+    const uint32_t pid = pid_of[t];
+    const uint32_t pos = off[pid] + key_of[t];
+    pkeys[pos] = pid;
+    order[pos] = (uint32_t)t;
+}
+
+// ---------------------------------------------------------------------------
 // SCAN executor for bulks of debit-credit transactions (blind increments,
 // the ADD refinement taken to its end).  Under Definition 1 the output of
 // transaction t is its account's balance before the bulk plus the deltas of
@@ -663,6 +710,51 @@ cudaError_t launch_gather_dc(gputx_bulk *b, const uint32_t *order)
     if (b->n == 0) return cudaSuccess;
     if (!b->sc.rec_dc) return cudaErrorInvalidValue;
     gather_dc_kernel<<<grid_for(b->n), TB, 0, b->stream>>>(b->db->dev, dev_bulk(b, 0), order, b->sc.rec_dc,
+                                                                &b->ctl->err);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate(gputx_bulk *b)
+{
+    if (b->n == 0) return cudaSuccess;
+    validate_kernel<<<grid_for(b->n), TB, 0, b->stream>>>(b->db->dev, dev_bulk(b, 0), b->ctl);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_part_count(gputx_bulk *b, int mode, int part_size, uint32_t *cnt, uint32_t *pid_of,
+                              uint32_t *key_of)
+{
+    if (b->n == 0) return cudaSuccess;
+    part_count_kernel<<<grid_for(b->n), TB, 0, b->stream>>>(b->db->dev, dev_bulk(b, mode), b->ctl, mode,
+                                                              part_size < 1 ? 1 : part_size, cnt, pid_of, key_of);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// exclusive offsets of `parts` counters: off[p] = start of partition p,
+// off[parts] = total (scan scratch supplied by the caller)
+cudaError_t launch_part_offsets(gputx_bulk *b, const uint32_t *cnt, uint32_t *off, int64_t parts, uint64_t *status,
+                                uint32_t *tile_ctr)
+{
+    if (parts <= 0) return cudaSuccess;
+    OffsetMode om{cnt, off, parts};
+    const int64_t tiles = (parts + SCAN_TILE - 1) / SCAN_TILE;
+    cudaError_t e = cudaMemsetAsync(status, 0, tiles * sizeof(uint64_t), b->stream);
+    if (!e) e = cudaMemsetAsync(tile_ctr, 0, sizeof(uint32_t), b->stream);
+    if (e) return e;
+    dualseg_scan_kernel<OffsetMode><<<(unsigned)tiles, SCAN_THREADS, 0, b->stream>>>(
+        om, parts, status, tile_ctr, &b->ctl->err, (uint64_t)b->db->cfg.spin_limit_ns);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_part_scatter(gputx_bulk *b, const uint32_t *off, const uint32_t *pid_of, const uint32_t *key_of,
+                                uint32_t *pkeys, uint32_t *order)
+{
+    if (b->n == 0) return cudaSuccess;
+    part_scatter_kernel<<<grid_for(b->n), TB, 0, b->stream>>>(b->n, off, pid_of, key_of, pkeys, order,
                                                                 &b->ctl->err);
     count_launches(1);
     return cudaGetLastError();

@@ -914,13 +914,28 @@ cudaError_t end_tail(gputx_bulk *b)
     return e;
 }
 
+// relaxed PART's counters: allocated once, for every possible partition
+gputx_status part_scratch(gputx_db *db, int64_t roots)
+{
+    if (db->part_cnt) return GPUTX_OK;
+    const int64_t tiles = (roots + 2047) / 2048;   // scan tiles of 2,048 counters
+    gputx_status st = dalloc(db, &db->part_cnt, roots, "part counters");
+    if (!st) st = dalloc(db, &db->part_off, roots + 1, "part counters");
+    if (!st) st = dalloc(db, &db->part_scan_status, tiles, "part counters");
+    if (!st) st = dalloc(db, &db->part_tile_ctr, 1, "part counters");
+    if (st) return st;
+    CK(cudaStreamSynchronize(db->stream), "part counters");
+    db->part_cnt_n = roots;
+    return GPUTX_OK;
+}
+
 }  // namespace
 
 gputx_status gputx_execute(gputx_db *db, gputx_bulk *b, int strategy, const gputx_exec_opts *opts)
 {
     if (!db || !b || b->db != db) return fail(db, GPUTX_EINVAL, "bad arguments");
     if (b->executed) return fail(db, GPUTX_ESTATE, "bulk already executed");
-    if (strategy < GPUTX_KSET || strategy > GPUTX_SCAN) return fail(db, GPUTX_EINVAL, "strategy %d", strategy);
+    if (strategy < GPUTX_KSET || strategy > GPUTX_TPL_RELAXED) return fail(db, GPUTX_EINVAL, "strategy %d", strategy);
     if (strategy == GPUTX_SCAN && db->dev.registered != (1u << GPUTX_T_DC_DEBIT_CREDIT))
         return fail(db, GPUTX_EINVAL, "SCAN needs a database whose only registered type is debit-credit");
     const int mode = opts ? opts->conflict_mode : GPUTX_CONFLICT_PAPER;
@@ -1025,6 +1040,50 @@ gputx_status gputx_execute(gputx_db *db, gputx_bulk *b, int strategy, const gput
             CK(launch_part(b, pk, 128, (roots + part_size - 1) / part_size, part_size), "part execute");
         }
     }
+    if (run == GPUTX_PART_RELAXED) {
+        // Appendix G: counters instead of the sort.  The counters are the
+        // database's, so all of it runs in the bulk's ordered tail.
+        const int64_t roots = std::max<int64_t>({db->dev.n_br, db->dev.n_sub, db->dev.n_wh, 1});
+        const int64_t parts = (roots + part_size - 1) / part_size;
+        if ((st = part_scratch(db, roots))) return st;
+        CK(begin_tail(b), "order");
+        CK(cudaMemsetAsync(db->part_cnt, 0, parts * sizeof(uint32_t), s), "part counters");
+        uint32_t *pid_of = b->sc.pid_key, *key_of = b->sc.pid_val, *pk = b->sc.pid_key2, *order = b->sc.pid_val2;
+        CK(launch_part_count(b, mode, part_size, db->part_cnt, pid_of, key_of), "part count");
+        if (b->timing) cudaEventRecord(b->ev[1], s);
+        if ((st = read_ctl(b))) return st;
+        if (b->host_ctl.err) {
+            CK(end_tail(b), "finish");
+            b->strategy_run = run;
+            return GPUTX_OK;   // reported by the sync
+        }
+        if (b->host_ctl.cross > 0) {
+            b->fallback = 1;   // cross-partition transactions: spin-lock TPL
+            run = GPUTX_TPL_RELAXED;
+        } else {
+            CK(launch_part_offsets(b, db->part_cnt, db->part_off, parts, db->part_scan_status, db->part_tile_ctr),
+               "part offsets");
+            CK(launch_part_scatter(b, db->part_off, pid_of, key_of, pk, order), "part scatter");
+            if (b->timing) cudaEventRecord(b->ev[2], s);
+            CK(launch_part_heads(b, pk, b->n), "partition heads");
+            if (part_dc_applies(db, part_size)) CK(launch_gather_dc(b, order), "gather");
+            else CK(launch_gather(b, order), "gather");
+            if (b->timing) cudaEventRecord(b->ev[3], s);
+            CK(launch_part(b, pk, 128, parts, part_size), "part execute");
+            b->serial_order = order;
+        }
+    }
+    if (run == GPUTX_TPL_RELAXED) {
+        if (strategy == GPUTX_TPL_RELAXED) {
+            if (b->timing) cudaEventRecord(b->ev[1], s);
+            CK(launch_validate(b), "validate");
+            if (b->timing) cudaEventRecord(b->ev[2], s);
+            CK(begin_tail(b), "order");
+        }
+        if (b->timing) cudaEventRecord(b->ev[3], s);
+        CK(launch_tpl_relaxed(b, b->sc.level, add), "tpl execute");
+        b->serial_order = b->sc.level;
+    }
     if (run == GPUTX_SCAN) {
         if ((st = run_kset_analysis(b, GPUTX_CONFLICT_ADD, part_size, sk, sv, ak, av, m))) return st;
         CK(begin_tail(b), "order");
@@ -1072,9 +1131,26 @@ gputx_status gputx_sync_bulk(gputx_bulk *b, gputx_exec_stats *stats)
             if (!cudaEventElapsedTime(&ms, b->ev[1], b->ev[2])) stats->ms_sort = ms;
             if (!cudaEventElapsedTime(&ms, b->ev[3], b->ev[4])) stats->ms_execute = ms;
             if (!cudaEventElapsedTime(&ms, b->ev[0], b->ev[7])) stats->ms_total = ms;
+            cudaGetLastError();   // a phase this strategy does not have leaves its events unrecorded
         }
     }
     return bulk_error(db, b->host_ctl.err);
+}
+
+gputx_status gputx_bulk_order(gputx_bulk *b, uint32_t *order, size_t n)
+{
+    if (!b) return GPUTX_EINVAL;
+    gputx_db *db = b->db;
+    if ((int64_t)n != b->n) return fail(db, GPUTX_EINVAL, "n %zu != bulk size %lld", n, (long long)b->n);
+    if (n && !order) return fail(db, GPUTX_EINVAL, "null order");
+    gputx_status st = gputx_sync_bulk(b, nullptr);
+    if (st) return st;
+    if (!b->serial_order) {
+        for (size_t i = 0; i < n; i++) order[i] = (uint32_t)i;   // timestamp order (Definition 1)
+        return GPUTX_OK;
+    }
+    CK(cudaMemcpy(order, b->serial_order, n * sizeof(uint32_t), cudaMemcpyDeviceToHost), "d2h");
+    return GPUTX_OK;
 }
 
 gputx_status gputx_read_results(gputx_bulk *b, int32_t *status, int64_t *values, size_t n, int n_values)

@@ -82,6 +82,13 @@ struct gputx_db {
     cudaStream_t pool[kPool] = {};
     int next_pool = 0;
     cudaEvent_t last_done = nullptr;
+    // relaxed PART: per-partition counters and their prefix-scan scratch,
+    // allocated at first use (used only inside a bulk's ordered tail)
+    uint32_t *part_cnt = nullptr;          // part_cnt_n counters, zero between bulks
+    uint32_t *part_off = nullptr;          // part_cnt_n + 1 offsets
+    int64_t part_cnt_n = 0;
+    uint64_t *part_scan_status = nullptr;
+    uint32_t *part_tile_ctr = nullptr;
 };
 
 struct gputx_bulk {
@@ -101,6 +108,7 @@ struct gputx_bulk {
     gtx::Scratch sc{};
     bool executed = false;
     bool synced = false;
+    const uint32_t *serial_order = nullptr;   // relaxed strategies: the serial order executed
     bool graph = false;    // fixed capacity, padded with inactive transactions,
                            // no host synchronisation (capturable in a CUDA graph)
     int strategy_run = -1;
@@ -144,6 +152,15 @@ cudaError_t launch_part(gputx_bulk *b, const uint32_t *pkeys, int block, int64_t
 cudaError_t launch_tpl(gputx_bulk *b, int block, bool atomic_add);
 // a conflict-free bulk (a 0-set) in one launch
 cudaError_t launch_independent(gputx_bulk *b, bool atomic_add);
+// relaxed timestamps (Appendix G)
+cudaError_t launch_tpl_relaxed(gputx_bulk *b, uint32_t *order, bool atomic_add);
+cudaError_t launch_validate(gputx_bulk *b);
+cudaError_t launch_part_count(gputx_bulk *b, int mode, int part_size, uint32_t *cnt, uint32_t *pid_of,
+                              uint32_t *key_of);
+cudaError_t launch_part_offsets(gputx_bulk *b, const uint32_t *cnt, uint32_t *off, int64_t parts, uint64_t *status,
+                                uint32_t *tile_ctr);
+cudaError_t launch_part_scatter(gputx_bulk *b, const uint32_t *off, const uint32_t *pid_of, const uint32_t *key_of,
+                                uint32_t *pkeys, uint32_t *order);
 // SCAN: segmented prefix sums over operations grouped by account
 cudaError_t launch_scan_exec(gputx_bulk *b, const uint32_t *sk, const uint32_t *sv, int64_t m);
 int exec_blocks_per_sm(int kind, int block);

@@ -85,6 +85,7 @@ struct gputx_server {
     std::vector<int32_t> p_type;
     std::vector<int64_t> p_params;
     std::vector<int64_t> p_arrival;
+    std::vector<uint8_t> p_need;      // insert rows per transaction (packed, see pack_need)
     int64_t pool_base = 0;            // id of p_*[0]
     int64_t next_consume = 0;         // first id not yet in a bulk
     int64_t next_id = 0;              // next id to assign
@@ -121,6 +122,28 @@ void insert_need(const gputx_server *s, int32_t type, const int64_t *p, int64_t 
     need[3] = type == GPUTX_T_OE_NEW_ORDER ? (p[3] > 0 && p[3] <= 15 ? p[3] : 0) : 0;
 }
 
+// call-forwarding (bit 0), order (bit 1) and order-line rows (bits 2-5) of
+// one transaction, packed at submission so a bulk's totals are a byte sum
+inline uint8_t pack_need(const int64_t need[4])
+{
+    return (uint8_t)(need[1] | (need[2] << 1) | (need[3] << 2));
+}
+
+void sum_needs(const gputx_server *s, int64_t first_id, int64_t n, int64_t out[4])
+{
+    const uint8_t *q = &s->p_need[first_id - s->pool_base];
+    int64_t cf = 0, ord = 0, ol = 0;
+    for (int64_t i = 0; i < n; i++) {
+        cf += q[i] & 1u;
+        ord += (q[i] >> 1) & 1u;
+        ol += q[i] >> 2;
+    }
+    out[0] = (s->db->dev.registered & 1u) ? n : 0;
+    out[1] = cf;
+    out[2] = ord;
+    out[3] = ol;
+}
+
 gputx_status set_worker_error(gputx_server *s, gputx_status st, const char *what)
 {
     s->worker_status = st;
@@ -145,14 +168,13 @@ void reap(gputx_server *s, bool block)
             gputx_status st = gputx_sync_bulk(sl.bulk, nullptr);
             if (st != GPUTX_OK) set_worker_error(s, st, "bulk");
         }
-        for (int64_t i = 0; i < sl.n; i++) {
-            const int64_t id = sl.first_id + i;
-            s->r_status[id] = sl.h_status[i];
-            std::memcpy(&s->r_values[id * s->R], sl.h_values + i * s->R, sizeof(int64_t) * s->R);
-            s->r_complete[id] = t;
-            s->r_done[id] = 1;
-            s->hist.add(t - s->p_arrival[id - s->pool_base]);
-        }
+        // a bulk is a contiguous id range: results move in block copies
+        std::memcpy(&s->r_status[sl.first_id], sl.h_status, sizeof(int32_t) * sl.n);
+        std::memcpy(&s->r_values[sl.first_id * s->R], sl.h_values, sizeof(int64_t) * sl.n * s->R);
+        std::fill(s->r_complete.begin() + sl.first_id, s->r_complete.begin() + sl.first_id + sl.n, t);
+        std::fill(s->r_done.begin() + sl.first_id, s->r_done.begin() + sl.first_id + sl.n, (uint8_t)1);
+        const int64_t *arr = &s->p_arrival[sl.first_id - s->pool_base];
+        for (int64_t i = 0; i < sl.n; i++) s->hist.add(t - arr[i]);
         s->completed += sl.n;
         s->last_complete = t;
         s->inflight_txns -= sl.n;
@@ -173,6 +195,7 @@ void reap(gputx_server *s, bool block)
         s->p_type.erase(s->p_type.begin(), s->p_type.begin() + drop);
         s->p_params.erase(s->p_params.begin(), s->p_params.begin() + drop * s->P);
         s->p_arrival.erase(s->p_arrival.begin(), s->p_arrival.begin() + drop);
+        s->p_need.erase(s->p_need.begin(), s->p_need.begin() + drop);
         s->pool_base = keep_from;
     }
 }
@@ -188,13 +211,8 @@ void launch(gputx_server *s, int slot_idx, int64_t n)
     const int64_t off = s->next_consume - s->pool_base;
     std::memcpy(sl.h_type, &s->p_type[off], sizeof(int32_t) * n);
     std::memcpy(sl.h_params, &s->p_params[off * s->P], sizeof(int64_t) * n * s->P);
-    for (int k = 0; k < 4; k++) sl.inserts[k] = 0;
-    for (int64_t i = 0; i < n; i++) {
-        sl.h_ts[i] = sl.first_id + i;
-        int64_t need[4];
-        insert_need(s, sl.h_type[i], sl.h_params + i * s->P, need);
-        for (int k = 0; k < 4; k++) sl.inserts[k] += need[k];
-    }
+    sum_needs(s, sl.first_id, n, sl.inserts);
+    for (int64_t i = 0; i < n; i++) sl.h_ts[i] = sl.first_id + i;
     s->next_consume += n;
     s->inflight_txns += n;
     s->bulks++;
@@ -337,7 +355,7 @@ void worker_zero_set(gputx_server *s)
                 s->r_done[id] = 1;
                 s->hist.add(t - s->p_arrival[id - s->pool_base]);
                 int64_t need[4];
-                insert_need(s, s->p_type[id - s->pool_base], &s->p_params[(id - s->pool_base) * s->P], need);
+                sum_needs(s, id, 1, need);
                 for (int q = 0; q < 4; q++) {
                     s->ins_reserved[q] -= need[q];
                     s->ins_used[q] += need[q];
@@ -354,6 +372,7 @@ void worker_zero_set(gputx_server *s)
                 s->p_type.erase(s->p_type.begin(), s->p_type.begin() + drop);
                 s->p_params.erase(s->p_params.begin(), s->p_params.begin() + drop * s->P);
                 s->p_arrival.erase(s->p_arrival.begin(), s->p_arrival.begin() + drop);
+                s->p_need.erase(s->p_need.begin(), s->p_need.begin() + drop);
                 s->pool_base += drop;
             }
             s->cv.notify_all();
@@ -453,6 +472,15 @@ gputx_status gputx_server_submit(gputx_server *s, const int32_t *type, const int
 {
     if (!s || (n && (!type || !params))) return GPUTX_EINVAL;
     const int64_t t = now_ns();
+    // insert rows of each transaction, before taking the lock
+    int64_t need[4] = {0, 0, 0, 0};
+    std::vector<uint8_t> packed(n);
+    for (size_t i = 0; i < n; i++) {
+        int64_t q[4];
+        insert_need(s, type[i], params + i * s->P, q);
+        for (int k = 0; k < 4; k++) need[k] += q[k];
+        packed[i] = pack_need(q);
+    }
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->worker_status != GPUTX_OK) return s->worker_status;
     // admission: the pool, the insert areas and free device memory
@@ -460,12 +488,6 @@ gputx_status gputx_server_submit(gputx_server *s, const int32_t *type, const int
     if (queued + (int64_t)n > s->cfg.queue_capacity) {
         s->refused += (int64_t)n;
         return GPUTX_ENOMEM;
-    }
-    int64_t need[4] = {0, 0, 0, 0};
-    for (size_t i = 0; i < n; i++) {
-        int64_t q[4];
-        insert_need(s, type[i], params + i * s->P, q);
-        for (int k = 0; k < 4; k++) need[k] += q[k];
     }
     for (int k = 0; k < 4; k++)
         if (need[k] && s->ins_used[k] + s->ins_reserved[k] + need[k] > s->ins_cap[k]) {
@@ -483,7 +505,9 @@ gputx_status gputx_server_submit(gputx_server *s, const int32_t *type, const int
     const int64_t id0 = s->next_id;
     s->p_type.insert(s->p_type.end(), type, type + n);
     s->p_params.insert(s->p_params.end(), params, params + n * s->P);
-    for (size_t i = 0; i < n; i++) s->p_arrival.push_back(arrival_ns ? arrival_ns[i] : t);
+    s->p_need.insert(s->p_need.end(), packed.begin(), packed.end());
+    if (arrival_ns) s->p_arrival.insert(s->p_arrival.end(), arrival_ns, arrival_ns + n);
+    else s->p_arrival.resize(s->p_arrival.size() + n, t);
     if (s->first_arrival < 0 && n) s->first_arrival = arrival_ns ? arrival_ns[0] : t;
     s->next_id += (int64_t)n;
     s->r_status.resize(s->next_id, 0);

@@ -288,3 +288,18 @@ def test_scan_needs_debit_credit_only():
     assert e.value.status == G.EINVAL
     b.free()
     g.close()
+
+
+def test_timing_stats_for_every_strategy():
+    """Phase timing on every strategy, bulk after bulk: phases a strategy does
+    not have report 0 and leave no error behind for the next bulk."""
+    g, o = make_pair(10, 100, 10000, 1 << 16)
+    ts0 = 0
+    for s in ("kset", "part", "tpl", "auto", "scan", "part_relaxed", "tpl_relaxed") * 2:
+        bulk = W.dc_bulk(2000, 10000, 0.5, seed=ts0 + 7, ts0=ts0)
+        ts0 += 2000
+        b = g.submit_dict(bulk).execute(s, timing=True)
+        stats = b.sync()
+        b.free()
+        assert stats["ms_total"] > 0 and stats["ms_execute"] >= 0 and stats["ms_sort"] >= 0, s
+    g.close()
