@@ -46,7 +46,7 @@ METRIC = "txns/sec on 1 GB300 per strategy & bulk size vs plain path; p50/p99 la
 EXEC_BYTES_PER_TXN = 32 + 64 + 0 + 40 + 12
 L2_FLUSH_BYTES = 256 << 20
 # the executor kernel that dominates each headline configuration
-DOMINANT_KERNEL = {("kset", "paper"): "kset_narrow_kernel", ("kset", "add"): "kset_level_kernel",
+DOMINANT_KERNEL = {("kset", "paper"): "kset_narrow_dc_kernel", ("kset", "add"): "kset_level_kernel",
                    ("part_relaxed", "paper"): "part_dc_kernel", ("tpl_relaxed", "paper"): "tpl_relaxed_kernel",
                    ("tpl_relaxed", "add"): "tpl_relaxed_kernel",
                    ("part", "paper"): "part_dc_kernel", ("part", "add"): "part_dc_kernel",
@@ -273,6 +273,19 @@ def run_engine(args, rank, world, local_rank):
         return
     peak, peak_kind = measured_peak_hbm()
     ex = statistics.median(exec_ms)
+    # the latency roofline of the level chain: the bare skeleton of a level
+    # (loads of rows another SM wrote, stores, cluster barrier) in the narrow
+    # runner's launch shape, with the executor's traffic and with the minimum
+    latency = None
+    if args.strategy == "kset" and stats and stats["depth"] > 0:
+        levels = stats["depth"] + 1
+        floor_dc = G.gputx_probe_level_chain(levels, 16, 64, 3, 10)
+        floor_min = G.gputx_probe_level_chain(levels, 16, 64, 1, 1)
+        measured = ex * 1e6 / levels
+        latency = {"levels": levels, "measured_ns_per_level": measured,
+                   "floor_ns_per_level": floor_dc, "floor_ns_per_level_min": floor_min,
+                   "frac": floor_dc / measured,
+                   "probe": "cluster 16 x 64 threads, 3 dependent loads + 10 stores per thread per level"}
     achieved = n * EXEC_BYTES_PER_TXN / (ex / 1e3) / 1e9
     line = {
         "metric": METRIC,
@@ -304,6 +317,7 @@ def run_engine(args, rank, world, local_rank):
                      # the level chain, not bandwidth, bounds K-SET on a deep graph
                      "levels": stats["depth"] + 1 if stats else None,
                      "ns_per_level": ex * 1e6 / (stats["depth"] + 1) if stats else None},
+        "latency_roofline": latency,
         "phases_ms": {"execute": ex, "op_sort": statistics.median(sort_ms),
                       "analysis": stats["ms_analysis"] if stats else None},
         "graph": {"depth": stats["depth"], "w0": stats["w0"], "cross": stats["cross"]} if stats else None,
@@ -351,18 +365,27 @@ def run_sweep(args, G, torch, dev, stream, flush):
                         continue
                     ts = []
                     st = None
-                    for i in range(3):
-                        flush.fill_(i)
-                        e0 = torch.cuda.Event(enable_timing=True)
-                        e1 = torch.cuda.Event(enable_timing=True)
-                        e0.record(stream)
-                        b = db.submit(dbig["ts"][:n], dbig["type"][:n], dbig["params"][:n])
-                        b.execute(strategy, conflict_mode=mode, timing=True)
-                        e1.record(stream)
-                        st = b.sync()
-                        b.free()
-                        if i:
-                            ts.append(e0.elapsed_time(e1))
+                    try:
+                        for i in range(3):
+                            flush.fill_(i)
+                            e0 = torch.cuda.Event(enable_timing=True)
+                            e1 = torch.cuda.Event(enable_timing=True)
+                            e0.record(stream)
+                            b = db.submit(dbig["ts"][:n], dbig["type"][:n], dbig["params"][:n])
+                            b.execute(strategy, conflict_mode=mode, timing=True)
+                            e1.record(stream)
+                            try:
+                                st = b.sync()
+                            finally:
+                                b.free()
+                            if i:
+                                ts.append(e0.elapsed_time(e1))
+                    except G.GputxError as err:
+                        # e.g. a spin lock held longer than the wait limit under
+                        # extreme contention: reported, not timed
+                        rec["error"] = str(err)
+                        out.append(rec)
+                        continue
                     ms = statistics.median(ts)
                     rec.update({"ms": ms, "txn_per_s": n / (ms / 1e3), "depth": st["depth"],
                                 "w0": st["w0"], "exec_ms": st["ms_execute"], "sort_ms": st["ms_sort"],

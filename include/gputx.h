@@ -436,6 +436,18 @@ const char *gputx_server_last_error(const gputx_server *s);
 /* Stops the worker after the pending transactions complete, frees buffers. */
 void gputx_server_destroy(gputx_server *s);
 
+/* Latency floor of a chain of levels on one thread-block cluster: the
+ * skeleton of the K-SET narrow-level runner (Section 5.3) with no transaction
+ * logic.  At each of `levels` levels, each of cluster_size x threads threads
+ * loads `loads` (0..8) values that the previous level wrote on another CTA,
+ * stores `stores` (1..16) values, and the cluster synchronises with
+ * release/acquire semantics.  *ns_per_level = the time of one timed launch
+ * (after a warm-up launch) divided by `levels`.  Allocates and frees its own
+ * device memory (levels x cluster_size x threads x 128 bytes).  EINVAL on a
+ * parameter out of range, ECUDA if the cluster shape cannot launch. */
+gputx_status gputx_probe_level_chain(int levels, int cluster_size, int threads, int loads, int stores,
+                                     double *ns_per_level);
+
 /* ---------------------------------------------------------------------------
  * Incremental 0-set execution (Section 5.3).  A device-resident pool of
  * pending transactions keeps their basic operations sorted by item.  New

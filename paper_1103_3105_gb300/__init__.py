@@ -50,7 +50,7 @@ EXPORTED = ("gputx_create_db", "gputx_destroy_db", "gputx_last_error", "gputx_re
             "gputx_server_last_error", "gputx_server_destroy", "gputx_batcher_create",
             "gputx_batcher_run", "gputx_batcher_choice", "gputx_batcher_destroy",
             "gputx_pool_create", "gputx_pool_add", "gputx_pool_step", "gputx_pool_results",
-            "gputx_pool_pending", "gputx_pool_destroy", "gputx_bulk_order")
+            "gputx_pool_pending", "gputx_pool_destroy", "gputx_bulk_order", "gputx_probe_level_chain")
 
 
 class GputxError(RuntimeError):
@@ -157,6 +157,8 @@ def lib():
             "gputx_read_results": ([p, p, p, sz, C.c_int], C.c_int),
             "gputx_bulk_results_device": ([p, C.POINTER(p), C.POINTER(p)], C.c_int),
             "gputx_bulk_order": ([p, p, sz], C.c_int),
+            "gputx_probe_level_chain": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                         C.POINTER(C.c_double)], C.c_int),
             "gputx_output_width": ([p], C.c_int),
             "gputx_free_bulk": ([p], None),
             "gputx_version": ([], C.c_char_p),
@@ -272,6 +274,15 @@ def gputx_read_results(db, bulk, n: int, width: int, status=None, values=None):
         values = np.zeros((n, width), dtype=np.int64)
     _check(db, lib().gputx_read_results(bulk, _ptr(status), _ptr(values), n, width))
     return status, values
+
+
+def gputx_probe_level_chain(levels: int, cluster_size: int, threads: int, loads: int, stores: int) -> float:
+    """ns per level of the bare level chain (see gputx.h)."""
+    ns = C.c_double()
+    st = lib().gputx_probe_level_chain(levels, cluster_size, threads, loads, stores, C.byref(ns))
+    if st != OK:
+        raise GputxError(st, "probe_level_chain")
+    return ns.value
 
 
 def gputx_bulk_order(db, bulk, n: int) -> np.ndarray:

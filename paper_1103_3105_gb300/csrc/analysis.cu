@@ -415,8 +415,8 @@ struct HeadMode {
     }
 };
 
-// PART records of a debit-credit bulk, packed in partition order (32 B: two
-// 16-byte loads), with the teller index precomputed
+// records of a debit-credit bulk packed in execution order (32 B: two
+// 16-byte loads), teller and branch precomputed
 __global__ void gather_dc_kernel(DevDB db, DevBulk b, const uint32_t *order, DcRecord *rec, const uint32_t *err)
 {
     const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -429,7 +429,7 @@ __global__ void gather_dc_kernel(DevDB db, DevBulk b, const uint32_t *order, DcR
     r.a = a;
     r.t = t;
     r.tl = db.div_tel.div(a);
-    r.pad = 0;
+    r.br = db.div_br.div(a);
     rec[pos] = r;
 }
 
@@ -510,26 +510,65 @@ __global__ void validate_kernel(DevDB db, DevBulk b, BulkCtl *ctl)
 }
 
 // each transaction takes the next counter value of its partition as its
-// position in the partition (the order of the atomics is the relaxation)
-__global__ void part_count_kernel(DevDB db, DevBulk b, BulkCtl *ctl, int mode, int part_size, uint32_t *cnt,
-                                  uint32_t *pid_of, uint32_t *key_of)
+// position in the partition (the order of the atomics is the relaxation).
+// With few partitions a block first counts in shared memory, then takes one
+// global range per partition it saw (kPartCountItems transactions a thread),
+// so 4 M transactions over 1,000 counters do not serialise on the counters.
+constexpr int kPartCountThreads = 1024, kPartCountItems = 8, kPartLocalMax = 4096;
+
+__device__ __forceinline__ bool part_of(const DevDB &db, const DevBulk &b, int64_t t, int mode, int part_size,
+                                        uint32_t &pid, bool &cross)
 {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (!txn_valid(db, b, t)) return false;
+    uint32_t obj[MAX_OPS], root[MAX_OPS];
+    uint8_t cls[MAX_OPS];
+    const int k = access_set(db, b.type[t], b.params + t * b.P, mode, obj, cls, root);
+    pid = k ? root[0] / (uint32_t)part_size : 0;
+    for (int j = 1; j < k; j++) cross |= (root[j] / (uint32_t)part_size) != pid;
+    return true;
+}
+
+template <bool LOCAL>
+__global__ void __launch_bounds__(kPartCountThreads) part_count_kernel(DevDB db, DevBulk b, BulkCtl *ctl, int mode,
+                                                                       int part_size, uint32_t *cnt, int64_t parts,
+                                                                       uint32_t *pid_of, uint32_t *key_of)
+{
+    __shared__ uint32_t scnt[LOCAL ? kPartLocalMax : 1], sbase[LOCAL ? kPartLocalMax : 1];
+    if (LOCAL) {
+        for (int64_t p = threadIdx.x; p < parts; p += blockDim.x) scnt[p] = 0;
+        __syncthreads();
+    }
+    const int64_t base = (int64_t)blockIdx.x * kPartCountThreads * kPartCountItems + threadIdx.x;
+    uint32_t pid[kPartCountItems], local[kPartCountItems];
+    bool ok[kPartCountItems];
     bool cross = false;
-    if (t < b.n) {
-        uint32_t pid = 0, key = 0;
-        if (txn_valid(db, b, t)) {
-            uint32_t obj[MAX_OPS], root[MAX_OPS];
-            uint8_t cls[MAX_OPS];
-            const int k = access_set(db, b.type[t], b.params + t * b.P, mode, obj, cls, root);
-            pid = k ? root[0] / (uint32_t)part_size : 0;
-            for (int j = 1; j < k; j++) cross |= (root[j] / (uint32_t)part_size) != pid;
-            key = atomicAdd(&cnt[pid], 1u);
-        } else {
-            set_err(&ctl->err, ERR_INVAL);
+#pragma unroll
+    for (int j = 0; j < kPartCountItems; j++) {
+        const int64_t t = base + (int64_t)j * kPartCountThreads;
+        pid[j] = 0;
+        local[j] = 0;
+        ok[j] = false;
+        if (t < b.n) {
+            ok[j] = part_of(db, b, t, mode, part_size, pid[j], cross);
+            if (!ok[j]) set_err(&ctl->err, ERR_INVAL);
+            else local[j] = LOCAL ? atomicAdd(&scnt[pid[j]], 1u) : atomicAdd(&cnt[pid[j]], 1u);
         }
-        pid_of[t] = pid;
-        key_of[t] = key;
+    }
+    if (LOCAL) {
+        __syncthreads();
+        // the block's first transaction of each partition takes the range
+#pragma unroll
+        for (int j = 0; j < kPartCountItems; j++)
+            if (ok[j] && local[j] == 0) sbase[pid[j]] = atomicAdd(&cnt[pid[j]], scnt[pid[j]]);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < kPartCountItems; j++) {
+        const int64_t t = base + (int64_t)j * kPartCountThreads;
+        if (t < b.n) {
+            pid_of[t] = pid[j];
+            key_of[t] = ok[j] ? (LOCAL ? sbase[pid[j]] + local[j] : local[j]) : 0;
+        }
     }
     const uint32_t cross_mask = __ballot_sync(0xffffffffu, cross);
     if ((threadIdx.x & 31) == 0 && cross_mask) atomicAdd(&ctl->cross, (uint32_t)__popc(cross_mask));
@@ -723,12 +762,19 @@ cudaError_t launch_validate(gputx_bulk *b)
     return cudaGetLastError();
 }
 
-cudaError_t launch_part_count(gputx_bulk *b, int mode, int part_size, uint32_t *cnt, uint32_t *pid_of,
-                              uint32_t *key_of)
+cudaError_t launch_part_count(gputx_bulk *b, int mode, int part_size, uint32_t *cnt, int64_t parts,
+                              uint32_t *pid_of, uint32_t *key_of)
 {
     if (b->n == 0) return cudaSuccess;
-    part_count_kernel<<<grid_for(b->n), TB, 0, b->stream>>>(b->db->dev, dev_bulk(b, mode), b->ctl, mode,
-                                                              part_size < 1 ? 1 : part_size, cnt, pid_of, key_of);
+    const int64_t per_block = (int64_t)kPartCountThreads * kPartCountItems;
+    const unsigned grid = (unsigned)((b->n + per_block - 1) / per_block);
+    const int ps = part_size < 1 ? 1 : part_size;
+    if (parts <= kPartLocalMax)
+        part_count_kernel<true><<<grid, kPartCountThreads, 0, b->stream>>>(b->db->dev, dev_bulk(b, mode), b->ctl,
+                                                                          mode, ps, cnt, parts, pid_of, key_of);
+    else
+        part_count_kernel<false><<<grid, kPartCountThreads, 0, b->stream>>>(b->db->dev, dev_bulk(b, mode), b->ctl,
+                                                                           mode, ps, cnt, parts, pid_of, key_of);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -1003,10 +1003,15 @@ gputx_status gputx_execute(gputx_db *db, gputx_bulk *b, int strategy, const gput
             CK(cudaStreamSynchronize(s), "level plan");
             if (!b->host_ctl.err) {
                 const int narrow = (opts && opts->narrow_max > 0) ? opts->narrow_max : 8192;
-                CK(launch_gather(b, rv), "gather");
+                // debit-credit-only bulks run from packed records
+                const bool dc_only = b->sc.rec_dc != nullptr;
+                if (dc_only) CK(launch_gather_dc(b, rv), "gather");
+                else CK(launch_gather(b, rv), "gather");
                 CK(begin_tail(b), "order");
                 if (b->timing) cudaEventRecord(b->ev[3], s);
-                CK(launch_kset_levels(b, b->level_off_host.data(), depth, narrow, add), "k-set execute");
+                CK(launch_kset_levels(b, b->level_off_host.data(), depth, narrow, add,
+                                      dc_only ? b->sc.rec_dc : nullptr),
+                   "k-set execute");
             }
         } else {
             CK(begin_tail(b), "order");   // empty bulk
@@ -1049,7 +1054,7 @@ gputx_status gputx_execute(gputx_db *db, gputx_bulk *b, int strategy, const gput
         CK(begin_tail(b), "order");
         CK(cudaMemsetAsync(db->part_cnt, 0, parts * sizeof(uint32_t), s), "part counters");
         uint32_t *pid_of = b->sc.pid_key, *key_of = b->sc.pid_val, *pk = b->sc.pid_key2, *order = b->sc.pid_val2;
-        CK(launch_part_count(b, mode, part_size, db->part_cnt, pid_of, key_of), "part count");
+        CK(launch_part_count(b, mode, part_size, db->part_cnt, parts, pid_of, key_of), "part count");
         if (b->timing) cudaEventRecord(b->ev[1], s);
         if ((st = read_ctl(b))) return st;
         if (b->host_ctl.err) {

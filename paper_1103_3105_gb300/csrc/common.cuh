@@ -96,11 +96,11 @@ struct DevDB {
     int out_width;
 };
 
-// a debit-credit transaction packed for the PART executor (32 B, 16-byte
-// aligned: two vector loads)
+// a debit-credit transaction packed for the executors (32 B, 16-byte
+// aligned: two vector loads), with its teller and branch precomputed
 struct __align__(16) DcRecord {
     int64_t delta, ts;
-    uint32_t a, t, tl, pad;
+    uint32_t a, t, tl, br;
 };
 
 // insert bases of one bulk: where its new rows start in each append area

@@ -147,7 +147,7 @@ cudaError_t launch_finish(gputx_bulk *b);
 // exec.cu
 cudaError_t launch_kset(gputx_bulk *b, const uint32_t *order, int64_t nchunks, int block, bool atomic_add);
 cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, int64_t depth, int narrow_max,
-                               bool atomic_add);
+                               bool atomic_add, const DcRecord *dc_records = nullptr);
 cudaError_t launch_part(gputx_bulk *b, const uint32_t *pkeys, int block, int64_t max_parts, int part_size);
 cudaError_t launch_tpl(gputx_bulk *b, int block, bool atomic_add);
 // a conflict-free bulk (a 0-set) in one launch
@@ -155,8 +155,8 @@ cudaError_t launch_independent(gputx_bulk *b, bool atomic_add);
 // relaxed timestamps (Appendix G)
 cudaError_t launch_tpl_relaxed(gputx_bulk *b, uint32_t *order, bool atomic_add);
 cudaError_t launch_validate(gputx_bulk *b);
-cudaError_t launch_part_count(gputx_bulk *b, int mode, int part_size, uint32_t *cnt, uint32_t *pid_of,
-                              uint32_t *key_of);
+cudaError_t launch_part_count(gputx_bulk *b, int mode, int part_size, uint32_t *cnt, int64_t parts,
+                              uint32_t *pid_of, uint32_t *key_of);
 cudaError_t launch_part_offsets(gputx_bulk *b, const uint32_t *cnt, uint32_t *off, int64_t parts, uint64_t *status,
                                 uint32_t *tile_ctr);
 cudaError_t launch_part_scatter(gputx_bulk *b, const uint32_t *off, const uint32_t *pid_of, const uint32_t *key_of,

@@ -73,6 +73,7 @@ struct LevelArgs {
     DevBulk b;
     const BulkCtl *ctl;
     const uint32_t *level_off;
+    const DcRecord *rec_dc;   // debit-credit-only bulks: packed records in execution order
     uint32_t k0, k1;     // levels [k0, k1)
     bool atomic_add;
 };
@@ -93,8 +94,54 @@ __global__ void __launch_bounds__(256) kset_level_kernel(LevelArgs a)
     if (a.ctl->err) return;
     const int64_t hb = a.ctl->base.hist;
     const uint32_t lo = __ldg(&a.level_off[a.k0]), hi = __ldg(&a.level_off[a.k0 + 1]);
-    for (uint32_t pos = lo + blockIdx.x * blockDim.x + threadIdx.x; pos < hi; pos += gridDim.x * blockDim.x)
-        exec_txn(a.db, a.b, view_at(a.b, pos, hb), a.atomic_add);
+    for (uint32_t pos = lo + blockIdx.x * blockDim.x + threadIdx.x; pos < hi; pos += gridDim.x * blockDim.x) {
+        if (a.rec_dc) exec_dc_record(a.db, a.b, a.rec_dc[pos], hb + pos, a.atomic_add);
+        else exec_txn(a.db, a.b, view_at(a.b, pos, hb), a.atomic_add);
+    }
+}
+
+// the narrow-level runner for debit-credit-only bulks: one packed record per
+// transaction (no type dispatch, no divisions), the next level's record
+// loaded while this level executes, its rows prefetched into L2 before the
+// barrier
+template <bool CLUSTER, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) kset_narrow_dc_kernel(LevelArgs a)
+{
+    if (a.ctl->err) return;   // set by an earlier launch only: uniform here
+    const int64_t hb = a.ctl->base.hist;
+    uint32_t nthreads = blockDim.x, rank = threadIdx.x;
+    if (CLUSTER) {
+        cg::cluster_group cl = cg::this_cluster();
+        nthreads = cl.num_threads();
+        rank = cl.thread_rank();
+    }
+    uint32_t lo = __ldg(&a.level_off[a.k0]);
+    uint32_t hi = __ldg(&a.level_off[a.k0 + 1]);
+    DcRecord v{};
+    if (lo + rank < hi) {
+        v = a.rec_dc[lo + rank];
+        prefetch_l2(&a.db.acc_bal[v.a]);
+    }
+    for (uint32_t k = a.k0; k < a.k1; k++) {
+        const uint32_t nlo = hi;
+        const uint32_t nhi = (k + 1 < a.k1) ? __ldg(&a.level_off[k + 2]) : nlo;
+        DcRecord nv{};
+        const bool has_next = nlo + rank < nhi;
+        if (has_next) nv = a.rec_dc[nlo + rank];
+        if (lo + rank < hi) exec_dc_record(a.db, a.b, v, hb + lo + rank, a.atomic_add);
+        for (uint32_t pos = lo + rank + nthreads; pos < hi; pos += nthreads)
+            exec_dc_record(a.db, a.b, a.rec_dc[pos], hb + pos, a.atomic_add);
+        if (has_next) {
+            prefetch_l2(&a.db.acc_bal[nv.a]);
+            prefetch_l2(&a.db.tel_bal[nv.tl]);
+            prefetch_l2(&a.db.br_bal[nv.br]);
+        }
+        if (CLUSTER) cg::this_cluster().sync();   // release/acquire at cluster scope
+        else __syncthreads();
+        lo = nlo;
+        hi = nhi;
+        v = nv;
+    }
 }
 
 // a run of narrow levels [k0, k1) on one thread-block cluster (CLUSTER) or
@@ -436,7 +483,7 @@ cudaError_t launch_kset(gputx_bulk *b, const uint32_t *order, int64_t nchunks, i
 }
 
 cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, int64_t depth, int narrow_max,
-                               bool atomic_add)
+                               bool atomic_add, const DcRecord *dc_records)
 {
     gputx_db *db = b->db;
     if (b->n == 0) return cudaSuccess;
@@ -445,6 +492,7 @@ cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, in
     a.b = make_dev_bulk(b, atomic_add ? GPUTX_CONFLICT_ADD : GPUTX_CONFLICT_PAPER);
     a.ctl = b->ctl;
     a.level_off = b->sc.level_off;
+    a.rec_dc = dc_records;
     a.atomic_add = atomic_add;
     const int64_t levels = depth + 1;
     static bool attr_set = false;
@@ -452,6 +500,8 @@ cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, in
         cudaFuncSetAttribute(kset_narrow_kernel<true, 256>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         cudaFuncSetAttribute(kset_narrow_kernel<true, 512>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         cudaFuncSetAttribute(kset_narrow_kernel<true, 1024>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(kset_narrow_dc_kernel<true, 256>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(kset_narrow_dc_kernel<true, 1024>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         attr_set = true;
     }
     int64_t k = 0;
@@ -488,8 +538,14 @@ cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, in
         threads = ((threads + 31) / 32) * 32;
         threads = threads < 32 ? 32 : (threads > 1024 ? 1024 : threads);
         if (csize <= 1) {
-            if (threads <= 256) kset_narrow_kernel<false, 256><<<1, threads, 0, b->stream>>>(a);
-            else kset_narrow_kernel<false, 1024><<<1, threads, 0, b->stream>>>(a);
+            // the records this bulk was gathered into decide the runner
+            if (a.rec_dc) {
+                if (threads <= 256) kset_narrow_dc_kernel<false, 256><<<1, threads, 0, b->stream>>>(a);
+                else kset_narrow_dc_kernel<false, 1024><<<1, threads, 0, b->stream>>>(a);
+            } else {
+                if (threads <= 256) kset_narrow_kernel<false, 256><<<1, threads, 0, b->stream>>>(a);
+                else kset_narrow_kernel<false, 1024><<<1, threads, 0, b->stream>>>(a);
+            }
         } else {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(csize, 1, 1);
@@ -504,9 +560,14 @@ cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, in
             cfg.numAttrs = 1;
             // up to 256 threads a CTA: more registers per thread for the
             // loads in flight
-            cudaError_t e2 = threads <= 256   ? cudaLaunchKernelEx(&cfg, kset_narrow_kernel<true, 256>, a)
-                             : threads <= 512 ? cudaLaunchKernelEx(&cfg, kset_narrow_kernel<true, 512>, a)
-                                              : cudaLaunchKernelEx(&cfg, kset_narrow_kernel<true, 1024>, a);
+            cudaError_t e2;
+            if (a.rec_dc)
+                e2 = threads <= 256 ? cudaLaunchKernelEx(&cfg, kset_narrow_dc_kernel<true, 256>, a)
+                                    : cudaLaunchKernelEx(&cfg, kset_narrow_dc_kernel<true, 1024>, a);
+            else
+                e2 = threads <= 256   ? cudaLaunchKernelEx(&cfg, kset_narrow_kernel<true, 256>, a)
+                     : threads <= 512 ? cudaLaunchKernelEx(&cfg, kset_narrow_kernel<true, 512>, a)
+                                      : cudaLaunchKernelEx(&cfg, kset_narrow_kernel<true, 1024>, a);
             if (e2) return e2;
         }
         count_launches(1);

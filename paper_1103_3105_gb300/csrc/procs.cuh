@@ -394,13 +394,10 @@ struct DcOut {
 // transactions of one level may add to one item).  False when the history
 // is full (the transaction is not executed; status 3).
 template <class Cells>
-__device__ __forceinline__ bool dc_state(const DevDB &db, const DevBulk &b, const TxnView &v, bool atomic_add,
-                                         Cells &cells, DcOut &o)
+__device__ __forceinline__ bool dc_state_core(const DevDB &db, const DevBulk &b, int64_t a, int64_t tl, int64_t br,
+                                              int64_t delta, int64_t ts, uint32_t t, int64_t slot, bool atomic_add,
+                                              Cells &cells, DcOut &o)
 {
-    const uint32_t t = v.t;
-    const int64_t a = v.p0, delta = v.p1;
-    const int64_t tl = db.div_tel.div((uint32_t)a), br = db.div_br.div((uint32_t)a);
-    const int64_t slot = v.hist_slot;
     // every load before any store: the three rows are distinct cells but the
     // compiler cannot prove it, so interleaving would serialise three L2
     // round trips
@@ -426,7 +423,7 @@ __device__ __forceinline__ bool dc_state(const DevDB &db, const DevBulk &b, cons
         cells.st(&db.br_bal[br], wrap_add(old_b, delta));
     }
     o.slot = slot;
-    o.ts = v.ts;
+    o.ts = ts;
     o.delta = delta;
     o.na = na;
     o.a = a;
@@ -434,6 +431,15 @@ __device__ __forceinline__ bool dc_state(const DevDB &db, const DevBulk &b, cons
     o.br = br;
     o.t = t;
     return true;
+}
+
+template <class Cells>
+__device__ __forceinline__ bool dc_state(const DevDB &db, const DevBulk &b, const TxnView &v, bool atomic_add,
+                                         Cells &cells, DcOut &o)
+{
+    const int64_t a = v.p0;
+    return dc_state_core(db, b, a, db.div_tel.div((uint32_t)a), db.div_br.div((uint32_t)a), v.p1, v.ts, v.t,
+                         v.hist_slot, atomic_add, cells, o);
 }
 
 __device__ __forceinline__ void dc_finish(const DevDB &db, const DevBulk &b, const DcOut &o)
@@ -453,6 +459,15 @@ __device__ __forceinline__ void exec_dc(const DevDB &db, const DevBulk &b, const
 {
     DcOut o;
     if (dc_state(db, b, v, atomic_add, cells, o)) dc_finish(db, b, o);
+}
+
+// the same transaction from a packed record (teller and branch precomputed)
+__device__ __forceinline__ void exec_dc_record(const DevDB &db, const DevBulk &b, const DcRecord &r, int64_t slot,
+                                               bool atomic_add)
+{
+    GlobalCells g;
+    DcOut o;
+    if (dc_state_core(db, b, r.a, r.tl, r.br, r.delta, r.ts, r.t, slot, atomic_add, g, o)) dc_finish(db, b, o);
 }
 
 // subscriber-location procedures (stand-ins shaped like TM-1, Appendix E)

@@ -15,6 +15,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -57,6 +58,76 @@ struct LatencyHist {
     }
 };
 
+// An append-only array stored in fixed-size chunks and indexed by absolute
+// position: appending never moves what is already there (no reallocation
+// copies while the server lock is held), and whole chunks below a position
+// can be released.
+template <class T> class Chunked {
+    static constexpr int64_t kShift = 20, kChunk = int64_t(1) << kShift, kMask = kChunk - 1;
+    std::vector<std::unique_ptr<T[]>> chunks_;   // chunks_[c - first_] holds [c * kChunk, (c + 1) * kChunk)
+    int64_t first_ = 0;                          // chunks before this one were released
+    int64_t size_ = 0;
+
+    T *at(int64_t i) { return &chunks_[(i >> kShift) - first_][i & kMask]; }
+    const T *at(int64_t i) const { return &chunks_[(i >> kShift) - first_][i & kMask]; }
+    // calls f(pointer, count) for the pieces of [i, i + n) chunk by chunk
+    template <class F> void pieces(int64_t i, int64_t n, F f)
+    {
+        while (n > 0) {
+            const int64_t k = std::min(n, kChunk - (i & kMask));
+            f(at(i), k);
+            i += k;
+            n -= k;
+        }
+    }
+
+  public:
+    int64_t size() const { return size_; }
+    T &operator[](int64_t i) { return *at(i); }
+    const T &operator[](int64_t i) const { return *at(i); }
+    // n more elements, each `v`
+    void grow(int64_t n, T v)
+    {
+        const int64_t end = size_ + n;
+        while ((int64_t)(chunks_.size() + first_) * kChunk < end) chunks_.emplace_back(new T[kChunk]());
+        const int64_t at0 = size_;
+        size_ = end;
+        fill(at0, n, v);
+    }
+    void append(const T *src, int64_t n)
+    {
+        const int64_t at0 = size_;
+        grow(n, T());
+        copy_in(at0, src, n);
+    }
+    void copy_in(int64_t i, const T *src, int64_t n)
+    {
+        pieces(i, n, [&](T *p, int64_t k) {
+            std::memcpy(p, src, sizeof(T) * k);
+            src += k;
+        });
+    }
+    void copy_out(int64_t i, int64_t n, T *dst)
+    {
+        pieces(i, n, [&](T *p, int64_t k) {
+            std::memcpy(dst, p, sizeof(T) * k);
+            dst += k;
+        });
+    }
+    void fill(int64_t i, int64_t n, T v)
+    {
+        pieces(i, n, [&](T *p, int64_t k) { std::fill(p, p + k, v); });
+    }
+    // frees the chunks that lie wholly below position i
+    void release_before(int64_t i)
+    {
+        const int64_t c = std::min(i, size_) >> kShift;
+        if (c <= first_) return;
+        chunks_.erase(chunks_.begin(), chunks_.begin() + (c - first_));
+        first_ = c;
+    }
+};
+
 struct Slot {
     gputx_bulk *bulk = nullptr;
     int64_t first_id = 0;
@@ -82,11 +153,10 @@ struct gputx_server {
     gputx_status worker_status = GPUTX_OK;
     std::string worker_error;
     // the pool: pending transactions, ids next_consume .. next_id-1
-    std::vector<int32_t> p_type;
-    std::vector<int64_t> p_params;
-    std::vector<int64_t> p_arrival;
-    std::vector<uint8_t> p_need;      // insert rows per transaction (packed, see pack_need)
-    int64_t pool_base = 0;            // id of p_*[0]
+    Chunked<int32_t> p_type;          // all indexed by id (params by id x P)
+    Chunked<int64_t> p_params;
+    Chunked<int64_t> p_arrival;
+    Chunked<uint8_t> p_need;          // insert rows per transaction (packed, see pack_need)
     int64_t next_consume = 0;         // first id not yet in a bulk
     int64_t next_id = 0;              // next id to assign
     int64_t inflight_txns = 0;
@@ -95,10 +165,10 @@ struct gputx_server {
     int64_t ins_used[4] = {0, 0, 0, 0};
     int64_t ins_cap[4] = {0, 0, 0, 0};
     // results, indexed by id
-    std::vector<int32_t> r_status;
-    std::vector<int64_t> r_values;
-    std::vector<int64_t> r_complete;
-    std::vector<uint8_t> r_done;
+    Chunked<int32_t> r_status;
+    Chunked<int64_t> r_values;
+    Chunked<int64_t> r_complete;
+    Chunked<uint8_t> r_done;
     int64_t completed = 0, bulks = 0, max_bulk_seen = 0, refused = 0;
     int64_t first_arrival = -1, last_complete = 0;
     LatencyHist hist;
@@ -129,14 +199,14 @@ inline uint8_t pack_need(const int64_t need[4])
     return (uint8_t)(need[1] | (need[2] << 1) | (need[3] << 2));
 }
 
-void sum_needs(const gputx_server *s, int64_t first_id, int64_t n, int64_t out[4])
+void sum_needs(gputx_server *s, int64_t first_id, int64_t n, int64_t out[4])
 {
-    const uint8_t *q = &s->p_need[first_id - s->pool_base];
     int64_t cf = 0, ord = 0, ol = 0;
-    for (int64_t i = 0; i < n; i++) {
-        cf += q[i] & 1u;
-        ord += (q[i] >> 1) & 1u;
-        ol += q[i] >> 2;
+    for (int64_t i = first_id; i < first_id + n; i++) {
+        const uint8_t q = s->p_need[i];
+        cf += q & 1u;
+        ord += (q >> 1) & 1u;
+        ol += q >> 2;
     }
     out[0] = (s->db->dev.registered & 1u) ? n : 0;
     out[1] = cf;
@@ -149,6 +219,15 @@ gputx_status set_worker_error(gputx_server *s, gputx_status st, const char *what
     s->worker_status = st;
     s->worker_error = std::string(what) + ": " + gputx_last_error(s->db);
     return st;
+}
+
+// frees the pool's chunks below id `keep_from` (no bulk needs them any more)
+void release_pool_before(gputx_server *s, int64_t keep_from)
+{
+    s->p_type.release_before(keep_from);
+    s->p_params.release_before(keep_from * s->P);
+    s->p_arrival.release_before(keep_from);
+    s->p_need.release_before(keep_from);
 }
 
 // reaps finished bulks in order (lock held)
@@ -169,12 +248,11 @@ void reap(gputx_server *s, bool block)
             if (st != GPUTX_OK) set_worker_error(s, st, "bulk");
         }
         // a bulk is a contiguous id range: results move in block copies
-        std::memcpy(&s->r_status[sl.first_id], sl.h_status, sizeof(int32_t) * sl.n);
-        std::memcpy(&s->r_values[sl.first_id * s->R], sl.h_values, sizeof(int64_t) * sl.n * s->R);
-        std::fill(s->r_complete.begin() + sl.first_id, s->r_complete.begin() + sl.first_id + sl.n, t);
-        std::fill(s->r_done.begin() + sl.first_id, s->r_done.begin() + sl.first_id + sl.n, (uint8_t)1);
-        const int64_t *arr = &s->p_arrival[sl.first_id - s->pool_base];
-        for (int64_t i = 0; i < sl.n; i++) s->hist.add(t - arr[i]);
+        s->r_status.copy_in(sl.first_id, sl.h_status, sl.n);
+        s->r_values.copy_in(sl.first_id * s->R, sl.h_values, sl.n * s->R);
+        s->r_complete.fill(sl.first_id, sl.n, t);
+        s->r_done.fill(sl.first_id, sl.n, (uint8_t)1);
+        for (int64_t i = sl.first_id; i < sl.first_id + sl.n; i++) s->hist.add(t - s->p_arrival[i]);
         s->completed += sl.n;
         s->last_complete = t;
         s->inflight_txns -= sl.n;
@@ -190,14 +268,7 @@ void reap(gputx_server *s, bool block)
     }
     // drop the pool's prefix no bulk still needs (arrivals of finished ids)
     const int64_t keep_from = s->order.empty() ? s->next_consume : s->slots[s->order.front()].first_id;
-    const int64_t drop = keep_from - s->pool_base;
-    if (drop > (1 << 20) && drop * 2 > (int64_t)s->p_type.size()) {
-        s->p_type.erase(s->p_type.begin(), s->p_type.begin() + drop);
-        s->p_params.erase(s->p_params.begin(), s->p_params.begin() + drop * s->P);
-        s->p_arrival.erase(s->p_arrival.begin(), s->p_arrival.begin() + drop);
-        s->p_need.erase(s->p_need.begin(), s->p_need.begin() + drop);
-        s->pool_base = keep_from;
-    }
+    release_pool_before(s, keep_from);
 }
 
 // cuts the next bulk [next_consume, next_consume + n) and launches it (lock
@@ -208,9 +279,8 @@ void launch(gputx_server *s, int slot_idx, int64_t n)
     sl.first_id = s->next_consume;
     sl.n = n;
     sl.busy = true;
-    const int64_t off = s->next_consume - s->pool_base;
-    std::memcpy(sl.h_type, &s->p_type[off], sizeof(int32_t) * n);
-    std::memcpy(sl.h_params, &s->p_params[off * s->P], sizeof(int64_t) * n * s->P);
+    s->p_type.copy_out(sl.first_id, n, sl.h_type);
+    s->p_params.copy_out(sl.first_id * s->P, n * s->P, sl.h_params);
     sum_needs(s, sl.first_id, n, sl.inserts);
     for (int64_t i = 0; i < n; i++) sl.h_ts[i] = sl.first_id + i;
     s->next_consume += n;
@@ -265,7 +335,7 @@ void worker_main(gputx_server *s)
             if (!s->slots[i].busy) { free_slot = i; break; }
         bool ready = false;
         if (pending > 0) {
-            const int64_t oldest = s->p_arrival[s->next_consume - s->pool_base];
+            const int64_t oldest = s->p_arrival[s->next_consume];
             ready = pending >= s->cfg.max_bulk || now_ns() - oldest >= deadline || s->stop || s->flush;
         }
         if (ready && free_slot >= 0) {
@@ -280,7 +350,7 @@ void worker_main(gputx_server *s)
         // submit arrives, or a bulk may have finished
         int64_t wait_ns = 200000;
         if (pending > 0) {
-            const int64_t oldest = s->p_arrival[s->next_consume - s->pool_base];
+            const int64_t oldest = s->p_arrival[s->next_consume];
             wait_ns = std::max<int64_t>(0, oldest + deadline - now_ns());
         }
         if (!s->order.empty()) wait_ns = std::min<int64_t>(wait_ns, 20000);
@@ -306,16 +376,17 @@ void worker_zero_set(gputx_server *s)
         if (s->stop && queued == 0 && in_pool == 0) break;
         bool take = false;
         if (queued > 0) {
-            const int64_t oldest = s->p_arrival[s->next_consume - s->pool_base];
+            const int64_t oldest = s->p_arrival[s->next_consume];
             take = in_pool > 0 || queued >= s->cfg.max_bulk || now_ns() - oldest >= deadline || s->stop || s->flush;
         }
         if (take) {
             // as many as the pool's capacity takes (halving on ECAPACITY)
             int64_t n = std::min<int64_t>(queued, s->cfg.max_bulk);
-            const int64_t off = s->next_consume - s->pool_base;
             a_ts.resize(n);
-            a_type.assign(s->p_type.begin() + off, s->p_type.begin() + off + n);
-            a_params.assign(s->p_params.begin() + off * s->P, s->p_params.begin() + (off + n) * s->P);
+            a_type.resize(n);
+            a_params.resize(n * s->P);
+            s->p_type.copy_out(s->next_consume, n, a_type.data());
+            s->p_params.copy_out(s->next_consume * s->P, n * s->P, a_params.data());
             for (int64_t i = 0; i < n; i++) a_ts[i] = s->next_consume + i;
             lk.unlock();
             gputx_status st = GPUTX_ECAPACITY;
@@ -350,10 +421,10 @@ void worker_zero_set(gputx_server *s)
             for (size_t i = 0; i < got; i++) {
                 const int64_t id = r_ts[i];
                 s->r_status[id] = r_st[i];
-                std::memcpy(&s->r_values[id * s->R], &r_vals[i * s->R], sizeof(int64_t) * s->R);
+                s->r_values.copy_in(id * s->R, &r_vals[i * s->R], s->R);
                 s->r_complete[id] = t;
                 s->r_done[id] = 1;
-                s->hist.add(t - s->p_arrival[id - s->pool_base]);
+                s->hist.add(t - s->p_arrival[id]);
                 int64_t need[4];
                 sum_needs(s, id, 1, need);
                 for (int q = 0; q < 4; q++) {
@@ -367,20 +438,13 @@ void worker_zero_set(gputx_server *s)
             s->bulks++;
             s->max_bulk_seen = std::max<int64_t>(s->max_bulk_seen, (int64_t)got);
             while (s->oldest_open < s->next_id && s->r_done[s->oldest_open]) s->oldest_open++;
-            const int64_t drop = std::min(s->oldest_open, s->next_consume) - s->pool_base;
-            if (drop > (1 << 20) && drop * 2 > (int64_t)s->p_type.size()) {
-                s->p_type.erase(s->p_type.begin(), s->p_type.begin() + drop);
-                s->p_params.erase(s->p_params.begin(), s->p_params.begin() + drop * s->P);
-                s->p_arrival.erase(s->p_arrival.begin(), s->p_arrival.begin() + drop);
-                s->p_need.erase(s->p_need.begin(), s->p_need.begin() + drop);
-                s->pool_base += drop;
-            }
+            release_pool_before(s, std::min(s->oldest_open, s->next_consume));
             s->cv.notify_all();
             continue;
         }
         int64_t wait_ns = 200000;
         if (queued > 0) {
-            const int64_t oldest = s->p_arrival[s->next_consume - s->pool_base];
+            const int64_t oldest = s->p_arrival[s->next_consume];
             wait_ns = std::max<int64_t>(0, oldest + deadline - now_ns());
         }
         if (wait_ns > 0) s->cv.wait_for(lk, std::chrono::nanoseconds(wait_ns));
@@ -503,17 +567,17 @@ gputx_status gputx_server_submit(gputx_server *s, const int32_t *type, const int
     }
     for (int k = 0; k < 4; k++) s->ins_reserved[k] += need[k];
     const int64_t id0 = s->next_id;
-    s->p_type.insert(s->p_type.end(), type, type + n);
-    s->p_params.insert(s->p_params.end(), params, params + n * s->P);
-    s->p_need.insert(s->p_need.end(), packed.begin(), packed.end());
-    if (arrival_ns) s->p_arrival.insert(s->p_arrival.end(), arrival_ns, arrival_ns + n);
-    else s->p_arrival.resize(s->p_arrival.size() + n, t);
+    s->p_type.append(type, (int64_t)n);
+    s->p_params.append(params, (int64_t)n * s->P);
+    s->p_need.append(packed.data(), (int64_t)n);
+    if (arrival_ns) s->p_arrival.append(arrival_ns, (int64_t)n);
+    else s->p_arrival.grow((int64_t)n, t);
     if (s->first_arrival < 0 && n) s->first_arrival = arrival_ns ? arrival_ns[0] : t;
     s->next_id += (int64_t)n;
-    s->r_status.resize(s->next_id, 0);
-    s->r_values.resize(s->next_id * s->R, 0);
-    s->r_complete.resize(s->next_id, 0);
-    s->r_done.resize(s->next_id, 0);
+    s->r_status.grow((int64_t)n, 0);
+    s->r_values.grow((int64_t)n * s->R, 0);
+    s->r_complete.grow((int64_t)n, 0);
+    s->r_done.grow((int64_t)n, 0);
     if (first_id) *first_id = id0;
     s->cv.notify_all();
     return GPUTX_OK;
@@ -531,7 +595,7 @@ gputx_status gputx_server_results(gputx_server *s, int64_t first_id, size_t n, i
         if (!s->r_done[id]) continue;
         done++;
         if (status) status[i] = s->r_status[id];
-        if (values) std::memcpy(values + i * s->R, &s->r_values[id * s->R], sizeof(int64_t) * s->R);
+        if (values) s->r_values.copy_out(id * s->R, s->R, values + i * s->R);
         if (complete_ns) complete_ns[i] = s->r_complete[id];
     }
     if (n_done) *n_done = done;

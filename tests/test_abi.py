@@ -53,3 +53,15 @@ def test_structs_match_header_sizes():
     assert ctypes.sizeof(G.BatchConfig) == 4 * 4 + 2 * 8 + 2 * 4
     assert ctypes.sizeof(G.PoolConfig) == 8 + 2 * 4 + 2 * 8
     assert ctypes.sizeof(G.BatchChoice) == 4 * 4 + 2 * 8 + 16 * 4 * 2 + 16 * 8 * 2
+
+
+def test_probe_rejects_bad_shapes_without_a_gpu():
+    """Argument checks come before any CUDA call, so they run on CPU."""
+    import paper_1103_3105_gb300 as G
+    if not os.path.exists(G.LIB_PATH):
+        pytest.skip("library not built")
+    for args in [(0, 16, 64, 3, 10), (10, 17, 64, 3, 10), (10, 16, 48, 3, 10), (10, 16, 64, 9, 10),
+                 (10, 16, 64, 3, 0), (10, 16, 64, 3, 17)]:
+        with pytest.raises(G.GputxError) as e:
+            G.gputx_probe_level_chain(*args)
+        assert e.value.status == G.EINVAL

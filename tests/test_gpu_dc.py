@@ -303,3 +303,12 @@ def test_timing_stats_for_every_strategy():
         b.free()
         assert stats["ms_total"] > 0 and stats["ms_execute"] >= 0 and stats["ms_sort"] >= 0, s
     g.close()
+
+
+def test_level_chain_probe():
+    """The bare level-chain skeleton: positive, more traffic per level never
+    faster than less, and below the full runner's time per level."""
+    floor_min = G.gputx_probe_level_chain(2000, 16, 64, 1, 1)
+    floor_dc = G.gputx_probe_level_chain(2000, 16, 64, 3, 10)
+    assert 0 < floor_min < 50_000 and 0 < floor_dc < 50_000
+    assert floor_dc > 0.8 * floor_min
