@@ -101,9 +101,11 @@ __global__ void __launch_bounds__(256) kset_level_kernel(LevelArgs a)
 }
 
 // the narrow-level runner for debit-credit-only bulks: one packed record per
-// transaction (no type dispatch, no divisions), the next level's record
-// loaded while this level executes, its rows prefetched into L2 before the
-// barrier
+// transaction (no type dispatch, no divisions).  Records run two levels
+// ahead: while level k executes, level k+1's record is already in registers
+// and level k+2's is loading; before the barrier, level k+2's rows are
+// prefetched into L2, so an account row coming from HBM has a whole level to
+// arrive before it is read.
 template <bool CLUSTER, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) kset_narrow_dc_kernel(LevelArgs a)
 {
@@ -115,32 +117,63 @@ __global__ void __launch_bounds__(MAXT, 1) kset_narrow_dc_kernel(LevelArgs a)
         nthreads = cl.num_threads();
         rank = cl.thread_rank();
     }
+    // [lo, hi): level k; [nlo, nhi): level k+1
     uint32_t lo = __ldg(&a.level_off[a.k0]);
     uint32_t hi = __ldg(&a.level_off[a.k0 + 1]);
-    DcRecord v{};
+    uint32_t nhi = (a.k0 + 1 < a.k1) ? __ldg(&a.level_off[a.k0 + 2]) : hi;
+    DcRecord v{}, nv{};
     if (lo + rank < hi) {
         v = a.rec_dc[lo + rank];
         prefetch_l2(&a.db.acc_bal[v.a]);
     }
+    if (hi + rank < nhi) {
+        nv = a.rec_dc[hi + rank];
+        prefetch_l2(&a.db.acc_bal[nv.a]);
+    }
     for (uint32_t k = a.k0; k < a.k1; k++) {
         const uint32_t nlo = hi;
-        const uint32_t nhi = (k + 1 < a.k1) ? __ldg(&a.level_off[k + 2]) : nlo;
-        DcRecord nv{};
-        const bool has_next = nlo + rank < nhi;
-        if (has_next) nv = a.rec_dc[nlo + rank];
-        if (lo + rank < hi) exec_dc_record(a.db, a.b, v, hb + lo + rank, a.atomic_add);
+        // level k+2: [nhi, nnhi)
+        const uint32_t nnhi = (k + 2 < a.k1) ? __ldg(&a.level_off[k + 3]) : nhi;
+        DcRecord nnv{};
+        const bool has_nn = nhi + rank < nnhi;
+        if (has_nn) nnv = a.rec_dc[nhi + rank];
+        // the balance updates (the only cells a later level reads) before the
+        // barrier's release; the history row and outputs after this thread has
+        // arrived, overlapping the other threads' arrival
+        DcOut o;
+        bool pending = false;
+        if (lo + rank < hi) {
+            GlobalCells g;
+            pending = dc_state_core(a.db, a.b, v.a, v.tl, v.br, v.delta, v.ts, v.t, hb + lo + rank, a.atomic_add,
+                                    g, o);
+        }
         for (uint32_t pos = lo + rank + nthreads; pos < hi; pos += nthreads)
             exec_dc_record(a.db, a.b, a.rec_dc[pos], hb + pos, a.atomic_add);
-        if (has_next) {
-            prefetch_l2(&a.db.acc_bal[nv.a]);
-            prefetch_l2(&a.db.tel_bal[nv.tl]);
-            prefetch_l2(&a.db.br_bal[nv.br]);
+        if (CLUSTER) {
+            // split cluster barrier: arrive with release semantics, do the
+            // work no other thread waits for, then wait with acquire
+            asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+            if (pending) dc_finish(a.db, a.b, o);
+            if (has_nn) {
+                prefetch_l2(&a.db.acc_bal[nnv.a]);
+                prefetch_l2(&a.db.tel_bal[nnv.tl]);
+                prefetch_l2(&a.db.br_bal[nnv.br]);
+            }
+            asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+        } else {
+            if (pending) dc_finish(a.db, a.b, o);
+            if (has_nn) {
+                prefetch_l2(&a.db.acc_bal[nnv.a]);
+                prefetch_l2(&a.db.tel_bal[nnv.tl]);
+                prefetch_l2(&a.db.br_bal[nnv.br]);
+            }
+            __syncthreads();
         }
-        if (CLUSTER) cg::this_cluster().sync();   // release/acquire at cluster scope
-        else __syncthreads();
         lo = nlo;
         hi = nhi;
+        nhi = nnhi;
         v = nv;
+        nv = nnv;
     }
 }
 
