@@ -128,7 +128,7 @@ def test_strategies_agree_across_a_sequence():
 
 def test_empty_bulk():
     g, o = make_pair(4, 40, 4000, 1024)
-    for s in STRATS:
+    for s in STRATS + ["auto", "part_relaxed", "tpl_relaxed"]:
         b = g.submit(np.zeros(0, np.int64), np.zeros(0, np.int32), np.zeros((0, 2), np.int64))
         b.execute(s)
         st, out = b.results()
@@ -312,3 +312,24 @@ def test_level_chain_probe():
     floor_dc = G.gputx_probe_level_chain(2000, 16, 64, 3, 10)
     assert 0 < floor_min < 50_000 and 0 < floor_dc < 50_000
     assert floor_dc > 0.8 * floor_min
+
+
+@pytest.mark.parametrize("strategy", STRATS + ["auto", "part_relaxed", "tpl_relaxed"])
+def test_bulk_of_exactly_max_bulk(strategy):
+    """A bulk filling max_bulk exactly (every per-bulk scratch array at its
+    capacity), twice in a row on one database."""
+    g, o = make_pair(10, 100, 10000, 1 << 17, max_bulk=1 << 15)
+    for k in range(2):
+        bulk = W.dc_bulk(1 << 15, 10000, 0.3, seed=400 + k, ts0=k << 15)
+        b = g.submit_dict(bulk).execute(strategy)
+        st, out = b.results()
+        order = b.order().astype(np.int64)
+        b.free()
+        ost, oout = o.execute(bulk, R=1, order=order)
+        assert np.array_equal(st, ost) and np.array_equal(out, oout)
+    gs, os_ = gpu_logical_state(g, dc=True), oracle_logical_state(o)
+    assert states_equal(gs, os_), state_diff(gs, os_)
+    with pytest.raises(G.GputxError) as e:   # one more than max_bulk
+        g.submit_dict(W.dc_bulk((1 << 15) + 1, 10000, 0.0, seed=9))
+    assert e.value.status == G.EINVAL
+    g.close()
