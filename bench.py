@@ -256,7 +256,7 @@ def run_engine(args, rank, world, local_rank):
         b.free()
     e2e_value = replica_throughput(n * K, sum(e2e_times), dist, dev)
 
-    sweep = serving = batched = None
+    sweep = serving = batched = subscriber = None
     if rank == 0:
         db.close()
         if args.sweep:
@@ -265,6 +265,8 @@ def run_engine(args, rank, world, local_rank):
             serving = run_serving(args, G, torch, stream)
         if args.batched:
             batched = run_batched(args, G, torch, stream)
+        if args.subscriber:
+            subscriber = run_subscriber(args, G, torch, stream)
 
     if rank != 0:
         if dist:
@@ -332,6 +334,8 @@ def run_engine(args, rank, world, local_rank):
         line["serving"] = serving
     if batched is not None:
         line["batched"] = batched
+    if subscriber is not None:
+        line["subscriber"] = subscriber
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -458,6 +462,57 @@ def run_serving(args, G, torch, stream):
     db.close()
     return {"db_bytes": int(db_bytes), "subscribers": n_sub, "accounts": ACCOUNTS, "history_rows": hist_rows,
             "mix": "50% debit-credit, 50% subscriber (30/25/25/8/8/2/2)", "runs": out}
+
+
+def run_subscriber(args, G, torch, stream):
+    """The subscriber-location schema (read-heavy, four tables): 10M
+    subscribers with their access_info, special_facility and call_forwarding
+    rows, bulks of 2^20 mixed transactions (30/25/25/8/8/2/2 %), subscriber
+    ids uniform or Zipf 0.8.  Every strategy, the paper's R/W model."""
+    t0 = time.perf_counter()
+    n_sub = args.sub_subscribers
+    tabs = W.sub_tables(n_sub, seed=W.seed_for(3, 1))
+    db = G.Database(sub=n_sub, sub_child_capacity=6 * n_sub, max_bulk=1 << 20, stream=stream.cuda_stream)
+    db.register(G.SUB_TYPES)
+    for t, r in W.sub_rows(tabs).items():
+        db.load(t, r)
+    del tabs
+    setup_s = time.perf_counter() - t0
+    out = []
+    ts0 = 0
+    n = 1 << 20
+    for theta in (0.0, 0.8):
+        bulk = W.sub_bulk(n, n_sub, theta, seed=W.seed_for(3, 10 + int(theta * 10)))
+        for strategy in ("kset", "part", "tpl", "auto", "part_relaxed", "tpl_relaxed"):
+            rec = {"theta": theta, "bulk": n, "strategy": strategy}
+            ms = []
+            st = None
+            try:
+                for rep in range(3):
+                    bulk["ts"] = np.arange(ts0, ts0 + n, dtype=np.int64)
+                    ts0 += n
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    b = db.submit_dict(bulk)
+                    b.execute(strategy, timing=True)
+                    e1.record(stream)
+                    try:
+                        st = b.sync()
+                    finally:
+                        b.free()
+                    if rep:
+                        ms.append(e0.elapsed_time(e1))
+            except G.GputxError as err:
+                rec["error"] = str(err)
+                out.append(rec)
+                continue
+            m = statistics.median(ms)
+            rec.update({"ms": m, "txn_per_s": n / (m / 1e3), "depth": st["depth"], "w0": st["w0"],
+                        "exec_ms": st["ms_execute"], "analysis_ms": st["ms_analysis"], "ran": st["strategy"]})
+            out.append(rec)
+    db.close()
+    return {"subscribers": n_sub, "setup_s": setup_s, "runs": out}
 
 
 def run_batched(args, G, torch, stream):
@@ -600,6 +655,9 @@ def main():
     ap.add_argument("--batched", dest="batched", action="store_true", default=True)
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--batch-txns", type=int, default=3_000_000)
+    ap.add_argument("--subscriber", dest="subscriber", action="store_true", default=True)
+    ap.add_argument("--no-subscriber", dest="subscriber", action="store_false")
+    ap.add_argument("--sub-subscribers", type=int, default=10_000_000)
     args = ap.parse_args()
     rank, world = env_int("RANK", 0), env_int("WORLD_SIZE", 1)
     local_rank = env_int("LOCAL_RANK", 0)

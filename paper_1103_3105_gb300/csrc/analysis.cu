@@ -200,50 +200,73 @@ struct TicketMode {
     }
 };
 
-// one Jacobi round of the exact-depth refinement (Section 4.1's longest
-// path): every operation of a run after its group's first run conflicts with
-// all operations of the run before it, so its transaction needs depth at
-// least 1 + the largest depth in that run.  Starting from the one-pass ranks
-// (a lower bound) the rounds climb to the longest-path depths.
-__global__ void runmax_kernel(const uint32_t *sv, const uint32_t *rid, const uint32_t *level, uint32_t *runmax,
-                              int64_t m, const uint32_t *err)
+// All refinement rounds in one cooperative launch (no host round trips).
+//
+// A round of plain Jacobi relaxation moves a depth one run along a group per
+// round, so a group of many runs needs that many rounds.  Each round here
+// instead carries depths along whole groups at once.  An operation of run j
+// needs depth at least max over earlier runs r of the same group of
+// (runmax(r) + j - r), which is j + (exclusive segmented max of
+// runmax(r) - r).  One segmented max-scan over the runs gives that bound
+// for every run.  The bound is implied by the chain of run-to-run
+// constraints, so the fixpoint is the same longest-path depth; only the number
+// of rounds drops, to about the number of group changes along the longest
+// path.  Grid barriers separate: clearing run maxima, gathering them, the
+// scan's block, grid and apply steps, and relaxing.  Round r reports growth in
+// changed_r[r % 3]; the flag of round r+1 is cleared during round r, after
+// every thread has read it two rounds ago.
+struct SegMax {
+    uint32_t f;   // a group starts within the span
+    int32_t v;    // max of runmax(r) - r since the last start
+};
+__device__ __forceinline__ SegMax segmax_combine(const SegMax &a, const SegMax &b)
 {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= m || *err || sv[i] == OP_SENTINEL) return;
-    atomicMax(&runmax[rid[i] & 0x7fffffffu], level[sv[i] >> 7]);
+    return SegMax{a.f | b.f, b.f ? b.v : (a.v > b.v ? a.v : b.v)};
+}
+__device__ __forceinline__ unsigned long long segmax_pack(const SegMax &x)
+{
+    return ((unsigned long long)x.f << 32) | (uint32_t)x.v;
+}
+__device__ __forceinline__ SegMax segmax_unpack(unsigned long long p)
+{
+    return SegMax{(uint32_t)(p >> 32), (int32_t)(uint32_t)p};
 }
 
-__global__ void relax_kernel(const uint32_t *sv, const uint32_t *rid, const uint32_t *runmax, uint32_t *level,
-                             BulkCtl *ctl, int64_t m)
-{
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    bool grew = false;
-    if (i < m && !ctl->err && sv[i] != OP_SENTINEL) {
-        const uint32_t r = rid[i];
-        if (!(r & 0x80000000u)) {
-            const uint32_t cand = runmax[(r & 0x7fffffffu) - 1u] + 1u;
-            grew = atomicMax(&level[sv[i] >> 7], cand) < cand;
-        }
-    }
-    if (__any_sync(0xffffffffu, grew) && (threadIdx.x & 31) == 0) ctl->changed = 1;
-}
-
-// All refinement rounds in one cooperative launch (no host round trips): a
-// grid barrier separates clearing run maxima, gathering them, and relaxing
-// depths.  Round r reports growth in changed_r[r % 3]; the flag of round r+1
-// is cleared during round r, after every thread has read it two rounds ago.
 __global__ void __launch_bounds__(256) fixpoint_coop_kernel(const uint32_t *sv, const uint32_t *rid,
-                                                           uint32_t *runmax, uint32_t *level, BulkCtl *ctl,
+                                                           uint32_t *runmax, uint32_t *level, int32_t *best,
+                                                           uint32_t *rfirst, unsigned long long *agg, BulkCtl *ctl,
                                                            int64_t m, uint32_t max_rounds)
 {
+    __shared__ SegMax s_warp[8];
     cooperative_groups::grid_group g = cooperative_groups::this_grid();
     if (ctl->err) return;   // set before this launch only: every block returns
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const SegMax ident{0u, INT32_MIN};
+    // the runs: count, and which run starts its group
+    if (i0 == 0) ctl->runs = 0;   // a replayed graph reuses the control block
+    g.sync();
+    for (int64_t i = i0; i < m; i += stride) {
+        const uint32_t v = sv[i], rr = rid[i];
+        if (v == OP_SENTINEL) continue;
+        if (i == 0 || rid[i - 1] != rr) {
+            rfirst[rr & 0x7fffffffu] = rr >> 31;
+            atomicMax(&ctl->runs, (rr & 0x7fffffffu) + 1u);
+        }
+    }
+    g.sync();
+    const int64_t R = *(volatile uint32_t *)&ctl->runs;
+    // this block's runs [b0, b1), this thread's [t0, t1)
+    const int64_t per_block = (R + gridDim.x - 1) / gridDim.x;
+    const int64_t b0 = blockIdx.x * per_block, b1 = b0 + per_block < R ? b0 + per_block : R;
+    const int64_t per_thread = (per_block + blockDim.x - 1) / blockDim.x;
+    const int64_t t0 = b0 + threadIdx.x * per_thread < b1 ? b0 + threadIdx.x * per_thread : b1;
+    const int64_t t1 = t0 + per_thread < b1 ? t0 + per_thread : b1;
     uint32_t r = 0;
     bool grew_any = true;
     for (; r < max_rounds && grew_any; r++) {
-        for (int64_t i = i0; i < m; i += stride) runmax[i] = 0;
+        for (int64_t i = i0; i < R; i += stride) runmax[i] = 0;
         if (i0 == 0) ctl->changed_r[(r + 1) % 3] = 0;
         g.sync();
         for (int64_t i = i0; i < m; i += stride) {
@@ -251,14 +274,79 @@ __global__ void __launch_bounds__(256) fixpoint_coop_kernel(const uint32_t *sv, 
             if (v != OP_SENTINEL) atomicMax(&runmax[rid[i] & 0x7fffffffu], level[v >> 7]);
         }
         g.sync();
+        // segmented max-scan of runmax(q) - q over the runs: thread, block
+        SegMax th = ident;
+#pragma unroll 8
+        for (int64_t q = t0; q < t1; q++)
+            th = segmax_combine(th, SegMax{rfirst[q], (int32_t)runmax[q] - (int32_t)q});
+        SegMax x = th;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            SegMax o{__shfl_up_sync(0xffffffffu, x.f, off), (int32_t)__shfl_up_sync(0xffffffffu, (uint32_t)x.v, off)};
+            if (lane >= (uint32_t)off) x = segmax_combine(o, x);
+        }
+        if (lane == 31) s_warp[warp] = x;
+        SegMax th_excl{__shfl_up_sync(0xffffffffu, x.f, 1), (int32_t)__shfl_up_sync(0xffffffffu, (uint32_t)x.v, 1)};
+        if (lane == 0) th_excl = ident;
+        __syncthreads();
+        SegMax warp_excl = ident;
+        for (uint32_t w = 0; w < warp; w++) warp_excl = segmax_combine(warp_excl, s_warp[w]);
+        if (threadIdx.x == 0) {
+            SegMax blk = ident;
+            for (uint32_t w = 0; w < blockDim.x / 32; w++) blk = segmax_combine(blk, s_warp[w]);
+            agg[blockIdx.x] = segmax_pack(blk);
+        }
+        g.sync();
+        // grid: exclusive prefixes of the block aggregates, in place, by block
+        // 0 (each thread a contiguous slice, then a block scan of the slices)
+        if (blockIdx.x == 0) {
+            const uint32_t per = (gridDim.x + blockDim.x - 1) / blockDim.x;
+            const uint32_t a0 = threadIdx.x * per < gridDim.x ? threadIdx.x * per : gridDim.x;
+            const uint32_t a1 = a0 + per < gridDim.x ? a0 + per : gridDim.x;
+            SegMax sl = ident;
+            for (uint32_t bb = a0; bb < a1; bb++) sl = segmax_combine(sl, segmax_unpack(agg[bb]));
+            SegMax y = sl;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                SegMax o{__shfl_up_sync(0xffffffffu, y.f, off),
+                         (int32_t)__shfl_up_sync(0xffffffffu, (uint32_t)y.v, off)};
+                if (lane >= (uint32_t)off) y = segmax_combine(o, y);
+            }
+            __syncthreads();   // s_warp: the block scan above has read it
+            if (lane == 31) s_warp[warp] = y;
+            SegMax sl_excl{__shfl_up_sync(0xffffffffu, y.f, 1), (int32_t)__shfl_up_sync(0xffffffffu, (uint32_t)y.v, 1)};
+            if (lane == 0) sl_excl = ident;
+            __syncthreads();
+            SegMax run = ident;
+            for (uint32_t w = 0; w < warp; w++) run = segmax_combine(run, s_warp[w]);
+            run = segmax_combine(run, sl_excl);
+            for (uint32_t bb = a0; bb < a1; bb++) {
+                const SegMax a = segmax_unpack(agg[bb]);
+                agg[bb] = segmax_pack(run);
+                run = segmax_combine(run, a);
+            }
+        }
+        g.sync();
+        // apply: best[q] = bound carried into run q from earlier runs of its group
+        SegMax carry = segmax_combine(segmax_combine(segmax_unpack(agg[blockIdx.x]), warp_excl), th_excl);
+#pragma unroll 8
+        for (int64_t q = t0; q < t1; q++) {
+            const uint32_t f = rfirst[q];
+            best[q] = f ? INT32_MIN : carry.v;
+            carry = segmax_combine(carry, SegMax{f, (int32_t)runmax[q] - (int32_t)q});
+        }
+        g.sync();
         bool grew = false;
         for (int64_t i = i0; i < m; i += stride) {
             const uint32_t v = sv[i], rr = rid[i];
             if (v == OP_SENTINEL || (rr & 0x80000000u)) continue;
-            const uint32_t cand = runmax[(rr & 0x7fffffffu) - 1u] + 1u;
+            const uint32_t j = rr & 0x7fffffffu;
+            const int32_t bj = best[j];
+            if (bj == INT32_MIN) continue;
+            const uint32_t cand = (uint32_t)((int64_t)j + bj);
             grew |= atomicMax(&level[v >> 7], cand) < cand;
         }
-        if (__any_sync(0xffffffffu, grew) && (threadIdx.x & 31) == 0) atomicOr(&ctl->changed_r[r % 3], 1u);
+        if (__any_sync(0xffffffffu, grew) && lane == 0) atomicOr(&ctl->changed_r[r % 3], 1u);
         g.sync();
         grew_any = *(volatile uint32_t *)&ctl->changed_r[r % 3] != 0;
     }
@@ -915,21 +1003,6 @@ cudaError_t launch_ticket_scan(gputx_bulk *b, const uint32_t *sk, const uint32_t
     return run_scan(b, tm, m, 2);
 }
 
-cudaError_t launch_fixpoint_round(gputx_bulk *b, const uint32_t *sv, int64_t m)
-{
-    cudaStream_t s = b->stream;
-    if (m == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(b->sc.runmax, 0, m * sizeof(uint32_t), s);
-    if (e) return e;
-    e = cudaMemsetAsync(&b->ctl->changed, 0, sizeof(uint32_t), s);
-    if (e) return e;
-    runmax_kernel<<<grid_for(m), TB, 0, s>>>(sv, b->sc.rid, b->sc.level, b->sc.runmax, m, &b->ctl->err);
-    count_launches(1);
-    relax_kernel<<<grid_for(m), TB, 0, s>>>(sv, b->sc.rid, b->sc.runmax, b->sc.level, b->ctl, m);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_fixpoint_device(gputx_bulk *b, const uint32_t *sv, int64_t m)
 {
     if (m == 0) return cudaSuccess;
@@ -941,6 +1014,8 @@ cudaError_t launch_fixpoint_device(gputx_bulk *b, const uint32_t *sv, int64_t m)
     int64_t grid = (int64_t)b->db->num_sms * blocks_per_sm;
     const int64_t need = (m + 255) / 256;
     if (grid > need) grid = need;
+    if (grid > kFixAggMax) grid = kFixAggMax;
+    if (!b->sc.fix_agg) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid, 1, 1);
     cfg.blockDim = dim3(256, 1, 1);
@@ -951,8 +1026,11 @@ cudaError_t launch_fixpoint_device(gputx_bulk *b, const uint32_t *sv, int64_t m)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const uint32_t max_rounds = (uint32_t)(b->n + 2 > 0xffffffffll ? 0xffffffffll : b->n + 2);
+    // the run bounds and run-start flags reuse the TPL buffers (free during
+    // the analysis)
     cudaError_t e = cudaLaunchKernelEx(&cfg, fixpoint_coop_kernel, sv, (const uint32_t *)b->sc.rid, b->sc.runmax,
-                                       b->sc.level, b->ctl, m, max_rounds);
+                                       b->sc.level, (int32_t *)b->sc.lock_key, b->sc.lock_ticket, b->sc.fix_agg,
+                                       b->ctl, m, max_rounds);
     count_launches(1);
     return e;
 }

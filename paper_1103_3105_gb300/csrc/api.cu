@@ -223,6 +223,7 @@ size_t carve_bulk(gputx_bulk *b, char *base, bool device_inputs)
     s.scan_tiles = (big + 2047) / 2048;
     s.scan_status = c.take<uint64_t>(s.scan_tiles);
     s.scan_vals = c.take<uint64_t>(2 * s.scan_tiles);
+    s.fix_agg = db->need_fixpoint ? c.take<unsigned long long>(kFixAggMax) : nullptr;
     s.rec_dc = db->dev.registered == (1u << GPUTX_T_DC_DEBIT_CREDIT) ? c.take<DcRecord>(nn) : nullptr;
     return c.off + 256;
 }

@@ -24,7 +24,10 @@ struct BulkCtl {
     InsertBase total;      // inserts this bulk reserves
     uint32_t changed_r[3]; // refinement rounds run on the device: rotating per-round flags
     uint32_t rounds;       // refinement rounds taken
+    uint32_t runs;         // refinement: runs of the sorted operations
 };
+
+constexpr int kFixAggMax = 4096;   // blocks of the cooperative refinement launch, at most
 
 // Scratch carved from one per-bulk allocation.
 struct Scratch {
@@ -51,6 +54,7 @@ struct Scratch {
     uint32_t *tile_ctr;    // 16 counters
     uint64_t *scan_status; // tiles
     uint64_t *scan_vals;   // 2 x tiles: per-tile values of 64-bit scans
+    unsigned long long *fix_agg;   // kFixAggMax: refinement's per-block scan aggregates
     DcRecord *rec_dc;      // n packed debit-credit records (debit-credit-only databases)
     int64_t m_cap;         // op capacity
     int64_t sort_tiles, scan_tiles, chunk_cap;
@@ -130,7 +134,6 @@ cudaError_t launch_sort(gputx_bulk *b, uint32_t *&keys, uint32_t *&vals, uint32_
                         uint32_t *&vals_alt, int64_t count, int bits);
 cudaError_t launch_rank_scan(gputx_bulk *b, const uint32_t *sk, const uint32_t *sv, int64_t m, bool want_rid);
 cudaError_t launch_ticket_scan(gputx_bulk *b, const uint32_t *sk, const uint32_t *sv, int64_t m);
-cudaError_t launch_fixpoint_round(gputx_bulk *b, const uint32_t *sv, int64_t m);
 cudaError_t launch_fixpoint_device(gputx_bulk *b, const uint32_t *sv, int64_t m);
 cudaError_t launch_level_stats(gputx_bulk *b);
 cudaError_t launch_regroup_keys(gputx_bulk *b, uint32_t *keys, uint32_t *vals);

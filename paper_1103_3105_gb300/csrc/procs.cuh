@@ -573,27 +573,50 @@ __device__ __forceinline__ void exec_oe(const DevDB &db, const DevBulk &b, const
         if (oslot >= db.ord_cap || lslot + cnt > db.ol_cap) {
             set_err(b.err, ERR_CAPACITY); st = 3; break;
         }
+        // the lines in chunks of kLineChunk: each chunk's loads first, then its
+        // stores.  The items are distinct (the signature was validated), so no
+        // store changes a row a later load reads, and a chunk's loads overlap
+        // in one round trip instead of one per line (chunks bound the
+        // registers the other executors of the same kernel pay for)
+        constexpr int kLineChunk = 5;
         const int64_t o_id = cells.ld(&db.d_next_o_id[d]);
         cells.st(&db.d_next_o_id[d], o_id + 1);
         int64_t total = 0;
-        for (int j = 0; j < cnt; j++) {
-            const int64_t line = p[4 + j];
-            const int64_t item = line & 0xFFFFFF, sw = (line >> 24) & 0xFFFF;
-            const int64_t qty = (line >> 40) & 0xFF;
-            const int64_t amount = qty * __ldg(&db.i_price[item]);
-            total += amount;
-            const int64_t s = sw * db.n_items + item;
-            int32_t q = ldg_cg(&db.s_quantity[s]);
-            const int64_t sy = cells.ld(&db.s_ytd[s]);
-            const int32_t so = ldg_cg(&db.s_order_cnt[s]);
-            q = (q >= qty + 10) ? (int32_t)(q - qty) : (int32_t)(q - qty + 91);
-            stg_cg(&db.s_quantity[s], q);
-            cells.st(&db.s_ytd[s], sy + qty);
-            stg_cg(&db.s_order_cnt[s], so + 1);
-            db.ol_item[lslot + j] = (int32_t)item;
-            db.ol_sw[lslot + j] = (int32_t)sw;
-            db.ol_qty[lslot + j] = (int32_t)qty;
-            stg_cg(&db.ol_amount[lslot + j], amount);
+        for (int j0 = 0; j0 < cnt; j0 += kLineChunk) {
+            int64_t price[kLineChunk], sy[kLineChunk];
+            int32_t q[kLineChunk], so[kLineChunk];
+#pragma unroll
+            for (int u = 0; u < kLineChunk; u++) {
+                if (j0 + u < cnt) {
+                    const int64_t line = p[4 + j0 + u];
+                    const int64_t item = line & 0xFFFFFF, sw = (line >> 24) & 0xFFFF;
+                    const int64_t s = sw * db.n_items + item;
+                    price[u] = __ldg(&db.i_price[item]);
+                    q[u] = ldg_cg(&db.s_quantity[s]);
+                    sy[u] = cells.ld(&db.s_ytd[s]);
+                    so[u] = ldg_cg(&db.s_order_cnt[s]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kLineChunk; u++) {
+                if (j0 + u < cnt) {
+                    const int j = j0 + u;
+                    const int64_t line = p[4 + j];
+                    const int64_t item = line & 0xFFFFFF, sw = (line >> 24) & 0xFFFF;
+                    const int64_t qty = (line >> 40) & 0xFF;
+                    const int64_t amount = qty * price[u];
+                    total += amount;
+                    const int64_t s = sw * db.n_items + item;
+                    const int32_t nq = (q[u] >= qty + 10) ? (int32_t)(q[u] - qty) : (int32_t)(q[u] - qty + 91);
+                    stg_cg(&db.s_quantity[s], nq);
+                    cells.st(&db.s_ytd[s], sy[u] + qty);
+                    stg_cg(&db.s_order_cnt[s], so[u] + 1);
+                    db.ol_item[lslot + j] = (int32_t)item;
+                    db.ol_sw[lslot + j] = (int32_t)sw;
+                    db.ol_qty[lslot + j] = (int32_t)qty;
+                    stg_cg(&db.ol_amount[lslot + j], amount);
+                }
+            }
         }
         db.o_w[oslot] = (int32_t)w;
         db.o_d[oslot] = (int32_t)p[1];
