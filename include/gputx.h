@@ -440,13 +440,14 @@ void gputx_server_destroy(gputx_server *s);
  * skeleton of the K-SET narrow-level runner (Section 5.3) with no transaction
  * logic.  At each of `levels` levels, each of cluster_size x threads threads
  * loads `loads` (0..8) values that the previous level wrote on another CTA,
- * stores `stores` (1..16) values, and the cluster synchronises with
- * release/acquire semantics.  *ns_per_level = the time of one timed launch
+ * stores `stores` (>= 1) values, arrives at the cluster barrier (release),
+ * stores `stores_after` (>= 0) more values, and waits (acquire);
+ * stores + stores_after <= 16.  *ns_per_level = the time of one timed launch
  * (after a warm-up launch) divided by `levels`.  Allocates and frees its own
  * device memory (levels x cluster_size x threads x 128 bytes).  EINVAL on a
  * parameter out of range, ECUDA if the cluster shape cannot launch. */
 gputx_status gputx_probe_level_chain(int levels, int cluster_size, int threads, int loads, int stores,
-                                     double *ns_per_level);
+                                     int stores_after, double *ns_per_level);
 
 /* ---------------------------------------------------------------------------
  * Incremental 0-set execution (Section 5.3).  A device-resident pool of

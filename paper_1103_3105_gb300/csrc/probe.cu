@@ -3,12 +3,14 @@
 //
 // A level of the K-SET narrow-level runner is: dependent loads of rows the
 // previous level wrote (possibly on another SM of the cluster), arithmetic,
-// stores, and a cluster barrier with release/acquire semantics.  This probe
-// runs exactly that skeleton with no transaction logic: at level k every
-// thread loads `loads` values written at level k-1 by threads of the next CTA,
-// stores `stores` values, and the cluster synchronises.  Its time per level is
-// the floor any level-by-level executor with that launch shape and that
-// memory traffic per level can reach.
+// stores, and a cluster barrier with release/acquire semantics, split so that
+// stores no later level reads follow the arrival.  This probe runs exactly
+// that skeleton with no transaction logic: at level k every thread loads
+// `loads` values written at level k-1 by threads of the next CTA, stores
+// `stores` values, arrives at the cluster barrier (release), stores
+// `stores_after` more values and waits (acquire).  Its time per level is the
+// floor any level-by-level executor with that launch shape and that memory
+// traffic per level can reach.
 #include <cooperative_groups.h>
 
 #include "engine.h"
@@ -21,7 +23,7 @@ namespace {
 constexpr int kProbeMaxLoads = 8, kProbeMaxStores = 16;
 
 __global__ void __launch_bounds__(1024, 1) probe_chain_kernel(int64_t *buf, int64_t *sink, int levels, int loads,
-                                                            int stores)
+                                                            int stores, int stores_after)
 {
     cg::cluster_group cl = cg::this_cluster();
     const uint32_t n = cl.num_threads(), r = cl.thread_rank();
@@ -35,7 +37,9 @@ __global__ void __launch_bounds__(1024, 1) probe_chain_kernel(int64_t *buf, int6
         for (int j = 0; j < loads; j++) v += __ldcg(&prev[(int64_t)j * n + src]);
         acc += v;
         for (int j = 0; j < stores; j++) __stcg(&cur[(int64_t)j * n + r], acc + j);
-        cl.sync();
+        asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+        for (int j = 0; j < stores_after; j++) __stcg(&cur[(int64_t)(stores + j) * n + r], acc - j);
+        asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
     }
     sink[r] = acc;   // keeps the chain live
 }
@@ -46,11 +50,11 @@ __global__ void __launch_bounds__(1024, 1) probe_chain_kernel(int64_t *buf, int6
 using namespace gtx;
 
 extern "C" gputx_status gputx_probe_level_chain(int levels, int cluster_size, int threads, int loads, int stores,
-                                                double *ns_per_level)
+                                                int stores_after, double *ns_per_level)
 {
     if (!ns_per_level || levels < 1 || levels > (1 << 20) || cluster_size < 1 || cluster_size > 16 ||
         threads < 32 || threads > 1024 || threads % 32 || loads < 0 || loads > kProbeMaxLoads || stores < 1 ||
-        stores > kProbeMaxStores)
+        stores_after < 0 || stores + stores_after > kProbeMaxStores)
         return GPUTX_EINVAL;
     const int64_t n = (int64_t)cluster_size * threads;
     const int64_t words = (int64_t)(levels + 1) * n * kProbeMaxStores;
@@ -78,9 +82,9 @@ extern "C" gputx_status gputx_probe_level_chain(int levels, int cluster_size, in
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         // one warm-up launch, then the timed one
-        e = cudaLaunchKernelEx(&cfg, probe_chain_kernel, buf, sink, levels, loads, stores);
+        e = cudaLaunchKernelEx(&cfg, probe_chain_kernel, buf, sink, levels, loads, stores, stores_after);
         if (!e) e = cudaEventRecord(e0, s);
-        if (!e) e = cudaLaunchKernelEx(&cfg, probe_chain_kernel, buf, sink, levels, loads, stores);
+        if (!e) e = cudaLaunchKernelEx(&cfg, probe_chain_kernel, buf, sink, levels, loads, stores, stores_after);
         if (!e) e = cudaEventRecord(e1, s);
         if (!e) e = cudaEventSynchronize(e1);
         float ms = 0;

@@ -310,7 +310,9 @@ def test_level_chain_probe():
     faster than less, and below the full runner's time per level."""
     floor_min = G.gputx_probe_level_chain(2000, 16, 64, 1, 1)
     floor_dc = G.gputx_probe_level_chain(2000, 16, 64, 3, 10)
-    assert 0 < floor_min < 50_000 and 0 < floor_dc < 50_000
+    floor_split = G.gputx_probe_level_chain(2000, 16, 64, 3, 3, 7)
+    for f in (floor_min, floor_dc, floor_split):
+        assert 0 < f < 50_000
     assert floor_dc > 0.8 * floor_min
 
 
