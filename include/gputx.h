@@ -440,14 +440,20 @@ void gputx_server_destroy(gputx_server *s);
  * skeleton of the K-SET narrow-level runner (Section 5.3) with no transaction
  * logic.  At each of `levels` levels, each of cluster_size x threads threads
  * loads `loads` (0..8) values that the previous level wrote on another CTA,
- * stores `stores` (>= 1) values, arrives at the cluster barrier (release),
+ * updates `stores` (>= 1) values, arrives at the cluster barrier (release),
  * stores `stores_after` (>= 0) more values, and waits (acquire);
- * stores + stores_after <= 16.  *ns_per_level = the time of one timed launch
- * (after a warm-up launch) divided by `levels`.  Allocates and frees its own
- * device memory (levels x cluster_size x threads x 128 bytes).  EINVAL on a
- * parameter out of range, ECUDA if the cluster shape cannot launch. */
+ * stores + stores_after <= 16.  rmw = 0: the updates are plain stores;
+ * rmw = 1: they are 64-bit atomic additions to cells that the previous level
+ * updated on another CTA, one a fetch-and-add whose old value feeds the
+ * stores after the arrival and the rest reductions (the shape of a runner
+ * applying its balance updates at L2).
+ * *ns_per_level = the time of one timed launch (after a warm-up launch)
+ * divided by `levels`.  Allocates and frees its own device memory
+ * ((levels + 17) x cluster_size x threads x 128 bytes).  EINVAL on a parameter
+ * out of range (rmw other than 0 or 1 included), ECUDA if the cluster shape
+ * cannot launch. */
 gputx_status gputx_probe_level_chain(int levels, int cluster_size, int threads, int loads, int stores,
-                                     int stores_after, double *ns_per_level);
+                                     int stores_after, int rmw, double *ns_per_level);
 
 /* ---------------------------------------------------------------------------
  * Incremental 0-set execution (Section 5.3).  A device-resident pool of

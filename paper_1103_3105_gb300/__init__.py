@@ -157,7 +157,7 @@ def lib():
             "gputx_read_results": ([p, p, p, sz, C.c_int], C.c_int),
             "gputx_bulk_results_device": ([p, C.POINTER(p), C.POINTER(p)], C.c_int),
             "gputx_bulk_order": ([p, p, sz], C.c_int),
-            "gputx_probe_level_chain": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+            "gputx_probe_level_chain": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                          C.POINTER(C.c_double)], C.c_int),
             "gputx_output_width": ([p], C.c_int),
             "gputx_free_bulk": ([p], None),
@@ -277,10 +277,11 @@ def gputx_read_results(db, bulk, n: int, width: int, status=None, values=None):
 
 
 def gputx_probe_level_chain(levels: int, cluster_size: int, threads: int, loads: int, stores: int,
-                            stores_after: int = 0) -> float:
+                            stores_after: int = 0, rmw: int = 0) -> float:
     """ns per level of the bare level chain (see gputx.h)."""
     ns = C.c_double()
-    st = lib().gputx_probe_level_chain(levels, cluster_size, threads, loads, stores, stores_after, C.byref(ns))
+    st = lib().gputx_probe_level_chain(levels, cluster_size, threads, loads, stores, stores_after, rmw,
+                                       C.byref(ns))
     if st != OK:
         raise GputxError(st, "probe_level_chain")
     return ns.value

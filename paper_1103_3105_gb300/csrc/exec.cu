@@ -95,17 +95,20 @@ __global__ void __launch_bounds__(256) kset_level_kernel(LevelArgs a)
     const int64_t hb = a.ctl->base.hist;
     const uint32_t lo = __ldg(&a.level_off[a.k0]), hi = __ldg(&a.level_off[a.k0 + 1]);
     for (uint32_t pos = lo + blockIdx.x * blockDim.x + threadIdx.x; pos < hi; pos += gridDim.x * blockDim.x) {
-        if (a.rec_dc) exec_dc_record(a.db, a.b, a.rec_dc[pos], hb + pos, a.atomic_add);
+        if (a.rec_dc) exec_dc_record(a.db, a.b, a.rec_dc[pos], hb + pos);
         else exec_txn(a.db, a.b, view_at(a.b, pos, hb), a.atomic_add);
     }
 }
 
 // the narrow-level runner for debit-credit-only bulks: one packed record per
-// transaction (no type dispatch, no divisions).  Records run two levels
-// ahead: while level k executes, level k+1's record is already in registers
-// and level k+2's is loading; before the barrier, level k+2's rows are
-// prefetched into L2, so an account row coming from HBM has a whole level to
-// arrive before it is read.
+// transaction (no type dispatch, no divisions), its balances updated by
+// atomics at L2 (dc_state_rmw), so nothing is loaded between the barrier's
+// acquire and the updates.  The inputs of later levels run ahead in a
+// pipeline, each stage a whole level before its use: while level k executes,
+// level k+1's and k+2's records are in registers, level k+3's record is
+// loading and level k+4's end offset too; after the arrival, level k+2's
+// rows are prefetched into L2, so an account row coming from HBM has a whole
+// level to arrive before it is updated.
 template <bool CLUSTER, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) kset_narrow_dc_kernel(LevelArgs a)
 {
@@ -117,63 +120,58 @@ __global__ void __launch_bounds__(MAXT, 1) kset_narrow_dc_kernel(LevelArgs a)
         nthreads = cl.num_threads();
         rank = cl.thread_rank();
     }
-    // [lo, hi): level k; [nlo, nhi): level k+1
+    // the end of level j (the start of level j+1); levels from k1 on are empty
+    auto end_of = [&](uint32_t j, uint32_t prev) { return j < a.k1 ? __ldg(&a.level_off[j + 1]) : prev; };
+    // level k is [lo, e0); levels k+1, k+2, k+3 end at e1, e2, e3
     uint32_t lo = __ldg(&a.level_off[a.k0]);
-    uint32_t hi = __ldg(&a.level_off[a.k0 + 1]);
-    uint32_t nhi = (a.k0 + 1 < a.k1) ? __ldg(&a.level_off[a.k0 + 2]) : hi;
-    DcRecord v{}, nv{};
-    if (lo + rank < hi) {
+    uint32_t e0 = end_of(a.k0, lo);
+    uint32_t e1 = end_of(a.k0 + 1, e0);
+    uint32_t e2 = end_of(a.k0 + 2, e1);
+    uint32_t e3 = end_of(a.k0 + 3, e2);
+    DcRecord v{}, r1{}, r2{};
+    if (lo + rank < e0) {
         v = a.rec_dc[lo + rank];
         prefetch_l2(&a.db.acc_bal[v.a]);
     }
-    if (hi + rank < nhi) {
-        nv = a.rec_dc[hi + rank];
-        prefetch_l2(&a.db.acc_bal[nv.a]);
+    if (e0 + rank < e1) {
+        r1 = a.rec_dc[e0 + rank];
+        prefetch_l2(&a.db.acc_bal[r1.a]);
     }
+    if (e1 + rank < e2) r2 = a.rec_dc[e1 + rank];
     for (uint32_t k = a.k0; k < a.k1; k++) {
-        const uint32_t nlo = hi;
-        // level k+2: [nhi, nnhi)
-        const uint32_t nnhi = (k + 2 < a.k1) ? __ldg(&a.level_off[k + 3]) : nhi;
-        DcRecord nnv{};
-        const bool has_nn = nhi + rank < nnhi;
-        if (has_nn) nnv = a.rec_dc[nhi + rank];
+        const uint32_t e4 = end_of(k + 4, e3);
+        DcRecord r3{};
+        if (e2 + rank < e3) r3 = a.rec_dc[e2 + rank];
+        const bool has2 = e1 + rank < e2;
         // the balance updates (the only cells a later level reads) before the
         // barrier's release; the history row and outputs after this thread has
         // arrived, overlapping the other threads' arrival
         DcOut o;
         bool pending = false;
-        if (lo + rank < hi) {
-            GlobalCells g;
-            pending = dc_state_core(a.db, a.b, v.a, v.tl, v.br, v.delta, v.ts, v.t, hb + lo + rank, a.atomic_add,
-                                    g, o);
-        }
-        for (uint32_t pos = lo + rank + nthreads; pos < hi; pos += nthreads)
-            exec_dc_record(a.db, a.b, a.rec_dc[pos], hb + pos, a.atomic_add);
+        if (lo + rank < e0) pending = dc_state_rmw(a.db, a.b, v, hb + lo + rank, o);
+        for (uint32_t pos = lo + rank + nthreads; pos < e0; pos += nthreads)
+            exec_dc_record(a.db, a.b, a.rec_dc[pos], hb + pos);
         if (CLUSTER) {
             // split cluster barrier: arrive with release semantics, do the
             // work no other thread waits for, then wait with acquire
             asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-            if (pending) dc_finish(a.db, a.b, o);
-            if (has_nn) {
-                prefetch_l2(&a.db.acc_bal[nnv.a]);
-                prefetch_l2(&a.db.tel_bal[nnv.tl]);
-                prefetch_l2(&a.db.br_bal[nnv.br]);
-            }
-            asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-        } else {
-            if (pending) dc_finish(a.db, a.b, o);
-            if (has_nn) {
-                prefetch_l2(&a.db.acc_bal[nnv.a]);
-                prefetch_l2(&a.db.tel_bal[nnv.tl]);
-                prefetch_l2(&a.db.br_bal[nnv.br]);
-            }
-            __syncthreads();
         }
-        lo = nlo;
-        hi = nhi;
-        nhi = nnhi;
-        v = nv;
-        nv = nnv;
+        if (pending) dc_finish(a.db, a.b, o);
+        if (has2) {
+            prefetch_l2(&a.db.acc_bal[r2.a]);
+            prefetch_l2(&a.db.tel_bal[r2.tl]);
+            prefetch_l2(&a.db.br_bal[r2.br]);
+        }
+        if (CLUSTER) asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+        else __syncthreads();
+        lo = e0;
+        e0 = e1;
+        e1 = e2;
+        e2 = e3;
+        e3 = e4;
+        v = r1;
+        r1 = r2;
+        r2 = r3;
     }
 }
 

@@ -461,13 +461,43 @@ __device__ __forceinline__ void exec_dc(const DevDB &db, const DevBulk &b, const
     if (dc_state(db, b, v, atomic_add, cells, o)) dc_finish(db, b, o);
 }
 
-// the same transaction from a packed record (teller and branch precomputed)
-__device__ __forceinline__ void exec_dc_record(const DevDB &db, const DevBulk &b, const DcRecord &r, int64_t slot,
-                                               bool atomic_add)
+// The state part of a transaction of one k-set, from a packed record (teller
+// and branch precomputed), as three read-modify-writes performed at L2: a
+// fetch-and-add on the account, whose returned old value gives the output,
+// and additions on teller and branch whose results nothing reads.  Within a
+// level no other transaction touches the account (Property 1 under either
+// conflict model: the account is a written object in both), and integer
+// additions to teller and branch commute, so this equals the read-add-write
+// of dc_state_core bit for bit.  No load precedes the updates: a level's
+// critical path loses the round trip of reading the balances.
+__device__ __forceinline__ bool dc_state_rmw(const DevDB &db, const DevBulk &b, const DcRecord &r, int64_t slot,
+                                             DcOut &o)
 {
-    GlobalCells g;
+    if (slot >= db.hist_cap) {              // history full: not executed
+        set_err(b.err, ERR_CAPACITY);
+        b.status[r.t] = 3;
+        return false;
+    }
+    const unsigned long long d = (unsigned long long)r.delta;
+    const int64_t old_a = (int64_t)atomicAdd((unsigned long long *)&db.acc_bal[r.a], d);
+    atomicAdd((unsigned long long *)&db.tel_bal[r.tl], d);
+    atomicAdd((unsigned long long *)&db.br_bal[r.br], d);
+    o.slot = slot;
+    o.ts = r.ts;
+    o.delta = r.delta;
+    o.na = wrap_add(old_a, r.delta);
+    o.a = r.a;
+    o.tl = r.tl;
+    o.br = r.br;
+    o.t = r.t;
+    return true;
+}
+
+// one whole transaction of a k-set from its packed record
+__device__ __forceinline__ void exec_dc_record(const DevDB &db, const DevBulk &b, const DcRecord &r, int64_t slot)
+{
     DcOut o;
-    if (dc_state_core(db, b, r.a, r.tl, r.br, r.delta, r.ts, r.t, slot, atomic_add, g, o)) dc_finish(db, b, o);
+    if (dc_state_rmw(db, b, r, slot, o)) dc_finish(db, b, o);
 }
 
 // subscriber-location procedures (stand-ins shaped like TM-1, Appendix E)

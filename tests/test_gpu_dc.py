@@ -311,7 +311,8 @@ def test_level_chain_probe():
     floor_min = G.gputx_probe_level_chain(2000, 16, 64, 1, 1)
     floor_dc = G.gputx_probe_level_chain(2000, 16, 64, 3, 10)
     floor_split = G.gputx_probe_level_chain(2000, 16, 64, 3, 3, 7)
-    for f in (floor_min, floor_dc, floor_split):
+    floor_rmw = G.gputx_probe_level_chain(2000, 16, 64, 0, 3, 7, rmw=1)
+    for f in (floor_min, floor_dc, floor_split, floor_rmw):
         assert 0 < f < 50_000
     assert floor_dc > 0.8 * floor_min
 
