@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgputx.so")
-SOURCES = ["api.cu", "analysis.cu", "exec.cu", "tables.cu", "serve.cu", "batch.cu", "pool.cu", "relaxed.cu", "probe.cu"]
+SOURCES = ["api.cu", "analysis.cu", "exec.cu", "exec_dc.cu", "tables.cu", "serve.cu", "batch.cu", "pool.cu", "relaxed.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

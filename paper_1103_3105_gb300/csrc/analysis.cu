@@ -521,12 +521,13 @@ __global__ void gather_dc_kernel(DevDB db, DevBulk b, const uint32_t *order, DcR
     rec[pos] = r;
 }
 
-__global__ void tpl_reset_kernel(const uint32_t *skeys, int64_t m, uint32_t *done, uint32_t n_objects)
+__global__ void tpl_reset_kernel(const uint32_t *skeys, int64_t m, uint32_t *done, uint32_t n_objects,
+                                 LockSlots slot)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= m) return;
     const uint32_t k = skeys[i];
-    if ((i == 0 || skeys[i - 1] != k) && k < n_objects) done[k] = 0;
+    if ((i == 0 || skeys[i - 1] != k) && k < n_objects) done[slot(k)] = 0;
 }
 
 template <class Mode>
@@ -1101,7 +1102,8 @@ cudaError_t launch_part_heads(gputx_bulk *b, const uint32_t *skeys, int64_t n)
 cudaError_t launch_tpl_reset(gputx_bulk *b, const uint32_t *skeys, int64_t m)
 {
     if (m == 0) return cudaSuccess;
-    tpl_reset_kernel<<<grid_for(m), TB, 0, b->stream>>>(skeys, m, b->db->d_done, b->db->dev.n_objects);
+    tpl_reset_kernel<<<grid_for(m), TB, 0, b->stream>>>(skeys, m, b->db->d_done, b->db->dev.n_objects,
+                                                        b->db->lock_slots);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -448,7 +448,11 @@ gputx_status gputx_create_db(const gputx_schema_desc *schema, const gputx_config
         TRY(alloc_hash(db, d.ord_idx, d.ord_cap, "order index"));
     }
     TRY(dalloc(db, &db->d_cursor, 1, "cursor"));
-    TRY(dalloc(db, &db->d_done, std::max<int64_t>(d.n_objects, 1), "lock counters"));
+    {
+        const uint32_t lines = (uint32_t)((std::max<int64_t>(d.n_objects, 1) + 31) / 32);
+        db->lock_slots.lines = FastDiv::make(lines);
+        TRY(dalloc(db, &db->d_done, (int64_t)lines * 32, "lock counters"));
+    }
 #undef TRY
     d.out_width = s.sub_subscribers > 0 ? 8 : s.oe_warehouses > 0 ? 4 : 1;
     if (cudaStreamSynchronize(db->stream) != cudaSuccess) {

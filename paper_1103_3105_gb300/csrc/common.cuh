@@ -173,4 +173,25 @@ __device__ __forceinline__ int64_t wrap_add(int64_t a, int64_t b)
 
 __device__ __forceinline__ void set_err(uint32_t *err, uint32_t bit) { atomicOr(err, bit); }
 
+// Where the counter (TPL) or lock (relaxed TPL) of item k lives: slot
+// (k mod L) * 32 + k / L of an array of 32 L words, a 32-column transposition
+// of the item order.  Consecutive items -- the branches of debit-credit, the
+// few hot items of a skewed bulk -- each get their own 128-byte line instead
+// of sharing one, so the waiters' polls spread over the L2 slices.
+struct LockSlots {
+    FastDiv lines;   // L
+    __device__ __forceinline__ uint32_t operator()(uint32_t k) const
+    {
+        const uint32_t q = lines.div(k);
+        return (k - q * lines.d) * 32u + q;
+    }
+};
+
+// L2 prefetch of a row a transaction will touch (a hint: it returns no data,
+// so it can run before the transaction is allowed to execute)
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 }  // namespace gtx

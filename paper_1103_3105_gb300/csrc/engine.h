@@ -74,6 +74,7 @@ struct gputx_db {
     std::vector<void *> allocs;
     gtx::InsertBase *d_cursor = nullptr;   // device insert cursors
     uint32_t *d_done = nullptr;            // TPL per-object counters, kept zero between bulks
+    gtx::LockSlots lock_slots{};           // item -> slot of d_done (32 x lines words)
     int kmax = 0;                          // largest op count of a registered type
     int uniform_k = 0;                     // every registered type has exactly this many ops (0 = no)
     bool need_fixpoint = false;            // a registered type's ops may leave one-pass ranks inexact

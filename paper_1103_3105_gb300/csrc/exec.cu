@@ -7,7 +7,8 @@
 //         narrow levels  one thread-block cluster (or one CTA) walks a run of
 //                        consecutive narrow levels, separated by cluster (or
 //                        CTA) barriers, loading the next level's signatures
-//                        and prefetching its rows into L2 before each barrier;
+//                        and prefetching its rows into L2 before each barrier
+//                        (debit-credit-only bulks: exec_dc.cu);
 //         persistent     a grid claims level-ordered chunks of one CTA; a
 //                        chunk of level k starts once every transaction of
 //                        level k-1 has finished (per-level counters).  Chunks
@@ -26,6 +27,7 @@
 #include <cooperative_groups.h>
 
 #include "engine.h"
+#include "levels.cuh"
 #include "procs.cuh"
 
 namespace cg = cooperative_groups;
@@ -68,16 +70,6 @@ __device__ __forceinline__ bool wait_at_least(const uint32_t *p, uint32_t need, 
     return true;
 }
 
-struct LevelArgs {
-    DevDB db;
-    DevBulk b;
-    const BulkCtl *ctl;
-    const uint32_t *level_off;
-    const DcRecord *rec_dc;   // debit-credit-only bulks: packed records in execution order
-    uint32_t k0, k1;     // levels [k0, k1)
-    bool atomic_add;
-};
-
 // a bulk known to hold no two conflicting transactions (a 0-set): every
 // transaction at once, straight from the bulk's signatures (timestamp order)
 __global__ void __launch_bounds__(256) independent_kernel(DevDB db, DevBulk b, const BulkCtl *ctl, bool atomic_add)
@@ -95,83 +87,8 @@ __global__ void __launch_bounds__(256) kset_level_kernel(LevelArgs a)
     const int64_t hb = a.ctl->base.hist;
     const uint32_t lo = __ldg(&a.level_off[a.k0]), hi = __ldg(&a.level_off[a.k0 + 1]);
     for (uint32_t pos = lo + blockIdx.x * blockDim.x + threadIdx.x; pos < hi; pos += gridDim.x * blockDim.x) {
-        if (a.rec_dc) exec_dc_record(a.db, a.b, a.rec_dc[pos], hb + pos);
+        if (a.rec_dc) exec_dc_record(a.db, a.b, a.rec_dc[pos], hb + pos, a.atomic_add);
         else exec_txn(a.db, a.b, view_at(a.b, pos, hb), a.atomic_add);
-    }
-}
-
-// the narrow-level runner for debit-credit-only bulks: one packed record per
-// transaction (no type dispatch, no divisions), its balances updated by
-// atomics at L2 (dc_state_rmw), so nothing is loaded between the barrier's
-// acquire and the updates.  The inputs of later levels run ahead in a
-// pipeline, each stage a whole level before its use: while level k executes,
-// level k+1's and k+2's records are in registers, level k+3's record is
-// loading and level k+4's end offset too; after the arrival, level k+2's
-// rows are prefetched into L2, so an account row coming from HBM has a whole
-// level to arrive before it is updated.
-template <bool CLUSTER, int MAXT>
-__global__ void __launch_bounds__(MAXT, 1) kset_narrow_dc_kernel(LevelArgs a)
-{
-    if (a.ctl->err) return;   // set by an earlier launch only: uniform here
-    const int64_t hb = a.ctl->base.hist;
-    uint32_t nthreads = blockDim.x, rank = threadIdx.x;
-    if (CLUSTER) {
-        cg::cluster_group cl = cg::this_cluster();
-        nthreads = cl.num_threads();
-        rank = cl.thread_rank();
-    }
-    // the end of level j (the start of level j+1); levels from k1 on are empty
-    auto end_of = [&](uint32_t j, uint32_t prev) { return j < a.k1 ? __ldg(&a.level_off[j + 1]) : prev; };
-    // level k is [lo, e0); levels k+1, k+2, k+3 end at e1, e2, e3
-    uint32_t lo = __ldg(&a.level_off[a.k0]);
-    uint32_t e0 = end_of(a.k0, lo);
-    uint32_t e1 = end_of(a.k0 + 1, e0);
-    uint32_t e2 = end_of(a.k0 + 2, e1);
-    uint32_t e3 = end_of(a.k0 + 3, e2);
-    DcRecord v{}, r1{}, r2{};
-    if (lo + rank < e0) {
-        v = a.rec_dc[lo + rank];
-        prefetch_l2(&a.db.acc_bal[v.a]);
-    }
-    if (e0 + rank < e1) {
-        r1 = a.rec_dc[e0 + rank];
-        prefetch_l2(&a.db.acc_bal[r1.a]);
-    }
-    if (e1 + rank < e2) r2 = a.rec_dc[e1 + rank];
-    for (uint32_t k = a.k0; k < a.k1; k++) {
-        const uint32_t e4 = end_of(k + 4, e3);
-        DcRecord r3{};
-        if (e2 + rank < e3) r3 = a.rec_dc[e2 + rank];
-        const bool has2 = e1 + rank < e2;
-        // the balance updates (the only cells a later level reads) before the
-        // barrier's release; the history row and outputs after this thread has
-        // arrived, overlapping the other threads' arrival
-        DcOut o;
-        bool pending = false;
-        if (lo + rank < e0) pending = dc_state_rmw(a.db, a.b, v, hb + lo + rank, o);
-        for (uint32_t pos = lo + rank + nthreads; pos < e0; pos += nthreads)
-            exec_dc_record(a.db, a.b, a.rec_dc[pos], hb + pos);
-        if (CLUSTER) {
-            // split cluster barrier: arrive with release semantics, do the
-            // work no other thread waits for, then wait with acquire
-            asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-        }
-        if (pending) dc_finish(a.db, a.b, o);
-        if (has2) {
-            prefetch_l2(&a.db.acc_bal[r2.a]);
-            prefetch_l2(&a.db.tel_bal[r2.tl]);
-            prefetch_l2(&a.db.br_bal[r2.br]);
-        }
-        if (CLUSTER) asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-        else __syncthreads();
-        lo = e0;
-        e0 = e1;
-        e1 = e2;
-        e2 = e3;
-        e3 = e4;
-        v = r1;
-        r1 = r2;
-        r2 = r3;
     }
 }
 
@@ -410,6 +327,7 @@ struct TplArgs {
     bool atomic_add;
     bool graph;          // fixed-capacity bulk: K slots per transaction, only the
                          // first op_count are real; padding transactions skipped
+    LockSlots slot;      // item -> its counter in `done`
 };
 
 __global__ void tpl_kernel(TplArgs a)
@@ -436,14 +354,14 @@ __global__ void tpl_kernel(TplArgs a)
             bool ok = true;
             for (int j = 0; j < cnt && ok; j++) {
                 const uint32_t tk = a.lock_ticket[off + j];
-                if (tk && !wait_at_least(&a.done[a.lock_key[off + j]], tk, a.spin_limit_ns, 250)) {
+                if (tk && !wait_at_least(&a.done[a.slot(a.lock_key[off + j])], tk, a.spin_limit_ns, 500)) {
                     set_err(&a.ctl->err, ERR_TIMEOUT);
                     ok = false;
                 }
             }
             if (ok) exec_txn(a.db, a.b, v, a.atomic_add);
-            __threadfence();
-            for (int j = 0; j < cnt; j++) red_release_add(&a.done[a.lock_key[off + j]], 1u);
+            // each release is a release: this transaction's writes before it
+            for (int j = 0; j < cnt; j++) red_release_add(&a.done[a.slot(a.lock_key[off + j])], 1u);
         }
         __syncthreads();
     }
@@ -531,8 +449,6 @@ cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, in
         cudaFuncSetAttribute(kset_narrow_kernel<true, 256>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         cudaFuncSetAttribute(kset_narrow_kernel<true, 512>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         cudaFuncSetAttribute(kset_narrow_kernel<true, 1024>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        cudaFuncSetAttribute(kset_narrow_dc_kernel<true, 256>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        cudaFuncSetAttribute(kset_narrow_dc_kernel<true, 1024>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         attr_set = true;
     }
     int64_t k = 0;
@@ -568,15 +484,13 @@ cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, in
         int threads = (int)((wmax + csize - 1) / csize);
         threads = ((threads + 31) / 32) * 32;
         threads = threads < 32 ? 32 : (threads > 1024 ? 1024 : threads);
-        if (csize <= 1) {
+        if (a.rec_dc) {
             // the records this bulk was gathered into decide the runner
-            if (a.rec_dc) {
-                if (threads <= 256) kset_narrow_dc_kernel<false, 256><<<1, threads, 0, b->stream>>>(a);
-                else kset_narrow_dc_kernel<false, 1024><<<1, threads, 0, b->stream>>>(a);
-            } else {
-                if (threads <= 256) kset_narrow_kernel<false, 256><<<1, threads, 0, b->stream>>>(a);
-                else kset_narrow_kernel<false, 1024><<<1, threads, 0, b->stream>>>(a);
-            }
+            cudaError_t e2 = launch_narrow_dc(a, csize, threads, b->stream);
+            if (e2) return e2;
+        } else if (csize <= 1) {
+            if (threads <= 256) kset_narrow_kernel<false, 256><<<1, threads, 0, b->stream>>>(a);
+            else kset_narrow_kernel<false, 1024><<<1, threads, 0, b->stream>>>(a);
         } else {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(csize, 1, 1);
@@ -591,14 +505,9 @@ cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, in
             cfg.numAttrs = 1;
             // up to 256 threads a CTA: more registers per thread for the
             // loads in flight
-            cudaError_t e2;
-            if (a.rec_dc)
-                e2 = threads <= 256 ? cudaLaunchKernelEx(&cfg, kset_narrow_dc_kernel<true, 256>, a)
-                                    : cudaLaunchKernelEx(&cfg, kset_narrow_dc_kernel<true, 1024>, a);
-            else
-                e2 = threads <= 256   ? cudaLaunchKernelEx(&cfg, kset_narrow_kernel<true, 256>, a)
-                     : threads <= 512 ? cudaLaunchKernelEx(&cfg, kset_narrow_kernel<true, 512>, a)
-                                      : cudaLaunchKernelEx(&cfg, kset_narrow_kernel<true, 1024>, a);
+            cudaError_t e2 = threads <= 256   ? cudaLaunchKernelEx(&cfg, kset_narrow_kernel<true, 256>, a)
+                             : threads <= 512 ? cudaLaunchKernelEx(&cfg, kset_narrow_kernel<true, 512>, a)
+                                              : cudaLaunchKernelEx(&cfg, kset_narrow_kernel<true, 1024>, a);
             if (e2) return e2;
         }
         count_launches(1);
@@ -675,6 +584,7 @@ cudaError_t launch_tpl(gputx_bulk *b, int block, bool atomic_add)
     a.atomic_add = atomic_add;
     cudaError_t e = cudaMemsetAsync(&b->ctl->claim, 0, sizeof(uint32_t), b->stream);
     if (e) return e;
+    a.slot = db->lock_slots;
     int64_t grid = (int64_t)db->num_sms * exec_blocks_per_sm(1, block);
     const int64_t chunks = (b->n + block - 1) / block;
     if (grid > chunks) grid = chunks;

@@ -13,6 +13,7 @@
 // never read are class ADD.
 #pragma once
 #include "common.cuh"
+#include "dc.cuh"
 
 namespace gtx {
 
@@ -241,15 +242,6 @@ __device__ __forceinline__ int64_t pack2(int32_t lo, int32_t hi)
     return (int64_t)((unsigned long long)(uint32_t)lo | ((unsigned long long)(uint32_t)hi << 32));
 }
 
-// ---------------------------------------------------------------------------
-// L2 prefetch of the rows a transaction will touch (a hint: it returns no
-// data, so it can run before the transaction is allowed to execute)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void prefetch_l2(const void *p)
-{
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
 // A transaction as the executors see it: its signature (from the bulk, or
 // from the records gathered into execution order) and where its results go.
 struct TxnView {
@@ -380,16 +372,6 @@ struct CachedCells {
     }
 };
 
-// A debit-credit transaction in two parts.  dc_state updates the three
-// balances -- the only cells later transactions of the bulk read -- and
-// returns what dc_finish writes: the history row and the outputs, which no
-// transaction of the bulk reads.  An executor may therefore publish the
-// state part (a barrier's release) before writing the rest.
-struct DcOut {
-    int64_t slot, ts, delta, na, a, tl, br;
-    uint32_t t;
-};
-
 // atomic_add: execute ADD-class increments with atomics (several
 // transactions of one level may add to one item).  False when the history
 // is full (the transaction is not executed; status 3).
@@ -442,17 +424,6 @@ __device__ __forceinline__ bool dc_state(const DevDB &db, const DevBulk &b, cons
                          v.hist_slot, atomic_add, cells, o);
 }
 
-__device__ __forceinline__ void dc_finish(const DevDB &db, const DevBulk &b, const DcOut &o)
-{
-    db.h_ts[o.slot] = o.ts;
-    db.h_acc[o.slot] = o.a;
-    db.h_tel[o.slot] = o.tl;
-    db.h_br[o.slot] = o.br;
-    db.h_delta[o.slot] = o.delta;
-    b.out[(int64_t)o.t * b.R] = o.na;
-    b.status[o.t] = 0;
-}
-
 template <class Cells>
 __device__ __forceinline__ void exec_dc(const DevDB &db, const DevBulk &b, const TxnView &v, bool atomic_add,
                                         Cells &cells)
@@ -461,43 +432,14 @@ __device__ __forceinline__ void exec_dc(const DevDB &db, const DevBulk &b, const
     if (dc_state(db, b, v, atomic_add, cells, o)) dc_finish(db, b, o);
 }
 
-// The state part of a transaction of one k-set, from a packed record (teller
-// and branch precomputed), as three read-modify-writes performed at L2: a
-// fetch-and-add on the account, whose returned old value gives the output,
-// and additions on teller and branch whose results nothing reads.  Within a
-// level no other transaction touches the account (Property 1 under either
-// conflict model: the account is a written object in both), and integer
-// additions to teller and branch commute, so this equals the read-add-write
-// of dc_state_core bit for bit.  No load precedes the updates: a level's
-// critical path loses the round trip of reading the balances.
-__device__ __forceinline__ bool dc_state_rmw(const DevDB &db, const DevBulk &b, const DcRecord &r, int64_t slot,
-                                             DcOut &o)
+// one whole transaction of a wide k-set from its packed record, reading its
+// balances then writing them (atomic_add: teller and branch by atomics)
+__device__ __forceinline__ void exec_dc_record(const DevDB &db, const DevBulk &b, const DcRecord &r, int64_t slot,
+                                               bool atomic_add)
 {
-    if (slot >= db.hist_cap) {              // history full: not executed
-        set_err(b.err, ERR_CAPACITY);
-        b.status[r.t] = 3;
-        return false;
-    }
-    const unsigned long long d = (unsigned long long)r.delta;
-    const int64_t old_a = (int64_t)atomicAdd((unsigned long long *)&db.acc_bal[r.a], d);
-    atomicAdd((unsigned long long *)&db.tel_bal[r.tl], d);
-    atomicAdd((unsigned long long *)&db.br_bal[r.br], d);
-    o.slot = slot;
-    o.ts = r.ts;
-    o.delta = r.delta;
-    o.na = wrap_add(old_a, r.delta);
-    o.a = r.a;
-    o.tl = r.tl;
-    o.br = r.br;
-    o.t = r.t;
-    return true;
-}
-
-// one whole transaction of a k-set from its packed record
-__device__ __forceinline__ void exec_dc_record(const DevDB &db, const DevBulk &b, const DcRecord &r, int64_t slot)
-{
+    GlobalCells g;
     DcOut o;
-    if (dc_state_rmw(db, b, r, slot, o)) dc_finish(db, b, o);
+    if (dc_state_core(db, b, r.a, r.tl, r.br, r.delta, r.ts, r.t, slot, atomic_add, g, o)) dc_finish(db, b, o);
 }
 
 // subscriber-location procedures (stand-ins shaped like TM-1, Appendix E)

@@ -22,21 +22,37 @@ struct TplRelaxedArgs {
     DevBulk b;
     BulkCtl *ctl;
     uint32_t *lock;      // one word per item, 0 = free (zero between bulks)
+    LockSlots slot;      // item -> its word of `lock`
     uint32_t *order;     // order[ticket] = transaction
     int mode;
     uint64_t spin_limit_ns;
     bool atomic_add;
 };
 
+// compare-and-swap 0 -> 1 with acquire semantics: a holder sees every write
+// its predecessors made before their release
+__device__ __forceinline__ bool try_lock(uint32_t *l)
+{
+    uint32_t old;
+    asm volatile("atom.acquire.gpu.global.cas.b32 %0, [%1], 0, 1;" : "=r"(old) : "l"(l) : "memory");
+    return old == 0u;
+}
+
+// the release: this transaction's writes before the lock reads free
+__device__ __forceinline__ void unlock(uint32_t *l)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], 0;" ::"l"(l) : "memory");
+}
+
 __device__ __forceinline__ bool spin_lock(uint32_t *l, uint64_t limit_ns)
 {
-    if (atomicCAS(l, 0u, 1u) == 0u) return true;
+    if (try_lock(l)) return true;
     const uint64_t t0 = globaltimer();
     uint32_t ns = 32;
     while (true) {
         __nanosleep(ns);
         if (ns < 1024) ns <<= 1;
-        if (atomicCAS(l, 0u, 1u) == 0u) return true;
+        if (try_lock(l)) return true;
         if (globaltimer() - t0 > limit_ns) return false;
     }
 }
@@ -65,18 +81,16 @@ __global__ void tpl_relaxed_kernel(TplRelaxedArgs a)
         int held = 0;
         bool ok = true;
         for (; held < m; held++)
-            if (!spin_lock(&a.lock[items[held]], a.spin_limit_ns)) {
+            if (!spin_lock(&a.lock[a.slot(items[held])], a.spin_limit_ns)) {
                 set_err(&a.ctl->err, ERR_TIMEOUT);
                 ok = false;
                 break;
             }
         if (ok) {
-            __threadfence();   // see the writes of the previous holders
             exec_txn(a.db, a.b, v, a.atomic_add);
             a.order[atomicAdd(&a.ctl->claim, 1u)] = (uint32_t)t;
-            __threadfence();   // this transaction's writes before the unlocks
         }
-        for (int j = 0; j < held; j++) atomicExch(&a.lock[items[j]], 0u);
+        for (int j = 0; j < held; j++) unlock(&a.lock[a.slot(items[j])]);
     }
 }
 
@@ -91,6 +105,7 @@ cudaError_t launch_tpl_relaxed(gputx_bulk *b, uint32_t *order, bool atomic_add)
     a.b = make_dev_bulk(b, atomic_add ? GPUTX_CONFLICT_ADD : GPUTX_CONFLICT_PAPER);
     a.ctl = b->ctl;
     a.lock = db->d_done;
+    a.slot = db->lock_slots;
     a.order = order;
     a.mode = atomic_add ? GPUTX_CONFLICT_ADD : GPUTX_CONFLICT_PAPER;
     a.spin_limit_ns = (uint64_t)db->cfg.spin_limit_ns;
