@@ -56,7 +56,7 @@ DOMINANT_KERNEL = {("kset", "paper"): "kset_narrow_dc_kernel", ("kset", "add"): 
 # kernel at this configuration, keyed by (strategy, mode, bulk log2); each
 # entry holds the digest of the kernel sources it was taken on, and is
 # reported as null once those sources change
-TRAFFIC = {("kset", "paper", 22): {"bytes": 340934144 + 293626624, "digest": "2276acfcfbe1e0a5"}}
+TRAFFIC = {("kset", "paper", 22): {"bytes": 341851136 + 293794048, "digest": "219a2a8a798209ab"}}
 KERNEL_SOURCES = ("common.cuh", "fastdiv.h", "engine.h", "dc.cuh", "levels.cuh", "exec_dc.cu")
 
 
@@ -297,6 +297,20 @@ def run_engine(args, rank, world, local_rank):
                    "probe": "cluster 16 x 64 threads; per thread and level 3 fetch-and-adds on cells another "
                             "CTA updated at the previous level, one line each, barrier arrive (release), "
                             "7 stores, barrier wait (acquire); best of 3 launches"}
+    # L2 atomic throughput (random cells of a 10M-cell table, the 10,000
+    # tellers, the 1,000 branches), beside the atomics the executor issues
+    atomics = None
+    if args.strategy in ("kset", "tpl") and stats:
+        atomics = {f"{kind}_{name}_gops": G.gputx_probe_atomics(cells, fetch)
+                   for name, cells in (("accounts", ACCOUNTS), ("tellers", TELLERS), ("branches", BRANCHES))
+                   for kind, fetch in (("red", 0), ("fetch_add", 1))}
+        # K-SET R/W: fetch-and-add + 2 reductions (narrow runner); K-SET ADD:
+        # teller and branch reductions; TPL: one counter release per lock
+        # (the branch, or the account under ADD) + the 2 reductions under ADD
+        per_txn = {("kset", "paper"): 3, ("kset", "add"): 2, ("tpl", "paper"): 1,
+                   ("tpl", "add"): 3}[(args.strategy, args.mode)]
+        atomics["executor_gops"] = n * per_txn / (ex / 1e3) / 1e9
+        atomics["executor_atomics_per_txn"] = per_txn
     achieved = n * EXEC_BYTES_PER_TXN / (ex / 1e3) / 1e9
     line = {
         "metric": METRIC,
@@ -329,6 +343,7 @@ def run_engine(args, rank, world, local_rank):
                      "levels": stats["depth"] + 1 if stats else None,
                      "ns_per_level": ex * 1e6 / (stats["depth"] + 1) if stats else None},
         "latency_roofline": latency,
+        "atomics": atomics,
         "phases_ms": {"execute": ex, "op_sort": statistics.median(sort_ms),
                       "analysis": stats["ms_analysis"] if stats else None},
         "graph": {"depth": stats["depth"], "w0": stats["w0"], "cross": stats["cross"]} if stats else None,

@@ -455,6 +455,18 @@ void gputx_server_destroy(gputx_server *s);
 gputx_status gputx_probe_level_chain(int levels, int cluster_size, int threads, int loads, int stores,
                                      int stores_after, int rmw, double *ns_per_level);
 
+/* Throughput of 64-bit atomic additions performed at L2, the operation TPL's
+ * counters, the ADD class's blind increments (Section 5.1's workload under
+ * the blind-increment refinement) and the debit-credit level runners rely on.
+ * A grid of (SMs x 8) CTAs of 256 threads each adds 1 to 64 cells drawn
+ * uniformly from a table of n_cells (1 .. 2^32) 8-byte cells: reductions
+ * (fetch = 0) or fetch-and-adds whose results are used (fetch = 1).  The
+ * table is zeroed and touched by one warm-up launch, so a table that fits in
+ * L2 is L2-resident.  *gops = atomic operations per nanosecond (G/s) of one
+ * timed launch.  Allocates and frees n_cells x 8 bytes.  EINVAL on a
+ * parameter out of range, ENOMEM, ECUDA. */
+gputx_status gputx_probe_atomics(int64_t n_cells, int fetch, double *gops);
+
 /* ---------------------------------------------------------------------------
  * Incremental 0-set execution (Section 5.3).  A device-resident pool of
  * pending transactions keeps their basic operations sorted by item.  New

@@ -50,7 +50,8 @@ EXPORTED = ("gputx_create_db", "gputx_destroy_db", "gputx_last_error", "gputx_re
             "gputx_server_last_error", "gputx_server_destroy", "gputx_batcher_create",
             "gputx_batcher_run", "gputx_batcher_choice", "gputx_batcher_destroy",
             "gputx_pool_create", "gputx_pool_add", "gputx_pool_step", "gputx_pool_results",
-            "gputx_pool_pending", "gputx_pool_destroy", "gputx_bulk_order", "gputx_probe_level_chain")
+            "gputx_pool_pending", "gputx_pool_destroy", "gputx_bulk_order", "gputx_probe_level_chain",
+            "gputx_probe_atomics")
 
 
 class GputxError(RuntimeError):
@@ -159,6 +160,7 @@ def lib():
             "gputx_bulk_order": ([p, p, sz], C.c_int),
             "gputx_probe_level_chain": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                          C.POINTER(C.c_double)], C.c_int),
+            "gputx_probe_atomics": ([C.c_int64, C.c_int, C.POINTER(C.c_double)], C.c_int),
             "gputx_output_width": ([p], C.c_int),
             "gputx_free_bulk": ([p], None),
             "gputx_version": ([], C.c_char_p),
@@ -285,6 +287,16 @@ def gputx_probe_level_chain(levels: int, cluster_size: int, threads: int, loads:
     if st != OK:
         raise GputxError(st, "probe_level_chain")
     return ns.value
+
+
+def gputx_probe_atomics(n_cells: int, fetch: int = 0) -> float:
+    """G atomic 64-bit additions per second on random cells of a table of
+    n_cells (see gputx.h)."""
+    g = C.c_double()
+    st = lib().gputx_probe_atomics(n_cells, fetch, C.byref(g))
+    if st != OK:
+        raise GputxError(st, "probe_atomics")
+    return g.value
 
 
 def gputx_bulk_order(db, bulk, n: int) -> np.ndarray:

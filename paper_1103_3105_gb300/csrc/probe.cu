@@ -64,10 +64,72 @@ __global__ void __launch_bounds__(1024, 1) probe_chain_kernel(int64_t *buf, int6
     sink[r] = acc;   // keeps the chain live
 }
 
+// the throughput of 64-bit atomic additions performed at L2: every thread
+// adds 1 to `ops` cells drawn uniformly from [0, n_cells) (SplitMix64 on a
+// per-thread counter), as reductions (fetch = 0) or as fetch-and-adds whose
+// results are summed (fetch = 1)
+__global__ void __launch_bounds__(256) probe_atomics_kernel(unsigned long long *cells, uint64_t n_cells, int ops,
+                                                            int fetch, uint64_t seed, unsigned long long *sink)
+{
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    unsigned long long acc = 0;
+    for (int i = 0; i < ops; i++) {
+        uint64_t z = seed + (tid * (uint64_t)ops + (uint64_t)i + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const uint64_t idx = __umul64hi(z, n_cells);
+        if (fetch) acc += atomicAdd(&cells[idx], 1ull);
+        else atomicAdd(&cells[idx], 1ull);
+    }
+    if (fetch && acc == 0x5a5a5a5a5a5a5a5aull) sink[0] = acc;   // keeps the results live
+}
+
 }  // namespace
 }  // namespace gtx
 
 using namespace gtx;
+
+extern "C" gputx_status gputx_probe_atomics(int64_t n_cells, int fetch, double *gops)
+{
+    if (!gops || n_cells < 1 || n_cells > (int64_t)1 << 32 || (fetch != 0 && fetch != 1)) return GPUTX_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) return GPUTX_ECUDA;
+    const int threads = 256, ops = 64;
+    const int64_t grid = (int64_t)sms * 8;
+    const double total = (double)grid * threads * ops;
+    unsigned long long *cells = nullptr, *sink = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    gputx_status st = GPUTX_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (!e) e = cudaMalloc(&cells, n_cells * sizeof(unsigned long long));
+    if (!e) e = cudaMalloc(&sink, sizeof(unsigned long long));
+    if (!e) e = cudaMemsetAsync(cells, 0, n_cells * sizeof(unsigned long long), s);
+    if (!e) e = cudaEventCreate(&e0);
+    if (!e) e = cudaEventCreate(&e1);
+    if (!e) {
+        // one warm-up launch (brings a table that fits into L2), then the timed one
+        probe_atomics_kernel<<<(unsigned)grid, threads, 0, s>>>(cells, (uint64_t)n_cells, ops, fetch, 1, sink);
+        e = cudaGetLastError();
+        if (!e) e = cudaEventRecord(e0, s);
+        if (!e) probe_atomics_kernel<<<(unsigned)grid, threads, 0, s>>>(cells, (uint64_t)n_cells, ops, fetch, 2, sink);
+        if (!e) e = cudaGetLastError();
+        if (!e) e = cudaEventRecord(e1, s);
+        if (!e) e = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (!e) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (!e) *gops = total / ((double)ms * 1e6);
+        count_launches(2);
+    }
+    if (e) st = e == cudaErrorMemoryAllocation ? GPUTX_ENOMEM : GPUTX_ECUDA;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (cells) cudaFree(cells);
+    if (sink) cudaFree(sink);
+    if (s) cudaStreamDestroy(s);
+    return st;
+}
 
 extern "C" gputx_status gputx_probe_level_chain(int levels, int cluster_size, int threads, int loads, int stores,
                                                 int stores_after, int rmw, double *ns_per_level)

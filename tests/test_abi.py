@@ -66,3 +66,7 @@ def test_probe_rejects_bad_shapes_without_a_gpu():
         with pytest.raises(G.GputxError) as e:
             G.gputx_probe_level_chain(*args)
         assert e.value.status == G.EINVAL
+    for args in [(0, 0), (-5, 1), ((1 << 32) + 1, 0), (1000, 2), (1000, -1)]:
+        with pytest.raises(G.GputxError) as e:
+            G.gputx_probe_atomics(*args)
+        assert e.value.status == G.EINVAL

@@ -317,6 +317,18 @@ def test_level_chain_probe():
     assert floor_dc > 0.8 * floor_min
 
 
+def test_atomics_probe():
+    """L2 atomic throughput: positive and finite for a hot table (1,000 cells)
+    and a large one, reductions and fetch-and-adds; spreading the additions
+    over many cells is never slower than piling them on one."""
+    rates = {}
+    for cells in (1, 1000, 10_000_000):
+        for fetch in (0, 1):
+            rates[(cells, fetch)] = G.gputx_probe_atomics(cells, fetch)
+            assert 0 < rates[(cells, fetch)] < 1e4, (cells, fetch)
+    assert rates[(1000, 0)] > rates[(1, 0)]
+
+
 @pytest.mark.parametrize("strategy", STRATS + ["auto", "part_relaxed", "tpl_relaxed"])
 def test_bulk_of_exactly_max_bulk(strategy):
     """A bulk filling max_bulk exactly (every per-bulk scratch array at its
