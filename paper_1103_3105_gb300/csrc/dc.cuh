@@ -1,7 +1,7 @@
 // dc.cuh -- the debit-credit procedure's parts shared by every executor
 // that runs it from packed records (Section 5.1's debit-credit workload):
 // what a transaction writes once its balances are updated, and the balance
-// update of a level's transaction as atomics performed at L2.
+// updates of a level's transaction as atomics performed at L2.
 #pragma once
 #include "common.cuh"
 
@@ -28,27 +28,33 @@ __device__ __forceinline__ void dc_finish(const DevDB &db, const DevBulk &b, con
     b.status[o.t] = 0;
 }
 
-// The state part of a transaction of one k-set, from a packed record (teller
-// and branch precomputed), as three read-modify-writes performed at L2: a
-// fetch-and-add on the account, whose returned old value gives the output,
-// and additions on teller and branch whose results nothing reads.  Within a
-// level no other transaction touches the account (Property 1 under either
-// conflict model: the account is a written object in both), and integer
-// additions to teller and branch commute, so this equals the read-add-write
-// of dc_state_core bit for bit.  No load precedes the updates: a level's
-// critical path loses the round trip of reading the balances.
-__device__ __forceinline__ bool dc_state_rmw(const DevDB &db, const DevBulk &b, const DcRecord &r, int64_t slot,
-                                             DcOut &o)
+// A transaction of one k-set from a packed record (teller and branch
+// precomputed), with its balance updates as atomics performed at L2 and split
+// by what a later level of the bulk depends on.
+//
+// dc_account_rmw: the fetch-and-add on the account, whose returned old value
+// gives the output.  Within a level no other transaction touches the account
+// (Property 1 under either conflict model: the account is a written object in
+// both), so this equals the read-add-write bit for bit; a later level's
+// transaction on the same account must see it, so it precedes the level
+// barrier's release.  No load precedes it: a level's critical path loses the
+// round trip of reading the balance.
+//
+// dc_finish_rmw: the additions to teller and branch, the history row and the
+// outputs.  No transaction of the bulk reads teller or branch balances or the
+// history, and integer additions commute, so these may complete in any order
+// before the launch ends: they follow the release, off the level's critical
+// path.  False from dc_account_rmw when the history is full (status 3, the
+// transaction is not executed).
+__device__ __forceinline__ bool dc_account_rmw(const DevDB &db, const DevBulk &b, const DcRecord &r, int64_t slot,
+                                               DcOut &o)
 {
     if (slot >= db.hist_cap) {              // history full: not executed
         set_err(b.err, ERR_CAPACITY);
         b.status[r.t] = 3;
         return false;
     }
-    const unsigned long long d = (unsigned long long)r.delta;
-    const int64_t old_a = (int64_t)atomicAdd((unsigned long long *)&db.acc_bal[r.a], d);
-    atomicAdd((unsigned long long *)&db.tel_bal[r.tl], d);
-    atomicAdd((unsigned long long *)&db.br_bal[r.br], d);
+    const int64_t old_a = (int64_t)atomicAdd((unsigned long long *)&db.acc_bal[r.a], (unsigned long long)r.delta);
     o.slot = slot;
     o.ts = r.ts;
     o.delta = r.delta;
@@ -60,11 +66,18 @@ __device__ __forceinline__ bool dc_state_rmw(const DevDB &db, const DevBulk &b, 
     return true;
 }
 
+__device__ __forceinline__ void dc_finish_rmw(const DevDB &db, const DevBulk &b, const DcOut &o)
+{
+    atomicAdd((unsigned long long *)&db.tel_bal[o.tl], (unsigned long long)o.delta);
+    atomicAdd((unsigned long long *)&db.br_bal[o.br], (unsigned long long)o.delta);
+    dc_finish(db, b, o);
+}
+
 // one whole transaction of a k-set from its packed record, by atomics
 __device__ __forceinline__ void exec_dc_record_rmw(const DevDB &db, const DevBulk &b, const DcRecord &r, int64_t slot)
 {
     DcOut o;
-    if (dc_state_rmw(db, b, r, slot, o)) dc_finish(db, b, o);
+    if (dc_account_rmw(db, b, r, slot, o)) dc_finish_rmw(db, b, o);
 }
 
 }  // namespace gtx

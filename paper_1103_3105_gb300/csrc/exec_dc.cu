@@ -20,8 +20,10 @@ namespace {
 
 // the narrow-level runner for debit-credit-only bulks: one packed record per
 // transaction (no type dispatch, no divisions), its balances updated by
-// atomics at L2 (dc_state_rmw), so nothing is loaded between the barrier's
-// acquire and the updates.  The inputs of later levels run ahead in a
+// atomics at L2, so nothing is loaded between the barrier's acquire and the
+// updates.  Only the account's fetch-and-add precedes the barrier's release
+// (dc_account_rmw); teller and branch additions, history row and outputs
+// follow it (dc_finish_rmw).  The inputs of later levels run ahead in a
 // pipeline, each stage a whole level before its use: while level k executes,
 // level k+1's and k+2's records are in registers, level k+3's record is
 // loading and level k+4's end offset too; after the arrival, level k+2's
@@ -61,12 +63,12 @@ __global__ void __launch_bounds__(MAXT, 1) kset_narrow_dc_kernel(LevelArgs a)
         DcRecord r3{};
         if (e2 + rank < e3) r3 = a.rec_dc[e2 + rank];
         const bool has2 = e1 + rank < e2;
-        // the balance updates (the only cells a later level reads) before the
-        // barrier's release; the history row and outputs after this thread has
-        // arrived, overlapping the other threads' arrival
+        // the account update (the only cell a later level reads) before the
+        // barrier's release; the rest after this thread has arrived,
+        // overlapping the other threads' arrival
         DcOut o;
         bool pending = false;
-        if (lo + rank < e0) pending = dc_state_rmw(a.db, a.b, v, hb + lo + rank, o);
+        if (lo + rank < e0) pending = dc_account_rmw(a.db, a.b, v, hb + lo + rank, o);
         for (uint32_t pos = lo + rank + nthreads; pos < e0; pos += nthreads)
             exec_dc_record_rmw(a.db, a.b, a.rec_dc[pos], hb + pos);
         if (CLUSTER) {
@@ -74,7 +76,7 @@ __global__ void __launch_bounds__(MAXT, 1) kset_narrow_dc_kernel(LevelArgs a)
             // work no other thread waits for, then wait with acquire
             asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
         }
-        if (pending) dc_finish(a.db, a.b, o);
+        if (pending) dc_finish_rmw(a.db, a.b, o);
         if (has2) {
             prefetch_l2(&a.db.acc_bal[r2.a]);
             prefetch_l2(&a.db.tel_bal[r2.tl]);
