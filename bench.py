@@ -50,7 +50,7 @@ DOMINANT_KERNEL = {("kset", "paper"): "kset_narrow_dc_kernel", ("kset", "add"): 
                    ("part_relaxed", "paper"): "part_dc_kernel", ("tpl_relaxed", "paper"): "tpl_relaxed_kernel",
                    ("tpl_relaxed", "add"): "tpl_relaxed_kernel",
                    ("part", "paper"): "part_dc_kernel", ("part", "add"): "part_dc_kernel",
-                   ("tpl", "paper"): "tpl_kernel", ("tpl", "add"): "tpl_kernel",
+                   ("tpl", "paper"): "tpl_dc_kernel", ("tpl", "add"): "tpl_dc_kernel",
                    ("scan", "paper"): "seg64_scan_kernel", ("scan", "add"): "seg64_scan_kernel"}
 # DRAM bytes (read + write) per launch from one ncu capture of the dominant
 # kernel at this configuration, keyed by (strategy, mode, bulk log2); each

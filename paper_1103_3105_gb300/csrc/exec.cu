@@ -367,6 +367,51 @@ __global__ void tpl_kernel(TplArgs a)
     }
 }
 
+// TPL for debit-credit-only bulks.  A transaction's one lock is its root
+// key's counter (the branch under R/W, the account under ADD).  Once it is
+// granted, the account takes a fetch-and-add at L2 (dc_account_rmw: its old
+// value gives the output) and the lock is released; the teller and branch
+// additions, the history row and the outputs follow the release.  No
+// transaction of the bulk reads a teller or branch balance or the history,
+// and integer additions commute, so the next holder may run before those
+// land: the hand-off waits for one atomic round trip instead of a load, the
+// stores and their acknowledgement.
+__global__ void tpl_dc_kernel(TplArgs a)
+{
+    __shared__ uint32_t s_c, s_stop;
+    const int64_t n = a.b.n;
+    const int64_t hb = a.ctl->base.hist;
+    while (true) {
+        if (threadIdx.x == 0) {
+            s_stop = *(volatile uint32_t *)&a.ctl->err ? 1u : 0u;
+            s_c = atomicAdd(&a.ctl->claim, 1u);
+        }
+        __syncthreads();
+        const int64_t start = (int64_t)s_c * blockDim.x;
+        if (s_stop || start >= n) break;
+        const int64_t t = start + threadIdx.x;
+        if (t < n) {
+            DcRecord r;
+            r.a = (uint32_t)__ldg(&a.b.params[t * a.b.P]);
+            r.delta = __ldg(&a.b.params[t * a.b.P + 1]);
+            r.ts = __ldg(&a.b.ts[t]);
+            r.t = (uint32_t)t;
+            r.tl = a.db.div_tel.div(r.a);
+            r.br = a.db.div_br.div(r.a);
+            prefetch_l2(&a.db.acc_bal[r.a]);
+            const uint32_t key = a.slot(a.lock_key[t]);
+            const uint32_t tk = a.lock_ticket[t];
+            const bool ok = !tk || wait_at_least(&a.done[key], tk, a.spin_limit_ns, 500);
+            if (!ok) set_err(&a.ctl->err, ERR_TIMEOUT);
+            DcOut o;
+            const bool pending = ok && dc_account_rmw(a.db, a.b, r, hb + t, o);
+            red_release_add(&a.done[key], 1u);
+            if (pending) dc_finish_rmw(a.db, a.b, o);
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 // clusters of this size that fit the device at once (0 = none)
@@ -588,7 +633,11 @@ cudaError_t launch_tpl(gputx_bulk *b, int block, bool atomic_add)
     int64_t grid = (int64_t)db->num_sms * exec_blocks_per_sm(1, block);
     const int64_t chunks = (b->n + block - 1) / block;
     if (grid > chunks) grid = chunks;
-    tpl_kernel<<<(unsigned)grid, block, 0, b->stream>>>(a);
+    // debit-credit-only bulks of single-lock transactions
+    if (db->dev.registered == (1u << GPUTX_T_DC_DEBIT_CREDIT) && !b->graph && db->uniform_k == 1)
+        tpl_dc_kernel<<<(unsigned)grid, block, 0, b->stream>>>(a);
+    else
+        tpl_kernel<<<(unsigned)grid, block, 0, b->stream>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
