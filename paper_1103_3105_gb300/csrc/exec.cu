@@ -414,6 +414,47 @@ __global__ void tpl_dc_kernel(TplArgs a)
 
 }  // namespace
 
+// size class of the launch shape a level of width w needs: threads in
+// powers of two from 32 (class 0) up
+static int width_class(uint32_t w)
+{
+    int c = 0;
+    while (c < 16 && (32u << c) < w) c++;
+    return c;
+}
+
+// The end of the segment of narrow levels that starts at k within the run
+// [k, run_end).  One launch executes a segment in the shape its widest level
+// needs, so a long tail of narrow levels (a skewed bulk's hot chain) must not
+// share a launch with a few wide ones: the segment is cut where the width
+// class rises, or where a stretch of at least kMinSegment levels of a smaller
+// class begins.  Shorter stretches stay in the segment, so every launch but a
+// run's last covers at least kMinSegment levels and the launch overhead stays
+// small against the levels' own latency.
+static int64_t narrow_segment_end(const uint32_t *level_off_host, int64_t k, int64_t run_end)
+{
+    constexpr int64_t kMinSegment = 64;
+    auto cls = [&](int64_t j) { return width_class(level_off_host[j + 1] - level_off_host[j]); };
+    int cmax = cls(k);
+    int64_t j = k + 1;
+    while (j < run_end) {
+        const int c = cls(j);
+        if (c > cmax) {
+            if (j - k >= kMinSegment) break;
+            cmax = c;
+            j++;
+        } else if (c < cmax) {
+            int64_t r = j;
+            while (r < run_end && r - j < kMinSegment && cls(r) < cmax) r++;
+            if (r - j >= kMinSegment) break;
+            j = r;
+        } else {
+            j++;
+        }
+    }
+    return j;
+}
+
 // clusters of this size that fit the device at once (0 = none)
 int max_cluster_ok(int csize)
 {
@@ -510,14 +551,16 @@ cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, in
             k++;
             continue;
         }
-        // maximal run of narrow levels
-        int64_t e = k;
+        // a run of narrow levels, cut where a long stretch of levels needs a
+        // launch shape of another size class (see narrow_segment_end)
+        int64_t run_end = k;
+        while (run_end < levels && (int64_t)(level_off_host[run_end + 1] - level_off_host[run_end]) <= narrow_max)
+            run_end++;
+        const int64_t e = narrow_segment_end(level_off_host, k, run_end);
         uint32_t wmax = 0;
-        while (e < levels) {
-            const uint32_t we = level_off_host[e + 1] - level_off_host[e];
-            if ((int64_t)we > narrow_max) break;
-            wmax = we > wmax ? we : wmax;
-            e++;
+        for (int64_t j = k; j < e; j++) {
+            const uint32_t wj = level_off_host[j + 1] - level_off_host[j];
+            wmax = wj > wmax ? wj : wmax;
         }
         a.k0 = (uint32_t)k;
         a.k1 = (uint32_t)e;
