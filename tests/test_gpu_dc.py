@@ -279,6 +279,23 @@ def test_scan_history_full_writes_nothing():
     g.close()
 
 
+@pytest.mark.parametrize("strategy", ["kset", "part", "tpl", "part_relaxed", "tpl_relaxed"])
+@pytest.mark.parametrize("mode", [G.CONFLICT_PAPER, G.CONFLICT_ADD])
+def test_history_full_is_an_error(strategy, mode):
+    """A bulk whose history rows overflow the table fails with ECAPACITY on
+    every executor (the debit-credit level runners, the TPL kernel for
+    debit-credit bulks, PART); no wait hangs on a transaction that was not
+    executed."""
+    g = G.Database(dc=(4, 40, 4000), history_capacity=150, max_bulk=1 << 10)
+    g.register(G.DC_TYPES)
+    b = g.submit_dict(W.dc_bulk(400, 4000, 0.5, seed=8)).execute(strategy, conflict_mode=mode)
+    with pytest.raises(G.GputxError) as e:
+        b.sync()
+    assert e.value.status == G.ECAPACITY
+    b.free()
+    g.close()
+
+
 def test_scan_needs_debit_credit_only():
     g = G.Database(dc=(4, 40, 4000), sub=100, history_capacity=1024, sub_child_capacity=1024, max_bulk=1024)
     g.register(G.DC_TYPES + G.SUB_TYPES)
