@@ -52,12 +52,13 @@ DOMINANT_KERNEL = {("kset", "paper"): "kset_narrow_dc_kernel", ("kset", "add"): 
                    ("part", "paper"): "part_dc_kernel", ("part", "add"): "part_dc_kernel",
                    ("tpl", "paper"): "tpl_dc_kernel", ("tpl", "add"): "tpl_dc_kernel",
                    ("scan", "paper"): "seg64_scan_kernel", ("scan", "add"): "seg64_scan_kernel"}
-# DRAM bytes (read + write) per launch from one ncu capture of the dominant
-# kernel at this configuration, keyed by (strategy, mode, bulk log2); each
-# entry holds the digest of the kernel sources it was taken on, and is
-# reported as null once those sources change
-TRAFFIC = {("kset", "paper", 22): {"bytes": 341851136 + 293794048, "digest": "219a2a8a798209ab"}}
-KERNEL_SOURCES = ("common.cuh", "fastdiv.h", "engine.h", "dc.cuh", "levels.cuh", "exec_dc.cu")
+# DRAM bytes (read + write) of the dominant kernel's launches for one bulk
+# (the narrow runner's segments: the main run and the narrow tail) from one
+# ncu capture at this configuration, keyed by (strategy, mode, bulk log2);
+# each entry holds the digest of the kernel and launch-planner sources it was
+# taken on, and is reported as null once those sources change
+TRAFFIC = {("kset", "paper", 22): {"bytes": 341222400 + 291092992, "digest": "57b4d8f06f9dff4e"}}
+KERNEL_SOURCES = ("common.cuh", "fastdiv.h", "engine.h", "dc.cuh", "levels.cuh", "exec_dc.cu", "exec.cu")
 
 
 def kernel_digest():

@@ -414,12 +414,16 @@ __global__ void tpl_dc_kernel(TplArgs a)
 
 }  // namespace
 
-// size class of the launch shape a level of width w needs: threads in
-// powers of two from 32 (class 0) up
+// size class of the launch shape a level of width w needs.  Class 0: one
+// CTA of up to 64 threads (a CTA barrier).  Class 1: a cluster of up to
+// 16 x 64 threads, whose level costs about what one CTA's does.  Classes 2,
+// 3, 4: 16 CTAs of 128, 256, 512 threads, each class markedly dearer per
+// level than the one below.
 static int width_class(uint32_t w)
 {
-    int c = 0;
-    while (c < 16 && (32u << c) < w) c++;
+    if (w <= 64) return 0;
+    int c = 1;
+    while (c < 16 && (1024u << (c - 1)) < w) c++;
     return c;
 }
 
