@@ -102,11 +102,13 @@ cudaError_t launch_narrow_dc(const LevelArgs &a, int csize, int threads, cudaStr
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(kset_narrow_dc_kernel<true, 256>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(kset_narrow_dc_kernel<true, 512>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         cudaFuncSetAttribute(kset_narrow_dc_kernel<true, 1024>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         attr_set = true;
     }
     if (csize <= 1) {
         if (threads <= 256) kset_narrow_dc_kernel<false, 256><<<1, threads, 0, s>>>(a);
+        else if (threads <= 512) kset_narrow_dc_kernel<false, 512><<<1, threads, 0, s>>>(a);
         else kset_narrow_dc_kernel<false, 1024><<<1, threads, 0, s>>>(a);
         return cudaGetLastError();
     }
@@ -121,9 +123,11 @@ cudaError_t launch_narrow_dc(const LevelArgs &a, int csize, int threads, cudaStr
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    // up to 256 threads a CTA: registers for the records in flight
-    return threads <= 256 ? cudaLaunchKernelEx(&cfg, kset_narrow_dc_kernel<true, 256>, a)
-                          : cudaLaunchKernelEx(&cfg, kset_narrow_dc_kernel<true, 1024>, a);
+    // the register budget follows the CTA size: the records in flight need
+    // more than the 64 a thread of a 1024-thread CTA may hold
+    return threads <= 256   ? cudaLaunchKernelEx(&cfg, kset_narrow_dc_kernel<true, 256>, a)
+           : threads <= 512 ? cudaLaunchKernelEx(&cfg, kset_narrow_dc_kernel<true, 512>, a)
+                            : cudaLaunchKernelEx(&cfg, kset_narrow_dc_kernel<true, 1024>, a);
 }
 
 }  // namespace gtx

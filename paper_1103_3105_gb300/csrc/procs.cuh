@@ -551,8 +551,11 @@ __device__ __forceinline__ void exec_oe(const DevDB &db, const DevBulk &b, const
         // in one round trip instead of one per line (chunks bound the
         // registers the other executors of the same kernel pay for)
         constexpr int kLineChunk = 5;
+        // the district's next order id and the read-only rates with the first
+        // chunk's loads, in one round trip: the district's counter is stored
+        // only after them
         const int64_t o_id = cells.ld(&db.d_next_o_id[d]);
-        cells.st(&db.d_next_o_id[d], o_id + 1);
+        const int64_t disc = __ldg(&db.c_discount[c]), w_tax = __ldg(&db.w_tax[w]), d_tax = __ldg(&db.d_tax[d]);
         int64_t total = 0;
         for (int j0 = 0; j0 < cnt; j0 += kLineChunk) {
             int64_t price[kLineChunk], sy[kLineChunk];
@@ -569,6 +572,7 @@ __device__ __forceinline__ void exec_oe(const DevDB &db, const DevBulk &b, const
                     so[u] = ldg_cg(&db.s_order_cnt[s]);
                 }
             }
+            if (j0 == 0) cells.st(&db.d_next_o_id[d], o_id + 1);
 #pragma unroll
             for (int u = 0; u < kLineChunk; u++) {
                 if (j0 + u < cnt) {
@@ -602,8 +606,7 @@ __device__ __forceinline__ void exec_oe(const DevDB &db, const DevBulk &b, const
         }
         cells.st(&db.c_last_o_id[c], o_id);
         out[0] = o_id;
-        out[1] = total * (10000 - __ldg(&db.c_discount[c])) *
-                 (10000 + __ldg(&db.w_tax[w]) + __ldg(&db.d_tax[d])) / 100000000;
+        out[1] = total * (10000 - disc) * (10000 + w_tax + d_tax) / 100000000;
         out[2] = cnt;
         break;
     }
