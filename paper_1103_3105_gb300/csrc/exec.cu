@@ -541,7 +541,7 @@ cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, in
         cudaFuncSetAttribute(kset_narrow_kernel<true, 1024>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         attr_set = true;
     }
-    int64_t k = 0;
+    int64_t k = 0, run_end = 0;
     while (k < levels) {
         const uint32_t w = level_off_host[k + 1] - level_off_host[k];
         if ((int64_t)w > narrow_max) {
@@ -555,11 +555,15 @@ cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, in
             k++;
             continue;
         }
-        // a run of narrow levels, cut where a long stretch of levels needs a
-        // launch shape of another size class (see narrow_segment_end)
-        int64_t run_end = k;
-        while (run_end < levels && (int64_t)(level_off_host[run_end + 1] - level_off_host[run_end]) <= narrow_max)
-            run_end++;
+        // a run of narrow levels (found once), cut where a long stretch of
+        // levels needs a launch shape of another size class (see
+        // narrow_segment_end)
+        if (run_end <= k) {
+            run_end = k;
+            while (run_end < levels &&
+                   (int64_t)(level_off_host[run_end + 1] - level_off_host[run_end]) <= narrow_max)
+                run_end++;
+        }
         const int64_t e = narrow_segment_end(level_off_host, k, run_end);
         uint32_t wmax = 0;
         for (int64_t j = k; j < e; j++) {
