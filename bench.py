@@ -336,6 +336,7 @@ def run_engine(args, rank, world, local_rank):
         atomics["executor_gops"] = n * per_txn / (ex / 1e3) / 1e9
         atomics["executor_atomics_per_txn"] = per_txn
     achieved = n * EXEC_BYTES_PER_TXN / (ex / 1e3) / 1e9
+    l2_bytes = int(getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 0))
     line = {
         "metric": METRIC,
         "value": value,
@@ -366,7 +367,15 @@ def run_engine(args, rank, world, local_rank):
                      "traffic": traffic_for(args.strategy, args.mode, args.bulk_log2),
                      # the level chain, not bandwidth, bounds K-SET on a deep graph
                      "levels": stats["depth"] + 1 if stats else None,
-                     "ns_per_level": ex * 1e6 / (stats["depth"] + 1) if stats else None},
+                     "ns_per_level": ex * 1e6 / (stats["depth"] + 1) if stats else None,
+                     # the mutable tables against L2: the teller and branch
+                     # balances (and, alone, the account column) fit, so the
+                     # 148 B model counts no DRAM bytes for teller and branch
+                     "l2": {"l2_bytes": l2_bytes, "account_bytes": ACCOUNTS * 8,
+                            "teller_branch_bytes": (TELLERS + BRANCHES) * 8,
+                            "fits": [t for t, nb in (("account", ACCOUNTS * 8),
+                                                     ("teller+branch", (TELLERS + BRANCHES) * 8))
+                                     if nb <= l2_bytes]}},
         "latency_roofline": latency,
         "atomics": atomics,
         "phases_ms": {"execute": ex, "op_sort": statistics.median(sort_ms),
