@@ -232,10 +232,16 @@ __device__ __forceinline__ SegMax segmax_unpack(unsigned long long p)
     return SegMax{(uint32_t)(p >> 32), (int32_t)(uint32_t)p};
 }
 
+// stamp (n words, nullable, contents arbitrary at entry): round + 1 of a
+// transaction's last level increase.  Levels only grow, so each run's maximum
+// persists across rounds and a round folds in only the levels that grew in
+// the round before (a stale stamp equal to the round only repeats a
+// maximum); a round's updates are atomics only where the bound exceeds the
+// level read.  Without stamp every operation is folded in every round.
 __global__ void __launch_bounds__(256) fixpoint_coop_kernel(const uint32_t *sv, const uint32_t *rid,
                                                            uint32_t *runmax, uint32_t *level, int32_t *best,
                                                            uint32_t *rfirst, unsigned long long *agg, BulkCtl *ctl,
-                                                           int64_t m, uint32_t max_rounds)
+                                                           int64_t m, uint32_t max_rounds, uint32_t *stamp)
 {
     __shared__ SegMax s_warp[8];
     cooperative_groups::grid_group g = cooperative_groups::this_grid();
@@ -265,13 +271,15 @@ __global__ void __launch_bounds__(256) fixpoint_coop_kernel(const uint32_t *sv, 
     const int64_t t1 = t0 + per_thread < b1 ? t0 + per_thread : b1;
     uint32_t r = 0;
     bool grew_any = true;
+    for (int64_t i = i0; i < R; i += stride) runmax[i] = 0;
     for (; r < max_rounds && grew_any; r++) {
-        for (int64_t i = i0; i < R; i += stride) runmax[i] = 0;
         if (i0 == 0) ctl->changed_r[(r + 1) % 3] = 0;
         g.sync();
         for (int64_t i = i0; i < m; i += stride) {
             const uint32_t v = sv[i];
-            if (v != OP_SENTINEL) atomicMax(&runmax[rid[i] & 0x7fffffffu], level[v >> 7]);
+            if (v == OP_SENTINEL) continue;
+            const uint32_t t = v >> 7;
+            if (r == 0 || !stamp || stamp[t] == r) atomicMax(&runmax[rid[i] & 0x7fffffffu], level[t]);
         }
         g.sync();
         // segmented max-scan of runmax(q) - q over the runs: thread, block
@@ -344,7 +352,12 @@ __global__ void __launch_bounds__(256) fixpoint_coop_kernel(const uint32_t *sv, 
             const int32_t bj = best[j];
             if (bj == INT32_MIN) continue;
             const uint32_t cand = (uint32_t)((int64_t)j + bj);
-            grew |= atomicMax(&level[v >> 7], cand) < cand;
+            const uint32_t t = v >> 7;
+            if (__ldcg(&level[t]) >= cand) continue;   // a stale read only costs an atomic
+            if (atomicMax(&level[t], cand) < cand) {
+                grew = true;
+                if (stamp) stamp[t] = r + 1;
+            }
         }
         if (__any_sync(0xffffffffu, grew) && lane == 0) atomicOr(&ctl->changed_r[r % 3], 1u);
         g.sync();
@@ -1029,9 +1042,11 @@ cudaError_t launch_fixpoint_device(gputx_bulk *b, const uint32_t *sv, int64_t m)
     const uint32_t max_rounds = (uint32_t)(b->n + 2 > 0xffffffffll ? 0xffffffffll : b->n + 2);
     // the run bounds and run-start flags reuse the TPL buffers (free during
     // the analysis)
+    // the round stamps reuse the PART sort keys (n words, free during the
+    // analysis)
     cudaError_t e = cudaLaunchKernelEx(&cfg, fixpoint_coop_kernel, sv, (const uint32_t *)b->sc.rid, b->sc.runmax,
                                        b->sc.level, (int32_t *)b->sc.lock_key, b->sc.lock_ticket, b->sc.fix_agg,
-                                       b->ctl, m, max_rounds);
+                                       b->ctl, m, max_rounds, b->sc.pid_key);
     count_launches(1);
     return e;
 }
