@@ -368,3 +368,43 @@ def test_extract_rejects_unknown_type():
         db.extract(bulk, oracle.MODE_PAPER, 3)
     with pytest.raises(ValueError):
         db.execute(bulk, 1)
+
+
+# ---------------------------------------------------------------------------
+# Replay in a given serial order (Appendix G: serializability)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", [3, 4])
+def test_dc_replay_in_a_given_order(seed):
+    """Executed in a permutation of the bulk, a debit-credit transaction's
+    output is its account's deltas summed over the transactions at or before
+    it in that order, and every final balance is the order-free sum."""
+    A, T, B, n = 400, 40, 4, 2000
+    db = _dc_db(B, T, A)
+    bulk = W.dc_bulk(n, A, 0.9, seed=W.seed_for(1, seed))
+    order = np.random.default_rng(seed).permutation(n)
+    st, out = db.execute(bulk, R=1, order=order)
+    acct, delta = bulk["params"][:, 0], bulk["params"][:, 1]
+    assert (st == 0).all()
+    run, want = {}, np.zeros(n, dtype=np.int64)
+    for t in order:
+        run[acct[t]] = run.get(acct[t], 0) + delta[t]
+        want[t] = run[acct[t]]
+    assert np.array_equal(out[:, 0], want)
+    assert np.array_equal(db["acc_bal"], np.array([delta[acct == i].sum() for i in range(A)]))
+    assert np.array_equal(db["br_bal"], np.array([delta[acct // (A // B) == i].sum() for i in range(B)]))
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1's structural parameters (Appendix D)
+# ---------------------------------------------------------------------------
+def test_graph_stats_by_hand():
+    """d, w0 and c of a hand-built example: c counts a transaction whose root
+    keys fall in two partitions of part_size consecutive keys, and nothing
+    else (one partition, one key, no operation)."""
+    level = np.array([0, 1, 0, 2, 1])
+    root = np.array([[0, 1], [1, 2], [5, -1], [-1, -1], [6, 7]])
+    assert oracle.graph_stats(level, root, part_size=2) == (2, 2, 1)
+    # partitions of one key: every two-key transaction is cross-partition
+    assert oracle.graph_stats(level, root, part_size=1) == (2, 2, 3)
+    # one partition holds keys 0..7: nothing crosses
+    assert oracle.graph_stats(level, root, part_size=8) == (2, 2, 0)
