@@ -27,8 +27,8 @@ namespace {
 // pipeline, each stage a whole level before its use: while level k executes,
 // level k+1's and k+2's records are in registers, level k+3's record is
 // loading and level k+4's end offset too; after the arrival, level k+2's
-// rows are prefetched into L2, so an account row coming from HBM has a whole
-// level to arrive before it is updated.
+// account rows are prefetched into L2, so an account row coming from HBM has
+// a whole level to arrive before it is updated.
 template <bool CLUSTER, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) kset_narrow_dc_kernel(LevelArgs a)
 {
@@ -77,11 +77,9 @@ __global__ void __launch_bounds__(MAXT, 1) kset_narrow_dc_kernel(LevelArgs a)
             asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
         }
         if (pending) dc_finish_rmw(a.db, a.b, o);
-        if (has2) {
-            prefetch_l2(&a.db.acc_bal[r2.a]);
-            prefetch_l2(&a.db.tel_bal[r2.tl]);
-            prefetch_l2(&a.db.br_bal[r2.br]);
-        }
+        // teller and branch rows need none: some level updates them nearly
+        // every level, so they stay in L2
+        if (has2) prefetch_l2(&a.db.acc_bal[r2.a]);
         if (CLUSTER) asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
         else __syncthreads();
         lo = e0;
