@@ -408,3 +408,25 @@ def test_graph_stats_by_hand():
     assert oracle.graph_stats(level, root, part_size=1) == (2, 2, 3)
     # one partition holds keys 0..7: nothing crosses
     assert oracle.graph_stats(level, root, part_size=8) == (2, 2, 0)
+
+
+@pytest.mark.parametrize("mode", [oracle.MODE_PAPER, oracle.MODE_ADD])
+@pytest.mark.parametrize("seed", [5, 6])
+def test_removing_the_0set_makes_the_1set_the_new_0set(mode, seed):
+    """Section 5.3 / Figure 2(d): once the 0-set leaves the pool, the depths
+    of the remaining transactions, recomputed on what remains, are their old
+    depths minus one -- so the former 1-set is the new 0-set.  Repeating the
+    step drains the bulk in exactly depth + 1 steps."""
+    kw = _mixed_small_db()
+    db = oracle.OracleDB(**kw)
+    bulk = _mixed_bulk(300, seed, kw)
+    obj, cls, _ = db.extract(bulk, mode, oracle.MAX_OPS)
+    lv = oracle.levels(obj, cls, db.num_objects())
+    keep = np.arange(len(lv))
+    steps = 0
+    while len(keep):
+        sub = oracle.levels(obj[keep], cls[keep], db.num_objects())
+        assert np.array_equal(sub, lv[keep] - steps)
+        keep = keep[sub > 0]
+        steps += 1
+    assert steps == lv.max() + 1
