@@ -58,6 +58,28 @@ struct LatencyHist {
     }
 };
 
+// memcpy of a large block split over a few threads: one host core copies
+// well below what the memory system moves, and a served bulk of 2^20
+// transactions moves tens of MB through these copies
+void par_memcpy(void *dst, const void *src, size_t bytes)
+{
+    constexpr size_t kPart = size_t(4) << 20;
+    constexpr int kMaxThreads = 8;
+    const int parts = (int)std::min<size_t>(kMaxThreads, bytes / kPart);
+    if (parts < 2) {
+        std::memcpy(dst, src, bytes);
+        return;
+    }
+    const size_t per = (bytes + parts - 1) / parts;
+    std::thread th[kMaxThreads];
+    for (int i = 1; i < parts; i++) {
+        const size_t o = per * (size_t)i, k = std::min(per, bytes - o);
+        th[i] = std::thread([=] { std::memcpy((char *)dst + o, (const char *)src + o, k); });
+    }
+    std::memcpy(dst, src, std::min(per, bytes));
+    for (int i = 1; i < parts; i++) th[i].join();
+}
+
 // An append-only array stored in fixed-size chunks and indexed by absolute
 // position: appending never moves what is already there (no reallocation
 // copies while the server lock is held), and whole chunks below a position
@@ -85,13 +107,19 @@ template <class T> class Chunked {
     int64_t size() const { return size_; }
     T &operator[](int64_t i) { return *at(i); }
     const T &operator[](int64_t i) const { return *at(i); }
+    // n more elements, left unwritten: for arrays each element of which is
+    // written before it is read
+    void grow_uninit(int64_t n)
+    {
+        const int64_t end = size_ + n;
+        while ((int64_t)(chunks_.size() + first_) * kChunk < end) chunks_.emplace_back(new T[kChunk]);
+        size_ = end;
+    }
     // n more elements, each `v`
     void grow(int64_t n, T v)
     {
-        const int64_t end = size_ + n;
-        while ((int64_t)(chunks_.size() + first_) * kChunk < end) chunks_.emplace_back(new T[kChunk]());
         const int64_t at0 = size_;
-        size_ = end;
+        grow_uninit(n);
         fill(at0, n, v);
     }
     void append(const T *src, int64_t n)
@@ -103,14 +131,14 @@ template <class T> class Chunked {
     void copy_in(int64_t i, const T *src, int64_t n)
     {
         pieces(i, n, [&](T *p, int64_t k) {
-            std::memcpy(p, src, sizeof(T) * k);
+            par_memcpy(p, src, sizeof(T) * k);
             src += k;
         });
     }
     void copy_out(int64_t i, int64_t n, T *dst)
     {
         pieces(i, n, [&](T *p, int64_t k) {
-            std::memcpy(dst, p, sizeof(T) * k);
+            par_memcpy(dst, p, sizeof(T) * k);
             dst += k;
         });
     }
@@ -312,11 +340,9 @@ void launch(gputx_server *s, int slot_idx, int64_t n)
         set_worker_error(s, st, "launch");
         if (!b) cudaEventRecord(sl.done, s->db->stream);
         else cudaEventRecord(sl.done, b->stream);
-        if (!b) {
-            // nothing on the device: complete the bulk with its error status
-            for (int64_t i = 0; i < n; i++) sl.h_status[i] = -(int32_t)st;
-            std::memset(sl.h_values, 0, sizeof(int64_t) * n * s->R);
-        }
+        // no results were queued: complete the bulk with its error status
+        for (int64_t i = 0; i < n; i++) sl.h_status[i] = -(int32_t)st;
+        std::memset(sl.h_values, 0, sizeof(int64_t) * n * s->R);
     }
 }
 
@@ -574,9 +600,10 @@ gputx_status gputx_server_submit(gputx_server *s, const int32_t *type, const int
     else s->p_arrival.grow((int64_t)n, t);
     if (s->first_arrival < 0 && n) s->first_arrival = arrival_ns ? arrival_ns[0] : t;
     s->next_id += (int64_t)n;
-    s->r_status.grow((int64_t)n, 0);
-    s->r_values.grow((int64_t)n * s->R, 0);
-    s->r_complete.grow((int64_t)n, 0);
+    // results are read only once r_done marks them written
+    s->r_status.grow_uninit((int64_t)n);
+    s->r_values.grow_uninit((int64_t)n * s->R);
+    s->r_complete.grow_uninit((int64_t)n);
     s->r_done.grow((int64_t)n, 0);
     if (first_id) *first_id = id0;
     s->cv.notify_all();
