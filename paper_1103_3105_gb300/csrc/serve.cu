@@ -74,10 +74,15 @@ void par_memcpy(void *dst, const void *src, size_t bytes)
     std::thread th[kMaxThreads];
     for (int i = 1; i < parts; i++) {
         const size_t o = per * (size_t)i, k = std::min(per, bytes - o);
-        th[i] = std::thread([=] { std::memcpy((char *)dst + o, (const char *)src + o, k); });
+        try {
+            th[i] = std::thread([=] { std::memcpy((char *)dst + o, (const char *)src + o, k); });
+        } catch (...) {   // no thread to spare: this part on the caller
+            std::memcpy((char *)dst + o, (const char *)src + o, k);
+        }
     }
     std::memcpy(dst, src, std::min(per, bytes));
-    for (int i = 1; i < parts; i++) th[i].join();
+    for (int i = 1; i < parts; i++)
+        if (th[i].joinable()) th[i].join();
 }
 
 // An append-only array stored in fixed-size chunks and indexed by absolute
