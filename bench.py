@@ -725,6 +725,11 @@ def main():
     local_rank = env_int("LOCAL_RANK", 0)
     if args.warmup < 3:
         args.warmup = 3
+    if world > 1:
+        # several GPUs: the replicas' timed steps only.  The CPU baseline is an
+        # N = 1 figure, and the single-GPU characterisations (sweep, serving,
+        # batching, subscriber schema) would hold every GPU for minutes
+        args.cpu_baseline = args.sweep = args.serve = args.batched = args.subscriber = False
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:
