@@ -365,3 +365,26 @@ def test_bulk_of_exactly_max_bulk(strategy):
         g.submit_dict(W.dc_bulk((1 << 15) + 1, 10000, 0.0, seed=9))
     assert e.value.status == G.EINVAL
     g.close()
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_narrow_run_cut_into_segments(mode):
+    """A run of narrow levels whose width falls from a cluster's class to one
+    CTA's for hundreds of levels (127 branches with 100 transactions each,
+    one branch with 400): the run executes as two launches of different
+    shapes, and every result still matches serial execution."""
+    B, A = 128, 128 * 100
+    g, o = make_pair(B, B * 10, A, 1 << 16)
+    rng = np.random.default_rng(W.seed_for(2, 7))
+    per = A // B
+    branch = np.concatenate([np.repeat(np.arange(B - 1), 100), np.full(400, B - 1)])
+    rng.shuffle(branch)
+    n = len(branch)
+    acct = branch * per + rng.integers(0, per, size=n)
+    bulk = {"ts": np.arange(n, dtype=np.int64), "type": np.zeros(n, np.int32),
+            "params": np.stack([acct, rng.integers(-99999, 100000, size=n)], axis=1).astype(np.int64), "P": 2}
+    stats, st, out, ost, oout = run_both(g, o, bulk, "kset", mode)
+    if mode == G.CONFLICT_PAPER:
+        assert stats["depth"] == 399
+    assert_same(g, o, st, out, ost, oout)
+    g.close()
