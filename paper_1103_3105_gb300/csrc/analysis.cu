@@ -232,6 +232,8 @@ __device__ __forceinline__ SegMax segmax_unpack(unsigned long long p)
     return SegMax{(uint32_t)(p >> 32), (int32_t)(uint32_t)p};
 }
 
+constexpr int kFixBatch = 8;   // operations a thread handles per step of the per-operation loops
+
 // stamp (n words, nullable, contents arbitrary at entry): round + 1 of a
 // transaction's last level increase.  Levels only grow, so each run's maximum
 // persists across rounds and a round folds in only the levels that grew in
@@ -275,11 +277,27 @@ __global__ void __launch_bounds__(256) fixpoint_coop_kernel(const uint32_t *sv, 
     for (; r < max_rounds && grew_any; r++) {
         if (i0 == 0) ctl->changed_r[(r + 1) % 3] = 0;
         g.sync();
-        for (int64_t i = i0; i < m; i += stride) {
-            const uint32_t v = sv[i];
-            if (v == OP_SENTINEL) continue;
-            const uint32_t t = v >> 7;
-            if (r == 0 || !stamp || stamp[t] == r) atomicMax(&runmax[rid[i] & 0x7fffffffu], level[t]);
+        // kFixBatch operations a thread at a time: all their loads, then the
+        // dependent gathers, then the atomics, so a thread keeps a batch of
+        // round trips in flight instead of one
+        for (int64_t i = i0; i < m; i += stride * kFixBatch) {
+            uint32_t v[kFixBatch], q[kFixBatch], lv[kFixBatch];
+            bool use[kFixBatch];
+#pragma unroll
+            for (int u = 0; u < kFixBatch; u++) {
+                const int64_t k = i + (int64_t)u * stride;
+                v[u] = k < m ? sv[k] : OP_SENTINEL;
+                q[u] = k < m ? rid[k] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < kFixBatch; u++) {
+                const uint32_t t = v[u] >> 7;
+                use[u] = v[u] != OP_SENTINEL && (r == 0 || !stamp || stamp[t] == r);
+                lv[u] = use[u] ? level[t] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < kFixBatch; u++)
+                if (use[u]) atomicMax(&runmax[q[u] & 0x7fffffffu], lv[u]);
         }
         g.sync();
         // segmented max-scan of runmax(q) - q over the runs: thread, block
@@ -345,18 +363,34 @@ __global__ void __launch_bounds__(256) fixpoint_coop_kernel(const uint32_t *sv, 
         }
         g.sync();
         bool grew = false;
-        for (int64_t i = i0; i < m; i += stride) {
-            const uint32_t v = sv[i], rr = rid[i];
-            if (v == OP_SENTINEL || (rr & 0x80000000u)) continue;
-            const uint32_t j = rr & 0x7fffffffu;
-            const int32_t bj = best[j];
-            if (bj == INT32_MIN) continue;
-            const uint32_t cand = (uint32_t)((int64_t)j + bj);
-            const uint32_t t = v >> 7;
-            if (__ldcg(&level[t]) >= cand) continue;   // a stale read only costs an atomic
-            if (atomicMax(&level[t], cand) < cand) {
-                grew = true;
-                if (stamp) stamp[t] = r + 1;
+        for (int64_t i = i0; i < m; i += stride * kFixBatch) {
+            uint32_t v[kFixBatch], rr[kFixBatch], cand[kFixBatch];
+            bool use[kFixBatch];
+#pragma unroll
+            for (int u = 0; u < kFixBatch; u++) {
+                const int64_t k = i + (int64_t)u * stride;
+                v[u] = k < m ? sv[k] : OP_SENTINEL;
+                rr[u] = k < m ? rid[k] : 0x80000000u;
+            }
+#pragma unroll
+            for (int u = 0; u < kFixBatch; u++) {
+                use[u] = v[u] != OP_SENTINEL && !(rr[u] & 0x80000000u);
+                const uint32_t j = rr[u] & 0x7fffffffu;
+                const int32_t bj = use[u] ? best[j] : INT32_MIN;
+                use[u] = use[u] && bj != INT32_MIN;
+                cand[u] = (uint32_t)((int64_t)j + bj);
+            }
+#pragma unroll
+            for (int u = 0; u < kFixBatch; u++)   // a stale read only costs an atomic
+                use[u] = use[u] && __ldcg(&level[v[u] >> 7]) < cand[u];
+#pragma unroll
+            for (int u = 0; u < kFixBatch; u++) {
+                if (!use[u]) continue;
+                const uint32_t t = v[u] >> 7;
+                if (atomicMax(&level[t], cand[u]) < cand[u]) {
+                    grew = true;
+                    if (stamp) stamp[t] = r + 1;
+                }
             }
         }
         if (__any_sync(0xffffffffu, grew) && lane == 0) atomicOr(&ctl->changed_r[r % 3], 1u);
