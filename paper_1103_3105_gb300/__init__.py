@@ -137,6 +137,52 @@ class ExecOpts(C.Structure):
 _lib = None
 
 
+def signatures() -> dict:
+    """ctypes (argument types, result type) of every entry point of
+    include/gputx.h, by name."""
+    p, sz = C.c_void_p, C.c_size_t
+    return {
+        "gputx_create_db": ([C.POINTER(SchemaDesc), C.POINTER(Config), p, C.POINTER(p)], C.c_int),
+        "gputx_destroy_db": ([p], None),
+        "gputx_last_error": ([p], C.c_char_p),
+        "gputx_register_types": ([p, p, C.c_int], C.c_int),
+        "gputx_load_table": ([p, C.c_int, p, sz], C.c_int),
+        "gputx_read_table": ([p, C.c_int, p, sz, C.POINTER(sz)], C.c_int),
+        "gputx_submit_bulk": ([p, p, p, p, C.c_int, sz, C.c_int, C.POINTER(p)], C.c_int),
+        "gputx_execute": ([p, p, C.c_int, C.POINTER(ExecOpts)], C.c_int),
+        "gputx_sync_bulk": ([p, C.POINTER(ExecStats)], C.c_int),
+        "gputx_read_results": ([p, p, p, sz, C.c_int], C.c_int),
+        "gputx_bulk_results_device": ([p, C.POINTER(p), C.POINTER(p)], C.c_int),
+        "gputx_bulk_order": ([p, p, sz], C.c_int),
+        "gputx_probe_level_chain": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                     C.POINTER(C.c_double)], C.c_int),
+        "gputx_probe_atomics": ([C.c_int64, C.c_int, C.POINTER(C.c_double)], C.c_int),
+        "gputx_output_width": ([p], C.c_int),
+        "gputx_free_bulk": ([p], None),
+        "gputx_version": ([], C.c_char_p),
+        "gputx_launch_count": ([], C.c_ulonglong),
+        "gputx_execute_kset_noalloc": ([p, p, p, p, C.c_int, sz, C.c_int, p, p], C.c_int),
+        "gputx_clock_ns": ([], C.c_int64),
+        "gputx_server_create": ([p, C.POINTER(ServeConfig), C.POINTER(p)], C.c_int),
+        "gputx_server_submit": ([p, p, p, sz, p, C.POINTER(C.c_int64)], C.c_int),
+        "gputx_server_results": ([p, C.c_int64, sz, p, p, p, C.POINTER(sz)], C.c_int),
+        "gputx_server_drain": ([p], C.c_int),
+        "gputx_server_stats": ([p, C.POINTER(ServeStats)], C.c_int),
+        "gputx_server_last_error": ([p], C.c_char_p),
+        "gputx_server_destroy": ([p], None),
+        "gputx_batcher_create": ([p, C.POINTER(BatchConfig), C.POINTER(p)], C.c_int),
+        "gputx_batcher_run": ([p, p, p, p, sz, p, p], C.c_int),
+        "gputx_batcher_choice": ([p, C.POINTER(BatchChoice)], C.c_int),
+        "gputx_batcher_destroy": ([p], None),
+        "gputx_pool_create": ([p, C.POINTER(PoolConfig), C.POINTER(p)], C.c_int),
+        "gputx_pool_add": ([p, p, p, p, sz], C.c_int),
+        "gputx_pool_step": ([p, C.POINTER(sz)], C.c_int),
+        "gputx_pool_results": ([p, p, p, p, sz, C.POINTER(sz)], C.c_int),
+        "gputx_pool_pending": ([p], sz),
+        "gputx_pool_destroy": ([p], None),
+    }
+
+
 def lib():
     """The loaded CUDA library; raises if it was not built."""
     global _lib
@@ -144,47 +190,7 @@ def lib():
         if not os.path.exists(LIB_PATH):
             raise GputxError(ECUDA, f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
         L = C.CDLL(LIB_PATH, mode=C.RTLD_GLOBAL)
-        p, i32, i64, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t
-        sig = {
-            "gputx_create_db": ([C.POINTER(SchemaDesc), C.POINTER(Config), p, C.POINTER(p)], C.c_int),
-            "gputx_destroy_db": ([p], None),
-            "gputx_last_error": ([p], C.c_char_p),
-            "gputx_register_types": ([p, p, C.c_int], C.c_int),
-            "gputx_load_table": ([p, C.c_int, p, sz], C.c_int),
-            "gputx_read_table": ([p, C.c_int, p, sz, C.POINTER(sz)], C.c_int),
-            "gputx_submit_bulk": ([p, p, p, p, C.c_int, sz, C.c_int, C.POINTER(p)], C.c_int),
-            "gputx_execute": ([p, p, C.c_int, C.POINTER(ExecOpts)], C.c_int),
-            "gputx_sync_bulk": ([p, C.POINTER(ExecStats)], C.c_int),
-            "gputx_read_results": ([p, p, p, sz, C.c_int], C.c_int),
-            "gputx_bulk_results_device": ([p, C.POINTER(p), C.POINTER(p)], C.c_int),
-            "gputx_bulk_order": ([p, p, sz], C.c_int),
-            "gputx_probe_level_chain": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
-                                         C.POINTER(C.c_double)], C.c_int),
-            "gputx_probe_atomics": ([C.c_int64, C.c_int, C.POINTER(C.c_double)], C.c_int),
-            "gputx_output_width": ([p], C.c_int),
-            "gputx_free_bulk": ([p], None),
-            "gputx_version": ([], C.c_char_p),
-            "gputx_launch_count": ([], C.c_ulonglong),
-            "gputx_execute_kset_noalloc": ([p, p, p, p, C.c_int, sz, C.c_int, p, p], C.c_int),
-            "gputx_clock_ns": ([], C.c_int64),
-            "gputx_server_create": ([p, C.POINTER(ServeConfig), C.POINTER(p)], C.c_int),
-            "gputx_server_submit": ([p, p, p, sz, p, C.POINTER(C.c_int64)], C.c_int),
-            "gputx_server_results": ([p, C.c_int64, sz, p, p, p, C.POINTER(sz)], C.c_int),
-            "gputx_server_drain": ([p], C.c_int),
-            "gputx_server_stats": ([p, C.POINTER(ServeStats)], C.c_int),
-            "gputx_server_last_error": ([p], C.c_char_p),
-            "gputx_server_destroy": ([p], None),
-            "gputx_batcher_create": ([p, C.POINTER(BatchConfig), C.POINTER(p)], C.c_int),
-            "gputx_batcher_run": ([p, p, p, p, sz, p, p], C.c_int),
-            "gputx_batcher_choice": ([p, C.POINTER(BatchChoice)], C.c_int),
-            "gputx_batcher_destroy": ([p], None),
-            "gputx_pool_create": ([p, C.POINTER(PoolConfig), C.POINTER(p)], C.c_int),
-            "gputx_pool_add": ([p, p, p, p, sz], C.c_int),
-            "gputx_pool_step": ([p, C.POINTER(sz)], C.c_int),
-            "gputx_pool_results": ([p, p, p, p, sz, C.POINTER(sz)], C.c_int),
-            "gputx_pool_pending": ([p], sz),
-            "gputx_pool_destroy": ([p], None),
-        }
+        sig = signatures()
         for name, (args, res) in sig.items():
             f = getattr(L, name)
             f.argtypes = args

@@ -42,6 +42,31 @@ def test_binding_covers_the_abi(libpath):
     assert G.gputx_version().startswith("gputx-gb300")
 
 
+def _declared_arity():
+    """name -> parameter count of every function the headers declare."""
+    out = {}
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if not f.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for name, params in re.findall(r"\b(gputx_\w+)\s*\(([^;{]*?)\)\s*;", text, flags=re.S):
+            params = params.strip()
+            out[name] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    """Every declared function has a ctypes signature with as many arguments
+    as the header gives it (a stale binding would pass garbage silently)."""
+    arity = _declared_arity()
+    sig = G.signatures()
+    assert len(arity) >= 30
+    assert set(arity) == set(sig), (set(arity) ^ set(sig))
+    wrong = {n: (arity[n], len(sig[n][0])) for n in arity if arity[n] != len(sig[n][0])}
+    assert not wrong, wrong
+
+
 def test_structs_match_header_sizes():
     # the binding's ctypes mirrors must keep the header's field order and sizes
     assert ctypes.sizeof(G.SchemaDesc) == 10 * 8
