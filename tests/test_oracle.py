@@ -430,3 +430,72 @@ def test_removing_the_0set_makes_the_1set_the_new_0set(mode, seed):
         keep = keep[sub > 0]
         steps += 1
     assert steps == lv.max() + 1
+
+
+# ---------------------------------------------------------------------------
+# Subscriber procedures on a hand-built database (Appendix E stand-ins)
+# ---------------------------------------------------------------------------
+def _pack2(lo, hi):
+    return (int(lo) & 0xFFFFFFFF) | ((int(hi) & 0xFFFFFFFF) << 32)
+
+
+def test_subscriber_procedures_by_hand():
+    """Each subscriber type on a two-subscriber database whose every row is
+    written out here, with the expected status and outputs worked by hand
+    from the procedures' definitions: lookups by key, the call-forwarding
+    range test (start_time <= the given start, end_time > the given end),
+    duplicate and missing keys, and the two-phase aborts."""
+    t = {
+        "sub": np.stack([np.arange(16) + 100, np.arange(16) + 200]).astype(np.int32),
+        "ai_present": np.array([[1, 0, 0, 0], [0, 1, 0, 0]], dtype=np.int32),
+        "ai_data": np.arange(2 * 4 * 4, dtype=np.int32).reshape(2, 4, 4) + 1000,
+        "sf_present": np.array([[1, 1, 0, 0], [0, 0, 1, 0]], dtype=np.int32),
+        "sf_active": np.array([[1, 0, 0, 0], [0, 0, 1, 0]], dtype=np.int32),
+        "sf_err": np.zeros((2, 4), dtype=np.int32),
+        "sf_data_a": np.zeros((2, 4), dtype=np.int32),
+        "sf_data_b": np.zeros((2, 4), dtype=np.int32),
+        "cf_present": np.zeros((2, 4, 3), dtype=np.int32),
+        "cf_end": np.zeros((2, 4, 3), dtype=np.int32),
+        "cf_numberx": np.zeros((2, 4, 3), dtype=np.int32),
+    }
+    # subscriber 0, facility 1: start 0 until 5 -> 111, start 8 until 12 -> 222
+    t["cf_present"][0, 0, :2] = 1
+    t["cf_end"][0, 0, :2] = (5, 12)
+    t["cf_numberx"][0, 0, :2] = (111, 222)
+    S = W
+    txns = [  # (type, params, status, outputs)
+        (S.SUB_GET_SUBSCRIBER, [0], 0, [_pack2(100 + 2 * j, 101 + 2 * j) for j in range(8)]),
+        (S.SUB_GET_ACCESS, [0, 1], 0, [_pack2(1000, 1001), _pack2(1002, 1003)]),
+        (S.SUB_GET_ACCESS, [0, 2], 1, []),
+        (S.SUB_GET_NEW_DEST, [0, 1, 8, 10], 0, [1, 222]),
+        (S.SUB_GET_NEW_DEST, [0, 2, 8, 10], 1, []),            # facility 2 inactive
+        (S.SUB_INSERT_CF, [0, 1, 16, 20, 333], 0, []),
+        (S.SUB_INSERT_CF, [0, 1, 16, 21, 444], 2, []),          # duplicate key
+        (S.SUB_INSERT_CF, [0, 3, 0, 5, 555], 1, []),            # no facility 3
+        (S.SUB_GET_NEW_DEST, [0, 1, 16, 17], 0, [1, 333]),
+        (S.SUB_DELETE_CF, [0, 1, 8], 0, []),
+        (S.SUB_DELETE_CF, [0, 1, 8], 1, []),                    # already gone
+        (S.SUB_GET_NEW_DEST, [0, 1, 16, 4], 0, [2, 111, 333]),
+        (S.SUB_UPDATE_LOCATION, [1, 77], 0, [215]),
+        (S.SUB_UPDATE_LOCATION, [1, 88], 0, [77]),
+        (S.SUB_UPDATE_FACILITY, [0, 1, 1, 9], 0, []),
+        (S.SUB_UPDATE_FACILITY, [1, 1, 1, 9], 1, []),           # subscriber 1 has no facility 1
+        (S.SUB_GET_SUBSCRIBER, [0], 0, [_pack2(1, 101)] + [_pack2(102 + 2 * j, 103 + 2 * j) for j in range(7)]),
+    ]
+    n = len(txns)
+    params = np.zeros((n, W.SUB_PARAMS), dtype=np.int64)
+    for i, (_, p, _, _) in enumerate(txns):
+        params[i, :len(p)] = p
+    bulk = {"ts": np.arange(n, dtype=np.int64), "type": np.array([x[0] for x in txns], dtype=np.int32),
+            "params": params, "P": W.SUB_PARAMS}
+    db = oracle.OracleDB(sub=t)
+    st, out = db.execute(bulk, R=8)
+    for i, (_, _, want_st, want_out) in enumerate(txns):
+        assert st[i] == want_st, i
+        got = [int(v) & 0xFFFFFFFFFFFFFFFF for v in out[i]]
+        want = [v & 0xFFFFFFFFFFFFFFFF for v in want_out] + [0] * (8 - len(want_out))
+        assert got == want, i
+    assert db["cf_present"][0, 0].tolist() == [1, 0, 1]
+    assert db["cf_end"][0, 0, 2] == 20 and db["cf_numberx"][0, 0, 2] == 333
+    assert db["sub"][1, 15] == 88 and db["sub"][0, 0] == 1 and db["sf_data_a"][0, 0] == 9
+    assert db["sf_data_a"][1, 0] == 0
