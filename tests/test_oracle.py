@@ -499,3 +499,60 @@ def test_subscriber_procedures_by_hand():
     assert db["cf_end"][0, 0, 2] == 20 and db["cf_numberx"][0, 0, 2] == 333
     assert db["sub"][1, 15] == 88 and db["sub"][0, 0] == 1 and db["sf_data_a"][0, 0] == 9
     assert db["sf_data_a"][1, 0] == 0
+
+
+# ---------------------------------------------------------------------------
+# Order-entry procedures on a hand-built database (Appendix E stand-ins)
+# ---------------------------------------------------------------------------
+def test_order_entry_procedures_by_hand():
+    """New-order, payment and order-status on one warehouse and four items,
+    every expected value worked by hand: the stock rule (take the quantity,
+    or take it and add 91 when fewer than quantity + 10 remain), the total
+    with discount and taxes in basis points, order ids from the district's
+    counter, a read-phase abort on an unknown item, and order-status reading
+    back the customer's last order and its lines."""
+    n_d, n_c, n_items = W.OE_DISTRICTS, W.OE_DISTRICTS * W.OE_CUSTOMERS, 4
+    t = {
+        "w_tax": np.array([1000], dtype=np.int64), "w_ytd": np.zeros(1, dtype=np.int64),
+        "d_tax": np.zeros(n_d, dtype=np.int64), "d_ytd": np.zeros(n_d, dtype=np.int64),
+        "d_next_o_id": np.ones(n_d, dtype=np.int64),
+        "c_discount": np.zeros(n_c, dtype=np.int64), "c_balance": np.zeros(n_c, dtype=np.int64),
+        "c_ytd": np.zeros(n_c, dtype=np.int64), "c_payment_cnt": np.zeros(n_c, dtype=np.int64),
+        "c_last_o_id": np.zeros(n_c, dtype=np.int64),
+        "i_price": np.array([100, 250, 1000, 40], dtype=np.int64),
+        "s_quantity": np.array([50, 12, 9, 100], dtype=np.int32),
+        "s_ytd": np.zeros(n_items, dtype=np.int64), "s_order_cnt": np.zeros(n_items, dtype=np.int32),
+    }
+    t["d_tax"][0] = 500
+    t["c_discount"][0] = 2000
+
+    def line(item, qty, sw=0):
+        return item | (sw << 24) | (qty << 40)
+
+    NO, PAY, OS = W.OE_NEW_ORDER, W.OE_PAYMENT, W.OE_ORDER_STATUS
+    txns = [  # (type, [w, d, c, x, lines...], status, outputs)
+        (NO, [0, 0, 0, 3, line(0, 5), line(1, 3), line(2, 2)], 0, [1, 2990, 3]),
+        (OS, [0, 0, 0], 0, [0, 1, 3, 3250]),
+        (PAY, [0, 0, 0, 700], 0, [-700]),
+        (OS, [0, 0, 1], 1, [0, 0]),                              # customer 1: no order yet
+        (NO, [0, 0, 1, 2, line(3, 10), line(7, 1)], 1, []),       # item 7 does not exist
+        (NO, [0, 0, 1, 1, line(0, 40)], 0, [2, 4600, 1]),
+        (OS, [0, 0, 1], 0, [0, 2, 1, 4000]),
+    ]
+    n = len(txns)
+    params = np.zeros((n, W.OE_PARAMS), dtype=np.int64)
+    for i, (_, p, _, _) in enumerate(txns):
+        params[i, :len(p)] = p
+    bulk = {"ts": np.arange(n, dtype=np.int64), "type": np.array([x[0] for x in txns], dtype=np.int32),
+            "params": params, "P": W.OE_PARAMS}
+    db = oracle.OracleDB(oe=t, ord_cap=16, ol_cap=64, oid_cap=16)
+    st, out = db.execute(bulk, R=4)
+    for i, (_, _, want_st, want_out) in enumerate(txns):
+        assert st[i] == want_st, i
+        assert out[i].tolist() == want_out + [0] * (4 - len(want_out)), i
+    # 3,250 x (1 - 20 %) x (1 + 10 % + 5 %) = 2,990 (first order)
+    assert db["s_quantity"].tolist() == [96, 100, 98, 100]
+    assert db["s_ytd"].tolist() == [45, 3, 2, 0] and db["s_order_cnt"].tolist() == [2, 1, 1, 0]
+    assert db["d_next_o_id"][0] == 3 and db["w_ytd"][0] == 700 and db["d_ytd"][0] == 700
+    assert db["c_balance"][0] == -700 and db["c_payment_cnt"][0] == 1 and db["c_last_o_id"][1] == 2
+    assert len(db.orders()) == 2 and len(db.order_lines()) == 4
