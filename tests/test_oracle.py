@@ -556,3 +556,24 @@ def test_order_entry_procedures_by_hand():
     assert db["d_next_o_id"][0] == 3 and db["w_ytd"][0] == 700 and db["d_ytd"][0] == 700
     assert db["c_balance"][0] == -700 and db["c_payment_cnt"][0] == 1 and db["c_last_o_id"][1] == 2
     assert len(db.orders()) == 2 and len(db.order_lines()) == 4
+
+
+@pytest.mark.parametrize("mode", [oracle.MODE_PAPER, oracle.MODE_ADD])
+def test_random_linear_extensions_of_a_larger_bulk(mode):
+    """The brute-force check at a size where the orders cannot be listed:
+    random orders that keep every conflicting pair in timestamp order, over
+    a hot mixed bulk of 160 transactions, all reach Definition 1's result."""
+    kw = _mixed_small_db()
+    bulk = _mixed_bulk(160, 777, kw)
+    ref_db = oracle.OracleDB(**kw)
+    obj, cls, _ = ref_db.extract(bulk, mode, oracle.MAX_OPS)
+    st0, out0 = ref_db.execute(bulk, R=8)
+    s0 = oracle_logical_state(ref_db)
+    orders = linear_extensions(len(bulk["ts"]), conflict_pairs(obj, cls), limit=40, seed=5)
+    assert len(orders) == 40
+    assert sum(not np.array_equal(o, np.arange(len(o))) for o in orders) >= 30
+    for order in orders:
+        db = oracle.OracleDB(**kw)
+        st, out = db.execute(bulk, R=8, order=order)
+        assert states_equal(s0, oracle_logical_state(db))
+        assert np.array_equal(st, st0) and np.array_equal(out, out0)
