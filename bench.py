@@ -100,7 +100,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except (OSError, FileNotFoundError):
@@ -337,6 +337,9 @@ def run_engine(args, rank, world, local_rank):
         atomics["executor_atomics_per_txn"] = per_txn
     achieved = n * EXEC_BYTES_PER_TXN / (ex / 1e3) / 1e9
     l2_bytes = int(getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 0))
+    clocks = clk.summary()
+    traffic = traffic_for(args.strategy, args.mode, args.bulk_log2)
+    levels = stats["depth"] + 1 if stats else None
     line = {
         "metric": METRIC,
         "value": value,
@@ -349,11 +352,11 @@ def run_engine(args, rank, world, local_rank):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "int64",
-        "data": "synthetic (seeded debit-credit bulks, random-free initial tables)",
+        "data": "synthetic (seeded debit-credit bulks, balances start at 0)",
         "config": {"workload": f"debit-credit at scale: {BRANCHES} branches, {TELLERS} tellers, "
                                f"{ACCOUNTS} accounts, bulk 2^{args.bulk_log2}, theta {args.theta}",
                    "strategy": args.strategy, "conflict_mode": args.mode, "bulk": n,
-                   "theta": args.theta, "l2": "flushed between steps (256 MiB write, outside the step events)",
+                   "l2": "flushed between steps (256 MiB write outside the events)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": "txn/s", "h2d_bytes_per_step": n * (8 + 4 + 16),
                 "d2h_bytes_per_step": n * (4 + 8 * db.width), "pipeline": "2 bulks in flight",
@@ -361,39 +364,36 @@ def run_engine(args, rank, world, local_rank):
         "gpu_launches": int(launches),
         "roofline": {"kernel": DOMINANT_KERNEL.get((args.strategy, args.mode), "executor"),
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_source": peak_kind,
-                     "algorithmic_bytes_per_txn": EXEC_BYTES_PER_TXN,
-                     "kernel_ms": ex, "kernel_source_digest": kernel_digest(),
-                     "traffic": traffic_for(args.strategy, args.mode, args.bulk_log2),
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": peak_kind, "bytes_per_txn": EXEC_BYTES_PER_TXN,
+                     "txn_per_launch_set": n, "kernel_ms": ex,
                      # the level chain, not bandwidth, bounds K-SET on a deep graph
-                     "levels": stats["depth"] + 1 if stats else None,
-                     "ns_per_level": ex * 1e6 / (stats["depth"] + 1) if stats else None,
-                     # the mutable tables against L2: the teller and branch
-                     # balances (and, alone, the account column) fit, so the
-                     # 148 B model counts no DRAM bytes for teller and branch
-                     "l2": {"l2_bytes": l2_bytes, "account_bytes": ACCOUNTS * 8,
-                            "teller_branch_bytes": (TELLERS + BRANCHES) * 8,
-                            "fits": [t for t, nb in (("account", ACCOUNTS * 8),
-                                                     ("teller+branch", (TELLERS + BRANCHES) * 8))
-                                     if nb <= l2_bytes]}},
-        "latency_roofline": latency,
-        "atomics": atomics,
-        "phases_ms": {"execute": ex, "op_sort": statistics.median(sort_ms),
-                      "analysis": stats["ms_analysis"] if stats else None},
-        "graph": {"depth": stats["depth"], "w0": stats["w0"], "cross": stats["cross"]} if stats else None,
-        "clocks": clk.summary(),
-        "wall_s_timed": wall,
+                     "levels": levels, "ns_per_level": ex * 1e6 / levels if levels else None},
+        "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons", "samples")},
     }
+    if latency is not None:
+        line["latency_roofline"] = {k: latency[k] for k in ("levels", "measured_ns_per_level",
+                                                             "floor_ns_per_level", "frac")}
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, bulks)
-    if sweep is not None:
-        line["sweep"] = sweep
-    if serving is not None:
-        line["serving"] = serving
-    if batched is not None:
-        line["batched"] = batched
-    if subscriber is not None:
-        line["subscriber"] = subscriber
+    # everything else goes to the detail file; stdout ends with the compact headline
+    detail = {"headline": line, "latency_roofline": latency, "atomics": atomics,
+              "phases_ms": {"execute": ex, "op_sort": statistics.median(sort_ms),
+                            "analysis": stats["ms_analysis"] if stats else None},
+              "graph": {"depth": stats["depth"], "w0": stats["w0"], "cross": stats["cross"]} if stats else None,
+              "clocks": clocks, "wall_s_timed": wall, "kernel_source_digest": kernel_digest(),
+              "l2": {"l2_bytes": l2_bytes, "account_bytes": ACCOUNTS * 8,
+                     "teller_branch_bytes": (TELLERS + BRANCHES) * 8},
+              "sweep": sweep, "serving": serving, "batched": batched, "subscriber": subscriber}
+    if args.detail_out:
+        try:
+            d = os.path.dirname(os.path.abspath(args.detail_out))
+            os.makedirs(d, exist_ok=True)
+            with open(args.detail_out, "w") as fh:
+                json.dump(detail, fh, indent=1)
+            line["detail"] = args.detail_out
+        except OSError as e:
+            line["detail"] = f"not written: {e}"
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -655,7 +655,7 @@ def oracle_rate(bulks, budget_s, max_bulks=None):
 
 def cpu_baseline(args, bulks):
     done, t, k = oracle_rate(bulks, args.cpu_budget_s)
-    return {"value": done / t, "unit": "txn/s", "cores": 1, "kind": "oracle",
+    return {"value": done / t, "unit": "txn/s", "cores": 1, "nproc": os.cpu_count(), "kind": "oracle",
             "sample": f"{k} bulks of {len(bulks[0]['ts'])} transactions, serial execution in "
                       f"timestamp order (Definition 1), {t:.1f} s on one host core"}
 
@@ -720,6 +720,9 @@ def main():
     ap.add_argument("--subscriber", dest="subscriber", action="store_true", default=True)
     ap.add_argument("--no-subscriber", dest="subscriber", action="store_false")
     ap.add_argument("--sub-subscribers", type=int, default=10_000_000)
+    ap.add_argument("--detail-out", default="bench_detail.json",
+                    help="file for the sections beside the headline (sweep, serving, batching, "
+                         "subscriber schema); '' writes none")
     args = ap.parse_args()
     rank, world = env_int("RANK", 0), env_int("WORLD_SIZE", 1)
     local_rank = env_int("LOCAL_RANK", 0)
