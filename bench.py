@@ -481,15 +481,11 @@ def run_serving(args, G, torch, stream):
         db.load(t, r)
     torch.cuda.synchronize()
     db_bytes = free0 - torch.cuda.mem_get_info()[0]
-    rng = np.random.default_rng(W.seed_for(5))
     mode = G.CONFLICT_ADD if args.mode == "add" else G.CONFLICT_PAPER
-    for rate in rates:
+    for ri, rate in enumerate(rates):
         n = int(rate * args.serve_seconds)
-        parts = [W.dc_bulk(n, ACCOUNTS, args.theta, seed=W.seed_for(5, int(rate // 1e6))),
-                 W.sub_bulk(n, n_sub, args.theta, seed=W.seed_for(5, 50 + int(rate // 1e6)))]
-        bulk = W.concat_bulks(parts, rng.integers(0, 2, size=n))
-        gaps = rng.exponential(1e9 / rate, size=n)
-        offs = np.cumsum(gaps).astype(np.int64)
+        bulk = W.served_mix(n, ACCOUNTS, n_sub, args.theta, rate, seed_variant=ri)
+        offs = bulk["arrival_offset_ns"]
         for deadline in deadlines:
             for label, inflight, zero in (("continuous", 3, False), ("plain", 1, False), ("zero_set", 1, True)):
                 if zero and rate > args.serve_zero_set_max_rate:
@@ -584,13 +580,8 @@ def run_batched(args, G, torch, stream):
     D2H inside the timing) for both."""
     n_wh, n_items = 64, 100_000
     init = W.oe_tables(n_wh, n_items=n_items, seed=W.seed_for(4))
-    rng = np.random.default_rng(W.seed_for(4, 1))
-    sizes, total = [], 0
-    while total < args.batch_txns:
-        k = int(2 ** rng.uniform(10, 21))
-        sizes.append(k)
-        total += k
-    stream_bulk = W.oe_bulk(total, n_wh, n_items=n_items, seed=W.seed_for(4, 2))
+    sizes, stream_bulk = W.oe_stream(args.batch_txns, n_wh, n_items)
+    total = sum(sizes)
     out = {"workload": f"order-entry {n_wh} warehouses, {n_items} items, {len(sizes)} bulks of "
                        f"2^10..2^21 transactions, {total} in all", "txn": total}
     for label in ("plain_kset", "batched_tuned"):

@@ -52,7 +52,14 @@ typedef enum {
     GPUTX_KSET = 0,       /* Section 5.3: k-sets level by level */
     GPUTX_PART = 1,       /* Section 5.2: one thread per partition */
     GPUTX_TPL = 2,        /* Section 5.1: ordered counter locks */
-    GPUTX_AUTO = 3,       /* Algorithm 1 over the measured d, w0, c */
+    GPUTX_AUTO = 3,       /* Algorithm 1 over the measured d, w0, c.  The
+                           * decision reads the one-pass ranks of Section 4.2
+                           * (w0 and c exact there, d a lower bound); the
+                           * refinement rounds of exact depth run only when
+                           * K-SET is chosen, so the reported depth of a PART
+                           * or TPL pick is the one-pass depth.  On a database
+                           * whose only registered type is debit-credit, AUTO
+                           * runs GPUTX_SCAN (same results, one pass). */
     /* Debit-credit bulks only (every registered type is
      * GPUTX_T_DC_DEBIT_CREDIT, else EINVAL): the blind-increment refinement
      * (GPUTX_CONFLICT_ADD) carried to the end.  Operations are grouped by
@@ -213,6 +220,44 @@ gputx_status gputx_load_table(gputx_db *db, int table, const int64_t *rows, size
  * Synchronises the database stream. */
 gputx_status gputx_read_table(gputx_db *db, int table, int64_t *rows, size_t capacity_rows,
                               size_t *n_rows);
+
+/* The primary indexes of the child and order tables (Section 3.2: tables
+ * are reached through their index), for checking them from outside.
+ *   index  0 access_info, 1 special_facility, 2 call_forwarding, 3 order.
+ *   keys   host uint64[capacity]: the raw open-addressing key array, in slot
+ *          order.  ~0 marks an empty slot, ~1 a deleted one (tombstone);
+ *          every other value is a live key:
+ *            access_info, special_facility   s_id * 4 + (type - 1)
+ *            call_forwarding                 (s_id * 4 + (sf_type - 1)) * 3 + start_time / 8
+ *            order                           (w * 10 + d) << 32 | o_id
+ *          A key sits at the first free slot at or after
+ *          mix(key) & (size - 1), probing linearly (mix = the 64-bit
+ *          finaliser of MurmurHash3), so a lookup finds it before any empty
+ *          slot.
+ *   rows   host uint32[capacity]: the table slot each key points to
+ *          (meaningful for live keys only; slots as gputx_read_slots numbers
+ *          them).
+ *   *size  receives the index size (a power of two); keys/rows == NULL only
+ *          query it.  EINVAL on an unknown index, one whose schema was not
+ *          created, or capacity < size.  Synchronises the database stream. */
+gputx_status gputx_read_index(gputx_db *db, int index, uint64_t *keys, uint32_t *rows, size_t capacity,
+                              size_t *size);
+
+/* The storage of a child or order table slot by slot, dead slots included,
+ * so that gputx_read_index's row numbers can be resolved.  `rows` (host,
+ * capacity_rows x (fields + 1) int64) receives for slot i the table's
+ * transfer-format fields (as gputx_read_table) followed by a live flag:
+ *   access_info, special_facility   slots 0 .. 4 * subscribers - 1, rows in
+ *       load order; the flag is 1 when the slot holds a loaded row (these
+ *       tables have no inserts or deletions after loading);
+ *   call_forwarding                  slots 0 .. rows ever inserted - 1; the
+ *       flag is 0 once the row was deleted;
+ *   order                            slots 0 .. order slots handed out - 1;
+ *       the flag is 0 for the slot of a new-order that aborted.
+ * *n_rows receives the slot count; rows == NULL only counts.  EINVAL on
+ * another table or capacity_rows < slots.  Synchronises the database
+ * stream. */
+gputx_status gputx_read_slots(gputx_db *db, int table, int64_t *rows, size_t capacity_rows, size_t *n_rows);
 
 /* Submits a bulk: n transactions as structure-of-arrays, ts[n] strictly
  * increasing int64 timestamps (the ids of Section 3.2), type[n] registered

@@ -42,7 +42,8 @@ OE_TYPES = (8, 9, 10)
 TABLE_FIELDS = (1, 1, 1, 5, 16, 6, 6, 5, 2, 3, 5, 1, 3, 5, 7)
 
 EXPORTED = ("gputx_create_db", "gputx_destroy_db", "gputx_last_error", "gputx_register_types",
-            "gputx_load_table", "gputx_read_table", "gputx_submit_bulk", "gputx_execute",
+            "gputx_load_table", "gputx_read_table", "gputx_read_index", "gputx_read_slots",
+            "gputx_submit_bulk", "gputx_execute",
             "gputx_sync_bulk", "gputx_read_results", "gputx_bulk_results_device",
             "gputx_output_width", "gputx_free_bulk", "gputx_version", "gputx_launch_count",
             "gputx_execute_kset_noalloc", "gputx_clock_ns", "gputx_server_create", "gputx_server_submit",
@@ -148,6 +149,8 @@ def signatures() -> dict:
         "gputx_register_types": ([p, p, C.c_int], C.c_int),
         "gputx_load_table": ([p, C.c_int, p, sz], C.c_int),
         "gputx_read_table": ([p, C.c_int, p, sz, C.POINTER(sz)], C.c_int),
+        "gputx_read_index": ([p, C.c_int, p, p, sz, C.POINTER(sz)], C.c_int),
+        "gputx_read_slots": ([p, C.c_int, p, sz, C.POINTER(sz)], C.c_int),
         "gputx_submit_bulk": ([p, p, p, p, C.c_int, sz, C.c_int, C.POINTER(p)], C.c_int),
         "gputx_execute": ([p, p, C.c_int, C.POINTER(ExecOpts)], C.c_int),
         "gputx_sync_bulk": ([p, C.POINTER(ExecStats)], C.c_int),
@@ -256,6 +259,29 @@ def gputx_read_table(db, table: int) -> np.ndarray:
     rows = np.zeros((n.value, TABLE_FIELDS[table]), dtype=np.int64)
     _check(db, lib().gputx_read_table(db, table, _ptr(rows), n.value, C.byref(n)))
     return rows[: n.value]
+
+
+INDEX_ACCESS_INFO, INDEX_SPECIAL_FACILITY, INDEX_CALL_FORWARDING, INDEX_ORDER = range(4)
+HKEY_EMPTY, HKEY_TOMB = (1 << 64) - 1, (1 << 64) - 2
+
+
+def gputx_read_index(db, index: int):
+    """(keys uint64[size], rows uint32[size]): the raw open-addressing arrays."""
+    n = C.c_size_t()
+    _check(db, lib().gputx_read_index(db, index, None, None, 0, C.byref(n)))
+    keys = np.zeros(n.value, dtype=np.uint64)
+    rows = np.zeros(n.value, dtype=np.uint32)
+    _check(db, lib().gputx_read_index(db, index, _ptr(keys), _ptr(rows), n.value, C.byref(n)))
+    return keys, rows
+
+
+def gputx_read_slots(db, table: int) -> np.ndarray:
+    """Every storage slot of a child or order table: fields + a live flag."""
+    n = C.c_size_t()
+    _check(db, lib().gputx_read_slots(db, table, None, 0, C.byref(n)))
+    rows = np.zeros((n.value, TABLE_FIELDS[table] + 1), dtype=np.int64)
+    _check(db, lib().gputx_read_slots(db, table, _ptr(rows), n.value, C.byref(n)))
+    return rows
 
 
 def gputx_submit_bulk(db, ts, type_, params, params_per_txn: int, n: int, mem: int = MEM_HOST):
@@ -407,6 +433,12 @@ class Database:
 
     def read(self, table: int) -> np.ndarray:
         return gputx_read_table(self.h, table)
+
+    def read_index(self, index: int):
+        return gputx_read_index(self.h, index)
+
+    def read_slots(self, table: int) -> np.ndarray:
+        return gputx_read_slots(self.h, table)
 
     def submit(self, ts, type_, params, mem=None) -> Bulk:
         """Host numpy arrays or CUDA tensors (mem inferred from the first)."""

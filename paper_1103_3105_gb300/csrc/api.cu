@@ -618,6 +618,114 @@ gputx_status gputx_load_table(gputx_db *db, int table, const int64_t *rows, size
     return fail(db, GPUTX_EINVAL, "table %d is read only", table);
 }
 
+gputx_status gputx_read_index(gputx_db *db, int index, uint64_t *keys, uint32_t *rows, size_t capacity,
+                              size_t *size)
+{
+    if (!db || !size) return fail(db, GPUTX_EINVAL, "bad arguments");
+    const DevDB &d = db->dev;
+    const HashIndex *h = nullptr;
+    switch (index) {
+    case 0: h = d.n_sub > 0 ? &d.ai_idx : nullptr; break;
+    case 1: h = d.n_sub > 0 ? &d.sf_idx : nullptr; break;
+    case 2: h = d.n_sub > 0 ? &d.cf_idx : nullptr; break;
+    case 3: h = d.n_wh > 0 ? &d.ord_idx : nullptr; break;
+    default: break;
+    }
+    if (!h || !h->keys) return fail(db, GPUTX_EINVAL, "index %d does not exist", index);
+    const size_t n = (size_t)h->mask + 1;
+    *size = n;
+    if (!keys && !rows) return GPUTX_OK;
+    if (!keys || !rows || capacity < n) return fail(db, GPUTX_EINVAL, "capacity %zu < index size %zu", capacity, n);
+    CK(cudaStreamWaitEvent(db->stream, db->last_done, 0), "sync");
+    CK(cudaMemcpyAsync(keys, h->keys, n * sizeof(uint64_t), cudaMemcpyDeviceToHost, db->stream), "read index");
+    CK(cudaMemcpyAsync(rows, h->rows, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, db->stream), "read index");
+    CK(cudaStreamSynchronize(db->stream), "read index");
+    return GPUTX_OK;
+}
+
+gputx_status gputx_read_slots(gputx_db *db, int table, int64_t *rows, size_t capacity_rows, size_t *n_rows)
+{
+    if (!db || !n_rows) return fail(db, GPUTX_EINVAL, "bad arguments");
+    const DevDB &d = db->dev;
+    const int f = table_fields(table);
+    CK(cudaStreamWaitEvent(db->stream, db->last_done, 0), "sync");
+    CK(cudaStreamSynchronize(db->stream), "sync");
+    InsertBase cur{};
+    CK(cudaMemcpy(&cur, db->d_cursor, sizeof cur, cudaMemcpyDeviceToHost), "cursor");
+    std::vector<std::vector<int64_t>> cols;
+    gputx_status st = GPUTX_OK;
+    auto add32 = [&](const int32_t *src, int64_t n) {
+        std::vector<int32_t> v;
+        if (!st) st = get_col(db, v, src, n);
+        cols.emplace_back(v.begin(), v.end());
+    };
+    auto add64 = [&](const int64_t *src, int64_t n) {
+        std::vector<int64_t> v;
+        if (!st) st = get_col(db, v, src, n);
+        cols.push_back(std::move(v));
+    };
+    auto add8 = [&](const uint8_t *src, int64_t n) {
+        std::vector<uint8_t> v;
+        if (!st) st = get_col(db, v, src, n);
+        cols.emplace_back(v.begin(), v.end());
+    };
+    int64_t n = 0;
+    switch (table) {
+    case GPUTX_TBL_SUB_ACCESS_INFO: {
+        if (d.n_sub <= 0) return fail(db, GPUTX_EINVAL, "subscriber schema not created");
+        n = 4 * d.n_sub;
+        add32(d.ai_sid, n); add32(d.ai_type, n);
+        std::vector<int32_t> data;
+        if (!st) st = get_col(db, data, d.ai_data, n * 4);
+        if (st) return st;
+        for (int j = 0; j < 4; j++) {
+            std::vector<int64_t> c((size_t)n);
+            for (int64_t i = 0; i < n; i++) c[i] = data[(size_t)i * 4 + j];
+            cols.push_back(std::move(c));
+        }
+        std::vector<int64_t> live((size_t)n);
+        for (int64_t i = 0; i < n; i++) live[i] = cols[1][i] >= 1;
+        cols.push_back(std::move(live));
+        break;
+    }
+    case GPUTX_TBL_SUB_SPECIAL_FACILITY: {
+        if (d.n_sub <= 0) return fail(db, GPUTX_EINVAL, "subscriber schema not created");
+        n = 4 * d.n_sub;
+        add32(d.sf_sid, n); add32(d.sf_type, n); add32(d.sf_active, n);
+        add32(d.sf_err, n); add32(d.sf_data_a, n); add32(d.sf_data_b, n);
+        if (st) return st;
+        std::vector<int64_t> live((size_t)n);
+        for (int64_t i = 0; i < n; i++) live[i] = cols[1][i] >= 1;
+        cols.push_back(std::move(live));
+        break;
+    }
+    case GPUTX_TBL_SUB_CALL_FORWARDING:
+        if (d.n_sub <= 0) return fail(db, GPUTX_EINVAL, "subscriber schema not created");
+        n = std::min<int64_t>(cur.cf, d.child_cap);
+        add32(d.cf_sid, n); add32(d.cf_type, n); add32(d.cf_start, n); add32(d.cf_end, n);
+        add32(d.cf_numberx, n); add8(d.cf_live, n);
+        break;
+    case GPUTX_TBL_OE_ORDER: {
+        if (d.n_wh <= 0) return fail(db, GPUTX_EINVAL, "order-entry schema not created");
+        n = std::min<int64_t>(cur.ord, d.ord_cap);
+        add32(d.o_w, n); add32(d.o_d, n); add64(d.o_id, n); add32(d.o_c, n); add32(d.o_cnt, n);
+        add8(d.o_live, n);
+        break;
+    }
+    default:
+        return fail(db, GPUTX_EINVAL, "table %d has no slot storage to read", table);
+    }
+    if (st) return st;
+    if ((int)cols.size() != f + 1) return fail(db, GPUTX_EINVAL, "table %d layout", table);
+    *n_rows = (size_t)n;
+    if (!rows) return GPUTX_OK;
+    if (capacity_rows < (size_t)n) return fail(db, GPUTX_EINVAL, "capacity %zu < %lld slots", capacity_rows,
+                                               (long long)n);
+    for (int64_t i = 0; i < n; i++)
+        for (int j = 0; j <= f; j++) rows[i * (f + 1) + j] = cols[j][i];
+    return GPUTX_OK;
+}
+
 gputx_status gputx_read_table(gputx_db *db, int table, int64_t *rows, size_t capacity_rows, size_t *n_rows)
 {
     if (!db || !n_rows) return fail(db, GPUTX_EINVAL, "bad arguments");
@@ -963,10 +1071,18 @@ gputx_status gputx_execute(gputx_db *db, gputx_bulk *b, int strategy, const gput
     int64_t m = 0;
     int run = strategy;
 
-    if (strategy == GPUTX_KSET || strategy == GPUTX_AUTO) {
+    // AUTO on a database whose only registered type is debit-credit: the
+    // segmented-sum strategy gives Definition 1's results bit for bit and
+    // moves each transaction once, whatever the depth of its graph
+    if (strategy == GPUTX_AUTO && db->dev.registered == (1u << GPUTX_T_DC_DEBIT_CREDIT)) run = GPUTX_SCAN;
+    if (strategy == GPUTX_KSET || (strategy == GPUTX_AUTO && run == GPUTX_AUTO)) {
         if ((st = run_kset_analysis(b, mode, part_size, sk, sv, ak, av, m))) return st;
         CK(launch_rank_scan(b, sk, sv, m, db->need_fixpoint), "rank");
-        if (db->need_fixpoint) CK(launch_fixpoint_device(b, sv, m), "fixpoint");
+        // AUTO decides on the one-pass ranks first: w0 and c are exact there
+        // (a transaction is a source exactly when all its operations have
+        // rank 0), and the one-pass depth bounds the exact one from below.
+        // The refinement rounds run only once K-SET is chosen.
+        if (db->need_fixpoint && strategy == GPUTX_KSET) CK(launch_fixpoint_device(b, sv, m), "fixpoint");
         CK(launch_level_stats(b), "stats");
         if ((st = read_ctl(b))) return st;
         if (b->host_ctl.err) {
@@ -984,6 +1100,17 @@ gputx_status gputx_execute(gputx_db *db, gputx_bulk *b, int strategy, const gput
             // (Section 5.2); the sorted operations are reused for tickets
             if (run == GPUTX_TPL && c && (c <= db->cfg.part_c_max || d >= db->cfg.part_d_min))
                 b->fallback = 1;
+            if (run == GPUTX_KSET && db->need_fixpoint) {
+                // exact depths for the level schedule (Property 1)
+                CK(launch_fixpoint_device(b, sv, m), "fixpoint");
+                CK(cudaMemsetAsync(&b->ctl->depth, 0, 2 * sizeof(uint32_t), s), "stats");
+                CK(launch_level_stats(b), "stats");
+                if ((st = read_ctl(b))) return st;
+                if (b->host_ctl.err) {
+                    CK(cudaEventRecord(b->ev[7], s), "event");
+                    return GPUTX_OK;
+                }
+            }
         }
     }
     if (run == GPUTX_KSET) {

@@ -207,8 +207,8 @@ def gpu_logical_state(db, dc=False, sub=False, oe=False, n_sub=0, n_wh=0, n_item
         ce = np.zeros((n_sub, 4, 3), dtype=np.int32)
         cn = np.zeros((n_sub, 4, 3), dtype=np.int32)
         idx = (cf[:, 0], cf[:, 1] - 1, cf[:, 2] // 8)
-        assert not cp[idx].any() and len(set(zip(*[x.tolist() for x in idx]))) == len(cf), \
-            "duplicate live call_forwarding key"
+        flat = (cf[:, 0] * 4 + (cf[:, 1] - 1)) * 3 + cf[:, 2] // 8
+        assert len(np.unique(flat)) == len(cf), "duplicate live call_forwarding key"
         cp[idx] = True
         ce[idx] = cf[:, 3]
         cn[idx] = cf[:, 4]
@@ -226,3 +226,115 @@ def gpu_logical_state(db, dc=False, sub=False, oe=False, n_sub=0, n_wh=0, n_item
         st["orders"] = _sorted_rows(db.read(G.TBL_OE_ORDER))
         st["order_lines"] = _sorted_rows(db.read(G.TBL_OE_ORDER_LINE))
     return st
+
+
+# ---------------------------------------------------------------------------
+# primary-index consistency (the survey's "every live row is found by its
+# key, and every index entry points to a live row with that key")
+# ---------------------------------------------------------------------------
+HKEY_EMPTY = np.uint64((1 << 64) - 1)
+HKEY_TOMB = np.uint64((1 << 64) - 2)
+
+
+def murmur_fmix64(k):
+    """The 64-bit finaliser of MurmurHash3 (Appleby), the index's hash."""
+    k = np.asarray(k, dtype=np.uint64).copy()
+    with np.errstate(over="ignore"):
+        k ^= k >> np.uint64(33)
+        k *= np.uint64(0xFF51AFD7ED558CCD)
+        k ^= k >> np.uint64(33)
+        k *= np.uint64(0xC4CEB9FE1A85EC53)
+        k ^= k >> np.uint64(33)
+    return k
+
+
+def slot_keys(table, slots):
+    """Index key of every storage slot (rows of gputx_read_slots)."""
+    import paper_1103_3105_gb300 as G
+    s = slots.astype(np.int64)
+    if table in (G.TBL_SUB_ACCESS_INFO, G.TBL_SUB_SPECIAL_FACILITY):
+        return (s[:, 0] * 4 + (s[:, 1] - 1)).astype(np.uint64)
+    if table == G.TBL_SUB_CALL_FORWARDING:
+        return ((s[:, 0] * 4 + (s[:, 1] - 1)) * 3 + s[:, 2] // 8).astype(np.uint64)
+    if table == G.TBL_OE_ORDER:
+        return ((((s[:, 0] * 10 + s[:, 1]) << 32) | (s[:, 2] & 0xFFFFFFFF))).astype(np.uint64)
+    raise ValueError(table)
+
+
+def index_violations(keys, rows, slots, table, expected_keys):
+    """Checks one open-addressing index against its table's slots.
+
+    keys/rows: the raw index arrays; slots: the table's storage with a live
+    flag in the last column; expected_keys: the live keys of the oracle's
+    table.  Returns a list of violations (empty when the index is exact)."""
+    bad = []
+    size = len(keys)
+    if size == 0 or size & (size - 1):
+        return [f"index size {size} is not a power of two"]
+    mask = np.uint64(size - 1)
+    occ = (keys != HKEY_EMPTY) & (keys != HKEY_TOMB)
+    pos = np.flatnonzero(occ)
+    k = keys[pos]
+    r = rows[pos].astype(np.int64)
+    if len(r) and r.max() >= len(slots):
+        return [f"entry points past the table ({r.max()} >= {len(slots)})"]
+    if not (slots[r, -1] == 1).all():
+        bad.append(f"{int((slots[r, -1] != 1).sum())} entries point at dead rows")
+    sk = slot_keys(table, slots[r])
+    if not np.array_equal(sk, k):
+        bad.append(f"{int((sk != k).sum())} entries point at a row with another key")
+    if len(np.unique(k)) != len(k):
+        bad.append("a key is indexed twice")
+    if len(np.unique(r)) != len(r):
+        bad.append("a row is indexed twice")
+    n_live = int(slots[:, -1].sum())
+    if n_live != len(k):
+        bad.append(f"{n_live} live rows but {len(k)} index entries")
+    # a lookup probes linearly from the key's home slot and stops at the
+    # first empty slot: no empty slot may lie between home and the key
+    home = (murmur_fmix64(k) & mask).astype(np.int64)
+    dist = (pos - home) & (size - 1)
+    empty = (keys == HKEY_EMPTY).astype(np.int64)
+    cs = np.concatenate([[0], np.cumsum(np.concatenate([empty, empty]))])
+    gaps = cs[home + dist] - cs[home]
+    if (gaps > 0).any():
+        bad.append(f"{int((gaps > 0).sum())} keys sit behind an empty slot (not found by a lookup)")
+    exp = np.sort(np.asarray(expected_keys, dtype=np.uint64))
+    if not np.array_equal(np.sort(k), exp):
+        bad.append(f"key set differs from the oracle's ({len(k)} vs {len(exp)} keys)")
+    return bad
+
+
+def oracle_index_keys(o, table):
+    """Live keys of the oracle's child or order table."""
+    import paper_1103_3105_gb300 as G
+    if table == G.TBL_SUB_ACCESS_INFO:
+        return np.flatnonzero(o["ai_present"].reshape(-1)).astype(np.uint64)
+    if table == G.TBL_SUB_SPECIAL_FACILITY:
+        return np.flatnonzero(o["sf_present"].reshape(-1)).astype(np.uint64)
+    if table == G.TBL_SUB_CALL_FORWARDING:
+        return np.flatnonzero(o["cf_present"].reshape(-1)).astype(np.uint64)
+    if table == G.TBL_OE_ORDER:
+        od = o.orders()
+        return (((od[:, 0] * 10 + od[:, 1]) << 32) | od[:, 2]).astype(np.uint64)
+    raise ValueError(table)
+
+
+def check_indexes(g, o, sub=False, oe=False):
+    """Every primary index of the engine's database against its table and
+    the oracle's live keys; returns {index name: violations}."""
+    import paper_1103_3105_gb300 as G
+    pairs = []
+    if sub:
+        pairs += [(G.INDEX_ACCESS_INFO, G.TBL_SUB_ACCESS_INFO), (G.INDEX_SPECIAL_FACILITY, G.TBL_SUB_SPECIAL_FACILITY),
+                  (G.INDEX_CALL_FORWARDING, G.TBL_SUB_CALL_FORWARDING)]
+    if oe:
+        pairs += [(G.INDEX_ORDER, G.TBL_OE_ORDER)]
+    out = {}
+    for idx, table in pairs:
+        keys, rows = g.read_index(idx)
+        slots = g.read_slots(table)
+        v = index_violations(keys, rows, slots, table, oracle_index_keys(o, table))
+        if v:
+            out[table] = v
+    return out

@@ -12,7 +12,7 @@ import pytest
 import oracle
 import paper_1103_3105_gb300 as G
 import workloads as W
-from tests._helpers import gpu_logical_state, oracle_logical_state, state_diff, states_equal
+from tests._helpers import check_indexes, gpu_logical_state, oracle_logical_state, state_diff, states_equal
 
 pytestmark = pytest.mark.gpu
 
@@ -103,4 +103,31 @@ def test_mixed_schema_stream_through_graphs():
     gs = gpu_logical_state(g, dc=True, sub=True, n_sub=n_sub)
     os_ = oracle_logical_state(o)
     assert states_equal(gs, os_), state_diff(gs, os_)
+    g.close()
+
+
+def test_config4_stream_at_full_size():
+    """The benchmark's batched order-entry run: 64 warehouses x 10 districts
+    x 3,000 customers, 100,000 items, 18 uneven bulks of 2^10..2^21 (4.28M
+    transactions) through the tuned graph batcher.  Every output, every
+    table and the order index equal serial execution of the whole stream."""
+    n_wh, n_items = 64, 100_000
+    init = W.oe_tables(n_wh, n_items=n_items, seed=W.seed_for(4))
+    sizes, bulk = W.oe_stream(3_000_000, n_wh, n_items)
+    total = sum(sizes)
+    cap = 2 * total + (1 << 22)
+    g = G.Database(oe=(n_wh, n_items), order_capacity=cap, orderline_capacity=cap * 15, max_bulk=1 << 21)
+    g.register(G.OE_TYPES)
+    for t, rows in W.oe_rows(init).items():
+        g.load(t, rows)
+    bt = G.Batcher(g, tune=True, params_per_txn=W.OE_PARAMS, bulk_size_max=1 << 21)
+    st, out = bt.run(bulk["ts"], bulk["type"], bulk["params"])
+    bt.close()
+    o = oracle.OracleDB(oe=init, ord_cap=total, ol_cap=total * 15, oid_cap=1 << 16)
+    ost, oout = o.execute(bulk, R=g.width)
+    bad = np.flatnonzero((st != ost) | (out != oout).any(axis=1))
+    assert len(bad) == 0, (len(bad), bad[:5])
+    gs, os_ = gpu_logical_state(g, oe=True), oracle_logical_state(o)
+    assert states_equal(gs, os_), state_diff(gs, os_)
+    assert not check_indexes(g, o, oe=True)
     g.close()

@@ -207,7 +207,8 @@ def test_bounded_wait_reports_timeout(strategy, launch):
     g2.close()
 
 
-@pytest.mark.parametrize("strategy,mode", [("kset", 0), ("kset", 1), ("tpl", 1), ("part", 0), ("scan", 0)])
+@pytest.mark.parametrize("strategy,mode", [("kset", 0), ("kset", 1), ("tpl", 0), ("tpl", 1), ("part", 0),
+                                           ("scan", 0), ("auto", 0)])
 def test_full_size_config2(strategy, mode):
     """The benchmark's workload: 1,000 branches, 10,000 tellers, 10,000,000
     accounts, a bulk of 2^22 transactions, in the benchmark's launch shape.
@@ -216,8 +217,36 @@ def test_full_size_config2(strategy, mode):
     g, o = make_pair(1000, 10000, A, 1 << 22, max_bulk=1 << 22)
     bulk = W.dc_bulk(1 << 22, A, 0.0, seed=W.seed_for(2, 22))
     stats, st, out, ost, oout = run_both(g, o, bulk, strategy, mode)
+    if strategy == "auto":
+        assert stats["strategy"] == G.SCAN   # a debit-credit-only database
     assert np.array_equal(st, ost)
     assert np.array_equal(out, oout)
+    assert np.array_equal(g.read(G.TBL_DC_ACCOUNT)[:, 0], o["acc_bal"])
+    assert np.array_equal(g.read(G.TBL_DC_BRANCH)[:, 0], o["br_bal"])
+    assert np.array_equal(g.read(G.TBL_DC_TELLER)[:, 0], o["tel_bal"])
+    h = g.read(G.TBL_DC_HISTORY)
+    assert np.array_equal(h[np.argsort(h[:, 0])], o.history())
+    g.close()
+
+
+@pytest.mark.parametrize("lg", [20, 22])
+@pytest.mark.parametrize("strategy,mode", [("kset", 0), ("kset", 1), ("part", 0), ("tpl", 0), ("tpl", 1)])
+def test_hot_accounts_at_sweep_sizes(lg, strategy, mode):
+    """Zipf 0.99 accounts at the sweep's 2^20 and 2^22 transactions over the
+    benchmark's tables: hot accounts make graphs thousands of levels deep,
+    a hot branch partition and long lock chains.  Every output and the
+    whole state are compared."""
+    A = 10_000_000
+    g, o = make_pair(1000, 10000, A, 1 << lg, max_bulk=1 << lg)
+    bulk = W.dc_bulk(1 << lg, A, 0.99, seed=W.seed_for(2, 199 + lg))
+    stats, st, out, ost, oout = run_both(g, o, bulk, strategy, mode)
+    assert np.array_equal(st, ost)
+    assert np.array_equal(out, oout)
+    if strategy == "kset":
+        ob = oracle.OracleDB(dc=W.dc_tables(1000, 10000, A), hist_cap=1)
+        obj, cls, root = ob.extract(bulk, mode, 3)
+        lv = oracle.levels(obj, cls, ob.num_objects())
+        assert (stats["depth"], stats["w0"]) == (int(lv.max()), int((lv == 0).sum()))
     assert np.array_equal(g.read(G.TBL_DC_ACCOUNT)[:, 0], o["acc_bal"])
     assert np.array_equal(g.read(G.TBL_DC_BRANCH)[:, 0], o["br_bal"])
     assert np.array_equal(g.read(G.TBL_DC_TELLER)[:, 0], o["tel_bal"])

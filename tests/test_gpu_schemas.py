@@ -10,7 +10,7 @@ import pytest
 import oracle
 import paper_1103_3105_gb300 as G
 import workloads as W
-from tests._helpers import gpu_logical_state, oracle_logical_state, state_diff, states_equal
+from tests._helpers import check_indexes, gpu_logical_state, oracle_logical_state, state_diff, states_equal
 
 pytestmark = pytest.mark.gpu
 
@@ -62,6 +62,10 @@ def check(g, o, st, out, ost, oout, **kw):
     assert len(bad) == 0, (len(bad), bad[:5], st[bad[:5]], ost[bad[:5]], out[bad[:3]], oout[bad[:3]])
     gs, os_ = gpu_logical_state(g, **kw), oracle_logical_state(o)
     assert states_equal(gs, os_), state_diff(gs, os_)
+    # the primary indexes themselves: every live row found by its key, every
+    # entry pointing at a live row with that key
+    bad = check_indexes(g, o, sub=kw.get("sub", False), oe=kw.get("oe", False))
+    assert not bad, bad
 
 
 # ---------------------------------------------------------------------------
@@ -103,11 +107,8 @@ def test_subscriber_full_size():
     bulk = W.sub_bulk(1 << 20, n_sub, 0.8, seed=W.seed_for(3, 1))
     _, st, out, ost, oout = run_both(g, o, bulk, "kset")
     assert np.array_equal(st, ost) and np.array_equal(out, oout)
-    sub = g.read(G.TBL_SUB_SUBSCRIBER).astype(np.int32)
-    assert np.array_equal(sub, o["sub"])
-    cf = g.read(G.TBL_SUB_CALL_FORWARDING)
-    assert len(cf) == int(o["cf_present"].sum())
-    assert o["cf_present"][cf[:, 0], cf[:, 1] - 1, cf[:, 2] // 8].all()
+    # every table, child-row fields included, and the three indexes
+    check(g, o, st, out, ost, oout, sub=True, n_sub=n_sub)
     g.close()
 
 
@@ -153,6 +154,33 @@ def test_order_entry_part_falls_back_on_cross_partition():
     local = W.oe_bulk(4000, 4, n_items=300, remote_frac=0.0, seed=9, ts0=4000)
     stats, st, out, ost, oout = run_both(g, o, local, "part")
     assert stats["fallback"] == 0 and stats["strategy"] == G.PART
+    check(g, o, st, out, ost, oout, oe=True)
+    g.close()
+
+
+@pytest.mark.parametrize("mode", [G.CONFLICT_PAPER, G.CONFLICT_ADD])
+def test_auto_refines_only_for_kset(mode):
+    """AUTO decides on the one-pass ranks: a TPL or PART pick runs no
+    refinement round; a K-SET pick (forced by a zero 0-set threshold) runs
+    them and reaches the exact longest-path depths."""
+    n_wh, n_items = 3, 200
+    bulk = W.oe_bulk(6000, n_wh, n_items=n_items, remote_frac=0.2, invalid_frac=0.02, seed=78)
+    ob = oracle.OracleDB(oe=W.oe_tables(n_wh, n_items=n_items, seed=2), ord_cap=1, ol_cap=1, oid_cap=1)
+    obj, cls, root = ob.extract(bulk, mode, oracle.MAX_OPS)
+    lv = oracle.levels(obj, cls, ob.num_objects())
+    d, w0, c = oracle.graph_stats(lv, root)
+    # Algorithm 1's K-SET threshold above any 0-set: TPL (c > 0), no rounds
+    g, o = oe_pair(n_wh, n_items, kset_w0_min=1 << 30)
+    stats, st, out, ost, oout = run_both(g, o, bulk, "auto", mode)
+    assert stats["strategy"] == G.TPL and stats["fixpoint_rounds"] == 0
+    assert stats["w0"] == w0 and stats["cross"] == c and stats["depth"] <= d
+    check(g, o, st, out, ost, oout, oe=True)
+    g.close()
+    # threshold 1: K-SET, refined to the exact depths
+    g, o = oe_pair(n_wh, n_items, kset_w0_min=1)
+    stats, st, out, ost, oout = run_both(g, o, bulk, "auto", mode)
+    assert stats["strategy"] == G.KSET and stats["fixpoint_rounds"] > 0
+    assert (stats["depth"], stats["w0"], stats["cross"]) == (d, w0, c)
     check(g, o, st, out, ost, oout, oe=True)
     g.close()
 

@@ -13,7 +13,7 @@ import pytest
 import oracle
 import paper_1103_3105_gb300 as G
 import workloads as W
-from tests._helpers import gpu_logical_state, oracle_logical_state, state_diff, states_equal
+from tests._helpers import check_indexes, gpu_logical_state, oracle_logical_state, state_diff, states_equal
 
 pytestmark = pytest.mark.gpu
 
@@ -186,4 +186,88 @@ def test_admission_refuses_what_does_not_fit():
     stats = srv.stats()
     assert stats["completed"] == 4000 and stats["refused"] == 4000 + 1500
     srv.close()
+    g.close()
+
+
+def test_admission_by_free_device_memory():
+    """With min_free_bytes set, a submission is refused (ENOMEM, counted)
+    while free device memory is below the limit, and the same submission is
+    admitted once memory is freed."""
+    import torch
+    torch.cuda.init()
+    g = dc_db()
+    bulk = W.dc_bulk(2000, 10_000, 0.0, seed=2)
+    probe = G.Server(g, deadline_us=100, max_bulk=1024)   # the server's own allocations
+    probe.submit(bulk["type"][:10], bulk["params"][:10])
+    probe.drain()
+    probe.close()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    limit = free0 - (2 << 30)
+    srv = G.Server(g, deadline_us=100, max_bulk=1024, min_free_bytes=limit)
+    srv.submit(bulk["type"][:500], bulk["params"][:500])  # 2 GiB above the limit: admitted
+    srv.drain()
+    hog = torch.empty(6 << 30, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] < limit
+    with pytest.raises(G.GputxError) as e:
+        srv.submit(bulk["type"][500:2000], bulk["params"][500:2000])
+    assert e.value.status == G.ENOMEM
+    assert srv.stats()["refused"] == 1500
+    del hog
+    torch.cuda.empty_cache()
+    torch.cuda.synchronize()
+    srv.submit(bulk["type"][500:2000], bulk["params"][500:2000])
+    srv.drain()
+    st, vals, _, nd = srv.results(0, 2000)
+    stats = srv.stats()
+    srv.close()
+    assert nd == 2000 and stats["completed"] == 2000 and stats["refused"] == 1500
+    o = oracle.OracleDB(dc=W.dc_tables(10, 100, 10_000), hist_cap=1 << 20)
+    o.execute({"ts": bulk["ts"][:10], "type": bulk["type"][:10], "params": bulk["params"][:10], "P": 2}, R=1)
+    ost, oout = o.execute(bulk, R=1)
+    assert np.array_equal(st, ost) and np.array_equal(vals, oout)
+    g.close()
+
+
+def test_served_mix_config5_against_the_oracle():
+    """The served mix: debit-credit (10M accounts) and subscriber (2M
+    subscribers with their child tables) in one device-resident database,
+    a 50/50 mix submitted open-loop at Poisson arrival times (5M txn/s,
+    1 ms deadline, three bulks in flight).  The whole served stream equals
+    serial execution in id order: every result, every table, every index."""
+    A, n_sub, n = 10_000_000, 2_000_000, 1_000_000
+    sub = W.sub_tables(n_sub, seed=W.seed_for(5, 1))
+    dc = W.dc_tables(1000, 10_000, A)
+    g = G.Database(dc=(1000, 10_000, A), sub=n_sub, history_capacity=n, sub_child_capacity=6 * n_sub,
+                   max_bulk=1 << 20)
+    g.register(G.DC_TYPES + G.SUB_TYPES)
+    for rows in (W.dc_rows(dc), W.sub_rows(sub)):
+        for t, r in rows.items():
+            g.load(t, r)
+    bulk = W.served_mix(n, A, n_sub, 0.0, 5e6)
+    srv = G.Server(g, deadline_us=1000, max_bulk=1 << 20, max_inflight=3, params_per_txn=bulk["P"])
+    t0 = G.gputx_clock_ns() + 2_000_000
+    arrivals = t0 + bulk["arrival_offset_ns"]
+    i = 0
+    while i < n:
+        j = int(np.searchsorted(arrivals, G.gputx_clock_ns(), side="right"))
+        if j > i:
+            srv.submit(bulk["type"][i:j], bulk["params"][i:j], arrivals[i:j])
+            i = j
+        else:
+            time.sleep(20e-6)
+    srv.drain()
+    st, vals, _, nd = srv.results(0, n)
+    stats = srv.stats()
+    srv.close()
+    assert nd == n and stats["completed"] == n and stats["bulks"] > 1
+    o = oracle.OracleDB(dc=dc, sub=sub, hist_cap=n)
+    ost, oout = o.execute(bulk, R=g.width)
+    bad = np.flatnonzero((st != ost) | (vals != oout).any(axis=1))
+    assert len(bad) == 0, (len(bad), bad[:5])
+    gs = gpu_logical_state(g, dc=True, sub=True, n_sub=n_sub)
+    os_ = oracle_logical_state(o)
+    assert states_equal(gs, os_), state_diff(gs, os_)
+    assert not check_indexes(g, o, sub=True)
     g.close()

@@ -54,6 +54,62 @@ def test_noalloc_matches_regular_entry_point_on_two_calls_in_a_row():
     nal.close()
 
 
+def _schema_pair(G, W, schema):
+    """Two identical databases of the subscriber or order-entry schema."""
+    dbs = []
+    for _ in range(2):
+        if schema == "sub":
+            g = G.Database(sub=300, sub_child_capacity=1 << 14, max_bulk=1 << 14)
+            g.register(G.SUB_TYPES)
+            for t, r in W.sub_rows(W.sub_tables(300, seed=21)).items():
+                g.load(t, r)
+        else:
+            g = G.Database(oe=(2, 500), order_capacity=1 << 15, orderline_capacity=15 << 15, max_bulk=1 << 14)
+            g.register(G.OE_TYPES)
+            for t, r in W.oe_rows(W.oe_tables(2, n_items=500, seed=22)).items():
+                g.load(t, r)
+        dbs.append(g)
+    return dbs
+
+
+@pytest.mark.parametrize("schema", ["sub", "oe"])
+def test_noalloc_matches_regular_entry_point_on_other_schemas(schema):
+    """Multi-item order-entry transactions (uneven operation counts, insert
+    slots for orders and order lines, refinement rounds) and subscriber
+    bulks with call-forwarding inserts and deletes: status, outputs and every
+    table equal the regular K-SET path's, on two calls in a row."""
+    torch = pytest.importorskip("torch")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1103_3105_gb300 as G
+    import workloads as W
+    from tests._helpers import gpu_logical_state, state_diff, states_equal
+
+    ref, nal = _schema_pair(G, W, schema)
+    ts0 = 0
+    for k, (n, mode) in enumerate([(5000, G.CONFLICT_PAPER), (7000, G.CONFLICT_ADD)]):
+        if schema == "sub":
+            bulk = W.sub_bulk(n, 300, 0.5, seed=600 + k, ts0=ts0, mix=(0.1, 0.05, 0.15, 0.05, 0.05, 0.35, 0.25))
+        else:
+            bulk = W.oe_bulk(n, 2, n_items=500, remote_frac=0.1, invalid_frac=0.02, seed=700 + k, ts0=ts0)
+        ts0 += n
+        b = ref.submit_dict(bulk).execute("kset", conflict_mode=mode)
+        st_ref, out_ref = b.results()
+        b.free()
+        d = {key: torch.from_numpy(bulk[key]).cuda() for key in ("ts", "type", "params")}
+        st = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+        out = torch.full((n, nal.width), -7, dtype=torch.int64, device="cuda")
+        torch.cuda.synchronize()
+        G.gputx_execute_kset_noalloc(nal.h, d["ts"], d["type"], d["params"], bulk["P"], n, mode, st, out)
+        assert np.array_equal(st.cpu().numpy(), st_ref), k
+        assert np.array_equal(out.cpu().numpy(), out_ref), k
+    kw = {"sub": True, "n_sub": 300} if schema == "sub" else {"oe": True}
+    a, b = gpu_logical_state(ref, **kw), gpu_logical_state(nal, **kw)
+    assert states_equal(a, b), state_diff(a, b)
+    ref.close()
+    nal.close()
+
+
 def test_noalloc_rejects_a_bulk_beyond_its_working_memory():
     torch = pytest.importorskip("torch")
     import __graft_entry__

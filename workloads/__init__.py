@@ -422,3 +422,39 @@ def concat_bulks(parts, pick) -> dict:
         params[m, : p["P"]] = p["params"][m]
         types[m] = p["type"][m]
     return {"ts": np.arange(n, dtype=np.int64), "type": types, "params": params, "P": P}
+
+
+def uneven_sizes(total: int, lo_log2: float = 10, hi_log2: float = 21, seed: int = 0) -> list:
+    """Bulk sizes 2^U(lo_log2, hi_log2) (log-uniform, seeded), drawn until
+    they add up to at least ``total``."""
+    rng = np.random.default_rng(seed)
+    sizes, acc = [], 0
+    while acc < total:
+        k = int(2 ** rng.uniform(lo_log2, hi_log2))
+        sizes.append(k)
+        acc += k
+    return sizes
+
+
+def oe_stream(total: int, n_wh: int = 64, n_items: int = 100_000) -> tuple:
+    """The batched order-entry stream: uneven bulk sizes 2^10..2^21 adding
+    up to at least ``total`` transactions, and one order-entry bulk holding
+    all of them in timestamp order.  Returns (sizes, bulk)."""
+    sizes = uneven_sizes(total, 10, 21, seed=seed_for(4, 1))
+    bulk = oe_bulk(sum(sizes), n_wh, n_items=n_items, seed=seed_for(4, 2))
+    return sizes, bulk
+
+
+def served_mix(n: int, n_accounts: int, n_sub: int, theta: float, rate: float, seed_variant: int = 0) -> dict:
+    """The served mix: n transactions, half debit-credit (accounts
+    uniform/Zipf theta over n_accounts) and half subscriber (the 30/25/25/
+    8/8/2/2 mix over n_sub subscribers), interleaved at random, with
+    open-loop Poisson arrival offsets (ns) at ``rate`` transactions/s."""
+    rng = np.random.default_rng(seed_for(5, seed_variant))
+    tag = int(rate // 1e6)
+    parts = [dc_bulk(n, n_accounts, theta, seed=seed_for(5, tag)),
+             sub_bulk(n, n_sub, theta, seed=seed_for(5, 50 + tag))]
+    bulk = concat_bulks(parts, rng.integers(0, 2, size=n))
+    gaps = rng.exponential(1e9 / rate, size=n)
+    bulk["arrival_offset_ns"] = np.cumsum(gaps).astype(np.int64)
+    return bulk
