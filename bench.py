@@ -460,7 +460,8 @@ def run_sweep(args, G, torch, dev, stream, flush):
 
 def run_serving(args, G, torch, stream):
     """The served mix: debit-credit and subscriber schemas loaded together in a
-    device-resident database of about 20 GB, open-loop Poisson arrivals of a
+    device-resident database of about 20 GB of live rows (22M subscribers
+    with their child tables and indexes), open-loop Poisson arrivals of a
     50/50 mix of the two schemas' transactions.  Three serving modes:
     continuous batching (several bulks in flight), the plain per-bulk path
     (one bulk at a time, closed every deadline) and incremental 0-set
@@ -469,25 +470,36 @@ def run_serving(args, G, torch, stream):
     rates = [float(r) for r in args.serve_rates.split(",")]
     deadlines = [int(d) for d in args.serve_deadlines_us.split(",")]
     n_sub = args.serve_subscribers
-    total = int(sum(rates) * args.serve_seconds * len(deadlines) * 3) + (1 << 22)
+    skewed_rates = [r for r in rates if r >= 20e6]
+    total = int((sum(rates) * len(deadlines) * 3 + sum(skewed_rates) * 2) * args.serve_seconds) + (1 << 22)
     free0 = torch.cuda.mem_get_info()[0]
-    # history rows fill the database to the configured size (at least what
-    # every served transaction needs)
-    hist_rows = max(total, int(args.serve_db_gb * 1e9 / 40))
+    # the database's size comes from its live rows (subscribers with their
+    # child tables and indexes, 10M accounts); history holds what the served
+    # transactions append, nothing more
+    hist_rows = total
     db = G.Database(dc=(BRANCHES, TELLERS, ACCOUNTS), sub=n_sub, history_capacity=hist_rows,
                     sub_child_capacity=6 * n_sub, max_bulk=1 << 20, stream=stream.cuda_stream)
     db.register(G.DC_TYPES + G.SUB_TYPES)
-    for t, r in W.sub_rows(W.sub_tables(n_sub, seed=W.seed_for(5, 1))).items():
+    sub_t = W.sub_tables(n_sub, seed=W.seed_for(5, 1))
+    for t, r in W.sub_rows(sub_t).items():
         db.load(t, r)
     torch.cuda.synchronize()
     db_bytes = free0 - torch.cuda.mem_get_info()[0]
     mode = G.CONFLICT_ADD if args.mode == "add" else G.CONFLICT_PAPER
-    for ri, rate in enumerate(rates):
+    # every rate and deadline at the benchmark's skew, then the high rates
+    # with Zipf 0.8 keys at the shorter deadline: hot subscribers and
+    # accounts make each bulk's k-set chain long, so its GPU time matters
+    plan = [(rate, args.theta, deadlines, ri) for ri, rate in enumerate(rates)]
+    plan += [(rate, 0.8, deadlines[:1], 100 + ri) for ri, rate in enumerate(skewed_rates)]
+    for rate, theta, dls, variant in plan:
         n = int(rate * args.serve_seconds)
-        bulk = W.served_mix(n, ACCOUNTS, n_sub, args.theta, rate, seed_variant=ri)
+        bulk = W.served_mix(n, ACCOUNTS, n_sub, theta, rate, seed_variant=variant)
         offs = bulk["arrival_offset_ns"]
-        for deadline in deadlines:
-            for label, inflight, zero in (("continuous", 3, False), ("plain", 1, False), ("zero_set", 1, True)):
+        for deadline in dls:
+            modes = (("continuous", 3, False), ("plain", 1, False), ("zero_set", 1, True))
+            if theta != args.theta:
+                modes = modes[:2]
+            for label, inflight, zero in modes:
                 if zero and rate > args.serve_zero_set_max_rate:
                     out.append({"offered_txn_per_s": rate, "deadline_us": deadline, "mode": label,
                                 "skipped": "rate above --serve-zero-set-max-rate"})
@@ -509,13 +521,27 @@ def run_serving(args, G, torch, stream):
                 srv.drain()
                 st = srv.stats()
                 srv.close()
-                out.append({"offered_txn_per_s": rate, "deadline_us": deadline, "mode": label,
+                out.append({"offered_txn_per_s": rate, "deadline_us": deadline, "mode": label, "theta": theta,
                             "max_inflight": inflight, "txn": n, "p50_us": st["p50_us"], "p99_us": st["p99_us"],
                             "mean_us": st["mean_us"], "txn_per_s": st["txn_per_s"], "bulks": st["bulks"],
                             "max_bulk": st["max_bulk_seen"]})
     db.close()
-    return {"db_bytes": int(db_bytes), "subscribers": n_sub, "accounts": ACCOUNTS, "history_rows": hist_rows,
-            "mix": "50% debit-credit, 50% subscriber (30/25/25/8/8/2/2)", "runs": out}
+    res = {"db_bytes": int(db_bytes), "subscribers": n_sub, "accounts": ACCOUNTS, "history_rows": hist_rows,
+           "mix": "50% debit-credit, 50% subscriber (30/25/25/8/8/2/2)", "runs": out}
+    if args.cpu_baseline:
+        # the oracle on a bounded sample of the served stream (1M transactions)
+        import oracle
+        oracle.build()
+        m = 1_000_000
+        o = oracle.OracleDB(dc=W.dc_tables(BRANCHES, TELLERS, ACCOUNTS), sub=sub_t, hist_cap=m)
+        bulk = W.served_mix(m, ACCOUNTS, n_sub, args.theta, 5e6)
+        t1 = time.perf_counter()
+        o.execute(bulk, R=8)
+        dt = time.perf_counter() - t1
+        res["cpu_baseline"] = {"value": m / dt, "unit": "txn/s", "cores": 1, "nproc": os.cpu_count(),
+                               "kind": "oracle", "sample": f"{m} transactions of the served mix, serial "
+                                                           f"execution in id order, {dt:.2f} s"}
+    return res
 
 
 def run_subscriber(args, G, torch, stream):
@@ -530,7 +556,6 @@ def run_subscriber(args, G, torch, stream):
     db.register(G.SUB_TYPES)
     for t, r in W.sub_rows(tabs).items():
         db.load(t, r)
-    del tabs
     setup_s = time.perf_counter() - t0
     out = []
     ts0 = 0
@@ -570,20 +595,54 @@ def run_subscriber(args, G, torch, stream):
                         "exec_ms": st["ms_execute"], "analysis_ms": st["ms_analysis"], "ran": st["strategy"]})
             out.append(rec)
     db.close()
-    return {"subscribers": n_sub, "setup_s": setup_s, "runs": out}
+    res = {"subscribers": n_sub, "setup_s": setup_s, "runs": out}
+    if args.cpu_baseline:
+        # the oracle on one bulk of the same workload (Zipf 0.8)
+        import oracle
+        oracle.build()
+        o = oracle.OracleDB(sub=tabs)
+        bulk = W.sub_bulk(n, n_sub, 0.8, seed=W.seed_for(3, 18))
+        t1 = time.perf_counter()
+        o.execute(bulk, R=8)
+        dt = time.perf_counter() - t1
+        res["cpu_baseline"] = {"value": n / dt, "unit": "txn/s", "cores": 1, "nproc": os.cpu_count(),
+                               "kind": "oracle", "sample": f"one bulk of {n} transactions (Zipf 0.8), serial "
+                                                           f"execution in timestamp order, {dt:.2f} s"}
+    return res
+
+
+# algorithmic bytes of one order-entry transaction at the mix (45 % new-order
+# with 10 lines on average, 43 % payment, 12 % order-status), one 32 B sector
+# per random cell, read + write for an updated one; the 64 warehouses' and
+# 640 districts' rates and year-to-date cells and the 800 KB item prices sit
+# in L2 (0 B):
+#   new-order     record 168 (19 params, ts, type, index), district counter
+#                 64, customer discount 32, per line stock quantity/ytd/count
+#                 3 x 64 + order-line row 20 (x 10), order row 33, index
+#                 insert 96, customer last order 32, outputs 28   -> 2,573 B
+#   payment       record 168, customer balance/ytd/count 3 x 64, output 12 -> 372 B
+#   order-status  record 168, customer 2 x 32, index probe 64, order row 64,
+#                 10 line amounts 96, outputs 36                  -> 492 B
+OE_EXEC_BYTES_PER_TXN = round(0.45 * 2573 + 0.43 * 372 + 0.12 * 492)
 
 
 def run_batched(args, G, torch, stream):
     """Order-entry stream of uneven bulks (64 warehouses x 10 districts x
     3,000 customers, 100,000 items): the graph batcher with its autotuner
+    (several bulks per graph replay, each keeping its own k-sets under K-SET)
     against the plain per-bulk K-SET path.  Host arrays in and out (H2D and
-    D2H inside the timing) for both."""
+    D2H inside the timing) for both.  Latency of a transaction = time from
+    the run's start until its results are on the host (the whole stream is
+    handed over at once)."""
     n_wh, n_items = 64, 100_000
     init = W.oe_tables(n_wh, n_items=n_items, seed=W.seed_for(4))
     sizes, stream_bulk = W.oe_stream(args.batch_txns, n_wh, n_items)
     total = sum(sizes)
     out = {"workload": f"order-entry {n_wh} warehouses, {n_items} items, {len(sizes)} bulks of "
-                       f"2^10..2^21 transactions, {total} in all", "txn": total}
+                       f"2^10..2^21 transactions, {total} in all", "txn": total,
+           "bytes_per_txn": OE_EXEC_BYTES_PER_TXN}
+    peak = measured_peak_hbm()[0]
+    mode = G.CONFLICT_ADD if args.mode == "add" else G.CONFLICT_PAPER
     for label in ("plain_kset", "batched_tuned"):
         cap = 2 * total + (1 << 22)
         db = G.Database(oe=(n_wh, n_items), order_capacity=cap, orderline_capacity=cap * 15,
@@ -595,30 +654,46 @@ def run_batched(args, G, torch, stream):
         t0 = time.perf_counter()
         if label == "plain_kset":
             i = 0
+            done = []          # (ms from start, transactions) per bulk
             for k in sizes:
                 b = db.submit(stream_bulk["ts"][i:i + k], stream_bulk["type"][i:i + k],
                               stream_bulk["params"][i:i + k])
-                b.execute("kset", conflict_mode=G.CONFLICT_ADD if args.mode == "add" else G.CONFLICT_PAPER)
+                b.execute("kset", conflict_mode=mode)
                 b.results()
                 b.free()
+                done.append(((time.perf_counter() - t0) * 1e3, k))
                 i += k
             choice = None
         else:
-            bt = G.Batcher(db, tune=True, params_per_txn=W.OE_PARAMS, bulk_size_max=1 << 21,
-                           conflict_mode=G.CONFLICT_ADD if args.mode == "add" else G.CONFLICT_PAPER)
-            bt.run(stream_bulk["ts"], stream_bulk["type"], stream_bulk["params"])
+            bt = G.Batcher(db, tune=True, params_per_txn=W.OE_PARAMS, bulk_size_max=1 << 21, conflict_mode=mode)
+            bt.run_bulks(stream_bulk["ts"], stream_bulk["type"], stream_bulk["params"], sizes)
             choice = bt.choice()
             bt.close()
         dt = time.perf_counter() - t0
-        out[label] = {"txn_per_s": total / dt, "seconds": dt}
-        if choice is not None:
-            names = {G.KSET: "kset", G.TPL: "tpl"}
-            out[label]["choice"] = {"strategy": names.get(choice["strategy"]), "bulk": choice["bulk_size"],
-                                    "block": choice["block_threads"],
-                                    "measured": [{"strategy": names.get(m["strategy"]), "bulk": m["bulk"],
-                                                  "block": m["block"], "ns_per_txn": m["ns_per_txn"]}
-                                                 for m in choice["measured"]]}
+        rec = {"txn_per_s": total / dt, "seconds": dt,
+               "hbm_frac_wall": total * OE_EXEC_BYTES_PER_TXN / dt / 1e9 / peak}
+        if choice is None:
+            done.sort()
+            acc, p50, p99 = 0, None, None
+            for ms, k in done:
+                acc += k
+                if p50 is None and acc > 0.5 * total:
+                    p50 = ms
+                if p99 is None and acc > 0.99 * total:
+                    p99 = ms
+            rec.update({"p50_us": p50 * 1e3, "p99_us": p99 * 1e3})
+        else:
+            names = {G.KSET: "kset", G.TPL: "tpl", G.PART: "part"}
+            rec.update({"p50_us": choice["p50_us"], "p99_us": choice["p99_us"], "segments": choice["bulks_run"],
+                        "choice": {"strategy": names.get(choice["strategy"]), "segment_capacity": choice["bulk_size"],
+                                   "block": choice["block_threads"],
+                                   "measured": [{"strategy": names.get(m["strategy"]), "capacity": m["bulk"],
+                                                 "block": m["block"], "ns_per_txn": m["ns_per_txn"]}
+                                                for m in choice["measured"]]}})
+        out[label] = rec
         db.close()
+    if args.cpu_baseline:
+        out["cpu_baseline"] = oracle_oe_rate(init, stream_bulk, sizes, args.cpu_budget_s)
     return out
 
 
@@ -642,6 +717,29 @@ def oracle_rate(bulks, budget_s, max_bulks=None):
         done += len(b["ts"])
         k += 1
     return done, t_exec, k
+
+
+def oracle_oe_rate(init, stream_bulk, sizes, budget_s):
+    """The oracle on the order-entry stream's bulks, one after another, until
+    about budget_s of CPU time (a bounded sample of the same stream)."""
+    import oracle
+    oracle.build()
+    total = sum(sizes)
+    o = oracle.OracleDB(oe=init, ord_cap=total, ol_cap=total * 15, oid_cap=1 << 16)
+    i, done, t_exec = 0, 0, 0.0
+    for k in sizes:
+        b = {key: stream_bulk[key][i:i + k] for key in ("ts", "type", "params")}
+        b["P"] = stream_bulk["P"]
+        t0 = time.perf_counter()
+        o.execute(b, R=4)
+        t_exec += time.perf_counter() - t0
+        done += k
+        i += k
+        if t_exec > budget_s:
+            break
+    return {"value": done / t_exec, "unit": "txn/s", "cores": 1, "nproc": os.cpu_count(), "kind": "oracle",
+            "sample": f"the first {done} transactions of the stream, serial execution in timestamp order, "
+                      f"{t_exec:.1f} s on one host core"}
 
 
 def cpu_baseline(args, bulks):
@@ -702,8 +800,7 @@ def main():
     ap.add_argument("--serve-deadlines-us", default="1000,10000")
     ap.add_argument("--serve-seconds", type=float, default=0.5)
     ap.add_argument("--serve-strategy", default="kset", choices=["kset", "part", "tpl", "auto"])
-    ap.add_argument("--serve-subscribers", type=int, default=2_000_000)
-    ap.add_argument("--serve-db-gb", type=float, default=20.0)
+    ap.add_argument("--serve-subscribers", type=int, default=22_000_000)
     ap.add_argument("--serve-zero-set-max-rate", type=float, default=5e6)
     ap.add_argument("--batched", dest="batched", action="store_true", default=True)
     ap.add_argument("--no-batched", dest="batched", action="store_false")

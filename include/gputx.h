@@ -370,11 +370,11 @@ typedef struct gputx_batcher gputx_batcher;
 
 typedef struct {
     int32_t tune;             /* 1 = choose strategy, bulk size, block shape */
-    int32_t strategy;         /* GPUTX_KSET or GPUTX_TPL when not tuning */
+    int32_t strategy;         /* GPUTX_KSET, GPUTX_TPL or GPUTX_PART when not tuning */
     int32_t block_threads;    /* when not tuning (default 256) */
     int32_t conflict_mode;    /* gputx_conflict_mode */
-    int64_t bulk_size;        /* transactions per bulk when not tuning (default 2^16) */
-    int64_t bulk_size_max;    /* largest bulk the tuner may pick (default: db max_bulk) */
+    int64_t bulk_size;        /* segment capacity when not tuning (default 2^16) */
+    int64_t bulk_size_max;    /* largest segment capacity the tuner may pick (default: db max_bulk) */
     int32_t params_per_txn;   /* parameter row width (default 2) */
     int32_t reserved;
 } gputx_batch_config;
@@ -382,18 +382,36 @@ typedef struct {
 typedef struct {
     int32_t tuned;            /* 1 once the tuner settled */
     int32_t strategy, block_threads, n_measured;
-    int64_t bulk_size, bulks_run;
+    int64_t bulk_size;        /* segment capacity (transactions per graph replay) */
+    int64_t bulks_run;        /* segments run (graph replays) */
     int32_t measured_strategy[16], measured_block[16];
     int64_t measured_bulk[16];
     double measured_ns_per_txn[16];
+    double p50_us, p99_us;    /* last run call: per-transaction time from the call's start to its
+                                 segment's results on the host */
 } gputx_batch_choice;
 
 /* ESTATE without registered types. */
 gputx_status gputx_batcher_create(gputx_db *db, const gputx_batch_config *cfg, gputx_batcher **out);
 
-/* Executes n transactions (host arrays, ts strictly increasing) and writes
- * their results (host arrays status[n], values[n x output width]); returns
- * after the last bulk finished.  Device errors as for gputx_sync_bulk. */
+/* Executes a stream of n_bulks bulks of uneven sizes: bulk k is transactions
+ * [bulk_off[k], bulk_off[k+1]) of the host arrays ts, type, params (ts
+ * strictly increasing over the whole stream; bulk_off[0] = 0, offsets
+ * non-decreasing, n = bulk_off[n_bulks]).  Results go to the host arrays
+ * status[n], values[n x output width]; returns after the last segment
+ * finished.  Consecutive bulks share a segment (one graph replay) up to the
+ * segment capacity the tuner chose (or cfg.bulk_size) and at most 63 bulks;
+ * a bulk above the capacity is cut into pieces, each its own bulk.  Under
+ * K-SET each bulk (piece) keeps its own dependency graph and k-sets
+ * (Definition 1 per bulk, bulks in order); TPL and PART run a segment in
+ * timestamp order.  EINVAL on bad offsets; device errors as for
+ * gputx_sync_bulk. */
+gputx_status gputx_batcher_run_bulks(gputx_batcher *bt, const int64_t *ts, const int32_t *type,
+                                     const int64_t *params, const int64_t *bulk_off, size_t n_bulks,
+                                     int32_t *status, int64_t *values);
+
+/* gputx_batcher_run_bulks over one bulk of n transactions (cut into
+ * segments of the chosen capacity). */
 gputx_status gputx_batcher_run(gputx_batcher *bt, const int64_t *ts, const int32_t *type, const int64_t *params,
                                size_t n, int32_t *status, int64_t *values);
 

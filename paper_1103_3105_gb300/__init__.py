@@ -49,7 +49,7 @@ EXPORTED = ("gputx_create_db", "gputx_destroy_db", "gputx_last_error", "gputx_re
             "gputx_execute_kset_noalloc", "gputx_clock_ns", "gputx_server_create", "gputx_server_submit",
             "gputx_server_results", "gputx_server_drain", "gputx_server_stats",
             "gputx_server_last_error", "gputx_server_destroy", "gputx_batcher_create",
-            "gputx_batcher_run", "gputx_batcher_choice", "gputx_batcher_destroy",
+            "gputx_batcher_run", "gputx_batcher_run_bulks", "gputx_batcher_choice", "gputx_batcher_destroy",
             "gputx_pool_create", "gputx_pool_add", "gputx_pool_step", "gputx_pool_results",
             "gputx_pool_pending", "gputx_pool_destroy", "gputx_bulk_order", "gputx_probe_level_chain",
             "gputx_probe_atomics")
@@ -113,7 +113,8 @@ class BatchChoice(C.Structure):
     _fields_ = [("tuned", C.c_int32), ("strategy", C.c_int32), ("block_threads", C.c_int32),
                 ("n_measured", C.c_int32), ("bulk_size", C.c_int64), ("bulks_run", C.c_int64),
                 ("measured_strategy", C.c_int32 * 16), ("measured_block", C.c_int32 * 16),
-                ("measured_bulk", C.c_int64 * 16), ("measured_ns_per_txn", C.c_double * 16)]
+                ("measured_bulk", C.c_int64 * 16), ("measured_ns_per_txn", C.c_double * 16),
+                ("p50_us", C.c_double), ("p99_us", C.c_double)]
 
     def as_dict(self):
         k = self.n_measured
@@ -121,7 +122,8 @@ class BatchChoice(C.Structure):
                 "bulk_size": self.bulk_size, "bulks_run": self.bulks_run,
                 "measured": [{"strategy": self.measured_strategy[i], "block": self.measured_block[i],
                               "bulk": self.measured_bulk[i], "ns_per_txn": self.measured_ns_per_txn[i]}
-                             for i in range(k)]}
+                             for i in range(k)],
+                "p50_us": self.p50_us, "p99_us": self.p99_us}
 
 
 class PoolConfig(C.Structure):
@@ -175,6 +177,7 @@ def signatures() -> dict:
         "gputx_server_destroy": ([p], None),
         "gputx_batcher_create": ([p, C.POINTER(BatchConfig), C.POINTER(p)], C.c_int),
         "gputx_batcher_run": ([p, p, p, p, sz, p, p], C.c_int),
+        "gputx_batcher_run_bulks": ([p, p, p, p, p, sz, p, p], C.c_int),
         "gputx_batcher_choice": ([p, C.POINTER(BatchChoice)], C.c_int),
         "gputx_batcher_destroy": ([p], None),
         "gputx_pool_create": ([p, C.POINTER(PoolConfig), C.POINTER(p)], C.c_int),
@@ -571,6 +574,11 @@ def gputx_batcher_run(db, bt, ts, type_, params, status, values):
                                        _ptr(values)))
 
 
+def gputx_batcher_run_bulks(db, bt, ts, type_, params, bulk_off, status, values):
+    _check(db, lib().gputx_batcher_run_bulks(bt, _ptr(ts), _ptr(type_), _ptr(params), _ptr(bulk_off),
+                                             len(bulk_off) - 1, _ptr(status), _ptr(values)))
+
+
 def gputx_batcher_choice(bt) -> dict:
     c = BatchChoice()
     lib().gputx_batcher_choice(bt, C.byref(c))
@@ -600,6 +608,18 @@ class Batcher:
         st = np.zeros(len(ts), dtype=np.int32)
         vals = np.zeros((len(ts), self.db.width), dtype=np.int64)
         gputx_batcher_run(self.db.h, self.h, ts, type_, params, st, vals)
+        return st, vals
+
+    def run_bulks(self, ts, type_, params, sizes):
+        """A stream of bulks of the given (uneven) sizes, in order."""
+        ts = np.ascontiguousarray(ts, dtype=np.int64)
+        type_ = np.ascontiguousarray(type_, dtype=np.int32)
+        params = np.ascontiguousarray(params, dtype=np.int64)
+        off = np.zeros(len(sizes) + 1, dtype=np.int64)
+        off[1:] = np.cumsum(np.asarray(sizes, dtype=np.int64))
+        st = np.zeros(len(ts), dtype=np.int32)
+        vals = np.zeros((len(ts), self.db.width), dtype=np.int64)
+        gputx_batcher_run_bulks(self.db.h, self.h, ts, type_, params, off, st, vals)
         return st, vals
 
     def choice(self) -> dict:

@@ -2,6 +2,7 @@
 // 1-2, Appendix D): basic-operation extraction, grouping by data item with a
 // radix sort, per-group ranks, transaction depths (k-set levels), regrouping
 // by (level, type), insert slots, partition ids.
+#include <algorithm>
 #include <cooperative_groups.h>
 #include <cstdio>
 
@@ -55,6 +56,9 @@ struct ExtractArgs {
     bool write_ops;
     bool sentinel_fill;            // fill unused slots with padding operations
     uint32_t sentinel_key;         // object id above every real one
+    const uint32_t *bulk_of;       // segmented graph bulks: the bulk above the object id (or null)
+    int obj_shift;                 // bits of the object id under the bulk
+    uint32_t pad_pid;              // PART: partition id of a padding transaction (after every real one)
 };
 
 __device__ __forceinline__ bool txn_padding(const DevBulk &b, int64_t t)
@@ -110,10 +114,11 @@ __global__ void extract_kernel(ExtractArgs a)
             for (int j = k; j < a.uniform_k; j++) { obj[j] = 0; cls[j] = CLS_R; root[j] = 0; }
             k = a.uniform_k;
         }
-        const uint32_t pid = k ? root[0] / (uint32_t)a.part_size : 0;
+        const uint32_t pid = pad ? a.pad_pid : (k ? root[0] / (uint32_t)a.part_size : 0);
+        const uint32_t seg = (a.bulk_of && !pad) ? (a.bulk_of[t] << a.obj_shift) : 0u;
         for (int j = 0; j < k; j++) {
             if (a.write_ops) {
-                a.keys[off + j] = obj[j];
+                a.keys[off + j] = obj[j] | seg;
                 a.vals[off + j] = ((uint32_t)t << 7) | ((uint32_t)j << 2) | cls[j];
             }
             cross |= (root[j] / (uint32_t)a.part_size) != pid;
@@ -426,7 +431,8 @@ __global__ void level_stats_kernel(const uint32_t *level, int64_t n, BulkCtl *ct
 // a6: regroup by (level, type) -- Appendix D's grouping by type, per level
 // ---------------------------------------------------------------------------
 __global__ void regroup_keys_kernel(const uint32_t *level, const int32_t *type, int64_t n, int tbits,
-                                    uint32_t *keys, uint32_t *vals, const uint32_t *n_live)
+                                    uint32_t *keys, uint32_t *vals, const uint32_t *n_live,
+                                    const uint32_t *bulk_of, const uint32_t *seg_base)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n) return;
@@ -434,17 +440,72 @@ __global__ void regroup_keys_kernel(const uint32_t *level, const int32_t *type, 
         keys[t] = (uint32_t)n << tbits;   // padding: past every real level
     } else {
         const int32_t ty = type[t];
-        keys[t] = (level[t] << tbits) | (tbits && ty > 0 ? (uint32_t)ty : 0u);
+        // a segment's levels run bulk after bulk: global level = the bulk's
+        // first global level + the level within the bulk
+        const uint32_t lv = level[t] + (bulk_of ? seg_base[bulk_of[t]] : 0u);
+        keys[t] = (lv << tbits) | (tbits && ty > 0 ? (uint32_t)ty : 0u);
     }
     vals[t] = (uint32_t)t;
 }
 
+// the bulk of each live transaction of a segment (seg_off: first
+// transaction of each of its n_seg bulks, ascending from 0)
+__global__ void seg_index_kernel(const uint32_t *seg_off, const BulkCtl *ctl, uint32_t *bulk_of, int64_t cap)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= cap) return;
+    const uint32_t nseg = ctl->n_seg < 1 ? 1u : (ctl->n_seg > (uint32_t)kSegMax ? (uint32_t)kSegMax : ctl->n_seg);
+    uint32_t lo = 0, hi = nseg - 1;   // last bulk whose start is <= t
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (seg_off[mid] <= (uint32_t)t) lo = mid;
+        else hi = mid - 1;
+    }
+    bulk_of[t] = lo;
+}
+
+__global__ void seg_depth_kernel(const uint32_t *level, const uint32_t *bulk_of, const BulkCtl *ctl,
+                                 uint32_t *seg_depth, int64_t cap)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= cap || t >= (int64_t)ctl->n_live) return;
+    atomicMax(&seg_depth[bulk_of[t]], level[t]);
+}
+
+// first global level of each bulk; the segment's depth becomes the last
+// global level
+__global__ void seg_base_kernel(const uint32_t *seg_depth, BulkCtl *ctl, uint32_t *seg_base)
+{
+    if (threadIdx.x != 0) return;
+    const uint32_t nseg = ctl->n_seg < 1 ? 1u : (ctl->n_seg > (uint32_t)kSegMax ? (uint32_t)kSegMax : ctl->n_seg);
+    uint32_t acc = 0;
+    for (uint32_t i = 0; i < nseg; i++) {
+        seg_base[i] = acc;
+        acc += seg_depth[i] + 1;
+    }
+    seg_base[nseg] = acc;
+    ctl->depth = acc - 1;
+}
+
+__global__ void part_fallback_kernel(BulkCtl *ctl)
+{
+    if (ctl->cross) ctl->err |= ERR_FALLBACK;
+}
+
+// Level boundaries from the keys sorted by (level << tbits | type); with
+// type_cut, also where each level's new-order, payment and order-status
+// transactions start (type_cut[3 k + j] = first position of level k whose
+// type is >= 8 + j), so the executors can give order-entry's line-parallel
+// types their lane groups.  A cut (k, type) lands on the first key at or
+// above k << tbits | type; levels are contiguous, so between two adjacent
+// keys at most two levels' cuts fall.
 __global__ void level_off_kernel(const uint32_t *skeys, int64_t n, int tbits, uint32_t *level_off,
-                                 const uint32_t *err)
+                                 uint32_t *type_cut, const uint32_t *err)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n || *err) return;
-    const uint32_t lv = skeys[i] >> tbits;
+    const uint32_t key = skeys[i];
+    const uint32_t lv = key >> tbits;
     const uint32_t prev = i ? (skeys[i - 1] >> tbits) : 0u;
     if (i == 0) {
         for (uint32_t k = 0; k <= lv; k++) level_off[k] = 0;
@@ -452,6 +513,19 @@ __global__ void level_off_kernel(const uint32_t *skeys, int64_t n, int tbits, ui
         for (uint32_t k = prev + 1; k <= lv; k++) level_off[k] = (uint32_t)i;
     }
     if (i == n - 1) level_off[lv + 1] = (uint32_t)n;
+    if (type_cut && (i == 0 || skeys[i - 1] != key)) {
+        const uint64_t below = i ? (uint64_t)skeys[i - 1] + 1 : 0;   // cuts in (key[i-1], key[i]]
+        for (uint32_t k = i ? prev : 0; k <= lv; k++)
+            for (uint32_t j = 0; j < 3; j++) {
+                const uint64_t cut = ((uint64_t)k << tbits) | (GPUTX_T_OE_NEW_ORDER + j);
+                if (cut >= below && cut <= key) type_cut[3 * k + j] = (uint32_t)i;
+            }
+    }
+    if (type_cut && i == n - 1)
+        for (uint32_t j = 0; j < 3; j++) {
+            const uint64_t cut = ((uint64_t)lv << tbits) | (GPUTX_T_OE_NEW_ORDER + j);
+            if (cut > key) type_cut[3 * lv + j] = (uint32_t)n;
+        }
 }
 
 struct ChunkMode {
@@ -537,14 +611,16 @@ struct HeadMode {
     uint32_t *part_start;
     BulkCtl *ctl;
     int64_t n;
-    __device__ bool head(int64_t i) const { return i == 0 || skeys[i] != skeys[i - 1]; }
+    const uint32_t *n_live;   // graph bulks: padding (sorted last) forms no partition
+    __device__ int64_t live() const { return n_live ? (int64_t)*n_live : n; }
+    __device__ bool head(int64_t i) const { return i < live() && (i == 0 || skeys[i] != skeys[i - 1]); }
     __device__ uint64_t element(int64_t i) const { return DualSeg::make(0, 0, 0, head(i) ? 1u : 0u); }
     __device__ void output(int64_t i, uint64_t s) const
     {
         const uint32_t c = DualSeg::v2(s);
         if (head(i)) part_start[c - 1] = (uint32_t)i;
-        if (i == n - 1) {
-            part_start[c] = (uint32_t)n;
+        if (i == live() - 1) {
+            part_start[c] = (uint32_t)live();
             ctl->npart = c;
         }
     }
@@ -957,8 +1033,41 @@ cudaError_t launch_finish(gputx_bulk *b)
     return cudaGetLastError();
 }
 
+int seg_bits(const gputx_db *db)
+{
+    // segment bulk ids sit above the object id in a 32-bit key
+    const int room = 32 - db->obj_bits;
+    return room < 1 ? 0 : (room > 6 ? 6 : room);
+}
+
+cudaError_t launch_seg_index(gputx_bulk *b)
+{
+    if (b->n == 0 || !b->sc.bulk_of) return cudaSuccess;
+    seg_index_kernel<<<grid_for(b->n), TB, 0, b->stream>>>(b->sc.seg_off, b->ctl, b->sc.bulk_of, b->n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seg_levels(gputx_bulk *b)
+{
+    if (b->n == 0 || !b->sc.bulk_of) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(b->sc.seg_depth, 0, kSegMax * sizeof(uint32_t), b->stream);
+    if (e) return e;
+    seg_depth_kernel<<<grid_for(b->n), TB, 0, b->stream>>>(b->sc.level, b->sc.bulk_of, b->ctl, b->sc.seg_depth, b->n);
+    seg_base_kernel<<<1, 32, 0, b->stream>>>(b->sc.seg_depth, b->ctl, b->sc.seg_base);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_part_fallback_check(gputx_bulk *b)
+{
+    part_fallback_kernel<<<1, 1, 0, b->stream>>>(b->ctl);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_extract(gputx_bulk *b, int mode, int part_size, uint32_t *pid_key, uint32_t *pid_val,
-                           bool write_ops)
+                           bool write_ops, bool segmented)
 {
     gputx_db *db = b->db;
     cudaStream_t s = b->stream;
@@ -978,6 +1087,15 @@ cudaError_t launch_extract(gputx_bulk *b, int mode, int part_size, uint32_t *pid
     a.sentinel_fill = b->graph;
     a.sentinel_key = db->dev.n_objects;
     if (b->graph) a.uniform_k = db->kmax;
+    if (segmented && b->graph && b->sc.bulk_of && seg_bits(db) > 0) {
+        a.bulk_of = b->sc.bulk_of;
+        a.obj_shift = db->obj_bits;
+        a.sentinel_key = (uint32_t)(((1ull << seg_bits(db)) - 1) << db->obj_bits);   // after every bulk
+    }
+    {
+        const int64_t roots = std::max<int64_t>({db->dev.n_br, db->dev.n_sub, db->dev.n_wh, 1});
+        a.pad_pid = (uint32_t)((roots + a.part_size - 1) / a.part_size);
+    }
     if (!db->uniform_k && write_ops && !b->graph) {
         // counts into level[] (free until the rank scan), then offsets
         count_ops_kernel<<<grid_for(b->n), TB, 0, s>>>(db->dev, a.b, b->ctl, b->sc.level);
@@ -1099,8 +1217,11 @@ cudaError_t launch_level_stats(gputx_bulk *b)
 cudaError_t launch_regroup_keys(gputx_bulk *b, uint32_t *keys, uint32_t *vals)
 {
     if (b->n == 0) return cudaSuccess;
+    const bool seg = b->graph && b->sc.bulk_of;
     regroup_keys_kernel<<<grid_for(b->n), TB, 0, b->stream>>>(b->sc.level, b->type, b->n, b->db->tbits,
-                                                               keys, vals, b->graph ? &b->ctl->n_live : nullptr);
+                                                               keys, vals, b->graph ? &b->ctl->n_live : nullptr,
+                                                               seg ? b->sc.bulk_of : nullptr,
+                                                               seg ? b->sc.seg_base : nullptr);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1109,7 +1230,8 @@ cudaError_t launch_level_tables(gputx_bulk *b, const uint32_t *skeys, int64_t de
 {
     cudaStream_t s = b->stream;
     if (b->n == 0) return cudaSuccess;
-    level_off_kernel<<<grid_for(b->n), TB, 0, s>>>(skeys, b->n, b->db->tbits, b->sc.level_off, &b->ctl->err);
+    level_off_kernel<<<grid_for(b->n), TB, 0, s>>>(skeys, b->n, b->db->tbits, b->sc.level_off,
+                                                   b->graph ? nullptr : b->sc.type_cut, &b->ctl->err);
     count_launches(1);
     if (!chunks) return cudaGetLastError();
     // graph bulks do not know their depth on the host: scan every possible level
@@ -1145,6 +1267,7 @@ cudaError_t launch_part_heads(gputx_bulk *b, const uint32_t *skeys, int64_t n)
     hm.part_start = b->sc.part_start;
     hm.ctl = b->ctl;
     hm.n = n;
+    hm.n_live = b->graph ? &b->ctl->n_live : nullptr;
     return run_scan(b, hm, n, 4);
 }
 

@@ -196,6 +196,7 @@ size_t carve_bulk(gputx_bulk *b, char *base, bool device_inputs)
     s.lock_key = c.take<uint32_t>(mm);
     s.lock_ticket = c.take<uint32_t>(mm);
     s.level_off = c.take<uint32_t>(nn + 2);
+    s.type_cut = db->group_oe ? c.take<uint32_t>(3 * (nn + 2)) : nullptr;
     s.chunk_off = c.take<uint32_t>(nn + 2);
     s.chunk_cap = nn + nn / 32 + 2;
     s.chunk_level = c.take<uint32_t>(s.chunk_cap);
@@ -225,6 +226,10 @@ size_t carve_bulk(gputx_bulk *b, char *base, bool device_inputs)
     s.scan_vals = c.take<uint64_t>(2 * s.scan_tiles);
     s.fix_agg = db->need_fixpoint ? c.take<unsigned long long>(kFixAggMax) : nullptr;
     s.rec_dc = db->dev.registered == (1u << GPUTX_T_DC_DEBIT_CREDIT) ? c.take<DcRecord>(nn) : nullptr;
+    s.seg_off = b->graph ? c.take<uint32_t>(kSegMax + 1) : nullptr;
+    s.bulk_of = b->graph ? c.take<uint32_t>(nn) : nullptr;
+    s.seg_depth = b->graph ? c.take<uint32_t>(kSegMax) : nullptr;
+    s.seg_base = b->graph ? c.take<uint32_t>(kSegMax + 1) : nullptr;
     return c.off + 256;
 }
 
@@ -498,6 +503,9 @@ gputx_status gputx_register_types(gputx_db *db, const int32_t *type_ids, int n)
     db->uniform_k = uniform > 0 ? uniform : 0;
     db->need_fixpoint = fix;
     db->tbits = ntypes > 1 ? bits_for((uint64_t)maxid) : 0;
+    // levels sorted by (level, type) know where each order-entry type starts
+    db->group_oe = db->tbits > 0 && (db->dev.registered & ((1u << GPUTX_T_OE_NEW_ORDER) |
+                                                           (1u << GPUTX_T_OE_ORDER_STATUS)));
     return GPUTX_OK;
 }
 
@@ -1131,6 +1139,11 @@ gputx_status gputx_execute(gputx_db *db, gputx_bulk *b, int strategy, const gput
             b->level_off_host.resize((size_t)depth + 2);
             CK(cudaMemcpyAsync(b->level_off_host.data(), b->sc.level_off, (depth + 2) * sizeof(uint32_t),
                                cudaMemcpyDeviceToHost, s), "level plan");
+            if (b->sc.type_cut) {
+                b->type_cut_host.resize(3 * ((size_t)depth + 1));
+                CK(cudaMemcpyAsync(b->type_cut_host.data(), b->sc.type_cut, 3 * (depth + 1) * sizeof(uint32_t),
+                                   cudaMemcpyDeviceToHost, s), "level plan");
+            }
             CK(cudaMemcpyAsync(&b->host_ctl.err, &b->ctl->err, 4, cudaMemcpyDeviceToHost, s), "level plan");
             CK(cudaStreamSynchronize(s), "level plan");
             if (!b->host_ctl.err) {
@@ -1142,7 +1155,8 @@ gputx_status gputx_execute(gputx_db *db, gputx_bulk *b, int strategy, const gput
                 CK(begin_tail(b), "order");
                 if (b->timing) cudaEventRecord(b->ev[3], s);
                 CK(launch_kset_levels(b, b->level_off_host.data(), depth, narrow, add,
-                                      dc_only ? b->sc.rec_dc : nullptr),
+                                      dc_only ? b->sc.rec_dc : nullptr,
+                                      b->sc.type_cut ? b->type_cut_host.data() : nullptr),
                    "k-set execute");
             }
         } else {

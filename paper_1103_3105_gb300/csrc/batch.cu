@@ -1,21 +1,32 @@
 // batch.cu -- batched execution through captured CUDA graphs, with an online
 // autotuner.
 //
-// A stream of transactions (uneven sizes, mixed types) runs as consecutive
-// bulks of a chosen size.  Each bulk size, strategy and block shape has one
-// fixed-capacity bulk whose whole pipeline -- extraction, grouping sort,
-// ranks, device-side refinement rounds, (level, type) regrouping, and one
-// persistent K-SET launch (or the TPL kernel) -- is captured once in a CUDA
-// graph and replayed for every bulk of that shape: no host synchronisation
-// inside the pipeline, one graph launch per bulk.  Bulks shorter than the
-// capacity are padded with inactive transactions.
+// A stream of bulks of uneven sizes and mixed types runs in segments: a
+// segment is a run of consecutive bulks (at most kSegMax, their total at
+// most the segment capacity; a bulk larger than that is cut into pieces)
+// that goes through ONE replay of a captured CUDA graph.  The graph holds
+// the whole pipeline for a fixed capacity -- extraction, grouping sort,
+// ranks, device-side refinement rounds, (level, type) regrouping and one
+// persistent executor launch -- and reads the segment's bulk boundaries from
+// a device descriptor array, so no host synchronisation happens inside it.
+// For K-SET every bulk keeps its own dependency graph: the bulk's index sits
+// above the object id in the grouping key, each bulk's levels are numbered
+// after those of the bulks before it, and the persistent executor walks the
+// levels of the whole segment in that order with per-level counters (bulk
+// by bulk, level by level).  TPL and PART need no boundary: their order is
+// the timestamp order, which runs across bulks.  Shorter segments are padded
+// with inactive transactions.
 //
-// The autotuner runs the stream's own first bulks under different
-// configurations (every bulk still executes exactly once, in order, so the
-// results are unaffected) and keeps the fastest per transaction.  Its first
-// guess follows Algorithm 1 (Appendix D) on the structural parameters of the
-// first bulk: a wide 0-set favours K-SET, otherwise TPL.
+// The autotuner runs the stream's own first segments under different
+// configurations (every transaction still executes exactly once, in order,
+// so the results are unaffected) and keeps the fastest per transaction.  Its
+// first guess follows Algorithm 1 (Appendix D) on the structural parameters
+// of the first segment: a wide 0-set favours K-SET, otherwise TPL; PART is
+// tried when that segment had no cross-partition transaction, and a PART
+// segment that turns out to have one runs nothing and is re-run with TPL
+// (Section 5.2's fallback, decided on the device).
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <vector>
 
@@ -25,7 +36,7 @@ namespace {
 
 struct GraphBulk {
     int64_t cap = 0;
-    int strategy = GPUTX_KSET, block = 256, mode = 0, P = 0;
+    int strategy = GPUTX_KSET, block = 256, mode = 0, P = 0, part_size = 1;
     gputx_bulk *b = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -62,17 +73,38 @@ cudaError_t enqueue_pipeline(GraphBulk *g)
     cudaError_t e;
     if ((e = gtx::launch_insert_slots(b))) return e;
     if ((e = cudaMemsetAsync(&b->ctl->cross, 0, 4, b->stream))) return e;
-    if ((e = gtx::launch_extract(b, g->mode, 1, nullptr, nullptr, true))) return e;
+    if (g->strategy == GPUTX_PART) {
+        // partition ids (Section 5.2 step 1); a segment with a
+        // cross-partition transaction is flagged and runs nothing
+        uint32_t *pk = b->sc.pid_key, *pv = b->sc.pid_val, *pk2 = b->sc.pid_key2, *pv2 = b->sc.pid_val2;
+        if ((e = gtx::launch_extract(b, g->mode, g->part_size, pk, pv, false))) return e;
+        if ((e = gtx::launch_part_fallback_check(b))) return e;
+        const int64_t roots = std::max<int64_t>({db->dev.n_br, db->dev.n_sub, db->dev.n_wh, 1});
+        const int64_t parts = (roots + g->part_size - 1) / g->part_size;   // the padding's id
+        if ((e = gtx::launch_sort(b, pk, pv, pk2, pv2, b->n, gtx::bits_for((uint64_t)parts)))) return e;
+        if ((e = gtx::launch_part_heads(b, pk, b->n))) return e;
+        if (gtx::part_dc_applies(db, g->part_size)) e = gtx::launch_gather_dc(b, pv);
+        else e = gtx::launch_gather(b, pv);
+        if (e) return e;
+        if ((e = gtx::launch_begin(b))) return e;
+        if ((e = gtx::launch_part(b, pk, 128, parts, g->part_size))) return e;
+        return gtx::launch_finish(b);
+    }
+    const bool seg = g->strategy == GPUTX_KSET && gtx::seg_bits(db) > 0;
+    if (seg && (e = gtx::launch_seg_index(b))) return e;
+    if ((e = gtx::launch_extract(b, g->mode, 1, nullptr, nullptr, true, seg))) return e;
     const int64_t m = b->n * db->kmax;
     uint32_t *sk = b->sc.keys_a, *sv = b->sc.vals_a, *ak = b->sc.keys_b, *av = b->sc.vals_b;
-    if ((e = gtx::launch_sort(b, sk, sv, ak, av, m, db->obj_bits))) return e;
+    const int kbits = db->obj_bits + (seg ? gtx::seg_bits(db) : 0);
+    if ((e = gtx::launch_sort(b, sk, sv, ak, av, m, kbits))) return e;
     if (g->strategy == GPUTX_KSET) {
         if ((e = gtx::launch_rank_scan(b, sk, sv, m, db->need_fixpoint))) return e;
         if (db->need_fixpoint && (e = gtx::launch_fixpoint_device(b, sv, m))) return e;
         if ((e = gtx::launch_level_stats(b))) return e;
+        if (seg && (e = gtx::launch_seg_levels(b))) return e;
         uint32_t *rk = ak, *rv = av, *rk2 = sk, *rv2 = sv;
         if ((e = gtx::launch_regroup_keys(b, rk, rv))) return e;
-        // depth < capacity, and the padding key is the capacity itself
+        // global levels < capacity, and the padding key is the capacity itself
         if ((e = gtx::launch_sort(b, rk, rv, rk2, rv2, b->n, gtx::bits_for((uint64_t)b->n) + db->tbits))) return e;
         if ((e = gtx::launch_level_tables(b, rk, 0, g->block, true))) return e;
         if ((e = gtx::launch_gather(b, rv))) return e;
@@ -98,8 +130,13 @@ struct gputx_batcher {
     std::vector<Candidate> cands;
     size_t next_cand = 0;
     bool tuned = false;
+    bool part_ok = false;              // the first segment had no cross-partition transaction
     Candidate best{GPUTX_KSET, 256, 1 << 16, 0};
-    int64_t bulks_run = 0;
+    int64_t bulks_run = 0;             // segments (graph replays) run
+    int part_size = 1;
+    // per-transaction latency of the last run call: (transactions, ms from
+    // the call's start to their segment's results on the host)
+    std::vector<std::pair<double, int64_t>> lat;
 };
 
 namespace {
@@ -129,6 +166,7 @@ gputx_status get_graph(gputx_batcher *bt, int64_t cap, int strategy, int block, 
     g->block = block;
     g->mode = bt->cfg.conflict_mode;
     g->P = bt->cfg.params_per_txn;
+    g->part_size = bt->part_size;
     gputx_bulk *b = new gputx_bulk();
     g->b = b;
     b->db = db;
@@ -153,6 +191,7 @@ gputx_status get_graph(gputx_batcher *bt, int64_t cap, int strategy, int block, 
     CKB(cudaMemsetAsync(b->type, 0xff, sizeof(int32_t) * cap, b->stream), "init");
     CKB(cudaMemsetAsync(b->params, 0, sizeof(int64_t) * cap * g->P, b->stream), "init");
     CKB(cudaMemsetAsync(b->ts, 0, sizeof(int64_t) * cap, b->stream), "init");
+    CKB(cudaMemsetAsync(b->sc.seg_off, 0, sizeof(uint32_t) * (gtx::kSegMax + 1), b->stream), "init");
     CKB(cudaStreamWaitEvent(b->stream, db->last_done, 0), "order");
     CKB(enqueue_pipeline(g), "warm-up");
     CKB(cudaStreamSynchronize(b->stream), "warm-up");
@@ -177,15 +216,19 @@ gputx_status get_graph(gputx_batcher *bt, int64_t cap, int strategy, int block, 
     return GPUTX_OK;
 }
 
-// one bulk of n <= cap transactions through a graph; returns its time
-gputx_status run_bulk(gputx_batcher *bt, GraphBulk *g, const int64_t *ts, const int32_t *type,
-                      const int64_t *params, int64_t n, int32_t *status, int64_t *values, double *ms,
-                      gtx::BulkCtl *ctl_out)
+// One segment of n <= cap transactions through a graph: n_seg bulks whose
+// first transactions (relative to the segment) are seg_off[0..n_seg-1].
+// Returns its device time; *fallback is set when a PART segment held a
+// cross-partition transaction (nothing ran).
+gputx_status run_segment(gputx_batcher *bt, GraphBulk *g, const int64_t *ts, const int32_t *type,
+                         const int64_t *params, int64_t n, const uint32_t *seg_off, uint32_t n_seg, int32_t *status,
+                         int64_t *values, double *ms, gtx::BulkCtl *ctl_out, bool *fallback)
 {
     gputx_db *db = bt->db;
     gputx_bulk *b = g->b;
     cudaStream_t s = b->stream;
     const int64_t cap = g->cap;
+    *fallback = false;
     // earlier work on the database stream (loads, other bulks) comes first
     CKB(cudaEventRecord(b->ev_in, db->stream), "order");
     CKB(cudaStreamWaitEvent(s, b->ev_in, 0), "order");
@@ -193,6 +236,8 @@ gputx_status run_bulk(gputx_batcher *bt, GraphBulk *g, const int64_t *ts, const 
     CKB(cudaMemsetAsync(b->ctl, 0, sizeof(gtx::BulkCtl), s), "reset");
     const uint32_t nl = (uint32_t)n;
     CKB(cudaMemcpyAsync(&b->ctl->n_live, &nl, sizeof nl, cudaMemcpyHostToDevice, s), "inputs");
+    CKB(cudaMemcpyAsync(&b->ctl->n_seg, &n_seg, sizeof n_seg, cudaMemcpyHostToDevice, s), "inputs");
+    CKB(cudaMemcpyAsync(b->sc.seg_off, seg_off, sizeof(uint32_t) * n_seg, cudaMemcpyHostToDevice, s), "inputs");
     CKB(cudaMemcpyAsync(b->ts, ts, sizeof(int64_t) * n, cudaMemcpyHostToDevice, s), "inputs");
     CKB(cudaMemcpyAsync(b->type, type, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s), "inputs");
     CKB(cudaMemcpyAsync(b->params, params, sizeof(int64_t) * n * g->P, cudaMemcpyHostToDevice, s), "inputs");
@@ -212,6 +257,10 @@ gputx_status run_bulk(gputx_batcher *bt, GraphBulk *g, const int64_t *ts, const 
     cudaEventElapsedTime(&t, g->e0, g->e1);
     *ms = t;
     if (ctl_out) *ctl_out = ctl;
+    if (ctl.err == gtx::ERR_FALLBACK) {
+        *fallback = true;
+        return GPUTX_OK;
+    }
     if (ctl.err & gtx::ERR_INVAL) return fail_bt(db, GPUTX_EINVAL, "invalid bulk contents");
     if (ctl.err & gtx::ERR_TIMEOUT) return fail_bt(db, GPUTX_ETIMEOUT, "a bounded device wait ran out");
     if (ctl.err & gtx::ERR_CAPACITY) return fail_bt(db, GPUTX_ECAPACITY, "an insert area is full");
@@ -225,8 +274,36 @@ void plan_candidates(gputx_batcher *bt, int first_strategy)
     for (int64_t sz : {int64_t(1) << 14, int64_t(1) << 16, int64_t(1) << 18, int64_t(1) << 20})
         if (sz <= bt->cfg.bulk_size_max) bt->cands.push_back({first_strategy, 256, sz, 0});
     if (bt->cands.empty()) bt->cands.push_back({first_strategy, 256, bt->cfg.bulk_size_max, 0});
-    // block shapes and the other strategy are tried at the best size found so
-    // far (filled in when the sizes are measured)
+    // block shapes and the other strategies are tried at the best size found
+    // so far (filled in when the sizes are measured)
+}
+
+// The next segment of the caller's bulks: starting at bulk `bi`, offset
+// `off` into it, consecutive bulks (pieces of at most cap) until cap
+// transactions or `seg_limit` bulks.  Fills seg_off (relative starts) and
+// returns the segment's transaction count; advances bi/off.
+int64_t next_segment(const int64_t *bulk_off, size_t n_bulks, size_t &bi, int64_t &off, int64_t cap, int seg_limit,
+                     std::vector<uint32_t> &seg_off)
+{
+    seg_off.clear();
+    int64_t total = 0;
+    while (bi < n_bulks && (int)seg_off.size() < seg_limit && total < cap) {
+        const int64_t left = bulk_off[bi + 1] - bulk_off[bi] - off;
+        if (left <= 0) {   // an empty bulk (or a finished one)
+            bi++;
+            off = 0;
+            continue;
+        }
+        const int64_t take = std::min<int64_t>(left, cap - total);
+        seg_off.push_back((uint32_t)total);
+        total += take;
+        off += take;
+        if (off >= bulk_off[bi + 1] - bulk_off[bi]) {
+            bi++;
+            off = 0;
+        }
+    }
+    return total;
 }
 
 }  // namespace
@@ -246,10 +323,124 @@ gputx_status gputx_batcher_create(gputx_db *db, const gputx_batch_config *cfg, g
     if (c.bulk_size_max <= 0 || c.bulk_size_max > db->cfg.max_bulk) c.bulk_size_max = db->cfg.max_bulk;
     if (c.bulk_size <= 0 || c.bulk_size > c.bulk_size_max) c.bulk_size = std::min<int64_t>(1 << 16, c.bulk_size_max);
     if (c.block_threads <= 0) c.block_threads = 256;
-    if (c.strategy != GPUTX_KSET && c.strategy != GPUTX_TPL) c.strategy = GPUTX_KSET;
+    if (c.strategy != GPUTX_KSET && c.strategy != GPUTX_TPL && c.strategy != GPUTX_PART) c.strategy = GPUTX_KSET;
+    bt->part_size = db->cfg.part_size > 0 ? db->cfg.part_size
+                                          : ((db->dev.n_sub > 0 && db->dev.n_acc == 0 && db->dev.n_wh == 0) ? 128 : 1);
     bt->best = {c.strategy, c.block_threads, c.bulk_size, 0};
     bt->tuned = !c.tune;
     *out = bt;
+    return GPUTX_OK;
+}
+
+gputx_status gputx_batcher_run_bulks(gputx_batcher *bt, const int64_t *ts, const int32_t *type,
+                                     const int64_t *params, const int64_t *bulk_off, size_t n_bulks,
+                                     int32_t *status, int64_t *values)
+{
+    if (!bt || (n_bulks && !bulk_off)) return GPUTX_EINVAL;
+    gputx_db *db = bt->db;
+    const size_t n = n_bulks ? (size_t)bulk_off[n_bulks] : 0;
+    if (n && (!ts || !type || !params || !status || !values)) return fail_bt(db, GPUTX_EINVAL, "null array");
+    if (n_bulks && bulk_off[0] != 0) return fail_bt(db, GPUTX_EINVAL, "bulk_off[0] must be 0");
+    for (size_t k = 0; k < n_bulks; k++)
+        if (bulk_off[k + 1] < bulk_off[k]) return fail_bt(db, GPUTX_EINVAL, "bulk offsets must not decrease");
+    const int P = bt->cfg.params_per_txn, R = db->dev.out_width;
+    // bulks in one segment: the bulk index must fit above the object id
+    const int sb = gtx::seg_bits(db);
+    const int seg_kset = sb > 0 ? std::min(gtx::kSegMax, (1 << sb) - 1) : 1;
+    const auto t_start = std::chrono::steady_clock::now();
+    bt->lat.clear();
+    size_t bi = 0;
+    int64_t boff = 0;
+    std::vector<uint32_t> seg_off;
+    while (bi < n_bulks) {
+        Candidate *cand = nullptr;
+        int strategy, block;
+        int64_t size;
+        bool first = false;
+        if (!bt->tuned && bt->cands.empty()) {
+            // first segment: K-SET at 2^16 gives d, w0, c; Algorithm 1 orders
+            // the strategies to try
+            strategy = GPUTX_KSET;
+            block = 256;
+            size = std::min<int64_t>(1 << 16, bt->cfg.bulk_size_max);
+            first = true;
+        } else {
+            if (!bt->tuned) {
+                if (bt->next_cand >= bt->cands.size()) {
+                    // the sizes are measured: then block shapes and the other
+                    // strategies at the best size, once each
+                    auto best = std::min_element(bt->cands.begin(), bt->cands.end(),
+                                                 [](const Candidate &a, const Candidate &b) {
+                                                     return a.ns_per_txn < b.ns_per_txn;
+                                                 });
+                    const Candidate bc = *best;
+                    const size_t before = bt->cands.size();
+                    auto have = [&](int st, int blk, int64_t sz) {
+                        for (auto &c : bt->cands)
+                            if (c.strategy == st && c.block == blk && c.bulk == sz) return true;
+                        return false;
+                    };
+                    for (int blk : {128, 512})
+                        if (!have(bc.strategy, blk, bc.bulk)) bt->cands.push_back({bc.strategy, blk, bc.bulk, 0});
+                    for (int other : {GPUTX_KSET, GPUTX_TPL, GPUTX_PART}) {
+                        if (other == GPUTX_PART && !bt->part_ok) continue;
+                        if (other != bc.strategy && !have(other, 256, bc.bulk))
+                            bt->cands.push_back({other, 256, bc.bulk, 0});
+                    }
+                    if (bt->cands.size() == before) {
+                        bt->best = bc;
+                        bt->tuned = true;
+                    }
+                }
+                if (!bt->tuned) cand = &bt->cands[bt->next_cand];
+            }
+            strategy = cand ? cand->strategy : bt->best.strategy;
+            block = cand ? cand->block : bt->best.block;
+            size = cand ? cand->bulk : bt->best.bulk;
+        }
+        const size_t bi0 = bi;
+        const int64_t boff0 = boff;
+        const int64_t first_txn = bulk_off[bi] + boff;
+        const int limit = strategy == GPUTX_KSET ? seg_kset : gtx::kSegMax;
+        const int64_t k = next_segment(bulk_off, n_bulks, bi, boff, size, limit, seg_off);
+        if (k == 0) continue;   // only empty bulks were left
+        GraphBulk *g = nullptr;
+        gputx_status st = get_graph(bt, size, strategy, block, &g);
+        if (st) return st;
+        double ms = 0;
+        gtx::BulkCtl ctl{};
+        bool fb = false;
+        st = run_segment(bt, g, ts + first_txn, type + first_txn, params + first_txn * P, k, seg_off.data(),
+                         (uint32_t)seg_off.size(), status + first_txn, values + first_txn * R, &ms, &ctl, &fb);
+        if (st) return st;
+        if (fb) {
+            // Section 5.2: a PART segment with a cross-partition transaction
+            // runs with TPL (nothing of it ran)
+            double ms2 = 0;
+            GraphBulk *gt = nullptr;
+            if ((st = get_graph(bt, size, GPUTX_TPL, block, &gt))) return st;
+            st = run_segment(bt, gt, ts + first_txn, type + first_txn, params + first_txn * P, k, seg_off.data(),
+                             (uint32_t)seg_off.size(), status + first_txn, values + first_txn * R, &ms2, nullptr,
+                             &fb);
+            if (st) return st;
+            ms += ms2;
+        }
+        (void)bi0;
+        (void)boff0;
+        bt->lat.push_back({std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start)
+                               .count(),
+                           k});
+        if (first) {
+            const bool wide = (int64_t)ctl.w0 >= std::min<int64_t>(db->cfg.kset_w0_min, k / 4);
+            bt->part_ok = ctl.cross == 0;
+            plan_candidates(bt, wide ? GPUTX_KSET : GPUTX_TPL);
+        } else if (cand) {
+            // a short segment is padded: charge it at least half its capacity
+            cand->ns_per_txn = ms * 1e6 / (double)std::max<int64_t>(k, size / 2);
+            bt->next_cand++;
+        }
+        bt->bulks_run++;
+    }
     return GPUTX_OK;
 }
 
@@ -257,77 +448,8 @@ gputx_status gputx_batcher_run(gputx_batcher *bt, const int64_t *ts, const int32
                                size_t n, int32_t *status, int64_t *values)
 {
     if (!bt || (n && (!ts || !type || !params || !status || !values))) return GPUTX_EINVAL;
-    gputx_db *db = bt->db;
-    const int P = bt->cfg.params_per_txn, R = db->dev.out_width;
-    size_t i = 0;
-    while (i < n) {
-        Candidate *cand = nullptr;
-        if (!bt->tuned) {
-            if (bt->cands.empty()) {
-                // first bulk: K-SET at 2^16 gives d, w0, c; Algorithm 1 orders
-                // the strategies to try
-                GraphBulk *g = nullptr;
-                const int64_t sz = std::min<int64_t>(1 << 16, bt->cfg.bulk_size_max);
-                gputx_status st = get_graph(bt, sz, GPUTX_KSET, 256, &g);
-                if (st) return st;
-                const int64_t k = std::min<int64_t>(sz, (int64_t)(n - i));
-                double ms = 0;
-                gtx::BulkCtl ctl{};
-                st = run_bulk(bt, g, ts + i, type + i, params + i * P, k, status + i, values + i * R, &ms, &ctl);
-                if (st) return st;
-                i += (size_t)k;
-                const bool wide = (int64_t)ctl.w0 >= std::min<int64_t>(db->cfg.kset_w0_min, k / 4);
-                plan_candidates(bt, wide ? GPUTX_KSET : GPUTX_TPL);
-                bt->bulks_run++;
-                continue;
-            }
-            if (bt->next_cand < bt->cands.size()) {
-                cand = &bt->cands[bt->next_cand];
-            } else {
-                // the sizes are measured: then block shapes and the other
-                // strategy at the best size, once each
-                auto best = std::min_element(bt->cands.begin(), bt->cands.end(),
-                                             [](const Candidate &a, const Candidate &b) {
-                                                 return a.ns_per_txn < b.ns_per_txn;
-                                             });
-                const Candidate bc = *best;
-                const size_t before = bt->cands.size();
-                auto have = [&](int s, int blk, int64_t sz) {
-                    for (auto &c : bt->cands)
-                        if (c.strategy == s && c.block == blk && c.bulk == sz) return true;
-                    return false;
-                };
-                for (int blk : {128, 512})
-                    if (!have(bc.strategy, blk, bc.bulk)) bt->cands.push_back({bc.strategy, blk, bc.bulk, 0});
-                const int other = bc.strategy == GPUTX_KSET ? GPUTX_TPL : GPUTX_KSET;
-                if (!have(other, 256, bc.bulk)) bt->cands.push_back({other, 256, bc.bulk, 0});
-                if (bt->cands.size() == before) {
-                    bt->best = bc;
-                    bt->tuned = true;
-                    continue;
-                }
-                cand = &bt->cands[bt->next_cand];
-            }
-        }
-        const int strategy = cand ? cand->strategy : bt->best.strategy;
-        const int block = cand ? cand->block : bt->best.block;
-        const int64_t size = cand ? cand->bulk : bt->best.bulk;
-        GraphBulk *g = nullptr;
-        gputx_status st = get_graph(bt, size, strategy, block, &g);
-        if (st) return st;
-        const int64_t k = std::min<int64_t>(size, (int64_t)(n - i));
-        double ms = 0;
-        st = run_bulk(bt, g, ts + i, type + i, params + i * P, k, status + i, values + i * R, &ms, nullptr);
-        if (st) return st;
-        if (cand) {
-            // a short tail bulk is padded: charge it its full capacity
-            cand->ns_per_txn = ms * 1e6 / (double)std::max<int64_t>(k, size / 2);
-            bt->next_cand++;
-        }
-        i += (size_t)k;
-        bt->bulks_run++;
-    }
-    return GPUTX_OK;
+    const int64_t off[2] = {0, (int64_t)n};   // one bulk: cut into segments of the tuned capacity
+    return gputx_batcher_run_bulks(bt, ts, type, params, off, n ? 1 : 0, status, values);
 }
 
 gputx_status gputx_batcher_choice(const gputx_batcher *bt, gputx_batch_choice *out)
@@ -335,9 +457,18 @@ gputx_status gputx_batcher_choice(const gputx_batcher *bt, gputx_batch_choice *o
     if (!bt || !out) return GPUTX_EINVAL;
     std::memset(out, 0, sizeof *out);
     out->tuned = bt->tuned;
-    out->strategy = bt->best.strategy;
-    out->block_threads = bt->best.block;
-    out->bulk_size = bt->best.bulk;
+    Candidate cur = bt->best;
+    if (!bt->tuned) {   // still tuning: the fastest measured so far
+        double best_ns = 0;
+        for (const Candidate &c : bt->cands)
+            if (c.ns_per_txn > 0 && (best_ns == 0 || c.ns_per_txn < best_ns)) {
+                best_ns = c.ns_per_txn;
+                cur = c;
+            }
+    }
+    out->strategy = cur.strategy;
+    out->block_threads = cur.block;
+    out->bulk_size = cur.bulk;
     out->bulks_run = bt->bulks_run;
     out->n_measured = 0;
     for (const Candidate &c : bt->cands) {
@@ -349,6 +480,22 @@ gputx_status gputx_batcher_choice(const gputx_batcher *bt, gputx_batch_choice *o
         out->measured_ns_per_txn[out->n_measured] = c.ns_per_txn;
         out->n_measured++;
     }
+    // per-transaction latency of the last run call
+    std::vector<std::pair<double, int64_t>> v = bt->lat;
+    std::sort(v.begin(), v.end());
+    int64_t total = 0;
+    for (auto &x : v) total += x.second;
+    auto pct = [&](double q) {
+        const int64_t want = (int64_t)(q * (double)total);
+        int64_t acc = 0;
+        for (auto &x : v) {
+            acc += x.second;
+            if (acc > want) return x.first * 1e3;
+        }
+        return v.empty() ? 0.0 : v.back().first * 1e3;
+    };
+    out->p50_us = pct(0.50);
+    out->p99_us = pct(0.99);
     return GPUTX_OK;
 }
 

@@ -29,6 +29,7 @@ enum : uint32_t {
     ERR_TIMEOUT = 1u << 1,
     ERR_BOUNDS = 1u << 2,
     ERR_CAPACITY = 1u << 3,
+    ERR_FALLBACK = 1u << 4,   // a graph bulk's PART segment has cross-partition transactions: not run
 };
 
 constexpr int MAX_OPS = 17;       // largest access set (new-order, 15 lines)

@@ -25,7 +25,10 @@ struct BulkCtl {
     uint32_t changed_r[3]; // refinement rounds run on the device: rotating per-round flags
     uint32_t rounds;       // refinement rounds taken
     uint32_t runs;         // refinement: runs of the sorted operations
+    uint32_t n_seg;        // segmented graph bulks: bulks in this segment (0 = one)
 };
+
+constexpr int kSegMax = 64;        // bulks in one segment of a graph bulk, at most
 
 constexpr int kFixAggMax = 4096;   // blocks of the cooperative refinement launch, at most
 
@@ -39,6 +42,7 @@ struct Scratch {
     uint32_t *lock_key;    // m: TPL per-op object, indexed by op slot
     uint32_t *lock_ticket; // m
     uint32_t *level_off;   // n+2
+    uint32_t *type_cut;    // 3 (n+2): per level, where types >= new-order, payment, order-status start
     uint32_t *chunk_off;   // n+2
     uint32_t *chunk_level; // n + n/min_block + 2
     uint32_t *done;        // n+1 per-level completion counters
@@ -56,6 +60,11 @@ struct Scratch {
     uint64_t *scan_vals;   // 2 x tiles: per-tile values of 64-bit scans
     unsigned long long *fix_agg;   // kFixAggMax: refinement's per-block scan aggregates
     DcRecord *rec_dc;      // n packed debit-credit records (debit-credit-only databases)
+    // graph bulks that carry a segment of several bulks
+    uint32_t *seg_off;     // kSegMax + 1: first transaction of each bulk
+    uint32_t *bulk_of;     // n: bulk of each transaction
+    uint32_t *seg_depth;   // kSegMax: largest level of each bulk
+    uint32_t *seg_base;    // kSegMax + 1: first global level of each bulk
     int64_t m_cap;         // op capacity
     int64_t sort_tiles, scan_tiles, chunk_cap;
 };
@@ -79,6 +88,7 @@ struct gputx_db {
     int uniform_k = 0;                     // every registered type has exactly this many ops (0 = no)
     bool need_fixpoint = false;            // a registered type's ops may leave one-pass ranks inexact
     int tbits = 0;                         // type bits in the level/type regroup key
+    bool group_oe = false;                 // K-SET runs new-order and order-status on 16-lane groups
     int obj_bits = 1;                      // key bits of object ids
     // Each bulk runs on a stream of this pool, so the analysis of one bulk
     // overlaps the execution of the one before; `last_done` orders the
@@ -123,6 +133,7 @@ struct gputx_bulk {
     cudaEvent_t ev[8] = {};
     gtx::BulkCtl host_ctl{};
     std::vector<uint32_t> level_off_host;   // K-SET level boundaries read back for launch planning
+    std::vector<uint32_t> type_cut_host;    // and where each order-entry type starts in each level
 };
 
 namespace gtx {
@@ -130,7 +141,15 @@ namespace gtx {
 // analysis.cu
 DevBulk make_dev_bulk(gputx_bulk *b, int mode);
 cudaError_t launch_extract(gputx_bulk *b, int mode, int part_size, uint32_t *pid_key, uint32_t *pid_val,
-                           bool write_ops);
+                           bool write_ops, bool segmented = false);
+// segmented graph bulks: bulk of each transaction; per-bulk depths and the
+// global level numbering (bulk by bulk, levels in order)
+int seg_bits(const gputx_db *db);
+cudaError_t launch_seg_index(gputx_bulk *b);
+cudaError_t launch_seg_levels(gputx_bulk *b);
+// PART in a graph: flags a segment with cross-partition transactions (it
+// then runs nothing and is re-run with TPL)
+cudaError_t launch_part_fallback_check(gputx_bulk *b);
 cudaError_t launch_sort(gputx_bulk *b, uint32_t *&keys, uint32_t *&vals, uint32_t *&keys_alt,
                         uint32_t *&vals_alt, int64_t count, int bits);
 cudaError_t launch_rank_scan(gputx_bulk *b, const uint32_t *sk, const uint32_t *sv, int64_t m, bool want_rid);
@@ -151,7 +170,8 @@ cudaError_t launch_finish(gputx_bulk *b);
 // exec.cu
 cudaError_t launch_kset(gputx_bulk *b, const uint32_t *order, int64_t nchunks, int block, bool atomic_add);
 cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, int64_t depth, int narrow_max,
-                               bool atomic_add, const DcRecord *dc_records = nullptr);
+                               bool atomic_add, const DcRecord *dc_records = nullptr,
+                               const uint32_t *type_cut_host = nullptr);
 cudaError_t launch_part(gputx_bulk *b, const uint32_t *pkeys, int block, int64_t max_parts, int part_size);
 cudaError_t launch_tpl(gputx_bulk *b, int block, bool atomic_add);
 // a conflict-free bulk (a 0-set) in one launch

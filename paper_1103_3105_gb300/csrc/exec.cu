@@ -24,6 +24,7 @@
 // Every wait is bounded by the configured limit; on expiry the kernel sets
 // ERR_TIMEOUT in the bulk's error word and returns.
 #include <algorithm>
+#include <vector>
 #include <cooperative_groups.h>
 
 #include "engine.h"
@@ -80,15 +81,71 @@ __global__ void __launch_bounds__(256) independent_kernel(DevDB db, DevBulk b, c
         exec_txn(db, b, view_of(b, (uint32_t)t, hb), atomic_add);
 }
 
+// The lanes of one level.  Records are sorted by (level, type) (Appendix
+// D's grouping by type), so a level is a run of each type in turn.  With
+// type cuts, order-entry's new-orders and order-statuses take 16 lanes each
+// (their line-parallel procedures), every group starting on a half warp;
+// every other transaction takes one lane.  Lane x maps to the record at
+// `pos`; gl = its index in a group, or -1 for a one-lane transaction.
+struct LevelLanes {
+    uint32_t lo, c8, c9, c10, a1, b1, a2, v;
+    __device__ __forceinline__ void make(uint32_t lo_, uint32_t hi, const uint32_t *cut)
+    {
+        lo = lo_;
+        if (!cut) {
+            c8 = c9 = c10 = hi;
+            a1 = b1 = a2 = v = hi - lo;
+            return;
+        }
+        c8 = __ldg(&cut[0]);
+        c9 = __ldg(&cut[1]);
+        c10 = __ldg(&cut[2]);
+        a1 = (c8 - lo + kGroup - 1) & ~(uint32_t)(kGroup - 1);      // new-order groups start here
+        b1 = a1 + kGroup * (c9 - c8);                               // payments
+        a2 = (b1 + (c10 - c9) + kGroup - 1) & ~(uint32_t)(kGroup - 1);   // order-status groups
+        v = a2 + kGroup * (hi - c10);
+    }
+    // false for an idle lane (alignment padding before a group run)
+    __device__ __forceinline__ bool at(uint32_t x, uint32_t &pos, int &gl) const
+    {
+        gl = -1;
+        if (x < c8 - lo) { pos = lo + x; return true; }
+        if (x < a1) return false;
+        if (x < b1) { pos = c8 + (x - a1) / kGroup; gl = (int)((x - a1) % kGroup); return true; }
+        if (x < b1 + (c10 - c9)) { pos = c9 + (x - b1); return true; }
+        if (x < a2) return false;
+        pos = c10 + (x - a2) / kGroup;
+        gl = (int)((x - a2) % kGroup);
+        return true;
+    }
+};
+
+__device__ __forceinline__ void exec_lane(const DevDB &db, const DevBulk &b, const TxnView &v, int gl,
+                                          bool atomic_add)
+{
+    GlobalCells g;
+    if (gl < 0) exec_txn(db, b, v, atomic_add, g);
+    else if (v.type == GPUTX_T_OE_NEW_ORDER) exec_new_order_group(db, b, v, (uint32_t)gl, g);
+    else exec_order_status_group(db, b, v, (uint32_t)gl, g);
+}
+
 // one wide level [level_off[k0], level_off[k0+1]) over the whole grid
 __global__ void __launch_bounds__(256) kset_level_kernel(LevelArgs a)
 {
     if (a.ctl->err) return;
     const int64_t hb = a.ctl->base.hist;
     const uint32_t lo = __ldg(&a.level_off[a.k0]), hi = __ldg(&a.level_off[a.k0 + 1]);
-    for (uint32_t pos = lo + blockIdx.x * blockDim.x + threadIdx.x; pos < hi; pos += gridDim.x * blockDim.x) {
-        if (a.rec_dc) exec_dc_record(a.db, a.b, a.rec_dc[pos], hb + pos, a.atomic_add);
-        else exec_txn(a.db, a.b, view_at(a.b, pos, hb), a.atomic_add);
+    if (a.rec_dc) {
+        for (uint32_t pos = lo + blockIdx.x * blockDim.x + threadIdx.x; pos < hi; pos += gridDim.x * blockDim.x)
+            exec_dc_record(a.db, a.b, a.rec_dc[pos], hb + pos, a.atomic_add);
+        return;
+    }
+    LevelLanes L;
+    L.make(lo, hi, a.type_cut ? a.type_cut + 3 * (int64_t)a.k0 : nullptr);
+    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < L.v; x += gridDim.x * blockDim.x) {
+        uint32_t pos;
+        int gl;
+        if (L.at(x, pos, gl)) exec_lane(a.db, a.b, view_at(a.b, pos, hb), gl, a.atomic_add);
     }
 }
 
@@ -106,31 +163,47 @@ __global__ void __launch_bounds__(MAXT, 1) kset_narrow_kernel(LevelArgs a)
         nthreads = cl.num_threads();
         rank = cl.thread_rank();
     }
-    uint32_t lo = __ldg(&a.level_off[a.k0]);
-    uint32_t hi = __ldg(&a.level_off[a.k0 + 1]);
-    // this thread's first transaction of the current level, loaded ahead
+    const uint32_t *cut = a.type_cut;
+    LevelLanes L;
+    L.make(__ldg(&a.level_off[a.k0]), __ldg(&a.level_off[a.k0 + 1]), cut ? cut + 3 * (int64_t)a.k0 : nullptr);
+    // this thread's first lane of the current level, loaded ahead
     TxnView v{};
-    if (lo + rank < hi) {
-        v = view_at(a.b, lo + rank, hb);
-        prefetch_txn(a.db, v);
+    uint32_t pos;
+    int gl = -1;
+    bool has = rank < L.v && L.at(rank, pos, gl);
+    if (has) {
+        v = view_at(a.b, pos, hb);
+        if (gl < 0) prefetch_txn(a.db, v);
+        else prefetch_group(a.db, v, (uint32_t)gl);
     }
     for (uint32_t k = a.k0; k < a.k1; k++) {
-        const uint32_t nlo = hi;
-        const uint32_t nhi = (k + 1 < a.k1) ? __ldg(&a.level_off[k + 2]) : nlo;
-        // the next level's first signature for this thread: loads in flight
+        LevelLanes N;
+        if (k + 1 < a.k1)
+            N.make(__ldg(&a.level_off[k + 1]), __ldg(&a.level_off[k + 2]), cut ? cut + 3 * (int64_t)(k + 1) : nullptr);
+        else N.make(0, 0, nullptr);
+        // the next level's first record for this thread: loads in flight
         // while this level executes
         TxnView nv{};
-        const bool has_next = nlo + rank < nhi;
-        if (has_next) nv = view_at(a.b, nlo + rank, hb);
-        if (lo + rank < hi) exec_txn(a.db, a.b, v, a.atomic_add);
-        for (uint32_t pos = lo + rank + nthreads; pos < hi; pos += nthreads)
-            exec_txn(a.db, a.b, view_at(a.b, pos, hb), a.atomic_add);
-        if (has_next) prefetch_txn(a.db, nv);     // rows into L2 before the barrier
+        uint32_t npos;
+        int ngl = -1;
+        const bool has_next = rank < N.v && N.at(rank, npos, ngl);
+        if (has_next) nv = view_at(a.b, npos, hb);
+        if (has) exec_lane(a.db, a.b, v, gl, a.atomic_add);
+        for (uint32_t x = rank + nthreads; x < L.v; x += nthreads) {
+            uint32_t p2;
+            int g2;
+            if (L.at(x, p2, g2)) exec_lane(a.db, a.b, view_at(a.b, p2, hb), g2, a.atomic_add);
+        }
+        if (has_next) {                             // rows into L2 before the barrier
+            if (ngl < 0) prefetch_txn(a.db, nv);
+            else prefetch_group(a.db, nv, (uint32_t)ngl);
+        }
         if (CLUSTER) cg::this_cluster().sync();   // release/acquire at cluster scope
         else __syncthreads();
-        lo = nlo;
-        hi = nhi;
+        L = N;
         v = nv;
+        has = has_next;
+        gl = ngl;
     }
 }
 
@@ -225,95 +298,137 @@ __global__ void part_kernel(DevDB db, DevBulk b, const BulkCtl *ctl, const uint3
     }
 }
 
-// PART for bulks of debit-credit transactions only, one partition per
-// branch (Section 5.2 with the branch as partition key).  No transaction of
-// another partition touches this branch, its tellers or its accounts, so:
-//   - the branch balance lives in a register and the branch's tellers in
-//     shared memory for the whole partition, and are written back once;
-//   - the partition runs in batches of G transactions.  A batch issues all
-//     its record and account loads at once (one memory round trip, the
-//     accounts already prefetched into L2 by the batch before), then executes
-//     its transactions one by one in timestamp order.  An account loaded for
-//     the batch may have been written by an earlier transaction of the same
-//     batch: that transaction's new balance is forwarded instead (compared in
-//     registers); writes of earlier batches precede the loads in program
-//     order, so the loaded values include them.
-// The result equals running the partition's transactions one by one.
-constexpr int kPartDcTellers = 32;   // tellers per branch held in shared memory
+constexpr int kPartDcTellers = 32;   // tellers per branch the PART runner keeps on chip
 
-template <int G>
-__global__ void __launch_bounds__(128) part_dc_kernel(DevDB db, DevBulk b, const BulkCtl *ctl,
-                                                      const DcRecord *rec, const uint32_t *pkeys,
-                                                      const uint32_t *part_start)
+
+constexpr uint32_t kFull = 0xffffffffu;
+
+// sum of `x` over the lanes of `m` (this lane's group) and its inclusive
+// prefix up to this lane, in lane order; every lane of the warp calls it
+__device__ __forceinline__ void group_sum(uint32_t m, int64_t x, int64_t &pre, int64_t &tot)
 {
-    extern __shared__ unsigned long long part_smem[];
-    const uint32_t nt = blockDim.x, x = threadIdx.x;
-    int64_t *tel = (int64_t *)part_smem;   // teller k of thread x at [k * nt + x]
-    const uint32_t p = blockIdx.x * nt + x;
-    if (p >= ctl->npart || ctl->err) return;   // no block barrier below
+    const uint32_t lane = threadIdx.x & 31;
+    pre = 0;
+    tot = 0;
+#pragma unroll 4
+    for (int L = 0; L < 32; L++) {
+        const int64_t d = __shfl_sync(kFull, x, L);
+        if ((m >> L) & 1u) {
+            tot += d;
+            if ((uint32_t)L <= lane) pre += d;
+        }
+    }
+}
+
+// the same over the lanes `in` only (every lane of `in` calls it; m is a
+// subset of `in`)
+__device__ __forceinline__ void group_sum_in(uint32_t in, uint32_t m, int64_t x, int64_t &pre, int64_t &tot)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    pre = 0;
+    tot = 0;
+    for (uint32_t r = in; r; r &= r - 1) {
+        const int L = __ffs(r) - 1;
+        const int64_t d = __shfl_sync(in, x, L);
+        if ((m >> L) & 1u) {
+            tot += d;
+            if ((uint32_t)L <= lane) pre += d;
+        }
+    }
+}
+
+// one addition per distinct cell among the lanes with `on`, by the lowest
+// lane of each: `key` selects the cell; every lane of the warp calls it
+__device__ __forceinline__ void warp_add(bool on, uint32_t key, unsigned long long *cell, int64_t x)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t m = __match_any_sync(kFull, on ? key : (0xFFFFFFE0u | lane));
+    if (__any_sync(kFull, on && __popc(m) > 1)) {
+        int64_t pre, tot;
+        group_sum(m, x, pre, tot);
+        x = tot;
+    }
+    if (on && lane == (uint32_t)(__ffs(m) - 1)) atomicAdd(cell, (unsigned long long)x);
+}
+
+// PART for debit-credit bulks with one warp per partition (branch).  The
+// warp runs its partition's transactions in timestamp order, 32 at a time:
+// each step loads 32 records and their accounts at once, and lanes that
+// share an account within the step are grouped by __match_any_sync -- each
+// lane's new balance is the balance loaded for the step plus the inclusive
+// prefix of the group's deltas in lane (timestamp) order, and the group's
+// last lane writes the account back.  That is the result of running the
+// step's transactions one by one, so the partition still executes serially
+// in the sense of Section 5.2 (no other partition touches its rows, no
+// locks); the step only spreads the order-independent work (records,
+// history rows, outputs, teller and branch sums) over the lanes.  The
+// branch balance and its tellers stay on chip for the whole partition.
+// __syncwarp between steps orders one step's account stores before the
+// next step's loads.
+__global__ void __launch_bounds__(256) part_dc_warp_kernel(DevDB db, DevBulk b, const BulkCtl *ctl,
+                                                           const DcRecord *rec, const uint32_t *pkeys,
+                                                           const uint32_t *part_start)
+{
+    __shared__ int64_t s_tel[8][32];   // this warp's tellers (at most 32 per branch)
+    const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint32_t p = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (p >= ctl->npart || ctl->err) return;   // whole warps; no block barrier below
     const int64_t hb = ctl->base.hist;
     const uint32_t lo = part_start[p], hi = part_start[p + 1];
     const uint32_t br = __ldg(&pkeys[lo]);     // partition key = branch
     const uint32_t tpb = (uint32_t)(db.acc_per_br / db.acc_per_tel);
     const uint32_t tel0 = br * tpb;
-    int64_t bbal = __ldcg(&db.br_bal[br]);
-    for (uint32_t k = 0; k < tpb; k++) tel[k * nt + x] = __ldcg(&db.tel_bal[tel0 + k]);
-    // the first batch's accounts into L2
-    for (uint32_t k = 0; k < G && lo + k < hi; k++) prefetch_l2(&db.acc_bal[__ldg(&rec[lo + k].a)]);
-    for (uint32_t base = lo; base < hi; base += G) {
-        const uint32_t cnt = min((uint32_t)G, hi - base);
-        DcRecord r[G];
-        uint32_t an[G];
-        int64_t v[G];
-#pragma unroll
-        for (int k = 0; k < G; k++) {
-            if (k < (int)cnt) r[k] = rec[base + k];
-            else r[k] = DcRecord{0, 0, 0, 0, 0, 0};
+    int64_t *tel = s_tel[wib];
+    tel[lane] = lane < tpb ? __ldcg(&db.tel_bal[tel0 + lane]) : 0;
+    int64_t bsum = 0;
+    __syncwarp();
+    // the first step's records and accounts on their way
+    DcRecord r{};
+    if (lo + lane < hi) r = rec[lo + lane];
+    for (uint32_t base = lo; base < hi; base += 32) {
+        const uint32_t i = base + lane;
+        const bool act = i < hi;
+        const int64_t slot = hb + i;
+        const bool run = act && slot < db.hist_cap;
+        if (act && !run) {                     // history full: not executed
+            set_err(b.err, ERR_CAPACITY);
+            b.status[r.t] = 3;
         }
-#pragma unroll
-        for (int k = 0; k < G; k++) an[k] = (base + G + k < hi) ? __ldg(&rec[base + G + k].a) : 0xffffffffu;
-#pragma unroll
-        for (int k = 0; k < G; k++) v[k] = (k < (int)cnt) ? __ldcg(&db.acc_bal[r[k].a]) : 0;
-        // the next batch's accounts into L2, the records after it into L1
-#pragma unroll
-        for (int k = 0; k < G; k++)
-            if (an[k] != 0xffffffffu) prefetch_l2(&db.acc_bal[an[k]]);
-#pragma unroll
-        for (int k = 0; k < G; k += 4)
-            if (base + 2 * G + k < hi) asm volatile("prefetch.global.L1 [%0];" ::"l"(rec + base + 2 * G + k));
-#pragma unroll
-        for (int k = 0; k < G; k++) {
-            if (k >= (int)cnt) break;
-            // the newest balance: forwarded from an earlier transaction of
-            // this batch on the same account, else the loaded value
-            int64_t old = v[k];
-#pragma unroll
-            for (int j = 0; j < k; j++)
-                if (r[j].a == r[k].a) old = v[j];
-            const int64_t slot = hb + base + k;
-            if (slot >= db.hist_cap) {          // history full: not executed
-                set_err(b.err, ERR_CAPACITY);
-                b.status[r[k].t] = 3;
-                v[k] = old;                     // later forwards see the unchanged balance
-                continue;
-            }
-            const int64_t na = wrap_add(old, r[k].delta);
-            v[k] = na;                          // from here on: this transaction's new balance
-            __stcg(&db.acc_bal[r[k].a], na);
-            int64_t *tc = &tel[(r[k].tl - tel0) * nt + x];
-            *tc = wrap_add(*tc, r[k].delta);
-            bbal = wrap_add(bbal, r[k].delta);
-            db.h_ts[slot] = r[k].ts;
-            db.h_acc[slot] = r[k].a;
-            db.h_tel[slot] = r[k].tl;
+        const int64_t old = run ? __ldcg(&db.acc_bal[r.a]) : 0;
+        // the next step's records, and its accounts into L2
+        DcRecord nr{};
+        if (base + 32 + lane < hi) {
+            nr = rec[base + 32 + lane];
+            prefetch_l2(&db.acc_bal[nr.a]);
+        }
+        const uint32_t am = __match_any_sync(kFull, run ? r.a : (0xFFFFFFE0u | lane));
+        int64_t pre = r.delta, tot = r.delta;
+        if (__any_sync(kFull, run && __popc(am) > 1)) group_sum(am, r.delta, pre, tot);
+        if (run) {
+            const int64_t na = wrap_add(old, pre);
+            if (lane == 31u - (uint32_t)__clz(am)) __stcg(&db.acc_bal[r.a], wrap_add(old, tot));
+            db.h_ts[slot] = r.ts;
+            db.h_acc[slot] = r.a;
+            db.h_tel[slot] = r.tl;
             db.h_br[slot] = br;
-            db.h_delta[slot] = r[k].delta;
-            b.out[(int64_t)r[k].t * b.R] = na;
-            b.status[r[k].t] = 0;
+            db.h_delta[slot] = r.delta;
+            b.out[(int64_t)r.t * b.R] = na;
+            b.status[r.t] = 0;
         }
+        // teller sums: one addition per teller by its group's first lane
+        const uint32_t tm = __match_any_sync(kFull, run ? r.tl : (0xFFFFFFE0u | lane));
+        int64_t tpre, ttot = r.delta;
+        if (__any_sync(kFull, run && __popc(tm) > 1)) group_sum(tm, r.delta, tpre, ttot);
+        if (run && lane == (uint32_t)(__ffs(tm) - 1)) tel[r.tl - tel0] = wrap_add(tel[r.tl - tel0], ttot);
+        bsum = wrap_add(bsum, run ? r.delta : 0);
+        __syncwarp();   // this step's account stores before the next step's loads
+        r = nr;
     }
-    __stcg(&db.br_bal[br], bbal);
-    for (uint32_t k = 0; k < tpb; k++) __stcg(&db.tel_bal[tel0 + k], tel[k * nt + x]);
+    // the branch: the sum of every lane's deltas
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bsum = wrap_add(bsum, __shfl_xor_sync(kFull, bsum, o));
+    if (lane == 0) __stcg(&db.br_bal[br], wrap_add(__ldcg(&db.br_bal[br]), bsum));
+    if (lane < tpb) __stcg(&db.tel_bal[tel0 + lane], tel[lane]);
 }
 
 struct TplArgs {
@@ -330,7 +445,32 @@ struct TplArgs {
     LockSlots slot;      // item -> its counter in `done`
 };
 
-__global__ void tpl_kernel(TplArgs a)
+// a relaxed poll of a lock counter: several can be in flight at once (an
+// acquire load would order each behind the one before); one acquire fence
+// follows once every lock of the transaction is granted
+__device__ __forceinline__ uint32_t ld_relaxed_gpu(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void fence_acquire_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+// TPL for any registered types.  Each transaction holds one ordered counter
+// lock per basic operation (Section 5.1, Appendix C's counter lock with
+// ticket semantics): an operation whose group has `ticket` operations before
+// its run may proceed once that many have released the item's counter.
+// Tickets follow the timestamp order of the group, so the earliest unfinished
+// transaction never waits and no deadlock can form.
+//
+// A transaction polls all its locks not yet granted at once (relaxed loads in
+// flight together: one round trip, not one per lock; a granted lock stays
+// granted, since no later operation releases before this one) and then only
+// the one furthest behind, sleeping about 500 ns per release it still misses;
+// once every lock is granted, one acquire fence orders its accesses after
+// the releases it saw.  The wait limit runs from the last lock granted.
+__global__ void __launch_bounds__(512, 1) tpl_kernel(TplArgs a)
 {
     __shared__ uint32_t s_c, s_stop;
     const int64_t n = a.b.n;
@@ -351,17 +491,67 @@ __global__ void tpl_kernel(TplArgs a)
                                                 : a.uniform_k);
             const TxnView v = view_of(a.b, (uint32_t)t, hb);
             prefetch_txn(a.db, v);
+            uint32_t granted = 0;                                   // bit j: lock j granted
+            const uint32_t all = cnt >= 32 ? kFull : ((1u << cnt) - 1u);
+            int blk = -1;                  // the lock holding it back (-1: poll every lock)
+            uint64_t t_prog = globaltimer();
+            uint32_t spins = 0;
             bool ok = true;
-            for (int j = 0; j < cnt && ok; j++) {
-                const uint32_t tk = a.lock_ticket[off + j];
-                if (tk && !wait_at_least(&a.done[a.slot(a.lock_key[off + j])], tk, a.spin_limit_ns, 500)) {
+            while (true) {
+                uint32_t gap = 0;
+                const uint32_t before = granted;
+                if (blk >= 0) {
+                    const uint32_t tk = __ldg(&a.lock_ticket[off + blk]);
+                    const uint32_t c = ld_relaxed_gpu(&a.done[a.slot(__ldg(&a.lock_key[off + blk]))]);
+                    if (c >= tk) {
+                        granted |= 1u << blk;
+                        blk = -1;
+                    } else {
+                        gap = tk - c;
+                    }
+                }
+                if (blk < 0 && granted != all) {
+                    uint32_t c[MAX_OPS], tk[MAX_OPS];
+#pragma unroll
+                    for (int j = 0; j < MAX_OPS; j++) {          // the polls, all in flight
+                        tk[j] = 0;
+                        c[j] = 0;
+                        if (j < cnt && !((granted >> j) & 1u)) {
+                            tk[j] = __ldg(&a.lock_ticket[off + j]);
+                            if (tk[j]) c[j] = ld_relaxed_gpu(&a.done[a.slot(__ldg(&a.lock_key[off + j]))]);
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < MAX_OPS; j++) {
+                        if (j < cnt && !((granted >> j) & 1u)) {
+                            if (c[j] >= tk[j]) {
+                                granted |= 1u << j;
+                            } else if (tk[j] - c[j] > gap) {    // the furthest behind
+                                gap = tk[j] - c[j];
+                                blk = j;
+                            }
+                        }
+                    }
+                }
+                if (granted == all) break;
+                const uint64_t now = globaltimer();
+                if (granted != before) {
+                    t_prog = now;
+                } else if (now - t_prog > a.spin_limit_ns) {
                     set_err(&a.ctl->err, ERR_TIMEOUT);
                     ok = false;
+                    break;
                 }
+                // missing `gap` releases take at least that many hand-offs
+                if (gap > 1) __nanosleep(gap > 64 ? 64 * 500 : gap * 500);
+                else if (++spins > 64) __nanosleep(32);
             }
-            if (ok) exec_txn(a.db, a.b, v, a.atomic_add);
+            if (ok) {
+                fence_acquire_gpu();   // with the polls: acquire of every granted lock
+                exec_txn(a.db, a.b, v, a.atomic_add);
+            }
             // each release is a release: this transaction's writes before it
-            for (int j = 0; j < cnt; j++) red_release_add(&a.done[a.slot(a.lock_key[off + j])], 1u);
+            for (int j = 0; j < cnt; j++) red_release_add(&a.done[a.slot(__ldg(&a.lock_key[off + j]))], 1u);
         }
         __syncthreads();
     }
@@ -369,18 +559,33 @@ __global__ void tpl_kernel(TplArgs a)
 
 // TPL for debit-credit-only bulks.  A transaction's one lock is its root
 // key's counter (the branch under R/W, the account under ADD).  Once it is
-// granted, the account takes a fetch-and-add at L2 (dc_account_rmw: its old
-// value gives the output) and the lock is released; the teller and branch
-// additions, the history row and the outputs follow the release.  No
-// transaction of the bulk reads a teller or branch balance or the history,
-// and integer additions commute, so the next holder may run before those
-// land: the hand-off waits for one atomic round trip instead of a load, the
-// stores and their acknowledgement.
+// granted, the account takes a fetch-and-add at L2 (its old value gives the
+// output) and the lock is released; the teller and branch additions, the
+// history row and the outputs follow the release.  No transaction of the
+// bulk reads a teller or branch balance or the history, and integer
+// additions commute, so the next holder may run before those land: the
+// hand-off waits for one atomic round trip instead of a load, the stores and
+// their acknowledgement.
+//
+// Lanes of a warp that need the same counter are grouped by
+// __match_any_sync.  Every operation here is a write and the warp holds
+// consecutive timestamps, so no other transaction's operation on that item
+// lies between two lanes of a group: their tickets are consecutive, and the
+// whole group runs, in lane (timestamp) order, as soon as its first lane's
+// ticket is granted.  Only that lane waits on the counter (the others wait
+// for it at the group's __syncwarp, not on memory), and one addition of the
+// group's size releases it.  Within a group, lanes on the same account
+// combine their deltas (warp-aggregated atomics): one fetch-and-add of the
+// sum, each lane's new balance = the old value plus the inclusive prefix of
+// the deltas in lane order -- the serial result bit for bit.  Teller and
+// branch additions are aggregated the same way.  Groups of one warp wait
+// independently of each other.
 __global__ void tpl_dc_kernel(TplArgs a)
 {
     __shared__ uint32_t s_c, s_stop;
     const int64_t n = a.b.n;
     const int64_t hb = a.ctl->base.hist;
+    const uint32_t lane = threadIdx.x & 31;
     while (true) {
         if (threadIdx.x == 0) {
             s_stop = *(volatile uint32_t *)&a.ctl->err ? 1u : 0u;
@@ -390,6 +595,7 @@ __global__ void tpl_dc_kernel(TplArgs a)
         const int64_t start = (int64_t)s_c * blockDim.x;
         if (s_stop || start >= n) break;
         const int64_t t = start + threadIdx.x;
+        const uint32_t live = __ballot_sync(kFull, t < n);
         if (t < n) {
             DcRecord r;
             r.a = (uint32_t)__ldg(&a.b.params[t * a.b.P]);
@@ -401,12 +607,54 @@ __global__ void tpl_dc_kernel(TplArgs a)
             prefetch_l2(&a.db.acc_bal[r.a]);
             const uint32_t key = a.slot(a.lock_key[t]);
             const uint32_t tk = a.lock_ticket[t];
-            const bool ok = !tk || wait_at_least(&a.done[key], tk, a.spin_limit_ns, 500);
-            if (!ok) set_err(&a.ctl->err, ERR_TIMEOUT);
-            DcOut o;
-            const bool pending = ok && dc_account_rmw(a.db, a.b, r, hb + t, o);
-            red_release_add(&a.done[key], 1u);
-            if (pending) dc_finish_rmw(a.db, a.b, o);
+            const uint32_t grp = __match_any_sync(live, key);
+            const uint32_t leader = __ffs(grp) - 1;
+            bool ok = true;
+            if (lane == leader && tk) ok = wait_at_least(&a.done[key], tk, a.spin_limit_ns, 500);
+            ok = __shfl_sync(grp, ok, leader);
+            __syncwarp(grp);   // the leader's acquire before the members' accesses
+            if (!ok && lane == leader) set_err(&a.ctl->err, ERR_TIMEOUT);
+            const int64_t slot = hb + t;
+            const bool run = ok && slot < a.db.hist_cap;
+            if (ok && !run) {                  // history full: not executed
+                set_err(a.b.err, ERR_CAPACITY);
+                a.b.status[r.t] = 3;
+            }
+            // the account: one fetch-and-add per distinct account of the group
+            const uint32_t am = __match_any_sync(grp, run ? r.a : (0xFFFFFFE0u | lane));
+            int64_t pre = r.delta, tot = r.delta;
+            if (__any_sync(grp, run && __popc(am) > 1)) group_sum_in(grp, am, r.delta, pre, tot);
+            const uint32_t al = __ffs(am) - 1;
+            int64_t old = 0;
+            if (run && lane == al)
+                old = (int64_t)atomicAdd((unsigned long long *)&a.db.acc_bal[r.a], (unsigned long long)tot);
+            old = __shfl_sync(grp, old, al);
+            __syncwarp(grp);
+            // one release for the group: every member's update precedes it
+            if (lane == leader) red_release_add(&a.done[key], (uint32_t)__popc(grp));
+            // teller and branch: one addition per distinct cell of the group
+            const uint32_t tm = __match_any_sync(grp, run ? r.tl : (0xFFFFFFE0u | lane));
+            int64_t tpre = r.delta, ttot = r.delta;
+            if (__any_sync(grp, run && __popc(tm) > 1)) group_sum_in(grp, tm, r.delta, tpre, ttot);
+            if (run && lane == (uint32_t)(__ffs(tm) - 1))
+                atomicAdd((unsigned long long *)&a.db.tel_bal[r.tl], (unsigned long long)ttot);
+            const uint32_t bm = __match_any_sync(grp, run ? r.br : (0xFFFFFFE0u | lane));
+            int64_t bpre = r.delta, btot = r.delta;
+            if (__any_sync(grp, run && __popc(bm) > 1)) group_sum_in(grp, bm, r.delta, bpre, btot);
+            if (run && lane == (uint32_t)(__ffs(bm) - 1))
+                atomicAdd((unsigned long long *)&a.db.br_bal[r.br], (unsigned long long)btot);
+            if (run) {
+                DcOut o;
+                o.slot = slot;
+                o.ts = r.ts;
+                o.delta = r.delta;
+                o.na = wrap_add(old, pre);
+                o.a = r.a;
+                o.tl = r.tl;
+                o.br = r.br;
+                o.t = r.t;
+                dc_finish(a.db, a.b, o);
+            }
         }
         __syncthreads();
     }
@@ -435,10 +683,10 @@ static int width_class(uint32_t w)
 // class begins.  Shorter stretches stay in the segment, so every launch but a
 // run's last covers at least kMinSegment levels and the launch overhead stays
 // small against the levels' own latency.
-static int64_t narrow_segment_end(const uint32_t *level_off_host, int64_t k, int64_t run_end)
+static int64_t narrow_segment_end(const uint32_t *width, int64_t k, int64_t run_end)
 {
     constexpr int64_t kMinSegment = 64;
-    auto cls = [&](int64_t j) { return width_class(level_off_host[j + 1] - level_off_host[j]); };
+    auto cls = [&](int64_t j) { return width_class(width[j]); };
     int cmax = cls(k);
     int64_t j = k + 1;
     while (j < run_end) {
@@ -457,6 +705,18 @@ static int64_t narrow_segment_end(const uint32_t *level_off_host, int64_t k, int
         }
     }
     return j;
+}
+
+// lanes a level takes (LevelLanes::v, on the host): one per transaction,
+// 16 per new-order and order-status when the type cuts are known
+static uint32_t level_lanes(uint32_t lo, uint32_t hi, const uint32_t *cut)
+{
+    if (!cut) return hi - lo;
+    const uint32_t c8 = cut[0], c9 = cut[1], c10 = cut[2];
+    const uint32_t a1 = (c8 - lo + kGroup - 1) & ~(uint32_t)(kGroup - 1);
+    const uint32_t b1 = a1 + kGroup * (c9 - c8);
+    const uint32_t a2 = (b1 + (c10 - c9) + kGroup - 1) & ~(uint32_t)(kGroup - 1);
+    return a2 + kGroup * (hi - c10);
 }
 
 // clusters of this size that fit the device at once (0 = none)
@@ -490,6 +750,7 @@ int exec_blocks_per_sm(int kind, int block)
 {
     int nb = 1;
     if (kind == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kset_kernel, block, 0);
+    else if (kind == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tpl_dc_kernel, block, 0);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tpl_kernel, block, 0);
     return nb < 1 ? 1 : nb;
 }
@@ -522,7 +783,7 @@ cudaError_t launch_kset(gputx_bulk *b, const uint32_t *order, int64_t nchunks, i
 }
 
 cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, int64_t depth, int narrow_max,
-                               bool atomic_add, const DcRecord *dc_records)
+                               bool atomic_add, const DcRecord *dc_records, const uint32_t *type_cut_host)
 {
     gputx_db *db = b->db;
     if (b->n == 0) return cudaSuccess;
@@ -532,8 +793,13 @@ cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, in
     a.ctl = b->ctl;
     a.level_off = b->sc.level_off;
     a.rec_dc = dc_records;
+    a.type_cut = (type_cut_host && !dc_records) ? b->sc.type_cut : nullptr;
     a.atomic_add = atomic_add;
     const int64_t levels = depth + 1;
+    // lanes per level: the launch shapes follow them
+    std::vector<uint32_t> width((size_t)levels);
+    for (int64_t j = 0; j < levels; j++)
+        width[j] = level_lanes(level_off_host[j], level_off_host[j + 1], a.type_cut ? type_cut_host + 3 * j : nullptr);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(kset_narrow_kernel<true, 256>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -543,7 +809,7 @@ cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, in
     }
     int64_t k = 0, run_end = 0;
     while (k < levels) {
-        const uint32_t w = level_off_host[k + 1] - level_off_host[k];
+        const uint32_t w = width[k];
         if ((int64_t)w > narrow_max) {
             a.k0 = (uint32_t)k;
             a.k1 = (uint32_t)k + 1;
@@ -560,16 +826,11 @@ cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, in
         // narrow_segment_end)
         if (run_end <= k) {
             run_end = k;
-            while (run_end < levels &&
-                   (int64_t)(level_off_host[run_end + 1] - level_off_host[run_end]) <= narrow_max)
-                run_end++;
+            while (run_end < levels && (int64_t)width[run_end] <= narrow_max) run_end++;
         }
-        const int64_t e = narrow_segment_end(level_off_host, k, run_end);
+        const int64_t e = narrow_segment_end(width.data(), k, run_end);
         uint32_t wmax = 0;
-        for (int64_t j = k; j < e; j++) {
-            const uint32_t wj = level_off_host[j + 1] - level_off_host[j];
-            wmax = wj > wmax ? wj : wmax;
-        }
+        for (int64_t j = k; j < e; j++) wmax = width[j] > wmax ? width[j] : wmax;
         a.k0 = (uint32_t)k;
         a.k1 = (uint32_t)e;
         // spread a level over up to 16 SMs, about 64 transactions each, so
@@ -634,14 +895,10 @@ cudaError_t launch_part(gputx_bulk *b, const uint32_t *pkeys, int block, int64_t
     threads = threads < 8 ? 8 : (threads > block ? block : threads);
     const int64_t grid = (parts + threads - 1) / threads;   // npart <= parts, read on the device
     if (part_dc_applies(db, part_size)) {
-        const size_t smem = (size_t)threads * kPartDcTellers * 8;
-        if (smem > (48u << 10)) {
-            const cudaError_t e = cudaFuncSetAttribute(part_dc_kernel<16>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e) return e;
-        }
-        part_dc_kernel<16><<<(unsigned)grid, threads, smem, b->stream>>>(db->dev, d, b->ctl, b->sc.rec_dc, pkeys,
-                                                                       b->sc.part_start);
+        // one warp per partition, 8 warps a CTA
+        const int64_t wgrid = (parts + 7) / 8;
+        part_dc_warp_kernel<<<(unsigned)wgrid, 256, 0, b->stream>>>(db->dev, d, b->ctl, b->sc.rec_dc, pkeys,
+                                                                    b->sc.part_start);
     } else {
         const size_t smem = (size_t)threads * 2 * CachedCells::kSlots * sizeof(unsigned long long);
         part_kernel<<<(unsigned)grid, threads, smem, b->stream>>>(db->dev, d, b->ctl, pkeys, b->sc.part_start);
@@ -681,11 +938,19 @@ cudaError_t launch_tpl(gputx_bulk *b, int block, bool atomic_add)
     cudaError_t e = cudaMemsetAsync(&b->ctl->claim, 0, sizeof(uint32_t), b->stream);
     if (e) return e;
     a.slot = db->lock_slots;
-    int64_t grid = (int64_t)db->num_sms * exec_blocks_per_sm(1, block);
+    // debit-credit-only bulks of single-lock transactions
+    const bool dc = db->dev.registered == (1u << GPUTX_T_DC_DEBIT_CREDIT) && !b->graph && db->uniform_k == 1;
+    // the general kernel's registers allow CTAs of up to 512 threads; the
+    // CTA size changes only how many transactions a CTA claims at once
+    if (!dc && block > 512) block = 512;
+    // resident transactions: enough to keep every lock chain moving, few
+    // enough that waiters' polls do not crowd the L2 slices of hot counters
+    // (three 256-thread CTAs an SM measured best for the debit-credit kernel)
+    int64_t grid = dc ? (int64_t)db->num_sms * std::max(1, 768 / block)
+                      : (int64_t)db->num_sms * exec_blocks_per_sm(1, block);
     const int64_t chunks = (b->n + block - 1) / block;
     if (grid > chunks) grid = chunks;
-    // debit-credit-only bulks of single-lock transactions
-    if (db->dev.registered == (1u << GPUTX_T_DC_DEBIT_CREDIT) && !b->graph && db->uniform_k == 1)
+    if (dc)
         tpl_dc_kernel<<<(unsigned)grid, block, 0, b->stream>>>(a);
     else
         tpl_kernel<<<(unsigned)grid, block, 0, b->stream>>>(a);

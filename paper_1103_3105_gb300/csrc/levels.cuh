@@ -12,6 +12,7 @@ struct LevelArgs {
     const BulkCtl *ctl;
     const uint32_t *level_off;
     const DcRecord *rec_dc;   // debit-credit-only bulks: packed records in execution order
+    const uint32_t *type_cut; // per level, where new-order, payment, order-status start (or null)
     uint32_t k0, k1;          // levels [k0, k1)
     bool atomic_add;
 };

@@ -653,6 +653,215 @@ __device__ __forceinline__ void exec_oe(const DevDB &db, const DevBulk &b, const
     b.status[t] = st;
 }
 
+// ---------------------------------------------------------------------------
+// order-entry's line-parallel procedures: one transaction on a group of 16
+// lanes (a half warp).  A new-order's lines touch distinct stock rows (its
+// items are distinct), so they need no order among themselves: lane l runs
+// line l, and the reads of all lines go out in one round trip instead of one
+// per chunk of lines.  Lane 0 also runs the transaction's own part (district
+// counter, order row, index, customer, outputs).  The results equal
+// exec_oe's bit for bit.  Every lane of the group calls these together;
+// `gl` is the lane's index in its group.
+// ---------------------------------------------------------------------------
+constexpr int kGroup = 16;
+
+__device__ __forceinline__ uint32_t group_mask() { return 0xFFFFu << ((threadIdx.x & 31) & 16); }
+
+__device__ __forceinline__ int64_t group_sum16(uint32_t gm, int64_t x)
+{
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) x += __shfl_xor_sync(gm, x, o, kGroup);
+    return x;
+}
+
+// the first slot at or after `home` (in probe order) whose key satisfies
+// `want` (1: equals key or empty -- a lookup; 2: empty or deleted -- an
+// insert), probing 16 slots per round trip; -1 if none
+__device__ __forceinline__ int64_t group_probe(uint32_t gm, uint32_t gl, const HashIndex &h, unsigned long long key,
+                                               int want, unsigned long long *found)
+{
+    const uint64_t home = hmix(key) & h.mask;
+    for (uint64_t base = 0; base <= h.mask; base += kGroup) {
+        const uint64_t i = (home + base + gl) & h.mask;
+        const unsigned long long k = (base + gl <= h.mask) ? __ldcg(&h.keys[i]) : key + 1;
+        const bool hit = (want == 1) ? (k == key || k == HKEY_EMPTY) : (k == HKEY_EMPTY || k == HKEY_TOMB);
+        const uint32_t m = __ballot_sync(gm, hit) & gm;
+        if (m) {
+            const int src = __ffs(m) - 1;
+            *found = __shfl_sync(gm, k, src & 15, kGroup);
+            return (int64_t)((home + base + (uint64_t)((src & 15))) & h.mask);
+        }
+    }
+    return -1;
+}
+
+template <class Cells>
+__device__ __forceinline__ void exec_new_order_group(const DevDB &db, const DevBulk &b, const TxnView &v, uint32_t gl,
+                                                     Cells &cells)
+{
+    const uint32_t gm = group_mask();
+    const int64_t *p = v.p;
+    const uint32_t t = v.t;
+    const int64_t w = v.p0, d = w * OE_DIST + v.p1;
+    const int64_t cw = __ldg(&p[2]);
+    const int64_t c = d * OE_CUST + cw;
+    const int cnt = (int)__ldg(&p[3]);
+    const bool mine = (int)gl < cnt;
+    int64_t line = 0, item = 0, sw = 0, qty = 0, s = 0;
+    if (mine) {
+        line = __ldg(&p[4 + gl]);
+        item = line & 0xFFFFFF;
+        sw = (line >> 24) & 0xFFFF;
+        qty = (line >> 40) & 0xFF;
+    }
+    // read phase: an unknown item aborts the order (status 1, no writes)
+    if (__any_sync(gm, mine && item >= db.n_items)) {
+        if (gl == 0) b.status[t] = 1;
+        return;
+    }
+    const int64_t oslot = b.base->ord + b.slot_ord[t];
+    const int64_t lslot = b.base->ol + b.slot_ol[t];
+    if (oslot >= db.ord_cap || lslot + cnt > db.ol_cap) {
+        if (gl == 0) {
+            set_err(b.err, ERR_CAPACITY);
+            b.status[t] = 3;
+        }
+        return;
+    }
+    // every read in one round trip: the district's counter and the rates on
+    // lane 0, each line's item and stock row on its lane
+    int64_t o_id = 0, disc = 0, w_tax = 0, d_tax = 0, price = 0, sy = 0;
+    int32_t q = 0, so = 0;
+    if (gl == 0) {
+        o_id = cells.ld(&db.d_next_o_id[d]);
+        disc = __ldg(&db.c_discount[c]);
+        w_tax = __ldg(&db.w_tax[w]);
+        d_tax = __ldg(&db.d_tax[d]);
+    }
+    if (mine) {
+        s = sw * db.n_items + item;
+        price = __ldg(&db.i_price[item]);
+        q = ldg_cg(&db.s_quantity[s]);
+        sy = cells.ld(&db.s_ytd[s]);
+        so = ldg_cg(&db.s_order_cnt[s]);
+    }
+    int64_t amount = 0;
+    if (mine) {
+        amount = qty * price;
+        const int32_t nq = (q >= qty + 10) ? (int32_t)(q - qty) : (int32_t)(q - qty + 91);
+        stg_cg(&db.s_quantity[s], nq);
+        cells.st(&db.s_ytd[s], sy + qty);
+        stg_cg(&db.s_order_cnt[s], so + 1);
+        db.ol_item[lslot + gl] = (int32_t)item;
+        db.ol_sw[lslot + gl] = (int32_t)sw;
+        db.ol_qty[lslot + gl] = (int32_t)qty;
+        stg_cg(&db.ol_amount[lslot + gl], amount);
+    }
+    const int64_t total = group_sum16(gm, amount);
+    o_id = __shfl_sync(gm, o_id, 0, kGroup);
+    // the order index: the first free slot on the key's probe path, claimed
+    // by compare-and-swap (other orders' inserts may race for it)
+    const unsigned long long key = ord_key(d, o_id);
+    bool inserted = false;
+    for (int attempt = 0; attempt < 64 && !inserted; attempt++) {
+        unsigned long long cur = 0;
+        const int64_t slot = group_probe(gm, gl, db.ord_idx, key, 2, &cur);
+        if (slot < 0) break;
+        unsigned long long prev = 0;
+        if (gl == 0) prev = atomicCAS(&db.ord_idx.keys[slot], cur, key);
+        prev = __shfl_sync(gm, prev, 0, kGroup);
+        if (prev == cur) {
+            if (gl == 0) __stcg(&db.ord_idx.rows[slot], (uint32_t)oslot);
+            inserted = true;
+        }
+    }
+    if (gl == 0) {
+        cells.st(&db.d_next_o_id[d], o_id + 1);
+        db.o_w[oslot] = (int32_t)w;
+        db.o_d[oslot] = (int32_t)v.p1;
+        db.o_c[oslot] = (int32_t)cw;
+        stg_cg(&db.o_cnt[oslot], (int32_t)cnt);
+        stg_cg(&db.o_id[oslot], o_id);
+        stg_cg(&db.o_first[oslot], lslot);
+        stg_cg(&db.o_live[oslot], (uint8_t)1);
+        int64_t *out = b.out + (int64_t)t * b.R;
+        if (!inserted) {
+            set_err(b.err, ERR_CAPACITY);
+            b.status[t] = 3;
+            return;
+        }
+        cells.st(&db.c_last_o_id[c], o_id);
+        out[0] = o_id;
+        out[1] = total * (10000 - disc) * (10000 + w_tax + d_tax) / 100000000;
+        out[2] = cnt;
+        b.status[t] = 0;
+    }
+}
+
+template <class Cells>
+__device__ __forceinline__ void exec_order_status_group(const DevDB &db, const DevBulk &b, const TxnView &v,
+                                                        uint32_t gl, Cells &cells)
+{
+    const uint32_t gm = group_mask();
+    const int64_t *p = v.p;
+    const uint32_t t = v.t;
+    const int64_t w = v.p0, d = w * OE_DIST + v.p1, c = d * OE_CUST + __ldg(&p[2]);
+    int64_t *out = b.out + (int64_t)t * b.R;
+    int64_t o = 0;
+    if (gl == 0) {
+        o = cells.ld(&db.c_last_o_id[c]);
+        const int64_t bal = cells.ld(&db.c_balance[c]);
+        out[0] = bal;
+        out[1] = o;
+    }
+    o = __shfl_sync(gm, o, 0, kGroup);
+    if (o == 0) {
+        if (gl == 0) b.status[t] = 1;
+        return;
+    }
+    unsigned long long k = 0;
+    const int64_t slot = group_probe(gm, gl, db.ord_idx, ord_key(d, o), 1, &k);
+    if (slot < 0 || k != ord_key(d, o)) {
+        if (gl == 0) {
+            set_err(b.err, ERR_BOUNDS);
+            b.status[t] = 1;
+        }
+        return;
+    }
+    const int64_t r = (int64_t)__ldcg(&db.ord_idx.rows[slot]);
+    const int cnt = ldg_cg(&db.o_cnt[r]);
+    const int64_t first = ldg_cg(&db.o_first[r]);
+    const int64_t amt = (int)gl < cnt ? ldg_cg(&db.ol_amount[first + gl]) : 0;
+    const int64_t sum = group_sum16(gm, amt);
+    if (gl == 0) {
+        out[2] = cnt;
+        out[3] = sum;
+        b.status[t] = 0;
+    }
+}
+
+// L2 prefetch of the rows lane gl of a group will touch
+__device__ __forceinline__ void prefetch_group(const DevDB &db, const TxnView &v, uint32_t gl)
+{
+    const int64_t *p = v.p;
+    if (v.type == GPUTX_T_OE_NEW_ORDER) {
+        if (gl == 0) prefetch_l2(&db.d_next_o_id[v.p0 * OE_DIST + v.p1]);
+        const int cnt = (int)__ldg(&p[3]);
+        if ((int)gl < cnt) {
+            const int64_t line = __ldg(&p[4 + gl]);
+            const int64_t item = line & 0xFFFFFF, sw = (line >> 24) & 0xFFFF;
+            if (item < db.n_items) {
+                prefetch_l2(&db.s_quantity[sw * db.n_items + item]);
+                prefetch_l2(&db.s_ytd[sw * db.n_items + item]);
+            }
+        }
+    } else if (gl == 0) {
+        const int64_t c = (v.p0 * OE_DIST + v.p1) * OE_CUST + __ldg(&p[2]);
+        prefetch_l2(&db.c_last_o_id[c]);
+        prefetch_l2(&db.c_balance[c]);
+    }
+}
+
 template <class Cells>
 __device__ __forceinline__ void exec_txn(const DevDB &db, const DevBulk &b, const TxnView &v, bool atomic_add,
                                          Cells &cells)

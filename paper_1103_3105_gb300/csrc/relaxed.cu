@@ -21,7 +21,7 @@ struct TplRelaxedArgs {
     DevDB db;
     DevBulk b;
     BulkCtl *ctl;
-    uint32_t *lock;      // one word per item, 0 = free (zero between bulks)
+    uint32_t *lock;      // one word per item (zero between bulks)
     LockSlots slot;      // item -> its word of `lock`
     uint32_t *order;     // order[ticket] = transaction
     int mode;
@@ -29,31 +29,59 @@ struct TplRelaxedArgs {
     bool atomic_add;
 };
 
-// compare-and-swap 0 -> 1 with acquire semantics: a holder sees every write
-// its predecessors made before their release
-__device__ __forceinline__ bool try_lock(uint32_t *l)
+constexpr uint32_t kFull = 0xffffffffu;
+
+// The lock of Figure 10 with a version in the word: even = free, odd = held.
+// Taking it swaps an even value v for v + 1, releasing stores v + 2, so the
+// word changes at every hand-off.  A waiter therefore tells a lock that is
+// passed along a long queue (progress: keep waiting) from one whose holder
+// never lets go (the wait limit runs from the last change it saw).
+//
+// compare-and-swap v -> v + 1 with acquire semantics: a holder sees every
+// write its predecessors made before their release
+__device__ __forceinline__ bool try_lock(uint32_t *l, uint32_t v)
 {
     uint32_t old;
-    asm volatile("atom.acquire.gpu.global.cas.b32 %0, [%1], 0, 1;" : "=r"(old) : "l"(l) : "memory");
-    return old == 0u;
+    asm volatile("atom.acquire.gpu.global.cas.b32 %0, [%1], %2, %3;" : "=r"(old) : "l"(l), "r"(v), "r"(v + 1) : "memory");
+    return old == v;
+}
+
+__device__ __forceinline__ uint32_t peek(const uint32_t *l)
+{
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(l) : "memory");
+    return v;
 }
 
 // the release: this transaction's writes before the lock reads free
-__device__ __forceinline__ void unlock(uint32_t *l)
+__device__ __forceinline__ void unlock(uint32_t *l, uint32_t held)
 {
-    asm volatile("st.release.gpu.global.u32 [%0], 0;" ::"l"(l) : "memory");
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(l), "r"(held + 1) : "memory");
 }
 
-__device__ __forceinline__ bool spin_lock(uint32_t *l, uint64_t limit_ns)
+// test-and-test-and-set with exponential back-off: waiters read the word
+// and try the swap only when it reads free, so a hot lock's line is not
+// flooded with atomics.  Returns the held (odd) value, or 0 when the word did
+// not change for limit_ns.
+__device__ __forceinline__ uint32_t spin_lock(uint32_t *l, uint64_t limit_ns)
 {
-    if (try_lock(l)) return true;
-    const uint64_t t0 = globaltimer();
-    uint32_t ns = 32;
+    uint32_t v = peek(l);
+    if (!(v & 1u) && try_lock(l, v)) return v + 1;
+    uint64_t t0 = globaltimer();
+    uint32_t ns = 64;
     while (true) {
         __nanosleep(ns);
-        if (ns < 1024) ns <<= 1;
-        if (try_lock(l)) return true;
-        if (globaltimer() - t0 > limit_ns) return false;
+        if (ns < 4096) ns <<= 1;
+        const uint32_t w = peek(l);
+        if (w != v) {            // handed on since the last look: progress
+            v = w;
+            t0 = globaltimer();
+        }
+        if (!(w & 1u)) {
+            if (try_lock(l, w)) return w + 1;
+        } else if (globaltimer() - t0 > limit_ns) {
+            return 0;
+        }
     }
 }
 
@@ -61,36 +89,78 @@ __global__ void tpl_relaxed_kernel(TplRelaxedArgs a)
 {
     if (*(volatile uint32_t *)&a.ctl->err) return;   // validation failed: uniform, set before this launch
     const int64_t hb = a.ctl->base.hist;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < a.b.n;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const TxnView v = view_of(a.b, (uint32_t)t, hb);
-        uint32_t obj[MAX_OPS], root[MAX_OPS], items[MAX_OPS];
-        uint8_t cls[MAX_OPS];
-        const int k = access_set(a.db, v.type, v.p, a.mode, obj, cls, root);
+    const uint32_t lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t base0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31u);
+    // whole warps step through the bulk together (the warp combining below
+    // needs every lane at the same step)
+    for (int64_t t0 = base0; t0 < a.b.n; t0 += stride) {
+        const int64_t t = t0 + lane;
+        const bool live = t < a.b.n;
+        TxnView v{};
+        uint32_t items[MAX_OPS];
         int m = 0;
-        for (int j = 0; j < k; j++) {
-            if (cls[j] == CLS_A) continue;   // an atomic increment needs no lock
-            // insertion into the sorted lock list
-            int q = m++;
-            while (q > 0 && items[q - 1] > obj[j]) {
-                items[q] = items[q - 1];
-                q--;
+        if (live) {
+            v = view_of(a.b, (uint32_t)t, hb);
+            uint32_t obj[MAX_OPS], root[MAX_OPS];
+            uint8_t cls[MAX_OPS];
+            const int k = access_set(a.db, v.type, v.p, a.mode, obj, cls, root);
+            for (int j = 0; j < k; j++) {
+                if (cls[j] == CLS_A) continue;   // an atomic increment needs no lock
+                // insertion into the sorted lock list
+                int q = m++;
+                while (q > 0 && items[q - 1] > obj[j]) {
+                    items[q] = items[q - 1];
+                    q--;
+                }
+                items[q] = obj[j];
             }
-            items[q] = obj[j];
         }
-        int held = 0;
-        bool ok = true;
-        for (; held < m; held++)
-            if (!spin_lock(&a.lock[a.slot(items[held])], a.spin_limit_ns)) {
-                set_err(&a.ctl->err, ERR_TIMEOUT);
-                ok = false;
-                break;
+        // Warp combining: lanes whose only lock is the same item form a group
+        // (__match_any_sync).  Its lowest lane takes the lock once and the
+        // group runs in lane order inside one critical section, each lane
+        // with consecutive commit tickets, so the serial order the tickets
+        // report is the order the group ran in.
+        const bool single = live && m == 1;
+        const uint32_t grp = __match_any_sync(kFull, single ? items[0] : (0xFFFFFFE0u | lane));
+        const uint32_t leader = __ffs(grp) - 1;
+        if (single) {
+            uint32_t held = 0;
+            if (lane == leader) held = spin_lock(&a.lock[a.slot(items[0])], a.spin_limit_ns);
+            held = __shfl_sync(grp, held, leader);
+            if (!held) {
+                if (lane == leader) set_err(&a.ctl->err, ERR_TIMEOUT);
+            } else {
+                uint32_t tk = 0;
+                if (lane == leader) tk = atomicAdd(&a.ctl->claim, (uint32_t)__popc(grp));
+                tk = __shfl_sync(grp, tk, leader);
+                for (uint32_t rest = grp; rest; rest &= rest - 1) {   // lane order
+                    if (lane == (uint32_t)(__ffs(rest) - 1)) {
+                        exec_txn(a.db, a.b, v, a.atomic_add);
+                        a.order[tk + __popc(grp & lanemask_lt())] = (uint32_t)t;
+                    }
+                    __syncwarp(grp);   // each lane's writes before the next one's reads
+                }
+                if (lane == leader) unlock(&a.lock[a.slot(items[0])], held);
             }
-        if (ok) {
-            exec_txn(a.db, a.b, v, a.atomic_add);
-            a.order[atomicAdd(&a.ctl->claim, 1u)] = (uint32_t)t;
+        } else if (live) {
+            uint32_t held_v[MAX_OPS];
+            int held = 0;
+            bool ok = true;
+            for (; held < m; held++) {
+                held_v[held] = spin_lock(&a.lock[a.slot(items[held])], a.spin_limit_ns);
+                if (!held_v[held]) {
+                    set_err(&a.ctl->err, ERR_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+            }
+            if (ok) {
+                exec_txn(a.db, a.b, v, a.atomic_add);
+                a.order[atomicAdd(&a.ctl->claim, 1u)] = (uint32_t)t;
+            }
+            for (int j = 0; j < held; j++) unlock(&a.lock[a.slot(items[j])], held_v[j]);
         }
-        for (int j = 0; j < held; j++) unlock(&a.lock[a.slot(items[j])]);
     }
 }
 
@@ -116,7 +186,10 @@ cudaError_t launch_tpl_relaxed(gputx_bulk *b, uint32_t *order, bool atomic_add)
     if (grid > (int64_t)db->num_sms * 8) grid = (int64_t)db->num_sms * 8;
     tpl_relaxed_kernel<<<(unsigned)grid, 256, 0, b->stream>>>(a);
     count_launches(1);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e) return e;
+    // the versioned words return to zero: TPL's ordered counters share them
+    return cudaMemsetAsync(db->d_done, 0, (size_t)db->lock_slots.lines.d * 32 * sizeof(uint32_t), b->stream);
 }
 
 }  // namespace gtx

@@ -77,7 +77,7 @@ def test_structs_match_header_sizes():
     assert ctypes.sizeof(G.ServeStats) == 5 * 8 + 4 * 8
     assert ctypes.sizeof(G.BatchConfig) == 4 * 4 + 2 * 8 + 2 * 4
     assert ctypes.sizeof(G.PoolConfig) == 8 + 2 * 4 + 2 * 8
-    assert ctypes.sizeof(G.BatchChoice) == 4 * 4 + 2 * 8 + 16 * 4 * 2 + 16 * 8 * 2
+    assert ctypes.sizeof(G.BatchChoice) == 4 * 4 + 2 * 8 + 16 * 4 * 2 + 16 * 8 * 2 + 2 * 8
 
 
 def test_probe_rejects_bad_shapes_without_a_gpu():

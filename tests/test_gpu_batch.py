@@ -74,7 +74,7 @@ def test_autotuned_order_entry_stream(mode):
     ch = bt.choice()
     bt.close()
     assert ch["tuned"] and len(ch["measured"]) >= 3
-    assert ch["strategy"] in (G.KSET, G.TPL) and ch["bulk_size"] <= 1 << 18
+    assert ch["strategy"] in (G.KSET, G.TPL, G.PART) and ch["bulk_size"] <= 1 << 18
     gs, os_ = gpu_logical_state(g, oe=True), oracle_logical_state(o)
     assert states_equal(gs, os_), state_diff(gs, os_)
     g.close()
@@ -109,7 +109,7 @@ def test_mixed_schema_stream_through_graphs():
 def test_config4_stream_at_full_size():
     """The benchmark's batched order-entry run: 64 warehouses x 10 districts
     x 3,000 customers, 100,000 items, 18 uneven bulks of 2^10..2^21 (4.28M
-    transactions) through the tuned graph batcher.  Every output, every
+    transactions) through the tuned graph batcher, bulk boundaries kept.  Every output, every
     table and the order index equal serial execution of the whole stream."""
     n_wh, n_items = 64, 100_000
     init = W.oe_tables(n_wh, n_items=n_items, seed=W.seed_for(4))
@@ -121,8 +121,10 @@ def test_config4_stream_at_full_size():
     for t, rows in W.oe_rows(init).items():
         g.load(t, rows)
     bt = G.Batcher(g, tune=True, params_per_txn=W.OE_PARAMS, bulk_size_max=1 << 21)
-    st, out = bt.run(bulk["ts"], bulk["type"], bulk["params"])
+    st, out = bt.run_bulks(bulk["ts"], bulk["type"], bulk["params"], sizes)
+    ch = bt.choice()
     bt.close()
+    assert len(ch["measured"]) >= 3 and 0 < ch["p50_us"] <= ch["p99_us"]
     o = oracle.OracleDB(oe=init, ord_cap=total, ol_cap=total * 15, oid_cap=1 << 16)
     ost, oout = o.execute(bulk, R=g.width)
     bad = np.flatnonzero((st != ost) | (out != oout).any(axis=1))
@@ -130,4 +132,47 @@ def test_config4_stream_at_full_size():
     gs, os_ = gpu_logical_state(g, oe=True), oracle_logical_state(o)
     assert states_equal(gs, os_), state_diff(gs, os_)
     assert not check_indexes(g, o, oe=True)
+    g.close()
+
+
+@pytest.mark.parametrize("strategy,mode", [("kset", 0), ("kset", 1), ("tpl", 0), ("part", 0)])
+@pytest.mark.parametrize("schema", ["dc", "oe"])
+def test_uneven_bulks_in_segments(strategy, mode, schema):
+    """Bulks of uneven sizes (empty and one-transaction bulks among them, and
+    bulks larger than the segment capacity) through segmented graph replays:
+    several bulks share one persistent launch, each with its own k-sets under
+    K-SET.  A PART segment holding a cross-partition order-entry transaction
+    runs nothing and is re-run with TPL.  Results equal serial execution."""
+    rng = np.random.default_rng(81)
+    sizes = [0, 1, 3000, 17, 9000, 1, 40000, 0, 2500, 777, 65536, 12]
+    total = sum(sizes)
+    if schema == "dc":
+        A = 20_000
+        g = G.Database(dc=(20, 200, A), history_capacity=1 << 20, max_bulk=1 << 15)
+        g.register(G.DC_TYPES)
+        o = oracle.OracleDB(dc=W.dc_tables(20, 200, A), hist_cap=1 << 20)
+        bulk = W.dc_bulk(total, A, 0.8, seed=82)
+        kw = {}
+    else:
+        n_wh, n_items = 4, 2000
+        init = W.oe_tables(n_wh, n_items=n_items, seed=83)
+        cap = 1 << 18
+        g = G.Database(oe=(n_wh, n_items), order_capacity=cap, orderline_capacity=cap * 15, max_bulk=1 << 15)
+        g.register(G.OE_TYPES)
+        for t, rows in W.oe_rows(init).items():
+            g.load(t, rows)
+        o = oracle.OracleDB(oe=init, ord_cap=cap, ol_cap=cap * 15, oid_cap=1 << 16)
+        bulk = W.oe_bulk(total, n_wh, n_items=n_items, remote_frac=0.002, seed=84)
+        kw = {"params_per_txn": W.OE_PARAMS}
+    bt = G.Batcher(g, tune=False, strategy=strategy, conflict_mode=mode, bulk_size=1 << 15, **kw)
+    st, out = bt.run_bulks(bulk["ts"], bulk["type"], bulk["params"], sizes)
+    ch = bt.choice()
+    bt.close()
+    assert ch["bulks_run"] < len([x for x in sizes if x])    # bulks share segments
+    ost, oout = o.execute(bulk, R=g.width)
+    bad = np.flatnonzero((st != ost) | (out != oout).any(axis=1))
+    assert len(bad) == 0, (len(bad), bad[:5])
+    kw2 = {"dc": True} if schema == "dc" else {"oe": True}
+    gs, os_ = gpu_logical_state(g, **kw2), oracle_logical_state(o)
+    assert states_equal(gs, os_), state_diff(gs, os_)
     g.close()
