@@ -460,8 +460,9 @@ def run_sweep(args, G, torch, dev, stream, flush):
 
 def run_serving(args, G, torch, stream):
     """The served mix: debit-credit and subscriber schemas loaded together in a
-    device-resident database of about 20 GB of live rows (22M subscribers
-    with their child tables and indexes), open-loop Poisson arrivals of a
+    device-resident database of about 20 GB of live rows (20M subscribers
+    with their child tables and indexes, 10M accounts, the history the
+    served transactions append), open-loop Poisson arrivals of a
     50/50 mix of the two schemas' transactions.  Three serving modes:
     continuous batching (several bulks in flight), the plain per-bulk path
     (one bulk at a time, closed every deadline) and incremental 0-set
@@ -471,7 +472,8 @@ def run_serving(args, G, torch, stream):
     deadlines = [int(d) for d in args.serve_deadlines_us.split(",")]
     n_sub = args.serve_subscribers
     skewed_rates = [r for r in rates if r >= 20e6]
-    total = int((sum(rates) * len(deadlines) * 3 + sum(skewed_rates) * 2) * args.serve_seconds) + (1 << 22)
+    # history rows: one per served debit-credit transaction (half the mix)
+    total = int(0.52 * (sum(rates) * len(deadlines) * 3 + sum(skewed_rates) * 2) * args.serve_seconds) + (1 << 20)
     free0 = torch.cuda.mem_get_info()[0]
     # the database's size comes from its live rows (subscribers with their
     # child tables and indexes, 10M accounts); history holds what the served
@@ -627,73 +629,84 @@ OE_EXEC_BYTES_PER_TXN = round(0.45 * 2573 + 0.43 * 372 + 0.12 * 492)
 
 
 def run_batched(args, G, torch, stream):
-    """Order-entry stream of uneven bulks (64 warehouses x 10 districts x
+    """Order-entry streams of uneven bulks (64 warehouses x 10 districts x
     3,000 customers, 100,000 items): the graph batcher with its autotuner
-    (several bulks per graph replay, each keeping its own k-sets under K-SET)
-    against the plain per-bulk K-SET path.  Host arrays in and out (H2D and
-    D2H inside the timing) for both.  Latency of a transaction = time from
-    the run's start until its results are on the host (the whole stream is
-    handed over at once)."""
+    (several bulks per graph replay, each keeping its own k-sets under K-SET,
+    two segments in flight once tuned) against the plain per-bulk K-SET path.
+    Two streams run back to back on one database: the first tunes the
+    batcher (and warms the plain path), the second is the steady state.
+    Host arrays in and out (H2D and D2H inside the timing) for both.  Latency
+    of a transaction = time from the stream's start until its results are on
+    the host (each stream is handed over at once)."""
     n_wh, n_items = 64, 100_000
     init = W.oe_tables(n_wh, n_items=n_items, seed=W.seed_for(4))
-    sizes, stream_bulk = W.oe_stream(args.batch_txns, n_wh, n_items)
-    total = sum(sizes)
-    out = {"workload": f"order-entry {n_wh} warehouses, {n_items} items, {len(sizes)} bulks of "
-                       f"2^10..2^21 transactions, {total} in all", "txn": total,
-           "bytes_per_txn": OE_EXEC_BYTES_PER_TXN}
+    sizes_a, stream_a = W.oe_stream(args.batch_txns, n_wh, n_items)
+    total_a = sum(sizes_a)
+    sizes_b, stream_b = W.oe_stream(args.batch_txns, n_wh, n_items, variant=1, ts0=total_a)
+    total_b = sum(sizes_b)
+    out = {"workload": f"order-entry {n_wh} warehouses, {n_items} items, two streams of {len(sizes_a)} and "
+                       f"{len(sizes_b)} bulks of 2^10..2^21 transactions ({total_a} and {total_b})",
+           "txn": total_b, "bytes_per_txn": OE_EXEC_BYTES_PER_TXN}
     peak = measured_peak_hbm()[0]
     mode = G.CONFLICT_ADD if args.mode == "add" else G.CONFLICT_PAPER
+
+    def pct(done, total):
+        done.sort()
+        acc, p50, p99 = 0, None, None
+        for ms, k in done:
+            acc += k
+            if p50 is None and acc > 0.5 * total:
+                p50 = ms
+            if p99 is None and acc > 0.99 * total:
+                p99 = ms
+        return p50 * 1e3, p99 * 1e3
+
     for label in ("plain_kset", "batched_tuned"):
-        cap = 2 * total + (1 << 22)
+        cap = 2 * (total_a + total_b) + (1 << 22)
         db = G.Database(oe=(n_wh, n_items), order_capacity=cap, orderline_capacity=cap * 15,
                         max_bulk=1 << 21, stream=stream.cuda_stream)
         db.register(G.OE_TYPES)
         for t, rows in W.oe_rows(init).items():
             db.load(t, rows)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        if label == "plain_kset":
-            i = 0
-            done = []          # (ms from start, transactions) per bulk
-            for k in sizes:
-                b = db.submit(stream_bulk["ts"][i:i + k], stream_bulk["type"][i:i + k],
-                              stream_bulk["params"][i:i + k])
-                b.execute("kset", conflict_mode=mode)
-                b.results()
-                b.free()
-                done.append(((time.perf_counter() - t0) * 1e3, k))
-                i += k
-            choice = None
-        else:
+        bt = None
+        if label == "batched_tuned":
             bt = G.Batcher(db, tune=True, params_per_txn=W.OE_PARAMS, bulk_size_max=1 << 21, conflict_mode=mode)
-            bt.run_bulks(stream_bulk["ts"], stream_bulk["type"], stream_bulk["params"], sizes)
-            choice = bt.choice()
-            bt.close()
-        dt = time.perf_counter() - t0
-        rec = {"txn_per_s": total / dt, "seconds": dt,
-               "hbm_frac_wall": total * OE_EXEC_BYTES_PER_TXN / dt / 1e9 / peak}
-        if choice is None:
-            done.sort()
-            acc, p50, p99 = 0, None, None
-            for ms, k in done:
-                acc += k
-                if p50 is None and acc > 0.5 * total:
-                    p50 = ms
-                if p99 is None and acc > 0.99 * total:
-                    p99 = ms
-            rec.update({"p50_us": p50 * 1e3, "p99_us": p99 * 1e3})
-        else:
+        rec = {}
+        for phase, sizes, sb, total in (("first", sizes_a, stream_a, total_a), ("steady", sizes_b, stream_b, total_b)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if bt is None:
+                i = 0
+                done = []          # (ms from start, transactions) per bulk
+                for k in sizes:
+                    b = db.submit(sb["ts"][i:i + k], sb["type"][i:i + k], sb["params"][i:i + k])
+                    b.execute("kset", conflict_mode=mode)
+                    b.results()
+                    b.free()
+                    done.append(((time.perf_counter() - t0) * 1e3, k))
+                    i += k
+                p50, p99 = pct(done, total)
+            else:
+                bt.run_bulks(sb["ts"], sb["type"], sb["params"], sizes)
+                ch = bt.choice()
+                p50, p99 = ch["p50_us"], ch["p99_us"]
+            dt = time.perf_counter() - t0
+            rec[phase] = {"txn_per_s": total / dt, "seconds": dt, "p50_us": p50, "p99_us": p99,
+                          "hbm_frac_wall": total * OE_EXEC_BYTES_PER_TXN / dt / 1e9 / peak}
+        if bt is not None:
+            ch = bt.choice()
             names = {G.KSET: "kset", G.TPL: "tpl", G.PART: "part"}
-            rec.update({"p50_us": choice["p50_us"], "p99_us": choice["p99_us"], "segments": choice["bulks_run"],
-                        "choice": {"strategy": names.get(choice["strategy"]), "segment_capacity": choice["bulk_size"],
-                                   "block": choice["block_threads"],
-                                   "measured": [{"strategy": names.get(m["strategy"]), "capacity": m["bulk"],
-                                                 "block": m["block"], "ns_per_txn": m["ns_per_txn"]}
-                                                for m in choice["measured"]]}})
+            rec["segments"] = ch["bulks_run"]
+            rec["choice"] = {"strategy": names.get(ch["strategy"]), "segment_capacity": ch["bulk_size"],
+                             "block": ch["block_threads"], "tuned": ch["tuned"],
+                             "measured": [{"strategy": names.get(m["strategy"]), "capacity": m["bulk"],
+                                           "block": m["block"], "ns_per_txn": m["ns_per_txn"]}
+                                          for m in ch["measured"]]}
+            bt.close()
         out[label] = rec
         db.close()
     if args.cpu_baseline:
-        out["cpu_baseline"] = oracle_oe_rate(init, stream_bulk, sizes, args.cpu_budget_s)
+        out["cpu_baseline"] = oracle_oe_rate(init, stream_a, sizes_a, args.cpu_budget_s)
     return out
 
 
@@ -777,6 +790,52 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# small cases for kernel profiles (ncu): one bulk, run twice, no JSON line
+# ---------------------------------------------------------------------------
+PROFILE_CASES = {
+    # name: (schema, bulk log2, theta, strategy, conflict mode)
+    "dc_kset_paper_20": ("dc", 20, 0.0, "kset", "paper"),
+    "dc_tpl_paper_20": ("dc", 20, 0.0, "tpl", "paper"),
+    "dc_part_20": ("dc", 20, 0.0, "part", "paper"),
+    "dc_part_zipf99_20": ("dc", 20, 0.99, "part", "paper"),
+    "dc_scan_22": ("dc", 22, 0.0, "scan", "paper"),
+    "oe_kset_paper_16": ("oe", 16, 0.0, "kset", "paper"),
+    "oe_tpl_paper_16": ("oe", 16, 0.0, "tpl", "paper"),
+}
+
+
+def run_profile_case(name):
+    import torch
+    import paper_1103_3105_gb300 as G
+    import __graft_entry__
+    __graft_entry__.build()
+    schema, lg, theta, strategy, mode_name = PROFILE_CASES[name]
+    mode = G.CONFLICT_ADD if mode_name == "add" else G.CONFLICT_PAPER
+    n = 1 << lg
+    dev = torch.device("cuda", 0)
+    if schema == "dc":
+        db = G.Database(dc=(BRANCHES, TELLERS, ACCOUNTS), history_capacity=3 * n, max_bulk=n)
+        db.register(G.DC_TYPES)
+        bulk = W.dc_bulk(n, ACCOUNTS, theta, seed=W.seed_for(2, 22))
+    else:
+        n_wh, n_items = 64, 100_000
+        db = G.Database(oe=(n_wh, n_items), order_capacity=4 * n, orderline_capacity=60 * n, max_bulk=n)
+        db.register(G.OE_TYPES)
+        for t, rows in W.oe_rows(W.oe_tables(n_wh, n_items=n_items, seed=W.seed_for(4))).items():
+            db.load(t, rows)
+        bulk = W.oe_bulk(n, n_wh, n_items=n_items, seed=W.seed_for(4, 2))
+    d = {k: torch.from_numpy(bulk[k]).to(dev) for k in ("ts", "type", "params")}
+    for r in range(2):
+        b = db.submit(d["ts"] + r * n, d["type"], d["params"])
+        b.execute(strategy, conflict_mode=mode, timing=True)
+        st = b.sync()
+        b.free()
+        print(f"{name} run {r}: execute {st['ms_execute']:.3f} ms, analysis {st['ms_analysis']:.3f} ms, "
+              f"depth {st['depth']}", flush=True)
+    db.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -800,7 +859,7 @@ def main():
     ap.add_argument("--serve-deadlines-us", default="1000,10000")
     ap.add_argument("--serve-seconds", type=float, default=0.5)
     ap.add_argument("--serve-strategy", default="kset", choices=["kset", "part", "tpl", "auto"])
-    ap.add_argument("--serve-subscribers", type=int, default=22_000_000)
+    ap.add_argument("--serve-subscribers", type=int, default=20_000_000)
     ap.add_argument("--serve-zero-set-max-rate", type=float, default=5e6)
     ap.add_argument("--batched", dest="batched", action="store_true", default=True)
     ap.add_argument("--no-batched", dest="batched", action="store_false")
@@ -811,7 +870,12 @@ def main():
     ap.add_argument("--detail-out", default="bench_detail.json",
                     help="file for the sections beside the headline (sweep, serving, batching, "
                          "subscriber schema); '' writes none")
+    ap.add_argument("--profile-case", choices=sorted(PROFILE_CASES),
+                    help="run one small case twice for a kernel profile and exit (no JSON line)")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args.profile_case)
+        return
     rank, world = env_int("RANK", 0), env_int("WORLD_SIZE", 1)
     local_rank = env_int("LOCAL_RANK", 0)
     if args.warmup < 3:

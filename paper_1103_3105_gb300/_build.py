@@ -23,12 +23,9 @@ def _nvcc():
     return path if os.path.exists(path) else "nvcc"
 
 
-def _flags(debug: bool):
-    f = ARCH + ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-                "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]
-    if debug:
-        f += ["-DGPUTX_DEBUG=1"]
-    return f
+def _flags():
+    return ARCH + ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+                   "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]
 
 
 def _stale(outputs, inputs):
@@ -38,7 +35,7 @@ def _stale(outputs, inputs):
     return min(os.path.getmtime(o) for o in outputs) < newest
 
 
-def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".cuh", ".h"))]
     headers.append(os.path.join(HERE, "..", "include", "gputx.h"))
@@ -49,7 +46,7 @@ def build(force: bool = False, verbose: bool = False, debug: bool = False) -> st
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale([o], [s] + headers):
-            jobs.append([_nvcc()] + _flags(debug) + ["-c", s, "-o", o])
+            jobs.append([_nvcc()] + _flags() + ["-c", s, "-o", o])
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
             futs = [ex.submit(subprocess.run, j, capture_output=True, text=True) for j in jobs]

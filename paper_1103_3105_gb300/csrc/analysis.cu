@@ -25,10 +25,11 @@ inline unsigned grid_for(int64_t n, int block = TB)
 // ---------------------------------------------------------------------------
 // bulk begin / finish: insert bases from the device cursors
 // ---------------------------------------------------------------------------
+// hist_rows < 0: the history rows were counted by the insert-slot scan
 __global__ void begin_kernel(const InsertBase *cursor, BulkCtl *ctl, int64_t hist_rows, bool live_rows)
 {
     ctl->base = *cursor;
-    ctl->total.hist = live_rows ? (int64_t)ctl->n_live : hist_rows;
+    if (hist_rows >= 0) ctl->total.hist = live_rows ? (int64_t)ctl->n_live : hist_rows;
 }
 
 __global__ void finish_kernel(InsertBase *cursor, const BulkCtl *ctl)
@@ -500,28 +501,33 @@ __global__ void part_fallback_kernel(BulkCtl *ctl)
 // above k << tbits | type; levels are contiguous, so between two adjacent
 // keys at most two levels' cuts fall.
 __global__ void level_off_kernel(const uint32_t *skeys, int64_t n, int tbits, uint32_t *level_off,
-                                 uint32_t *type_cut, const uint32_t *err)
+                                 uint32_t *type_cut, const BulkCtl *ctl, const uint32_t *err)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n || *err) return;
+    // real levels are 0..depth; a graph bulk's padding sorts after them as
+    // level n, whose boundary is the only one needed past depth
+    const uint32_t top = ctl->depth + 1;
     const uint32_t key = skeys[i];
     const uint32_t lv = key >> tbits;
+    const uint32_t lvc = lv < top ? lv : top;
     const uint32_t prev = i ? (skeys[i - 1] >> tbits) : 0u;
     if (i == 0) {
-        for (uint32_t k = 0; k <= lv; k++) level_off[k] = 0;
+        for (uint32_t k = 0; k <= lvc; k++) level_off[k] = 0;
     } else if (lv != prev) {
-        for (uint32_t k = prev + 1; k <= lv; k++) level_off[k] = (uint32_t)i;
+        for (uint32_t k = prev + 1; k <= lvc; k++) level_off[k] = (uint32_t)i;
     }
-    if (i == n - 1) level_off[lv + 1] = (uint32_t)n;
+    if (i == n - 1 && lv < top) level_off[lv + 1] = (uint32_t)n;
     if (type_cut && (i == 0 || skeys[i - 1] != key)) {
         const uint64_t below = i ? (uint64_t)skeys[i - 1] + 1 : 0;   // cuts in (key[i-1], key[i]]
-        for (uint32_t k = i ? prev : 0; k <= lv; k++)
+        const uint32_t kmax = lv < top ? lv : top - 1;
+        for (uint32_t k = i ? prev : 0; k <= kmax; k++)
             for (uint32_t j = 0; j < 3; j++) {
                 const uint64_t cut = ((uint64_t)k << tbits) | (GPUTX_T_OE_NEW_ORDER + j);
                 if (cut >= below && cut <= key) type_cut[3 * k + j] = (uint32_t)i;
             }
     }
-    if (type_cut && i == n - 1)
+    if (type_cut && i == n - 1 && lv < top)
         for (uint32_t j = 0; j < 3; j++) {
             const uint64_t cut = ((uint64_t)lv << tbits) | (GPUTX_T_OE_NEW_ORDER + j);
             if (cut > key) type_cut[3 * lv + j] = (uint32_t)n;
@@ -533,10 +539,11 @@ struct ChunkMode {
     uint32_t *chunk_off;
     uint32_t block;
     const BulkCtl *ctl;   // levels = depth + 1, read on the device
+    const uint32_t *type_cut;   // chunks count lanes (order-entry groups) when set
     __device__ uint64_t element(int64_t k) const
     {
         if (k > (int64_t)ctl->depth) return 0;
-        const uint32_t w = level_off[k + 1] - level_off[k];
+        const uint32_t w = level_lane_count(level_off[k], level_off[k + 1], type_cut ? type_cut + 3 * k : nullptr);
         return DualSeg::make(0, 0, 0, (w + block - 1) / block);
     }
     __device__ void output(int64_t k, uint64_t s) const
@@ -687,6 +694,7 @@ inline DevBulk dev_bulk(gputx_bulk *b, int mode)
     d.slot_cf = b->sc.slot_cf;
     d.slot_ord = b->sc.slot_ord;
     d.slot_ol = b->sc.slot_ol;
+    d.slot_hist = b->sc.slot_hist;
     d.rec_params = b->sc.rec_params;
     d.rec_ts = b->sc.rec_ts;
     d.rec_type = b->sc.rec_type;
@@ -1021,7 +1029,8 @@ cudaError_t launch_part_scatter(gputx_bulk *b, const uint32_t *off, const uint32
 cudaError_t launch_begin(gputx_bulk *b)
 {
     const bool dc = (b->db->dev.registered & 1u) != 0;
-    begin_kernel<<<1, 1, 0, b->stream>>>(b->db->d_cursor, b->ctl, dc ? b->n : 0, dc && b->graph);
+    const int64_t rows = b->sc.slot_hist ? -1 : (dc ? b->n : 0);
+    begin_kernel<<<1, 1, 0, b->stream>>>(b->db->d_cursor, b->ctl, rows, dc && b->graph);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1230,13 +1239,13 @@ cudaError_t launch_level_tables(gputx_bulk *b, const uint32_t *skeys, int64_t de
 {
     cudaStream_t s = b->stream;
     if (b->n == 0) return cudaSuccess;
-    level_off_kernel<<<grid_for(b->n), TB, 0, s>>>(skeys, b->n, b->db->tbits, b->sc.level_off,
-                                                   b->graph ? nullptr : b->sc.type_cut, &b->ctl->err);
+    level_off_kernel<<<grid_for(b->n), TB, 0, s>>>(skeys, b->n, b->db->tbits, b->sc.level_off, b->sc.type_cut,
+                                                   b->ctl, &b->ctl->err);
     count_launches(1);
     if (!chunks) return cudaGetLastError();
     // graph bulks do not know their depth on the host: scan every possible level
     const int64_t levels = b->graph ? b->n : depth + 1;
-    ChunkMode cm{b->sc.level_off, b->sc.chunk_off, (uint32_t)block, b->ctl};
+    ChunkMode cm{b->sc.level_off, b->sc.chunk_off, (uint32_t)block, b->ctl, b->sc.type_cut};
     cudaError_t e = run_scan(b, cm, levels, 3);
     if (e) return e;
     chunk_level_kernel<<<grid_for(b->sc.chunk_cap), TB, 0, s>>>(b->sc.chunk_off, b->ctl, b->sc.chunk_level,
@@ -1245,9 +1254,31 @@ cudaError_t launch_level_tables(gputx_bulk *b, const uint32_t *skeys, int64_t de
     return cudaGetLastError();
 }
 
+// history rows of a mixed bulk: exclusive count of debit-credit transactions
+// in timestamp order
+struct HistSlotMode {
+    const int32_t *type;
+    int64_t n;
+    uint32_t *slot;
+    BulkCtl *ctl;
+    __device__ uint32_t a(int64_t t) const { return type[t] == GPUTX_T_DC_DEBIT_CREDIT ? 1u : 0u; }
+    __device__ uint64_t element(int64_t t) const { return DualSeg::make(0, 0, 0, a(t)); }
+    __device__ void output(int64_t t, uint64_t s) const
+    {
+        const uint32_t v = DualSeg::v2(s);
+        slot[t] = v - a(t);
+        if (t == n - 1) ctl->total.hist = v;
+    }
+};
+
 cudaError_t launch_insert_slots(gputx_bulk *b)
 {
     if (b->n == 0) return cudaSuccess;
+    if (b->sc.slot_hist) {
+        HistSlotMode hm{b->type, b->n, b->sc.slot_hist, b->ctl};
+        cudaError_t e = run_scan(b, hm, b->n, 7);
+        if (e) return e;
+    }
     const uint32_t reg = b->db->dev.registered;
     const bool sub_ins = (reg >> GPUTX_T_SUB_INSERT_CF) & 1u;
     const bool oe_no = (reg >> GPUTX_T_OE_NEW_ORDER) & 1u;

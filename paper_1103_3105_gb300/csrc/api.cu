@@ -198,7 +198,9 @@ size_t carve_bulk(gputx_bulk *b, char *base, bool device_inputs)
     s.level_off = c.take<uint32_t>(nn + 2);
     s.type_cut = db->group_oe ? c.take<uint32_t>(3 * (nn + 2)) : nullptr;
     s.chunk_off = c.take<uint32_t>(nn + 2);
-    s.chunk_cap = nn + nn / 32 + 2;
+    // chunks count lanes: at most lanes / block + levels, and order-entry
+    // groups take up to 16 lanes a transaction (+ half-warp padding)
+    s.chunk_cap = db->group_oe ? 2 * nn + 2 : nn + nn / 32 + 2;
     s.chunk_level = c.take<uint32_t>(s.chunk_cap);
     s.done = c.take<uint32_t>(nn + 1);
     s.part_start = c.take<uint32_t>(nn + 1);
@@ -215,6 +217,7 @@ size_t carve_bulk(gputx_bulk *b, char *base, bool device_inputs)
     s.slot_cf = slots ? c.take<uint32_t>(nn) : nullptr;
     s.slot_ord = slots ? c.take<uint32_t>(nn) : nullptr;
     s.slot_ol = slots ? c.take<uint32_t>(nn) : nullptr;
+    s.slot_hist = db->hist_by_type ? c.take<uint32_t>(nn) : nullptr;
     s.sort_hist = c.take<uint32_t>(4 * 256);
     s.sort_offs = c.take<uint32_t>(4 * 256);
     const int64_t big = std::max(mm, nn + 2);
@@ -503,6 +506,9 @@ gputx_status gputx_register_types(gputx_db *db, const int32_t *type_ids, int n)
     db->uniform_k = uniform > 0 ? uniform : 0;
     db->need_fixpoint = fix;
     db->tbits = ntypes > 1 ? bits_for((uint64_t)maxid) : 0;
+    // a bulk that mixes debit-credit with other types takes history rows
+    // for its debit-credit transactions only
+    db->hist_by_type = (db->dev.registered & 1u) && db->dev.registered != 1u;
     // levels sorted by (level, type) know where each order-entry type starts
     db->group_oe = db->tbits > 0 && (db->dev.registered & ((1u << GPUTX_T_OE_NEW_ORDER) |
                                                            (1u << GPUTX_T_OE_ORDER_STATUS)));

@@ -121,6 +121,9 @@ struct DevBulk {
     const InsertBase *base;        // device: where this bulk's inserts start
     // per-transaction insert slots (exclusive prefix counts in ts order)
     const uint32_t *slot_cf, *slot_ord, *slot_ol;
+    // history row of each debit-credit transaction when other types share
+    // the bulk (null: the row is the transaction's position)
+    const uint32_t *slot_hist;
     // signatures gathered into this strategy's execution order
     const int64_t *rec_params, *rec_ts;
     const int32_t *rec_type;

@@ -52,6 +52,7 @@ struct Scratch {
     int32_t *rec_type;
     uint32_t *rec_t;
     uint32_t *slot_cf, *slot_ord, *slot_ol;   // n each
+    uint32_t *slot_hist;   // n: history rows of debit-credit transactions in mixed databases
     uint32_t *sort_hist;   // 4 x 256
     uint32_t *sort_offs;   // 4 x 256
     uint32_t *sort_status; // 4 x tiles x 256
@@ -89,6 +90,7 @@ struct gputx_db {
     bool need_fixpoint = false;            // a registered type's ops may leave one-pass ranks inexact
     int tbits = 0;                         // type bits in the level/type regroup key
     bool group_oe = false;                 // K-SET runs new-order and order-status on 16-lane groups
+    bool hist_by_type = false;             // debit-credit and other types: history rows for debit-credit only
     int obj_bits = 1;                      // key bits of object ids
     // Each bulk runs on a stream of this pool, so the analysis of one bulk
     // overlaps the execution of the one before; `last_done` orders the

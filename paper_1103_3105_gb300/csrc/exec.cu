@@ -42,6 +42,7 @@ struct KsetArgs {
     DevBulk b;
     BulkCtl *ctl;
     const uint32_t *order, *level_off, *chunk_off, *chunk_level;
+    const uint32_t *type_cut;   // per level, where new-order, payment, order-status start (or null)
     uint32_t *done;
     int64_t levels;
     uint64_t spin_limit_ns;
@@ -213,15 +214,17 @@ __global__ void kset_kernel(KsetArgs a)
     const int64_t levels = (int64_t)a.ctl->depth + 1;   // from the analysis, on the device
     const uint32_t nchunks = a.chunk_off[levels];
     const int64_t hb = a.ctl->base.hist;
+    const uint32_t *cut = a.type_cut;
     while (true) {
         if (threadIdx.x == 0) {
             uint32_t stop = *(volatile uint32_t *)&a.ctl->err ? 1u : 0u;
             const uint32_t c = stop ? nchunks : atomicAdd(&a.ctl->claim, 1u);
             if (c < nchunks) {
+                // a chunk is a run of blockDim lanes of one level
                 const uint32_t k = a.chunk_level[c];
-                const uint32_t lo = a.level_off[k], hi = a.level_off[k + 1];
-                const uint32_t start = lo + (c - a.chunk_off[k]) * blockDim.x;
-                const uint32_t cnt = (hi - start) < blockDim.x ? (hi - start) : blockDim.x;
+                const uint32_t w = level_lane_count(a.level_off[k], a.level_off[k + 1], cut ? cut + 3 * k : nullptr);
+                const uint32_t start = (c - a.chunk_off[k]) * blockDim.x;
+                const uint32_t cnt = (w - start) < blockDim.x ? (w - start) : blockDim.x;
                 s_k = k;
                 s_start = start;
                 s_cnt = cnt;
@@ -232,24 +235,31 @@ __global__ void kset_kernel(KsetArgs a)
         }
         __syncthreads();
         if (s_stop) break;
+        LevelLanes L;
+        L.make(a.level_off[s_k], a.level_off[s_k + 1], cut ? cut + 3 * (int64_t)s_k : nullptr);
         // signatures are immutable: load them and prefetch the rows while the
         // previous level may still be running
         TxnView v{};
-        if (threadIdx.x < s_cnt) {
-            v = view_at(a.b, s_start + threadIdx.x, hb);
-            prefetch_txn(a.db, v);
+        uint32_t pos;
+        int gl = -1;
+        const bool mine = threadIdx.x < s_cnt && L.at(s_start + threadIdx.x, pos, gl);
+        if (mine) {
+            v = view_at(a.b, pos, hb);
+            if (gl < 0) prefetch_txn(a.db, v);
+            else prefetch_group(a.db, v, (uint32_t)gl);
         }
         if (threadIdx.x == 0 && s_k > 0) {
-            const uint32_t k = s_k, lo = a.level_off[k];
-            if (!wait_at_least(&a.done[k - 1], lo - a.level_off[k - 1], a.spin_limit_ns)) {
+            const uint32_t k = s_k;
+            const uint32_t prev = level_lane_count(a.level_off[k - 1], a.level_off[k], cut ? cut + 3 * (k - 1) : nullptr);
+            if (!wait_at_least(&a.done[k - 1], prev, a.spin_limit_ns)) {
                 set_err(&a.ctl->err, ERR_TIMEOUT);
                 s_stop = 1;
             }
         }
         __syncthreads();
         if (s_stop) break;
-        if (threadIdx.x < s_cnt) {
-            exec_txn(a.db, a.b, v, a.atomic_add);
+        if (mine) {
+            exec_lane(a.db, a.b, v, gl, a.atomic_add);
             __threadfence();
         }
         __syncthreads();
@@ -313,23 +323,6 @@ __device__ __forceinline__ void group_sum(uint32_t m, int64_t x, int64_t &pre, i
 #pragma unroll 4
     for (int L = 0; L < 32; L++) {
         const int64_t d = __shfl_sync(kFull, x, L);
-        if ((m >> L) & 1u) {
-            tot += d;
-            if ((uint32_t)L <= lane) pre += d;
-        }
-    }
-}
-
-// the same over the lanes `in` only (every lane of `in` calls it; m is a
-// subset of `in`)
-__device__ __forceinline__ void group_sum_in(uint32_t in, uint32_t m, int64_t x, int64_t &pre, int64_t &tot)
-{
-    const uint32_t lane = threadIdx.x & 31;
-    pre = 0;
-    tot = 0;
-    for (uint32_t r = in; r; r &= r - 1) {
-        const int L = __ffs(r) - 1;
-        const int64_t d = __shfl_sync(in, x, L);
         if ((m >> L) & 1u) {
             tot += d;
             if ((uint32_t)L <= lane) pre += d;
@@ -457,6 +450,21 @@ __device__ __forceinline__ uint32_t ld_relaxed_gpu(const uint32_t *p)
 
 __device__ __forceinline__ void fence_acquire_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
+// releases of the lanes with `rel` (every lane of the warp calls it): lanes
+// releasing the same counter are grouped by __match_any_sync and their
+// lowest lane adds the group's size (warp-aggregated atomics)
+__device__ __forceinline__ void warp_release(const TplArgs &a, bool rel, int64_t off, int cnt)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const int jmax = __reduce_max_sync(kFull, rel ? (uint32_t)cnt : 0u);
+    for (int j = 0; j < jmax; j++) {
+        const bool r = rel && j < cnt;
+        const uint32_t key = r ? a.slot(__ldg(&a.lock_key[off + j])) : (0xFFFFFFE0u | lane);
+        const uint32_t m = __match_any_sync(kFull, key);
+        if (r && lane == (uint32_t)(__ffs(m) - 1)) red_release_add(&a.done[key], (uint32_t)__popc(m));
+    }
+}
+
 // TPL for any registered types.  Each transaction holds one ordered counter
 // lock per basic operation (Section 5.1, Appendix C's counter lock with
 // ticket semantics): an operation whose group has `ticket` operations before
@@ -464,17 +472,25 @@ __device__ __forceinline__ void fence_acquire_gpu() { asm volatile("fence.acq_re
 // Tickets follow the timestamp order of the group, so the earliest unfinished
 // transaction never waits and no deadlock can form.
 //
-// A transaction polls all its locks not yet granted at once (relaxed loads in
-// flight together: one round trip, not one per lock; a granted lock stays
-// granted, since no later operation releases before this one) and then only
-// the one furthest behind, sleeping about 500 ns per release it still misses;
-// once every lock is granted, one acquire fence orders its accesses after
-// the releases it saw.  The wait limit runs from the last lock granted.
-__global__ void __launch_bounds__(512, 1) tpl_kernel(TplArgs a)
+// A warp runs its 32 transactions in lockstep rounds.  A waiting lane polls
+// all its locks not yet granted at once (relaxed loads in flight together:
+// one round trip, not one per lock; a granted lock stays granted, since no
+// later operation releases before this one), then only the lock furthest
+// behind, again after about 500 ns per release that lock still misses.
+// Every lane whose locks are all granted takes one acquire fence and runs
+// its procedure: first the short ones, then the new-orders (up to four of
+// them on a half warp each, one lane per order line), each phase followed by
+// its releases.  Releases are warp-aggregated: lanes releasing the same
+// counter in a phase are grouped by __match_any_sync and their lowest lane
+// adds the group's size.  A round in which nothing is granted sleeps until
+// the first lane is due to poll, so a lane about to be granted never sleeps
+// behind one far back in its chain.
+__global__ void __launch_bounds__(512) tpl_kernel(TplArgs a)
 {
     __shared__ uint32_t s_c, s_stop;
     const int64_t n = a.b.n;
     const int64_t hb = a.ctl->base.hist;
+    const uint32_t lane = threadIdx.x & 31;
     while (true) {
         if (threadIdx.x == 0) {
             s_stop = *(volatile uint32_t *)&a.ctl->err ? 1u : 0u;
@@ -484,23 +500,29 @@ __global__ void __launch_bounds__(512, 1) tpl_kernel(TplArgs a)
         const int64_t start = (int64_t)s_c * blockDim.x;
         if (s_stop || start >= n) break;
         const int64_t t = start + threadIdx.x;
-        if (t < n && !(a.b.n_live && t >= (int64_t)*a.b.n_live)) {
-            const int64_t off = a.op_off ? (int64_t)a.op_off[t] : t * a.uniform_k;
-            const int cnt = a.op_off ? (int)(a.op_off[t + 1] - a.op_off[t])
-                                     : (a.graph ? op_count(a.db, a.b.type[t], a.b.params + t * a.b.P)
-                                                : a.uniform_k);
-            const TxnView v = view_of(a.b, (uint32_t)t, hb);
+        const bool live = t < n && !(a.b.n_live && t >= (int64_t)*a.b.n_live);
+        int64_t off = 0;
+        int cnt = 0;
+        TxnView v{};
+        if (live) {
+            off = a.op_off ? (int64_t)a.op_off[t] : t * a.uniform_k;
+            cnt = a.op_off ? (int)(a.op_off[t + 1] - a.op_off[t])
+                           : (a.graph ? op_count(a.db, a.b.type[t], a.b.params + t * a.b.P) : a.uniform_k);
+            v = view_of(a.b, (uint32_t)t, hb);
             prefetch_txn(a.db, v);
-            uint32_t granted = 0;                                   // bit j: lock j granted
-            const uint32_t all = cnt >= 32 ? kFull : ((1u << cnt) - 1u);
-            int blk = -1;                  // the lock holding it back (-1: poll every lock)
-            uint64_t t_prog = globaltimer();
-            uint32_t spins = 0;
-            bool ok = true;
-            while (true) {
+        }
+        uint32_t granted = 0;                                  // bit j: lock j granted
+        const uint32_t all = cnt >= 32 ? kFull : ((1u << cnt) - 1u);
+        int blk = -1;              // the lock holding this lane back (-1: poll every lock)
+        uint64_t t_next = 0;       // when this lane polls next
+        bool pending = live;
+        uint64_t t_prog = globaltimer();
+        uint32_t idle = 0;
+        while (__any_sync(kFull, pending)) {
+            const uint64_t now = globaltimer();
+            if (pending && granted != all && now >= t_next) {
                 uint32_t gap = 0;
-                const uint32_t before = granted;
-                if (blk >= 0) {
+                if (blk >= 0) {        // only the lock that held it back last time
                     const uint32_t tk = __ldg(&a.lock_ticket[off + blk]);
                     const uint32_t c = ld_relaxed_gpu(&a.done[a.slot(__ldg(&a.lock_key[off + blk]))]);
                     if (c >= tk) {
@@ -513,7 +535,7 @@ __global__ void __launch_bounds__(512, 1) tpl_kernel(TplArgs a)
                 if (blk < 0 && granted != all) {
                     uint32_t c[MAX_OPS], tk[MAX_OPS];
 #pragma unroll
-                    for (int j = 0; j < MAX_OPS; j++) {          // the polls, all in flight
+                    for (int j = 0; j < MAX_OPS; j++) {         // the polls, all in flight
                         tk[j] = 0;
                         c[j] = 0;
                         if (j < cnt && !((granted >> j) & 1u)) {
@@ -526,32 +548,77 @@ __global__ void __launch_bounds__(512, 1) tpl_kernel(TplArgs a)
                         if (j < cnt && !((granted >> j) & 1u)) {
                             if (c[j] >= tk[j]) {
                                 granted |= 1u << j;
-                            } else if (tk[j] - c[j] > gap) {    // the furthest behind
+                            } else if (tk[j] - c[j] > gap) {   // the furthest behind
                                 gap = tk[j] - c[j];
                                 blk = j;
                             }
                         }
                     }
                 }
-                if (granted == all) break;
-                const uint64_t now = globaltimer();
-                if (granted != before) {
-                    t_prog = now;
-                } else if (now - t_prog > a.spin_limit_ns) {
-                    set_err(&a.ctl->err, ERR_TIMEOUT);
-                    ok = false;
-                    break;
-                }
-                // missing `gap` releases take at least that many hand-offs
-                if (gap > 1) __nanosleep(gap > 64 ? 64 * 500 : gap * 500);
-                else if (++spins > 64) __nanosleep(32);
+                // a lock missing `gap` releases needs at least that many
+                // hand-offs: poll again after about that long
+                if (granted != all) t_next = now + (gap > 1 ? (uint64_t)(gap > 64 ? 64 : gap) * 500 : 0);
             }
-            if (ok) {
-                fence_acquire_gpu();   // with the polls: acquire of every granted lock
+            bool ready = pending && granted == all;
+            bool failed = false;
+            if (!__any_sync(kFull, ready)) {
+                if (now - t_prog > a.spin_limit_ns) {
+                    // nothing granted within the limit: give up, but release,
+                    // so no later waiter hangs on these counters
+                    failed = ready = pending;
+                    if (failed) set_err(&a.ctl->err, ERR_TIMEOUT);
+                } else {
+                    // sleep until the first lane is due to poll
+                    const uint32_t due = (pending && t_next > now) ? (uint32_t)min(t_next - now, (uint64_t)32000)
+                                                                    : (pending ? 0u : kFull);
+                    const uint32_t d = __reduce_min_sync(kFull, due);
+                    if (d > 0 && d != kFull) __nanosleep(d);
+                    else if (++idle > 64) __nanosleep(32);
+                    continue;
+                }
+            }
+            if (ready && !failed) fence_acquire_gpu();   // with the polls: acquire of every granted lock
+            // The round runs in two phases, each ending with its releases, so
+            // a short transaction's hand-off never waits for a new-order of
+            // the same warp.  Phase 1: every other granted transaction, one
+            // lane each (and the releases of timed-out ones).
+            const bool no = ready && !failed && v.type == GPUTX_T_OE_NEW_ORDER;
+            const bool r1 = ready && !no;
+            if (r1 && !failed) exec_txn(a.db, a.b, v, a.atomic_add);
+            __syncwarp();   // every lane's writes precede the releases of its phase
+            warp_release(a, r1, off, cnt);
+            // Phase 2: the granted new-orders.  Up to four run on a half warp
+            // each, two at a time (the line-parallel procedure: one lane per
+            // order line, as in the K-SET runners); more run one lane each.
+            uint32_t m2 = __ballot_sync(kFull, no);
+            if (m2 && __popc(m2) <= 4) {
+                while (m2) {
+                    const int l0 = __ffs(m2) - 1;
+                    m2 &= m2 - 1;
+                    const int l1 = m2 ? __ffs(m2) - 1 : -1;
+                    if (l1 >= 0) m2 &= m2 - 1;
+                    const int src = (lane < 16 || l1 < 0) ? l0 : l1;
+                    TxnView g;
+                    g.p = (const int64_t *)__shfl_sync(kFull, (unsigned long long)v.p, src);
+                    g.p0 = __shfl_sync(kFull, v.p0, src);
+                    g.p1 = __shfl_sync(kFull, v.p1, src);
+                    g.ts = __shfl_sync(kFull, v.ts, src);
+                    g.hist_slot = __shfl_sync(kFull, v.hist_slot, src);
+                    g.t = __shfl_sync(kFull, v.t, src);
+                    g.type = __shfl_sync(kFull, v.type, src);
+                    if (lane < 16 || l1 >= 0) {
+                        GlobalCells gc;
+                        exec_new_order_group(a.db, a.b, g, lane & 15u, gc);
+                    }
+                }
+            } else if (no) {
                 exec_txn(a.db, a.b, v, a.atomic_add);
             }
-            // each release is a release: this transaction's writes before it
-            for (int j = 0; j < cnt; j++) red_release_add(&a.done[a.slot(__ldg(&a.lock_key[off + j]))], 1u);
+            __syncwarp();
+            warp_release(a, no, off, cnt);
+            pending = pending && !ready;
+            t_prog = globaltimer();
+            idle = 0;
         }
         __syncthreads();
     }
@@ -567,19 +634,22 @@ __global__ void __launch_bounds__(512, 1) tpl_kernel(TplArgs a)
 // hand-off waits for one atomic round trip instead of a load, the stores and
 // their acknowledgement.
 //
-// Lanes of a warp that need the same counter are grouped by
-// __match_any_sync.  Every operation here is a write and the warp holds
-// consecutive timestamps, so no other transaction's operation on that item
-// lies between two lanes of a group: their tickets are consecutive, and the
-// whole group runs, in lane (timestamp) order, as soon as its first lane's
-// ticket is granted.  Only that lane waits on the counter (the others wait
-// for it at the group's __syncwarp, not on memory), and one addition of the
-// group's size releases it.  Within a group, lanes on the same account
-// combine their deltas (warp-aggregated atomics): one fetch-and-add of the
-// sum, each lane's new balance = the old value plus the inclusive prefix of
-// the deltas in lane order -- the serial result bit for bit.  Teller and
-// branch additions are aggregated the same way.  Groups of one warp wait
-// independently of each other.
+// A warp works on 32 consecutive transactions and resolves the conflicts
+// among them itself.  __match_any_sync groups the lanes that need the same
+// counter.  Every operation here is a write and the warp holds consecutive
+// timestamps, so no other transaction's operation on that item lies between
+// two lanes of a group: their tickets are consecutive, and the whole group
+// runs, in lane (timestamp) order, as soon as its first lane's ticket is
+// granted.  Only that lane polls the counter, and one addition of the group's
+// size releases it.  Within a group, lanes on the same account combine their
+// deltas (warp-aggregated atomics): one fetch-and-add of the sum, each lane's
+// new balance = the old value plus the inclusive prefix of the deltas in lane
+// order -- the serial result bit for bit.  Teller and branch additions are
+// aggregated the same way.  The warp polls in lockstep rounds: each group
+// polls again after about 500 ns per release it still misses, and the warp
+// sleeps until the first group is due, so a group whose counter is about to
+// be released never sleeps behind one far back in its chain.  A warp in which no two lanes share a counter needs none of this:
+// there each lane waits on its own counter and runs as soon as it is granted.
 __global__ void tpl_dc_kernel(TplArgs a)
 {
     __shared__ uint32_t s_c, s_stop;
@@ -595,9 +665,10 @@ __global__ void tpl_dc_kernel(TplArgs a)
         const int64_t start = (int64_t)s_c * blockDim.x;
         if (s_stop || start >= n) break;
         const int64_t t = start + threadIdx.x;
-        const uint32_t live = __ballot_sync(kFull, t < n);
-        if (t < n) {
-            DcRecord r;
+        const bool live = t < n;
+        DcRecord r{};
+        uint32_t key = 0xFFFFFFE0u | lane, tk = 0;   // a key of its own for an idle lane
+        if (live) {
             r.a = (uint32_t)__ldg(&a.b.params[t * a.b.P]);
             r.delta = __ldg(&a.b.params[t * a.b.P + 1]);
             r.ts = __ldg(&a.b.ts[t]);
@@ -605,55 +676,94 @@ __global__ void tpl_dc_kernel(TplArgs a)
             r.tl = a.db.div_tel.div(r.a);
             r.br = a.db.div_br.div(r.a);
             prefetch_l2(&a.db.acc_bal[r.a]);
-            const uint32_t key = a.slot(a.lock_key[t]);
-            const uint32_t tk = a.lock_ticket[t];
-            const uint32_t grp = __match_any_sync(live, key);
-            const uint32_t leader = __ffs(grp) - 1;
-            bool ok = true;
-            if (lane == leader && tk) ok = wait_at_least(&a.done[key], tk, a.spin_limit_ns, 500);
-            ok = __shfl_sync(grp, ok, leader);
-            __syncwarp(grp);   // the leader's acquire before the members' accesses
-            if (!ok && lane == leader) set_err(&a.ctl->err, ERR_TIMEOUT);
-            const int64_t slot = hb + t;
-            const bool run = ok && slot < a.db.hist_cap;
-            if (ok && !run) {                  // history full: not executed
-                set_err(a.b.err, ERR_CAPACITY);
-                a.b.status[r.t] = 3;
-            }
-            // the account: one fetch-and-add per distinct account of the group
-            const uint32_t am = __match_any_sync(grp, run ? r.a : (0xFFFFFFE0u | lane));
-            int64_t pre = r.delta, tot = r.delta;
-            if (__any_sync(grp, run && __popc(am) > 1)) group_sum_in(grp, am, r.delta, pre, tot);
-            const uint32_t al = __ffs(am) - 1;
-            int64_t old = 0;
-            if (run && lane == al)
-                old = (int64_t)atomicAdd((unsigned long long *)&a.db.acc_bal[r.a], (unsigned long long)tot);
-            old = __shfl_sync(grp, old, al);
-            __syncwarp(grp);
-            // one release for the group: every member's update precedes it
-            if (lane == leader) red_release_add(&a.done[key], (uint32_t)__popc(grp));
-            // teller and branch: one addition per distinct cell of the group
-            const uint32_t tm = __match_any_sync(grp, run ? r.tl : (0xFFFFFFE0u | lane));
-            int64_t tpre = r.delta, ttot = r.delta;
-            if (__any_sync(grp, run && __popc(tm) > 1)) group_sum_in(grp, tm, r.delta, tpre, ttot);
-            if (run && lane == (uint32_t)(__ffs(tm) - 1))
-                atomicAdd((unsigned long long *)&a.db.tel_bal[r.tl], (unsigned long long)ttot);
-            const uint32_t bm = __match_any_sync(grp, run ? r.br : (0xFFFFFFE0u | lane));
-            int64_t bpre = r.delta, btot = r.delta;
-            if (__any_sync(grp, run && __popc(bm) > 1)) group_sum_in(grp, bm, r.delta, bpre, btot);
-            if (run && lane == (uint32_t)(__ffs(bm) - 1))
-                atomicAdd((unsigned long long *)&a.db.br_bal[r.br], (unsigned long long)btot);
-            if (run) {
+            key = a.slot(a.lock_key[t]);
+            tk = a.lock_ticket[t];
+        }
+        const uint32_t grp = __match_any_sync(kFull, key);
+        if (!__any_sync(kFull, live && __popc(grp) > 1)) {
+            // no two lanes of the warp share a counter: each waits on its own,
+            // without the warp's lockstep rounds
+            if (live) {
+                const bool ok = !tk || wait_at_least(&a.done[key], tk, a.spin_limit_ns, 500);
+                if (!ok) set_err(&a.ctl->err, ERR_TIMEOUT);
                 DcOut o;
-                o.slot = slot;
-                o.ts = r.ts;
-                o.delta = r.delta;
-                o.na = wrap_add(old, pre);
-                o.a = r.a;
-                o.tl = r.tl;
-                o.br = r.br;
-                o.t = r.t;
-                dc_finish(a.db, a.b, o);
+                const bool pend = ok && dc_account_rmw(a.db, a.b, r, hb + t, o);
+                red_release_add(&a.done[key], 1u);
+                if (pend) dc_finish_rmw(a.db, a.b, o);
+            }
+        } else {
+            const uint32_t leader = __ffs(grp) - 1;
+            const uint32_t need = __shfl_sync(kFull, tk, leader);   // the group's first ticket
+            bool pending = live;
+            uint64_t t_prog = globaltimer(), t_next = 0;   // t_next: when the group polls next
+            uint32_t idle = 0, seen = 0;
+            while (__any_sync(kFull, pending)) {
+                const uint64_t now = globaltimer();
+                uint32_t v = need ? seen : need;
+                if (pending && lane == leader && need && now >= t_next) {
+                    v = seen = ld_acquire(&a.done[key]);
+                    // missing `gap` releases take at least that many hand-offs
+                    const uint32_t gap = v < need ? need - v : 0;
+                    t_next = now + (gap > 1 ? (uint64_t)(gap > 64 ? 64 : gap) * 500 : 0);
+                }
+                v = __shfl_sync(kFull, v, leader);
+                bool ready = pending && v >= need;
+                bool failed = false;
+                if (!__any_sync(kFull, ready)) {
+                    if (now - t_prog > a.spin_limit_ns) {
+                        // no group made progress within the limit: give up, but
+                        // release, so no later waiter hangs on these counters
+                        failed = ready = pending;
+                        if (failed && lane == leader) set_err(&a.ctl->err, ERR_TIMEOUT);
+                    } else {
+                        // sleep until the first group is due to poll
+                        const uint32_t due = (pending && lane == leader)
+                                                 ? (t_next > now ? (uint32_t)min(t_next - now, (uint64_t)32000) : 0u)
+                                                 : kFull;
+                        const uint32_t d = __reduce_min_sync(kFull, due);
+                        if (d > 0 && d != kFull) __nanosleep(d);
+                        else if (++idle > 64) __nanosleep(32);
+                        continue;
+                    }
+                }
+                // the lanes of `ready` groups run now; the leader's acquire
+                // orders the members' accesses after the previous holder's
+                __syncwarp();
+                const int64_t slot = hb + t;
+                const bool run = ready && !failed && slot < a.db.hist_cap;
+                if (ready && !failed && !run) {      // history full: not executed
+                    set_err(a.b.err, ERR_CAPACITY);
+                    a.b.status[r.t] = 3;
+                }
+                // the account: one fetch-and-add per distinct account
+                const uint32_t am = __match_any_sync(kFull, run ? r.a : (0xFFFFFFE0u | lane));
+                int64_t pre = r.delta, tot = r.delta;
+                if (__any_sync(kFull, run && __popc(am) > 1)) group_sum(am, r.delta, pre, tot);
+                const uint32_t al = __ffs(am) - 1;
+                int64_t old = 0;
+                if (run && lane == al)
+                    old = (int64_t)atomicAdd((unsigned long long *)&a.db.acc_bal[r.a], (unsigned long long)tot);
+                old = __shfl_sync(kFull, old, al);
+                __syncwarp();
+                // one release per group: every member's update precedes it
+                if (ready && lane == leader) red_release_add(&a.done[key], (uint32_t)__popc(grp));
+                warp_add(run, r.tl, (unsigned long long *)&a.db.tel_bal[r.tl], r.delta);
+                warp_add(run, r.br, (unsigned long long *)&a.db.br_bal[r.br], r.delta);
+                if (run) {
+                    DcOut o;
+                    o.slot = slot;
+                    o.ts = r.ts;
+                    o.delta = r.delta;
+                    o.na = wrap_add(old, pre);
+                    o.a = r.a;
+                    o.tl = r.tl;
+                    o.br = r.br;
+                    o.t = r.t;
+                    dc_finish(a.db, a.b, o);
+                }
+                pending = pending && !ready;
+                t_prog = globaltimer();
+                idle = 0;
             }
         }
         __syncthreads();
@@ -707,18 +817,6 @@ static int64_t narrow_segment_end(const uint32_t *width, int64_t k, int64_t run_
     return j;
 }
 
-// lanes a level takes (LevelLanes::v, on the host): one per transaction,
-// 16 per new-order and order-status when the type cuts are known
-static uint32_t level_lanes(uint32_t lo, uint32_t hi, const uint32_t *cut)
-{
-    if (!cut) return hi - lo;
-    const uint32_t c8 = cut[0], c9 = cut[1], c10 = cut[2];
-    const uint32_t a1 = (c8 - lo + kGroup - 1) & ~(uint32_t)(kGroup - 1);
-    const uint32_t b1 = a1 + kGroup * (c9 - c8);
-    const uint32_t a2 = (b1 + (c10 - c9) + kGroup - 1) & ~(uint32_t)(kGroup - 1);
-    return a2 + kGroup * (hi - c10);
-}
-
 // clusters of this size that fit the device at once (0 = none)
 int max_cluster_ok(int csize)
 {
@@ -767,6 +865,7 @@ cudaError_t launch_kset(gputx_bulk *b, const uint32_t *order, int64_t nchunks, i
     a.level_off = b->sc.level_off;
     a.chunk_off = b->sc.chunk_off;
     a.chunk_level = b->sc.chunk_level;
+    a.type_cut = b->sc.type_cut;
     a.done = b->sc.done;
     a.levels = 0;
     a.spin_limit_ns = (uint64_t)db->cfg.spin_limit_ns;
@@ -799,7 +898,7 @@ cudaError_t launch_kset_levels(gputx_bulk *b, const uint32_t *level_off_host, in
     // lanes per level: the launch shapes follow them
     std::vector<uint32_t> width((size_t)levels);
     for (int64_t j = 0; j < levels; j++)
-        width[j] = level_lanes(level_off_host[j], level_off_host[j + 1], a.type_cut ? type_cut_host + 3 * j : nullptr);
+        width[j] = level_lane_count(level_off_host[j], level_off_host[j + 1], a.type_cut ? type_cut_host + 3 * j : nullptr);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(kset_narrow_kernel<true, 256>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -943,11 +1042,7 @@ cudaError_t launch_tpl(gputx_bulk *b, int block, bool atomic_add)
     // the general kernel's registers allow CTAs of up to 512 threads; the
     // CTA size changes only how many transactions a CTA claims at once
     if (!dc && block > 512) block = 512;
-    // resident transactions: enough to keep every lock chain moving, few
-    // enough that waiters' polls do not crowd the L2 slices of hot counters
-    // (three 256-thread CTAs an SM measured best for the debit-credit kernel)
-    int64_t grid = dc ? (int64_t)db->num_sms * std::max(1, 768 / block)
-                      : (int64_t)db->num_sms * exec_blocks_per_sm(1, block);
+    int64_t grid = (int64_t)db->num_sms * exec_blocks_per_sm(dc ? 2 : 1, block);
     const int64_t chunks = (b->n + block - 1) / block;
     if (grid > chunks) grid = chunks;
     if (dc)

@@ -264,7 +264,7 @@ __device__ __forceinline__ TxnView view_at(const DevBulk &b, uint32_t pos, int64
     v.ts = __ldg(&b.rec_ts[pos]);
     v.type = __ldg(&b.rec_type[pos]);
     v.t = __ldg(&b.rec_t[pos]);
-    v.hist_slot = hist_base + pos;
+    v.hist_slot = hist_base + (b.slot_hist ? (int64_t)__ldg(&b.slot_hist[v.t]) : (int64_t)pos);
     return v;
 }
 
@@ -278,7 +278,7 @@ __device__ __forceinline__ TxnView view_of(const DevBulk &b, uint32_t t, int64_t
     v.ts = __ldg(&b.ts[t]);
     v.type = __ldg(&b.type[t]);
     v.t = t;
-    v.hist_slot = hist_base + t;
+    v.hist_slot = hist_base + (b.slot_hist ? (int64_t)__ldg(&b.slot_hist[t]) : (int64_t)t);
     return v;
 }
 
@@ -664,6 +664,19 @@ __device__ __forceinline__ void exec_oe(const DevDB &db, const DevBulk &b, const
 // `gl` is the lane's index in its group.
 // ---------------------------------------------------------------------------
 constexpr int kGroup = 16;
+
+// lanes a level [lo, hi) takes: one per transaction, 16 per new-order and
+// order-status, each run of groups starting on a half warp.  cut = where the
+// level's types >= new-order, payment, order-status start (null: no groups)
+__host__ __device__ inline uint32_t level_lane_count(uint32_t lo, uint32_t hi, const uint32_t *cut)
+{
+    if (!cut) return hi - lo;
+    const uint32_t c8 = cut[0], c9 = cut[1], c10 = cut[2];
+    const uint32_t a1 = (c8 - lo + kGroup - 1) & ~(uint32_t)(kGroup - 1);
+    const uint32_t b1 = a1 + kGroup * (c9 - c8);
+    const uint32_t a2 = (b1 + (c10 - c9) + kGroup - 1) & ~(uint32_t)(kGroup - 1);
+    return a2 + kGroup * (hi - c10);
+}
 
 __device__ __forceinline__ uint32_t group_mask() { return 0xFFFFu << ((threadIdx.x & 31) & 16); }
 

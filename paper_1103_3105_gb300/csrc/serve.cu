@@ -215,33 +215,37 @@ struct gputx_server {
 
 namespace {
 
-// rows of each append area one transaction takes (history rows are taken per
-// bulk position when the debit-credit schema exists)
+// rows of each append area one transaction takes (a history row per
+// debit-credit transaction)
 void insert_need(const gputx_server *s, int32_t type, const int64_t *p, int64_t need[4])
 {
-    need[0] = (s->db->dev.registered & 1u) ? 1 : 0;
+    (void)s;
+    need[0] = type == GPUTX_T_DC_DEBIT_CREDIT ? 1 : 0;
     need[1] = type == GPUTX_T_SUB_INSERT_CF ? 1 : 0;
     need[2] = type == GPUTX_T_OE_NEW_ORDER ? 1 : 0;
     need[3] = type == GPUTX_T_OE_NEW_ORDER ? (p[3] > 0 && p[3] <= 15 ? p[3] : 0) : 0;
 }
 
-// call-forwarding (bit 0), order (bit 1) and order-line rows (bits 2-5) of
-// one transaction, packed at submission so a bulk's totals are a byte sum
+// call-forwarding (bit 0), order (bit 1), order-line rows (bits 2-5) and
+// history (bit 6) of one transaction, packed at submission so a bulk's
+// totals are a byte sum
 inline uint8_t pack_need(const int64_t need[4])
 {
-    return (uint8_t)(need[1] | (need[2] << 1) | (need[3] << 2));
+    return (uint8_t)(need[1] | (need[2] << 1) | (need[3] << 2) | (need[0] << 6));
 }
 
 void sum_needs(gputx_server *s, int64_t first_id, int64_t n, int64_t out[4])
 {
-    int64_t cf = 0, ord = 0, ol = 0;
+    int64_t cf = 0, ord = 0, ol = 0, hist = 0;
     for (int64_t i = first_id; i < first_id + n; i++) {
         const uint8_t q = s->p_need[i];
         cf += q & 1u;
         ord += (q >> 1) & 1u;
-        ol += q >> 2;
+        ol += (q >> 2) & 15u;
+        hist += q >> 6;
     }
-    out[0] = (s->db->dev.registered & 1u) ? n : 0;
+    // a debit-credit-only database takes a row per bulk position
+    out[0] = s->db->dev.registered == 1u ? n : hist;
     out[1] = cf;
     out[2] = ord;
     out[3] = ol;

@@ -436,12 +436,12 @@ def uneven_sizes(total: int, lo_log2: float = 10, hi_log2: float = 21, seed: int
     return sizes
 
 
-def oe_stream(total: int, n_wh: int = 64, n_items: int = 100_000) -> tuple:
+def oe_stream(total: int, n_wh: int = 64, n_items: int = 100_000, variant: int = 0, ts0: int = 0) -> tuple:
     """The batched order-entry stream: uneven bulk sizes 2^10..2^21 adding
     up to at least ``total`` transactions, and one order-entry bulk holding
-    all of them in timestamp order.  Returns (sizes, bulk)."""
-    sizes = uneven_sizes(total, 10, 21, seed=seed_for(4, 1))
-    bulk = oe_bulk(sum(sizes), n_wh, n_items=n_items, seed=seed_for(4, 2))
+    all of them in timestamp order (from ts0).  Returns (sizes, bulk)."""
+    sizes = uneven_sizes(total, 10, 21, seed=seed_for(4, 1 + 10 * variant))
+    bulk = oe_bulk(sum(sizes), n_wh, n_items=n_items, seed=seed_for(4, 2 + 10 * variant), ts0=ts0)
     return sizes, bulk
 
 
