@@ -36,10 +36,21 @@ namespace {
 
 struct GraphBulk {
     int64_t cap = 0;
-    int strategy = GPUTX_KSET, block = 256, mode = 0, P = 0, part_size = 1;
+    int strategy = GPUTX_KSET, block = 256, mode = 0, P = 0, part_size = 1, slot = 0;
     gputx_bulk *b = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr, done = nullptr;
+};
+
+// pinned host staging of one segment in flight: inputs copied in by the host,
+// results and the control block copied back by the device
+struct Staging {
+    int64_t cap = 0;
+    int P = 0, R = 0;
+    int64_t *ts = nullptr, *params = nullptr, *values = nullptr;
+    int32_t *type = nullptr, *status = nullptr;
+    uint32_t *ctl_words = nullptr;   // n_live, n_seg, seg_off[kSegMax]
+    gtx::BulkCtl *ctl = nullptr;
 };
 
 struct Candidate {
@@ -137,9 +148,42 @@ struct gputx_batcher {
     // per-transaction latency of the last run call: (transactions, ms from
     // the call's start to their segment's results on the host)
     std::vector<std::pair<double, int64_t>> lat;
+    Staging stage[2];                  // double buffer: one segment runs while the next is staged
 };
 
 namespace {
+
+void free_staging(Staging &st)
+{
+    cudaFreeHost(st.ts);
+    cudaFreeHost(st.params);
+    cudaFreeHost(st.values);
+    cudaFreeHost(st.type);
+    cudaFreeHost(st.status);
+    cudaFreeHost(st.ctl_words);
+    cudaFreeHost(st.ctl);
+    st = Staging{};
+}
+
+// pinned buffers for segments of up to cap transactions
+gputx_status ensure_staging(gputx_batcher *bt, Staging &st, int64_t cap)
+{
+    gputx_db *db = bt->db;
+    const int P = bt->cfg.params_per_txn, R = db->dev.out_width;
+    if (st.cap >= cap && st.P == P && st.R == R) return GPUTX_OK;
+    free_staging(st);
+    CKB(cudaMallocHost(&st.ts, sizeof(int64_t) * cap), "staging");
+    CKB(cudaMallocHost(&st.params, sizeof(int64_t) * cap * P), "staging");
+    CKB(cudaMallocHost(&st.values, sizeof(int64_t) * cap * R), "staging");
+    CKB(cudaMallocHost(&st.type, sizeof(int32_t) * cap), "staging");
+    CKB(cudaMallocHost(&st.status, sizeof(int32_t) * cap), "staging");
+    CKB(cudaMallocHost(&st.ctl_words, sizeof(uint32_t) * (gtx::kSegMax + 2)), "staging");
+    CKB(cudaMallocHost(&st.ctl, sizeof(gtx::BulkCtl)), "staging");
+    st.cap = cap;
+    st.P = P;
+    st.R = R;
+    return GPUTX_OK;
+}
 
 void destroy_graph(GraphBulk *g)
 {
@@ -147,16 +191,17 @@ void destroy_graph(GraphBulk *g)
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->e0) cudaEventDestroy(g->e0);
     if (g->e1) cudaEventDestroy(g->e1);
+    if (g->done) cudaEventDestroy(g->done);
     if (g->b) gputx_free_bulk(g->b);
     delete g;
 }
 
 // the fixed-capacity bulk and captured graph for a shape (created on first use)
-gputx_status get_graph(gputx_batcher *bt, int64_t cap, int strategy, int block, GraphBulk **out)
+gputx_status get_graph(gputx_batcher *bt, int64_t cap, int strategy, int block, int slot, GraphBulk **out)
 {
     gputx_db *db = bt->db;
     for (GraphBulk *g : bt->graphs)
-        if (g->cap == cap && g->strategy == strategy && g->block == block) {
+        if (g->cap == cap && g->strategy == strategy && g->block == block && g->slot == slot) {
             *out = g;
             return GPUTX_OK;
         }
@@ -164,6 +209,7 @@ gputx_status get_graph(gputx_batcher *bt, int64_t cap, int strategy, int block, 
     g->cap = cap;
     g->strategy = strategy;
     g->block = block;
+    g->slot = slot;
     g->mode = bt->cfg.conflict_mode;
     g->P = bt->cfg.params_per_txn;
     g->part_size = bt->part_size;
@@ -184,6 +230,7 @@ gputx_status get_graph(gputx_batcher *bt, int64_t cap, int strategy, int block, 
     CKB(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming), "event");
     CKB(cudaEventCreate(&g->e0), "event");
     CKB(cudaEventCreate(&g->e1), "event");
+    CKB(cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming), "event");
     b->executed = true;
     // one uncaptured run sets up per-kernel attributes; its inputs are all
     // padding, so it changes nothing
@@ -217,30 +264,35 @@ gputx_status get_graph(gputx_batcher *bt, int64_t cap, int strategy, int block, 
 }
 
 // One segment of n <= cap transactions through a graph: n_seg bulks whose
-// first transactions (relative to the segment) are seg_off[0..n_seg-1].
-// Returns its device time; *fallback is set when a PART segment held a
-// cross-partition transaction (nothing ran).
-gputx_status run_segment(gputx_batcher *bt, GraphBulk *g, const int64_t *ts, const int32_t *type,
-                         const int64_t *params, int64_t n, const uint32_t *seg_off, uint32_t n_seg, int32_t *status,
-                         int64_t *values, double *ms, gtx::BulkCtl *ctl_out, bool *fallback)
+// first transactions (relative to the segment) are seg_off[0..n_seg-1].  The
+// host copies the inputs into the pinned staging `st`; the device copies them
+// in, replays the graph and copies the results and the control block back
+// into `st`, then records g->done.  Nothing here waits for the device.
+gputx_status enqueue_segment(gputx_batcher *bt, GraphBulk *g, Staging &st, const int64_t *ts, const int32_t *type,
+                             const int64_t *params, int64_t n, const uint32_t *seg_off, uint32_t n_seg)
 {
     gputx_db *db = bt->db;
     gputx_bulk *b = g->b;
     cudaStream_t s = b->stream;
     const int64_t cap = g->cap;
-    *fallback = false;
+    std::memcpy(st.ts, ts, sizeof(int64_t) * n);
+    std::memcpy(st.type, type, sizeof(int32_t) * n);
+    std::memcpy(st.params, params, sizeof(int64_t) * n * g->P);
+    st.ctl_words[0] = (uint32_t)n;
+    st.ctl_words[1] = n_seg;
+    std::memcpy(st.ctl_words + 2, seg_off, sizeof(uint32_t) * n_seg);
     // earlier work on the database stream (loads, other bulks) comes first
     CKB(cudaEventRecord(b->ev_in, db->stream), "order");
     CKB(cudaStreamWaitEvent(s, b->ev_in, 0), "order");
     CKB(cudaStreamWaitEvent(s, db->last_done, 0), "order");
     CKB(cudaMemsetAsync(b->ctl, 0, sizeof(gtx::BulkCtl), s), "reset");
-    const uint32_t nl = (uint32_t)n;
-    CKB(cudaMemcpyAsync(&b->ctl->n_live, &nl, sizeof nl, cudaMemcpyHostToDevice, s), "inputs");
-    CKB(cudaMemcpyAsync(&b->ctl->n_seg, &n_seg, sizeof n_seg, cudaMemcpyHostToDevice, s), "inputs");
-    CKB(cudaMemcpyAsync(b->sc.seg_off, seg_off, sizeof(uint32_t) * n_seg, cudaMemcpyHostToDevice, s), "inputs");
-    CKB(cudaMemcpyAsync(b->ts, ts, sizeof(int64_t) * n, cudaMemcpyHostToDevice, s), "inputs");
-    CKB(cudaMemcpyAsync(b->type, type, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s), "inputs");
-    CKB(cudaMemcpyAsync(b->params, params, sizeof(int64_t) * n * g->P, cudaMemcpyHostToDevice, s), "inputs");
+    CKB(cudaMemcpyAsync(&b->ctl->n_live, &st.ctl_words[0], sizeof(uint32_t), cudaMemcpyHostToDevice, s), "inputs");
+    CKB(cudaMemcpyAsync(&b->ctl->n_seg, &st.ctl_words[1], sizeof(uint32_t), cudaMemcpyHostToDevice, s), "inputs");
+    CKB(cudaMemcpyAsync(b->sc.seg_off, st.ctl_words + 2, sizeof(uint32_t) * n_seg, cudaMemcpyHostToDevice, s),
+        "inputs");
+    CKB(cudaMemcpyAsync(b->ts, st.ts, sizeof(int64_t) * n, cudaMemcpyHostToDevice, s), "inputs");
+    CKB(cudaMemcpyAsync(b->type, st.type, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s), "inputs");
+    CKB(cudaMemcpyAsync(b->params, st.params, sizeof(int64_t) * n * g->P, cudaMemcpyHostToDevice, s), "inputs");
     if (n < cap) CKB(cudaMemsetAsync(b->type + n, 0xff, sizeof(int32_t) * (cap - n), s), "inputs");
     CKB(cudaMemsetAsync(b->out, 0, sizeof(int64_t) * cap * b->R, s), "inputs");
     CKB(cudaEventRecord(g->e0, s), "event");
@@ -248,14 +300,26 @@ gputx_status run_segment(gputx_batcher *bt, GraphBulk *g, const int64_t *ts, con
     CKB(cudaEventRecord(g->e1, s), "event");
     CKB(cudaEventRecord(db->last_done, s), "order");
     CKB(cudaStreamWaitEvent(db->stream, db->last_done, 0), "order");
-    CKB(cudaMemcpyAsync(status, b->status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s), "results");
-    CKB(cudaMemcpyAsync(values, b->out, sizeof(int64_t) * n * b->R, cudaMemcpyDeviceToHost, s), "results");
-    gtx::BulkCtl ctl{};
-    CKB(cudaMemcpyAsync(&ctl, b->ctl, sizeof ctl, cudaMemcpyDeviceToHost, s), "results");
-    CKB(cudaStreamSynchronize(s), "results");
+    CKB(cudaMemcpyAsync(st.status, b->status, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s), "results");
+    CKB(cudaMemcpyAsync(st.values, b->out, sizeof(int64_t) * n * b->R, cudaMemcpyDeviceToHost, s), "results");
+    CKB(cudaMemcpyAsync(st.ctl, b->ctl, sizeof(gtx::BulkCtl), cudaMemcpyDeviceToHost, s), "results");
+    CKB(cudaEventRecord(g->done, s), "event");
+    return GPUTX_OK;
+}
+
+// Waits for a segment enqueued by enqueue_segment, copies its results to the
+// caller's arrays and returns its device time.  *fallback is set when a PART
+// segment held a cross-partition transaction (nothing ran).
+gputx_status finish_segment(gputx_batcher *bt, GraphBulk *g, Staging &st, int64_t n, int32_t *status,
+                            int64_t *values, double *ms, gtx::BulkCtl *ctl_out, bool *fallback)
+{
+    gputx_db *db = bt->db;
+    *fallback = false;
+    CKB(cudaEventSynchronize(g->done), "results");
     float t = 0;
     cudaEventElapsedTime(&t, g->e0, g->e1);
     *ms = t;
+    const gtx::BulkCtl ctl = *st.ctl;
     if (ctl_out) *ctl_out = ctl;
     if (ctl.err == gtx::ERR_FALLBACK) {
         *fallback = true;
@@ -265,6 +329,8 @@ gputx_status run_segment(gputx_batcher *bt, GraphBulk *g, const int64_t *ts, con
     if (ctl.err & gtx::ERR_TIMEOUT) return fail_bt(db, GPUTX_ETIMEOUT, "a bounded device wait ran out");
     if (ctl.err & gtx::ERR_CAPACITY) return fail_bt(db, GPUTX_ECAPACITY, "an insert area is full");
     if (ctl.err) return fail_bt(db, GPUTX_EBOUNDS, "device bounds check failed");
+    std::memcpy(status, st.status, sizeof(int32_t) * n);
+    std::memcpy(values, st.values, sizeof(int64_t) * n * st.R);
     return GPUTX_OK;
 }
 
@@ -349,9 +415,58 @@ gputx_status gputx_batcher_run_bulks(gputx_batcher *bt, const int64_t *ts, const
     const int seg_kset = sb > 0 ? std::min(gtx::kSegMax, (1 << sb) - 1) : 1;
     const auto t_start = std::chrono::steady_clock::now();
     bt->lat.clear();
+    // a segment enqueued and not yet finished
+    struct InFlight {
+        bool valid = false, first = false;
+        GraphBulk *g = nullptr;
+        int buf = 0, strategy = GPUTX_KSET, block = 256;
+        int64_t first_txn = 0, k = 0, size = 0;
+        Candidate *cand = nullptr;
+        std::vector<uint32_t> seg_off;
+    };
+    auto finish = [&](InFlight &f) -> gputx_status {
+        f.valid = false;
+        double ms = 0;
+        gtx::BulkCtl ctl{};
+        bool fb = false;
+        Staging &stg = bt->stage[f.buf];
+        gputx_status st = finish_segment(bt, f.g, stg, f.k, status + f.first_txn, values + f.first_txn * R, &ms, &ctl,
+                                         &fb);
+        if (st) return st;
+        if (fb) {
+            // Section 5.2: a PART segment with a cross-partition transaction
+            // runs with TPL (nothing of it ran)
+            GraphBulk *gt = nullptr;
+            if ((st = get_graph(bt, f.size, GPUTX_TPL, f.block, f.g->slot, &gt))) return st;
+            if ((st = enqueue_segment(bt, gt, stg, ts + f.first_txn, type + f.first_txn, params + f.first_txn * P, f.k,
+                                      f.seg_off.data(), (uint32_t)f.seg_off.size())))
+                return st;
+            double ms2 = 0;
+            if ((st = finish_segment(bt, gt, stg, f.k, status + f.first_txn, values + f.first_txn * R, &ms2, nullptr,
+                                     &fb)))
+                return st;
+            ms += ms2;
+        }
+        bt->lat.push_back(
+            {std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count(), f.k});
+        if (f.first) {
+            const bool wide = (int64_t)ctl.w0 >= std::min<int64_t>(db->cfg.kset_w0_min, f.k / 4);
+            bt->part_ok = ctl.cross == 0;
+            plan_candidates(bt, wide ? GPUTX_KSET : GPUTX_TPL);
+        } else if (f.cand) {
+            // a short segment is padded: charge it at least half its capacity
+            f.cand->ns_per_txn = ms * 1e6 / (double)std::max<int64_t>(f.k, f.size / 2);
+            bt->next_cand++;
+        }
+        bt->bulks_run++;
+        return GPUTX_OK;
+    };
+    InFlight prev;
+    int buf = 0;
     size_t bi = 0;
     int64_t boff = 0;
     std::vector<uint32_t> seg_off;
+    gputx_status st = GPUTX_OK;
     while (bi < n_bulks) {
         Candidate *cand = nullptr;
         int strategy, block;
@@ -375,9 +490,9 @@ gputx_status gputx_batcher_run_bulks(gputx_batcher *bt, const int64_t *ts, const
                                                  });
                     const Candidate bc = *best;
                     const size_t before = bt->cands.size();
-                    auto have = [&](int st, int blk, int64_t sz) {
+                    auto have = [&](int s_, int blk, int64_t sz) {
                         for (auto &c : bt->cands)
-                            if (c.strategy == st && c.block == blk && c.bulk == sz) return true;
+                            if (c.strategy == s_ && c.block == blk && c.bulk == sz) return true;
                         return false;
                     };
                     for (int blk : {128, 512})
@@ -398,50 +513,49 @@ gputx_status gputx_batcher_run_bulks(gputx_batcher *bt, const int64_t *ts, const
             block = cand ? cand->block : bt->best.block;
             size = cand ? cand->bulk : bt->best.bulk;
         }
-        const size_t bi0 = bi;
-        const int64_t boff0 = boff;
+        // tuning segments and PART segments (whose fallback must run before
+        // any later segment) complete before the next is enqueued; a tuned
+        // K-SET or TPL stream keeps two segments in flight, so the host's
+        // copies of one overlap the other's execution
+        const bool sync = !bt->tuned || strategy == GPUTX_PART;
+        const int first_limit = strategy == GPUTX_KSET ? seg_kset : gtx::kSegMax;
         const int64_t first_txn = bulk_off[bi] + boff;
-        const int limit = strategy == GPUTX_KSET ? seg_kset : gtx::kSegMax;
-        const int64_t k = next_segment(bulk_off, n_bulks, bi, boff, size, limit, seg_off);
+        const int64_t k = next_segment(bulk_off, n_bulks, bi, boff, size, first_limit, seg_off);
         if (k == 0) continue;   // only empty bulks were left
         GraphBulk *g = nullptr;
-        gputx_status st = get_graph(bt, size, strategy, block, &g);
-        if (st) return st;
-        double ms = 0;
-        gtx::BulkCtl ctl{};
-        bool fb = false;
-        st = run_segment(bt, g, ts + first_txn, type + first_txn, params + first_txn * P, k, seg_off.data(),
-                         (uint32_t)seg_off.size(), status + first_txn, values + first_txn * R, &ms, &ctl, &fb);
-        if (st) return st;
-        if (fb) {
-            // Section 5.2: a PART segment with a cross-partition transaction
-            // runs with TPL (nothing of it ran)
-            double ms2 = 0;
-            GraphBulk *gt = nullptr;
-            if ((st = get_graph(bt, size, GPUTX_TPL, block, &gt))) return st;
-            st = run_segment(bt, gt, ts + first_txn, type + first_txn, params + first_txn * P, k, seg_off.data(),
-                             (uint32_t)seg_off.size(), status + first_txn, values + first_txn * R, &ms2, nullptr,
-                             &fb);
-            if (st) return st;
-            ms += ms2;
+        if ((st = get_graph(bt, size, strategy, block, sync ? 0 : buf, &g))) break;
+        if ((st = ensure_staging(bt, bt->stage[buf], size))) break;
+        if ((st = enqueue_segment(bt, g, bt->stage[buf], ts + first_txn, type + first_txn, params + first_txn * P, k,
+                                  seg_off.data(), (uint32_t)seg_off.size())))
+            break;
+        InFlight cur;
+        cur.valid = true;
+        cur.first = first;
+        cur.g = g;
+        cur.buf = buf;
+        cur.strategy = strategy;
+        cur.block = block;
+        cur.first_txn = first_txn;
+        cur.k = k;
+        cur.size = size;
+        cur.cand = cand;
+        cur.seg_off = seg_off;
+        if (prev.valid && (st = finish(prev))) {
+            cudaEventSynchronize(g->done);   // nothing left in flight
+            return st;
         }
-        (void)bi0;
-        (void)boff0;
-        bt->lat.push_back({std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start)
-                               .count(),
-                           k});
-        if (first) {
-            const bool wide = (int64_t)ctl.w0 >= std::min<int64_t>(db->cfg.kset_w0_min, k / 4);
-            bt->part_ok = ctl.cross == 0;
-            plan_candidates(bt, wide ? GPUTX_KSET : GPUTX_TPL);
-        } else if (cand) {
-            // a short segment is padded: charge it at least half its capacity
-            cand->ns_per_txn = ms * 1e6 / (double)std::max<int64_t>(k, size / 2);
-            bt->next_cand++;
+        if (sync) {
+            if ((st = finish(cur))) return st;
+        } else {
+            prev = cur;
         }
-        bt->bulks_run++;
+        buf ^= 1;
     }
-    return GPUTX_OK;
+    if (prev.valid) {
+        gputx_status st2 = finish(prev);
+        if (!st) st = st2;
+    }
+    return st;
 }
 
 gputx_status gputx_batcher_run(gputx_batcher *bt, const int64_t *ts, const int32_t *type, const int64_t *params,
@@ -503,6 +617,7 @@ void gputx_batcher_destroy(gputx_batcher *bt)
 {
     if (!bt) return;
     for (GraphBulk *g : bt->graphs) destroy_graph(g);
+    for (Staging &st : bt->stage) free_staging(st);
     delete bt;
 }
 
