@@ -57,7 +57,7 @@ DOMINANT_KERNEL = {("kset", "paper"): "kset_narrow_dc_kernel", ("kset", "add"): 
 # ncu capture at this configuration, keyed by (strategy, mode, bulk log2);
 # each entry holds the digest of the kernel and launch-planner sources it was
 # taken on, and is reported as null once those sources change
-TRAFFIC = {("kset", "paper", 22): {"bytes": 340776448 + 290629888, "digest": "ea76176d16856ae1"}}
+TRAFFIC = {("kset", "paper", 22): {"bytes": 340535040 + 362240 + 290906112, "digest": "ba35a042b8637d7f"}}
 KERNEL_SOURCES = ("common.cuh", "fastdiv.h", "engine.h", "dc.cuh", "levels.cuh", "exec_dc.cu", "exec.cu")
 
 
