@@ -16,7 +16,8 @@ import weakref
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libgputx.so")
+# GPUTX_DEBUG=1 loads the bounds-checked build (``_build.build(debug=True)``)
+LIB_PATH = os.path.join(_HERE, "libgputx_debug.so" if os.environ.get("GPUTX_DEBUG") == "1" else "libgputx.so")
 
 # --- constants mirrored from include/gputx.h --------------------------------
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBOUNDS, ESTATE, ECAPACITY = range(8)

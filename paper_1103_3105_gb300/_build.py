@@ -2,6 +2,10 @@
 
 Each translation unit compiles in parallel; the shared library links against
 the shared CUDA runtime so that it and PyTorch use one runtime instance.
+``build(debug=True)`` builds libgputx_debug.so instead, with -DGPUTX_DEBUG:
+the same engine with a bounds check on every index its executors gather or
+scatter by (a failed check fails the bulk with GPUTX_EBOUNDS).  The binding
+loads it when GPUTX_DEBUG=1 is set in the environment.
 """
 from __future__ import annotations
 
@@ -13,6 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgputx.so")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libgputx_debug.so")
 SOURCES = ["api.cu", "analysis.cu", "exec.cu", "exec_dc.cu", "tables.cu", "serve.cu", "batch.cu", "pool.cu", "relaxed.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -35,7 +41,9 @@ def _stale(outputs, inputs):
     return min(os.path.getmtime(o) for o in outputs) < newest
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    BUILD, LIB = (BUILD_DEBUG, LIB_DEBUG) if debug else (globals()["BUILD"], globals()["LIB"])
+    flags = _flags() + (["-DGPUTX_DEBUG"] if debug else [])
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".cuh", ".h"))]
     headers.append(os.path.join(HERE, "..", "include", "gputx.h"))
@@ -46,7 +54,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale([o], [s] + headers):
-            jobs.append([_nvcc()] + _flags() + ["-c", s, "-o", o])
+            jobs.append([_nvcc()] + flags + ["-c", s, "-o", o])
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
             futs = [ex.submit(subprocess.run, j, capture_output=True, text=True) for j in jobs]
@@ -69,4 +77,4 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, debug="--debug" in sys.argv))

@@ -177,6 +177,28 @@ __device__ __forceinline__ int64_t wrap_add(int64_t a, int64_t b)
 
 __device__ __forceinline__ void set_err(uint32_t *err, uint32_t bit) { atomicOr(err, bit); }
 
+// Debug builds (compiled with -DGPUTX_DEBUG into libgputx_debug.so) check,
+// inside the executors, every index that a gather or scatter takes: positions
+// in the bulk and in its execution order, the rows a transaction's parameters
+// name, the rows an index probe returns, lock counters, level bounds.  A
+// failed check records ERR_BOUNDS in the bulk's error word and the access is
+// skipped (its transaction is not executed), so the bulk fails at its sync
+// with GPUTX_EBOUNDS instead of touching memory it does not own.  In release
+// builds every check compiles away.
+#ifdef GPUTX_DEBUG
+constexpr bool kDebug = true;
+#else
+constexpr bool kDebug = false;
+#endif
+
+// i in [0, n): a debug build's check (always true in a release build)
+__device__ __forceinline__ bool dbg_in(int64_t i, int64_t n, uint32_t *err)
+{
+    if (!kDebug || (i >= 0 && i < n)) return true;
+    set_err(err, ERR_BOUNDS);
+    return false;
+}
+
 // Where the counter (TPL) or lock (relaxed TPL) of item k lives: slot
 // (k mod L) * 32 + k / L of an array of 32 L words, a 32-column transposition
 // of the item order.  Consecutive items -- the branches of debit-credit, the

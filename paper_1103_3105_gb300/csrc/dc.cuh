@@ -17,6 +17,16 @@ struct DcOut {
     uint32_t t;
 };
 
+// a debug build's check of the rows a debit-credit transaction touches and of
+// its index in the bulk (always true in a release build)
+__device__ __forceinline__ bool dbg_dc_rows(const DevDB &db, const DevBulk &b, int64_t a, int64_t tl, int64_t br,
+                                            int64_t t)
+{
+    if (!kDebug) return true;
+    return dbg_in(a, db.n_acc, b.err) && dbg_in(tl, db.n_tel, b.err) && dbg_in(br, db.n_br, b.err) &&
+           dbg_in(t, b.n, b.err);
+}
+
 __device__ __forceinline__ void dc_finish(const DevDB &db, const DevBulk &b, const DcOut &o)
 {
     db.h_ts[o.slot] = o.ts;
@@ -49,6 +59,7 @@ __device__ __forceinline__ void dc_finish(const DevDB &db, const DevBulk &b, con
 __device__ __forceinline__ bool dc_account_rmw(const DevDB &db, const DevBulk &b, const DcRecord &r, int64_t slot,
                                                DcOut &o)
 {
+    if (!dbg_dc_rows(db, b, r.a, r.tl, r.br, r.t)) return false;
     if (slot >= db.hist_cap) {              // history full: not executed
         set_err(b.err, ERR_CAPACITY);
         b.status[r.t] = 3;

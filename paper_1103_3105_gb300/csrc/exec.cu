@@ -282,6 +282,7 @@ __global__ void part_kernel(DevDB db, DevBulk b, const BulkCtl *ctl, const uint3
     const int64_t hb = ctl->base.hist;
     const uint32_t n = (uint32_t)b.n;
     uint32_t i = part_start[p];
+    if (!dbg_in(i, n, b.err)) return;
     const uint32_t key = __ldg(&pkeys[i]);
     // a two-deep pipeline along the partition's timestamp order: while
     // transaction i executes, i+1's rows are already in L2 and i+2's record
@@ -368,9 +369,17 @@ __global__ void __launch_bounds__(256) part_dc_warp_kernel(DevDB db, DevBulk b, 
     if (p >= ctl->npart || ctl->err) return;   // whole warps; no block barrier below
     const int64_t hb = ctl->base.hist;
     const uint32_t lo = part_start[p], hi = part_start[p + 1];
+    if (kDebug && (lo >= hi || !dbg_in(hi, b.n + 1, b.err))) {   // warp-uniform
+        set_err(b.err, ERR_BOUNDS);
+        return;
+    }
     const uint32_t br = __ldg(&pkeys[lo]);     // partition key = branch
     const uint32_t tpb = (uint32_t)(db.acc_per_br / db.acc_per_tel);
     const uint32_t tel0 = br * tpb;
+    if (kDebug && (tpb > 32 || !dbg_in((int64_t)tel0 + tpb, db.n_tel + 1, b.err))) {
+        set_err(b.err, ERR_BOUNDS);
+        return;
+    }
     int64_t *tel = s_tel[wib];
     tel[lane] = lane < tpb ? __ldcg(&db.tel_bal[tel0 + lane]) : 0;
     int64_t bsum = 0;
@@ -380,7 +389,12 @@ __global__ void __launch_bounds__(256) part_dc_warp_kernel(DevDB db, DevBulk b, 
     if (lo + lane < hi) r = rec[lo + lane];
     for (uint32_t base = lo; base < hi; base += 32) {
         const uint32_t i = base + lane;
-        const bool act = i < hi;
+        bool act = i < hi;
+        if (kDebug && act && !(dbg_dc_rows(db, b, r.a, r.tl, r.br, r.t) && r.br == br && r.tl >= tel0 &&
+                               r.tl < tel0 + tpb)) {
+            set_err(b.err, ERR_BOUNDS);       // a record outside this partition's rows
+            act = false;
+        }
         const int64_t slot = hb + i;
         const bool run = act && slot < db.hist_cap;
         if (act && !run) {                     // history full: not executed
@@ -392,7 +406,7 @@ __global__ void __launch_bounds__(256) part_dc_warp_kernel(DevDB db, DevBulk b, 
         DcRecord nr{};
         if (base + 32 + lane < hi) {
             nr = rec[base + 32 + lane];
-            prefetch_l2(&db.acc_bal[nr.a]);
+            if (!kDebug || nr.a < db.n_acc) prefetch_l2(&db.acc_bal[nr.a]);
         }
         const uint32_t am = __match_any_sync(kFull, run ? r.a : (0xFFFFFFE0u | lane));
         int64_t pre = r.delta, tot = r.delta;
@@ -436,7 +450,16 @@ struct TplArgs {
     bool graph;          // fixed-capacity bulk: K slots per transaction, only the
                          // first op_count are real; padding transactions skipped
     LockSlots slot;      // item -> its counter in `done`
+    int when_hot;        // debit-credit executors: -1 run, 1 run only if ctl->hot, 0 only if not
 };
+
+// whether a debit-credit TPL executor sits this bulk out (the other one runs)
+__device__ __forceinline__ bool tpl_skip(const TplArgs &a)
+{
+    if (a.when_hot < 0) return false;
+    const bool hot = *(volatile const uint32_t *)&a.ctl->hot != 0u;
+    return hot != (a.when_hot == 1);
+}
 
 // a relaxed poll of a lock counter: several can be in flight at once (an
 // acquire load would order each behind the one before); one acquire fence
@@ -648,11 +671,13 @@ __global__ void __launch_bounds__(512) tpl_kernel(TplArgs a)
 // aggregated the same way.  The warp polls in lockstep rounds: each group
 // polls again after about 500 ns per release it still misses, and the warp
 // sleeps until the first group is due, so a group whose counter is about to
-// be released never sleeps behind one far back in its chain.  A warp in which no two lanes share a counter needs none of this:
-// there each lane waits on its own counter and runs as soon as it is granted.
+// be released never sleeps behind one far back in its chain.  A warp in
+// which no two lanes share a counter needs none of this: there each lane
+// waits on its own counter and runs as soon as it is granted.
 __global__ void tpl_dc_kernel(TplArgs a)
 {
     __shared__ uint32_t s_c, s_stop;
+    if (tpl_skip(a)) return;
     const int64_t n = a.b.n;
     const int64_t hb = a.ctl->base.hist;
     const uint32_t lane = threadIdx.x & 31;
@@ -668,6 +693,7 @@ __global__ void tpl_dc_kernel(TplArgs a)
         const bool live = t < n;
         DcRecord r{};
         uint32_t key = 0xFFFFFFE0u | lane, tk = 0;   // a key of its own for an idle lane
+        bool rows_ok = true;   // a debug build's check of the record's rows
         if (live) {
             r.a = (uint32_t)__ldg(&a.b.params[t * a.b.P]);
             r.delta = __ldg(&a.b.params[t * a.b.P + 1]);
@@ -675,7 +701,8 @@ __global__ void tpl_dc_kernel(TplArgs a)
             r.t = (uint32_t)t;
             r.tl = a.db.div_tel.div(r.a);
             r.br = a.db.div_br.div(r.a);
-            prefetch_l2(&a.db.acc_bal[r.a]);
+            rows_ok = dbg_dc_rows(a.db, a.b, r.a, r.tl, r.br, r.t);
+            if (rows_ok) prefetch_l2(&a.db.acc_bal[r.a]);
             key = a.slot(a.lock_key[t]);
             tk = a.lock_ticket[t];
         }
@@ -730,8 +757,8 @@ __global__ void tpl_dc_kernel(TplArgs a)
                 // orders the members' accesses after the previous holder's
                 __syncwarp();
                 const int64_t slot = hb + t;
-                const bool run = ready && !failed && slot < a.db.hist_cap;
-                if (ready && !failed && !run) {      // history full: not executed
+                const bool run = ready && !failed && rows_ok && slot < a.db.hist_cap;
+                if (ready && !failed && rows_ok && !run) {      // history full: not executed
                     set_err(a.b.err, ERR_CAPACITY);
                     a.b.status[r.t] = 3;
                 }
@@ -766,6 +793,199 @@ __global__ void tpl_dc_kernel(TplArgs a)
                 idle = 0;
             }
         }
+        __syncthreads();
+    }
+}
+
+// TPL for debit-credit-only bulks with the lock groups formed over the whole
+// CTA (up to 256 consecutive transactions) instead of one warp.  The CTA's
+// transactions that need the same counter form one group (a shared-memory
+// hash of the counter slots, a lane mask per group): their tickets are
+// consecutive, since the chunk holds consecutive timestamps, so the group
+// runs as soon as its first lane's ticket is granted.  That lane waits on the
+// counter and publishes the grant in shared memory; within the group, lanes
+// on the same account combine their deltas (one fetch-and-add of the sum by
+// the account's first lane, each lane's new balance = the old value plus the
+// inclusive prefix of the deltas in timestamp order); once every member has
+// its balance, the first lane releases the counter by the group's size.  On a
+// hot item a whole chunk's operations cost one hand-off through L2.  Every
+// wait in shared memory is bounded like the counter waits.
+constexpr int kBlkTab = 512;          // hash slots for the chunk's counters (2 x the chunk)
+constexpr uint32_t kBlkEmpty = 0xffffffffu;
+
+__device__ __forceinline__ bool wait_smem(volatile uint32_t *f, uint64_t limit_ns)
+{
+    if (*f) return true;
+    const uint64_t t0 = globaltimer();
+    uint32_t spins = 0;
+    while (!*f) {
+        if (++spins > 32) __nanosleep(64);
+        if (globaltimer() - t0 > limit_ns) return false;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(256) tpl_dc_block_kernel(TplArgs a)
+{
+    __shared__ uint32_t s_c, s_stop;
+    __shared__ uint32_t h_key[kBlkTab], h_state[kBlkTab], h_fin[kBlkTab];
+    __shared__ uint32_t h_mask[kBlkTab][8];
+    __shared__ int64_t s_delta[256], s_old[256];
+    __shared__ uint32_t s_acct[256], s_aflag[256];
+    if (tpl_skip(a)) return;
+    const int64_t n = a.b.n;
+    const int64_t hb = a.ctl->base.hist;
+    const uint32_t tid = threadIdx.x;
+    while (true) {
+        if (tid == 0) {
+            s_stop = *(volatile uint32_t *)&a.ctl->err ? 1u : 0u;
+            s_c = atomicAdd(&a.ctl->claim, 1u);
+        }
+        for (uint32_t i = tid; i < (uint32_t)kBlkTab; i += blockDim.x) {
+            h_key[i] = kBlkEmpty;
+            h_state[i] = 0;
+            h_fin[i] = 0;
+#pragma unroll
+            for (int w = 0; w < 8; w++) h_mask[i][w] = 0;
+        }
+        __syncthreads();
+        const int64_t start = (int64_t)s_c * blockDim.x;
+        if (s_stop || start >= n) break;
+        const int64_t t = start + tid;
+        const bool live = t < n;
+        DcRecord r{};
+        uint32_t key = 0, tk = 0, e = 0;
+        bool rows_ok = true;   // a debug build's check of the record's rows
+        if (live) {
+            r.a = (uint32_t)__ldg(&a.b.params[t * a.b.P]);
+            r.delta = __ldg(&a.b.params[t * a.b.P + 1]);
+            r.ts = __ldg(&a.b.ts[t]);
+            r.t = (uint32_t)t;
+            r.tl = a.db.div_tel.div(r.a);
+            r.br = a.db.div_br.div(r.a);
+            rows_ok = dbg_dc_rows(a.db, a.b, r.a, r.tl, r.br, r.t);
+            if (rows_ok) prefetch_l2(&a.db.acc_bal[r.a]);
+            key = a.slot(a.lock_key[t]);
+            tk = a.lock_ticket[t];
+            // the counter's slot in the chunk's table (linear probing)
+            e = (key * 2654435761u) & (kBlkTab - 1);
+            while (true) {
+                const uint32_t prev = atomicCAS(&h_key[e], kBlkEmpty, key);
+                if (prev == kBlkEmpty || prev == key) break;
+                e = (e + 1) & (kBlkTab - 1);
+            }
+            atomicOr(&h_mask[e][tid >> 5], 1u << (tid & 31));
+        }
+        const int64_t slot = hb + t;
+        const bool run = live && rows_ok && slot < a.db.hist_cap;
+        s_delta[tid] = run ? r.delta : 0;
+        s_acct[tid] = r.a;
+        s_aflag[tid] = 0;
+        __syncthreads();
+        if (live) {
+            uint32_t m[8];
+#pragma unroll
+            for (int w = 0; w < 8; w++) m[w] = h_mask[e][w];
+            uint32_t leader = 0, size = 0;
+            bool found = false;
+#pragma unroll
+            for (int w = 0; w < 8; w++) {
+                if (!found && m[w]) {
+                    leader = 32u * w + (uint32_t)(__ffs(m[w]) - 1);
+                    found = true;
+                }
+                size += __popc(m[w]);
+            }
+            if (size == 1) {
+                // the only transaction of the chunk on its counter: it waits
+                // on its own and runs as soon as it is granted
+                const bool ok1 = !tk || wait_at_least(&a.done[key], tk, a.spin_limit_ns, 500);
+                if (!ok1) set_err(&a.ctl->err, ERR_TIMEOUT);
+                DcOut o;
+                const bool pend = ok1 && dc_account_rmw(a.db, a.b, r, slot, o);
+                red_release_add(&a.done[key], 1u);
+                if (pend) dc_finish_rmw(a.db, a.b, o);
+                goto next_chunk;
+            }
+            // the lanes of the group on this lane's account: the first of
+            // them, the inclusive prefix of their deltas and their sum
+            uint32_t afirst = tid;
+            int64_t pre = 0, tot = 0;
+            for (int w = 0; w < 8; w++) {
+                for (uint32_t bits = m[w]; bits; bits &= bits - 1) {
+                    const uint32_t j = 32u * w + (uint32_t)(__ffs(bits) - 1);
+                    if (s_acct[j] != r.a) continue;
+                    const int64_t d = s_delta[j];
+                    tot = wrap_add(tot, d);
+                    if (j <= tid) pre = wrap_add(pre, d);
+                    if (j < afirst) afirst = j;
+                }
+            }
+            volatile uint32_t *state = &h_state[e];
+            bool ok = true;
+            if (tid == leader) {
+                ok = !tk || wait_at_least(&a.done[key], tk, a.spin_limit_ns, 500);
+                if (!ok) set_err(&a.ctl->err, ERR_TIMEOUT);
+                __threadfence_block();
+                *state = ok ? 1u : 2u;
+            } else if (!wait_smem(state, a.spin_limit_ns) || *state != 1u) {
+                ok = false;
+                if (*state == 0u) set_err(&a.ctl->err, ERR_TIMEOUT);
+            }
+            if (ok && tid == leader) ok = *state == 1u;
+            __threadfence_block();   // the leader's acquire before this lane's accesses
+            if (ok && !run && live && rows_ok) {   // history full: not executed
+                set_err(a.b.err, ERR_CAPACITY);
+                a.b.status[r.t] = 3;
+            }
+            int64_t old = 0;
+            bool have = false;
+            if (ok && run) {
+                if (afirst == tid) {
+                    old = (int64_t)atomicAdd((unsigned long long *)&a.db.acc_bal[r.a], (unsigned long long)tot);
+                    s_old[tid] = old;
+                    __threadfence_block();
+                    *(volatile uint32_t *)&s_aflag[tid] = 1u;
+                    have = true;
+                } else if (wait_smem(&s_aflag[afirst], a.spin_limit_ns)) {
+                    old = *(volatile int64_t *)&s_old[afirst];
+                    have = true;
+                } else {
+                    set_err(&a.ctl->err, ERR_TIMEOUT);
+                }
+            }
+            // every member counted once its account update is done (or it gave up)
+            __threadfence_block();
+            atomicAdd(&h_fin[e], 1u);
+            if (tid == leader) {
+                // the group's updates precede its one release
+                volatile uint32_t *fin = &h_fin[e];
+                const uint64_t t0 = globaltimer();
+                while (*fin < size) {
+                    __nanosleep(32);
+                    if (globaltimer() - t0 > a.spin_limit_ns) {
+                        set_err(&a.ctl->err, ERR_TIMEOUT);
+                        break;
+                    }
+                }
+                red_release_add(&a.done[key], size);
+            }
+            if (have) {
+                atomicAdd((unsigned long long *)&a.db.tel_bal[r.tl], (unsigned long long)r.delta);
+                atomicAdd((unsigned long long *)&a.db.br_bal[r.br], (unsigned long long)r.delta);
+                DcOut o;
+                o.slot = slot;
+                o.ts = r.ts;
+                o.delta = r.delta;
+                o.na = wrap_add(old, pre);
+                o.a = r.a;
+                o.tl = r.tl;
+                o.br = r.br;
+                o.t = r.t;
+                dc_finish(a.db, a.b, o);
+            }
+        }
+    next_chunk:
         __syncthreads();
     }
 }
@@ -849,6 +1069,7 @@ int exec_blocks_per_sm(int kind, int block)
     int nb = 1;
     if (kind == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kset_kernel, block, 0);
     else if (kind == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tpl_dc_kernel, block, 0);
+    else if (kind == 3) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tpl_dc_block_kernel, block, 0);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tpl_kernel, block, 0);
     return nb < 1 ? 1 : nb;
 }
@@ -1045,11 +1266,26 @@ cudaError_t launch_tpl(gputx_bulk *b, int block, bool atomic_add)
     int64_t grid = (int64_t)db->num_sms * exec_blocks_per_sm(dc ? 2 : 1, block);
     const int64_t chunks = (b->n + block - 1) / block;
     if (grid > chunks) grid = chunks;
-    if (dc)
+    a.when_hot = -1;
+    if (dc && block <= 256) {
+        // CTAs of up to 256 threads can group over the whole CTA: the ticket
+        // scan's flag picks that executor when a counter's chain is long
+        // enough to put several of its operations in one chunk, else the
+        // warp groups (both are launched; the one not picked returns at once)
+        a.when_hot = 1;
+        int64_t grid_b = (int64_t)db->num_sms * exec_blocks_per_sm(3, block);
+        if (grid_b > chunks) grid_b = chunks;
+        tpl_dc_block_kernel<<<(unsigned)grid_b, block, 0, b->stream>>>(a);
+        a.when_hot = 0;
         tpl_dc_kernel<<<(unsigned)grid, block, 0, b->stream>>>(a);
-    else
-        tpl_kernel<<<(unsigned)grid, block, 0, b->stream>>>(a);
-    count_launches(1);
+        count_launches(2);
+    } else {
+        if (dc)
+            tpl_dc_kernel<<<(unsigned)grid, block, 0, b->stream>>>(a);
+        else
+            tpl_kernel<<<(unsigned)grid, block, 0, b->stream>>>(a);
+        count_launches(1);
+    }
     return cudaGetLastError();
 }
 

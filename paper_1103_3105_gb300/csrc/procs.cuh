@@ -255,15 +255,24 @@ struct TxnView {
 
 // signature at position pos of the gathered execution-order records; the
 // loads are issued here, so building a view early hides their latency
+// (a debug build turns a position or index outside the bulk into a view of
+// type -1, which no procedure executes)
 __device__ __forceinline__ TxnView view_at(const DevBulk &b, uint32_t pos, int64_t hist_base)
 {
     TxnView v;
+    bool bad = !dbg_in(pos, b.n, b.err);
+    if (kDebug && bad) pos = 0;
     v.p = b.rec_params + (int64_t)pos * b.P;
     v.p0 = __ldg(&v.p[0]);
     v.p1 = b.P > 1 ? __ldg(&v.p[1]) : 0;
     v.ts = __ldg(&b.rec_ts[pos]);
     v.type = __ldg(&b.rec_type[pos]);
     v.t = __ldg(&b.rec_t[pos]);
+    if (kDebug && !dbg_in(v.t, b.n, b.err)) {
+        bad = true;
+        v.t = 0;
+    }
+    if (kDebug && bad) v.type = -1;
     v.hist_slot = hist_base + (b.slot_hist ? (int64_t)__ldg(&b.slot_hist[v.t]) : (int64_t)pos);
     return v;
 }
@@ -272,11 +281,13 @@ __device__ __forceinline__ TxnView view_at(const DevBulk &b, uint32_t pos, int64
 __device__ __forceinline__ TxnView view_of(const DevBulk &b, uint32_t t, int64_t hist_base)
 {
     TxnView v;
+    const bool bad = !dbg_in(t, b.n, b.err);
+    if (kDebug && bad) t = 0;
     v.p = b.params + (int64_t)t * b.P;
     v.p0 = __ldg(&v.p[0]);
     v.p1 = b.P > 1 ? __ldg(&v.p[1]) : 0;
     v.ts = __ldg(&b.ts[t]);
-    v.type = __ldg(&b.type[t]);
+    v.type = (kDebug && bad) ? -1 : __ldg(&b.type[t]);
     v.t = t;
     v.hist_slot = hist_base + (b.slot_hist ? (int64_t)__ldg(&b.slot_hist[t]) : (int64_t)t);
     return v;
@@ -380,6 +391,7 @@ __device__ __forceinline__ bool dc_state_core(const DevDB &db, const DevBulk &b,
                                               int64_t delta, int64_t ts, uint32_t t, int64_t slot, bool atomic_add,
                                               Cells &cells, DcOut &o)
 {
+    if (!dbg_dc_rows(db, b, a, tl, br, t)) return false;
     // every load before any store: the three rows are distinct cells but the
     // compiler cannot prove it, so interleaving would serialise three L2
     // round trips
@@ -466,6 +478,7 @@ __device__ __forceinline__ void exec_sub(const DevDB &db, const DevBulk &b, cons
     case GPUTX_T_SUB_GET_ACCESS: {
         int64_t r = hash_find(db.ai_idx, ai_key(s, p[1]));
         if (r < 0) { st = 1; break; }
+        if (!dbg_in(r, db.child_cap, b.err)) { st = 3; break; }
         const int4 v = __ldcg(reinterpret_cast<const int4 *>(db.ai_data + r * 4));
         out[0] = pack2(v.x, v.y);
         out[1] = pack2(v.z, v.w);
@@ -473,12 +486,14 @@ __device__ __forceinline__ void exec_sub(const DevDB &db, const DevBulk &b, cons
     }
     case GPUTX_T_SUB_GET_NEW_DEST: {
         int64_t r = hash_find(db.sf_idx, sf_key(s, p[1]));
+        if (r >= 0 && !dbg_in(r, db.child_cap, b.err)) { st = 3; break; }
         if (r < 0 || __ldcg(&db.sf_active[r]) != 1) { st = 1; break; }
         int cnt = 0;
         for (int k = 0; k < 3; k++) {
             const int64_t stt = 8 * k;
             if (stt > p[2]) continue;
             int64_t c = hash_find(db.cf_idx, cf_key(s, p[1], stt));
+            if (c >= 0 && !dbg_in(c, db.child_cap, b.err)) c = -1;
             if (c >= 0 && __ldcg(&db.cf_end[c]) > p[3]) out[1 + cnt++] = __ldcg(&db.cf_numberx[c]);
         }
         out[0] = cnt;
@@ -492,6 +507,7 @@ __device__ __forceinline__ void exec_sub(const DevDB &db, const DevBulk &b, cons
     case GPUTX_T_SUB_UPDATE_FACILITY: {
         int64_t r = hash_find(db.sf_idx, sf_key(s, p[1]));
         if (r < 0) { st = 1; break; }                  // read phase: abort
+        if (!dbg_in(r, db.child_cap, b.err)) { st = 3; break; }
         stg_cg(&row[0], (int32_t)p[2]);
         stg_cg(&db.sf_data_a[r], (int32_t)p[3]);
         break;
@@ -515,6 +531,7 @@ __device__ __forceinline__ void exec_sub(const DevDB &db, const DevBulk &b, cons
         const unsigned long long key = cf_key(s, p[1], p[2]);
         int64_t r = hash_find(db.cf_idx, key);
         if (r < 0) { st = 1; break; }
+        if (!dbg_in(r, db.child_cap, b.err)) { st = 3; break; }
         hash_erase(db.cf_idx, key);
         stg_cg(&db.cf_live[r], (uint8_t)0);
         break;
@@ -641,8 +658,10 @@ __device__ __forceinline__ void exec_oe(const DevDB &db, const DevBulk &b, const
         if (o == 0) { st = 1; break; }
         const int64_t r = hash_find(db.ord_idx, ord_key(d, o));
         if (r < 0) { set_err(b.err, ERR_BOUNDS); st = 1; break; }
+        if (!dbg_in(r, db.ord_cap, b.err)) { st = 1; break; }
         const int cnt = ldg_cg(&db.o_cnt[r]);
         const int64_t first = ldg_cg(&db.o_first[r]);
+        if (kDebug && (cnt < 0 || !dbg_in(first, db.ol_cap - cnt + 1, b.err))) { st = 1; break; }
         int64_t sum = 0;
         for (int j = 0; j < cnt; j++) sum += ldg_cg(&db.ol_amount[first + j]);
         out[2] = cnt;
@@ -712,6 +731,10 @@ template <class Cells>
 __device__ __forceinline__ void exec_new_order_group(const DevDB &db, const DevBulk &b, const TxnView &v, uint32_t gl,
                                                      Cells &cells)
 {
+    if (kDebug && (v.type != GPUTX_T_OE_NEW_ORDER || !valid_txn(db, v.type, v.p, b.P))) {
+        if (gl == 0) set_err(b.err, ERR_BOUNDS);   // the group's lanes all leave here
+        return;
+    }
     const uint32_t gm = group_mask();
     const int64_t *p = v.p;
     const uint32_t t = v.t;
@@ -815,6 +838,10 @@ template <class Cells>
 __device__ __forceinline__ void exec_order_status_group(const DevDB &db, const DevBulk &b, const TxnView &v,
                                                         uint32_t gl, Cells &cells)
 {
+    if (kDebug && (v.type != GPUTX_T_OE_ORDER_STATUS || !valid_txn(db, v.type, v.p, b.P))) {
+        if (gl == 0) set_err(b.err, ERR_BOUNDS);   // the group's lanes all leave here
+        return;
+    }
     const uint32_t gm = group_mask();
     const int64_t *p = v.p;
     const uint32_t t = v.t;
@@ -841,9 +868,11 @@ __device__ __forceinline__ void exec_order_status_group(const DevDB &db, const D
         }
         return;
     }
-    const int64_t r = (int64_t)__ldcg(&db.ord_idx.rows[slot]);
-    const int cnt = ldg_cg(&db.o_cnt[r]);
+    int64_t r = (int64_t)__ldcg(&db.ord_idx.rows[slot]);
+    if (kDebug && !dbg_in(r, db.ord_cap, b.err)) r = 0;
+    int cnt = ldg_cg(&db.o_cnt[r]);
     const int64_t first = ldg_cg(&db.o_first[r]);
+    if (kDebug && (cnt < 0 || cnt > kGroup || !dbg_in(first, db.ol_cap - cnt + 1, b.err))) cnt = 0;
     const int64_t amt = (int)gl < cnt ? ldg_cg(&db.ol_amount[first + gl]) : 0;
     const int64_t sum = group_sum16(gm, amt);
     if (gl == 0) {
@@ -856,6 +885,7 @@ __device__ __forceinline__ void exec_order_status_group(const DevDB &db, const D
 // L2 prefetch of the rows lane gl of a group will touch
 __device__ __forceinline__ void prefetch_group(const DevDB &db, const TxnView &v, uint32_t gl)
 {
+    if (kDebug && v.type < 0) return;
     const int64_t *p = v.p;
     if (v.type == GPUTX_T_OE_NEW_ORDER) {
         if (gl == 0) prefetch_l2(&db.d_next_o_id[v.p0 * OE_DIST + v.p1]);
@@ -879,6 +909,12 @@ template <class Cells>
 __device__ __forceinline__ void exec_txn(const DevDB &db, const DevBulk &b, const TxnView &v, bool atomic_add,
                                          Cells &cells)
 {
+    // a debug build re-validates the signature it was handed (the rows its
+    // parameters name) before any access
+    if (kDebug && v.type >= 0 && !valid_txn(db, v.type, v.p, b.P)) {
+        set_err(b.err, ERR_BOUNDS);
+        return;
+    }
     switch (v.type) {
     case GPUTX_T_DC_DEBIT_CREDIT: exec_dc(db, b, v, atomic_add, cells); break;
     case GPUTX_T_SUB_GET_SUBSCRIBER:

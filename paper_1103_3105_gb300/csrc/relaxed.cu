@@ -68,10 +68,10 @@ __device__ __forceinline__ uint32_t spin_lock(uint32_t *l, uint64_t limit_ns)
     uint32_t v = peek(l);
     if (!(v & 1u) && try_lock(l, v)) return v + 1;
     uint64_t t0 = globaltimer();
-    uint32_t ns = 64;
+    uint32_t ns = 32;
     while (true) {
         __nanosleep(ns);
-        if (ns < 4096) ns <<= 1;
+        if (ns < 128) ns <<= 1;
         const uint32_t w = peek(l);
         if (w != v) {            // handed on since the last look: progress
             v = w;
@@ -115,6 +115,13 @@ __global__ void tpl_relaxed_kernel(TplRelaxedArgs a)
                 }
                 items[q] = obj[j];
             }
+            if (kDebug)
+                for (int j = 0; j < m; j++)
+                    if (!dbg_in(items[j], a.db.n_objects, a.b.err)) {
+                        m = 0;          // no lock taken and nothing executed
+                        v.type = -1;
+                        break;
+                    }
         }
         // Warp combining: lanes whose only lock is the same item form a group
         // (__match_any_sync).  Its lowest lane takes the lock once and the

@@ -95,3 +95,13 @@ def test_probe_rejects_bad_shapes_without_a_gpu():
         with pytest.raises(G.GputxError) as e:
             G.gputx_probe_atomics(*args)
         assert e.value.status == G.EINVAL
+
+
+def test_debug_build_exports_every_declared_symbol():
+    """The bounds-checked build (-DGPUTX_DEBUG) compiles from the same sources
+    into its own library with the same entry points."""
+    path = _build.build(debug=True)
+    assert path.endswith("libgputx_debug.so") and path != _build.LIB
+    lib = ctypes.CDLL(path)
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, missing

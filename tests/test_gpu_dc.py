@@ -255,6 +255,30 @@ def test_hot_accounts_at_sweep_sizes(lg, strategy, mode):
     g.close()
 
 
+@pytest.mark.parametrize("hot_ops", [64, 65])
+@pytest.mark.parametrize("mode", MODES)
+def test_tpl_executor_pick_at_the_hot_chain(hot_ops, mode):
+    """Debit-credit TPL runs one of two executors: lock groups over a warp, or
+    over the whole CTA once some counter's chain reaches n/1024 operations (64
+    of 2^16).  One account here takes 64 operations (warp groups) or 65 (CTA
+    groups), spread over the bulk with a cluster of them in one chunk; the
+    other accounts are few enough that lanes of a warp share them too.  Both
+    executors must give the serial result."""
+    n = 1 << 16
+    g, o = make_pair(4, 40, 4000, n, max_bulk=n)
+    bulk = W.dc_bulk(n, 4000, 0.0, seed=W.seed_for(1, hot_ops))
+    rng = np.random.default_rng(hot_ops)
+    hot = 1234
+    acct = bulk["params"][:, 0]
+    acct[acct == hot] = hot + 1
+    idx = np.concatenate([np.arange(1000, 1020), rng.choice(np.arange(2000, n), hot_ops - 20, replace=False)])
+    acct[idx] = hot
+    assert int((acct == hot).sum()) == hot_ops
+    stats, st, out, ost, oout = run_both(g, o, bulk, "tpl", mode)
+    assert_same(g, o, st, out, ost, oout)
+    g.close()
+
+
 @pytest.mark.parametrize("strategy,mode", [("kset", 0), ("kset", 1), ("tpl", 0), ("part", 0), ("scan", 0)])
 def test_back_to_back_bulks_without_sync(strategy, mode):
     """Bulks executed one after another without waiting: each bulk's analysis
