@@ -27,6 +27,7 @@ struct BulkCtl {
     uint32_t runs;         // refinement: runs of the sorted operations
     uint32_t n_seg;        // segmented graph bulks: bulks in this segment (0 = one)
     uint32_t hot;          // TPL: some counter has a chain of at least the hot ticket
+    uint32_t chunk;        // relaxed TPL: next chunk to claim (claim counts commit tickets)
 };
 
 constexpr int kSegMax = 64;        // bulks in one segment of a graph bulk, at most

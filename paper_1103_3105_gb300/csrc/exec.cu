@@ -30,6 +30,7 @@
 #include "engine.h"
 #include "levels.cuh"
 #include "procs.cuh"
+#include "cta_groups.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -798,40 +799,17 @@ __global__ void tpl_dc_kernel(TplArgs a)
 }
 
 // TPL for debit-credit-only bulks with the lock groups formed over the whole
-// CTA (up to 256 consecutive transactions) instead of one warp.  The CTA's
-// transactions that need the same counter form one group (a shared-memory
-// hash of the counter slots, a lane mask per group): their tickets are
-// consecutive, since the chunk holds consecutive timestamps, so the group
-// runs as soon as its first lane's ticket is granted.  That lane waits on the
-// counter and publishes the grant in shared memory; within the group, lanes
-// on the same account combine their deltas (one fetch-and-add of the sum by
-// the account's first lane, each lane's new balance = the old value plus the
-// inclusive prefix of the deltas in timestamp order); once every member has
-// its balance, the first lane releases the counter by the group's size.  On a
-// hot item a whole chunk's operations cost one hand-off through L2.  Every
-// wait in shared memory is bounded like the counter waits.
-constexpr int kBlkTab = 512;          // hash slots for the chunk's counters (2 x the chunk)
-constexpr uint32_t kBlkEmpty = 0xffffffffu;
-
-__device__ __forceinline__ bool wait_smem(volatile uint32_t *f, uint64_t limit_ns)
-{
-    if (*f) return true;
-    const uint64_t t0 = globaltimer();
-    uint32_t spins = 0;
-    while (!*f) {
-        if (++spins > 32) __nanosleep(64);
-        if (globaltimer() - t0 > limit_ns) return false;
-    }
-    return true;
-}
-
-__global__ void __launch_bounds__(256) tpl_dc_block_kernel(TplArgs a)
+// CTA (up to 256 consecutive transactions) instead of one warp
+// (cta_groups.cuh).  The chunk holds consecutive timestamps, so a group's
+// tickets are consecutive and the group runs as soon as its first member's
+// ticket is granted: that member waits on the counter and publishes the grant
+// in shared memory; once every member has its account balance it releases
+// the counter by the group's size.  On a hot item a whole chunk's operations
+// cost one hand-off through L2.
+__global__ void __launch_bounds__(kCtaMax) tpl_dc_block_kernel(TplArgs a)
 {
     __shared__ uint32_t s_c, s_stop;
-    __shared__ uint32_t h_key[kBlkTab], h_state[kBlkTab], h_fin[kBlkTab];
-    __shared__ uint32_t h_mask[kBlkTab][8];
-    __shared__ int64_t s_delta[256], s_old[256];
-    __shared__ uint32_t s_acct[256], s_aflag[256];
+    __shared__ CtaGroupTables g;
     if (tpl_skip(a)) return;
     const int64_t n = a.b.n;
     const int64_t hb = a.ctl->base.hist;
@@ -841,21 +819,15 @@ __global__ void __launch_bounds__(256) tpl_dc_block_kernel(TplArgs a)
             s_stop = *(volatile uint32_t *)&a.ctl->err ? 1u : 0u;
             s_c = atomicAdd(&a.ctl->claim, 1u);
         }
-        for (uint32_t i = tid; i < (uint32_t)kBlkTab; i += blockDim.x) {
-            h_key[i] = kBlkEmpty;
-            h_state[i] = 0;
-            h_fin[i] = 0;
-#pragma unroll
-            for (int w = 0; w < 8; w++) h_mask[i][w] = 0;
-        }
+        cta_groups_reset(g, tid, blockDim.x);
         __syncthreads();
         const int64_t start = (int64_t)s_c * blockDim.x;
         if (s_stop || start >= n) break;
         const int64_t t = start + tid;
         const bool live = t < n;
         DcRecord r{};
-        uint32_t key = 0, tk = 0, e = 0;
         bool rows_ok = true;   // a debug build's check of the record's rows
+        uint32_t key = 0, tk = 0, e = 0;
         if (live) {
             r.a = (uint32_t)__ldg(&a.b.params[t * a.b.P]);
             r.delta = __ldg(&a.b.params[t * a.b.P + 1]);
@@ -867,36 +839,18 @@ __global__ void __launch_bounds__(256) tpl_dc_block_kernel(TplArgs a)
             if (rows_ok) prefetch_l2(&a.db.acc_bal[r.a]);
             key = a.slot(a.lock_key[t]);
             tk = a.lock_ticket[t];
-            // the counter's slot in the chunk's table (linear probing)
-            e = (key * 2654435761u) & (kBlkTab - 1);
-            while (true) {
-                const uint32_t prev = atomicCAS(&h_key[e], kBlkEmpty, key);
-                if (prev == kBlkEmpty || prev == key) break;
-                e = (e + 1) & (kBlkTab - 1);
-            }
-            atomicOr(&h_mask[e][tid >> 5], 1u << (tid & 31));
+            e = cta_group_join(g, key, tid);
         }
         const int64_t slot = hb + t;
         const bool run = live && rows_ok && slot < a.db.hist_cap;
-        s_delta[tid] = run ? r.delta : 0;
-        s_acct[tid] = r.a;
-        s_aflag[tid] = 0;
+        g.delta[tid] = run ? r.delta : 0;
+        g.acct[tid] = r.a;
+        g.aflag[tid] = 0;
         __syncthreads();
         if (live) {
-            uint32_t m[8];
-#pragma unroll
-            for (int w = 0; w < 8; w++) m[w] = h_mask[e][w];
-            uint32_t leader = 0, size = 0;
-            bool found = false;
-#pragma unroll
-            for (int w = 0; w < 8; w++) {
-                if (!found && m[w]) {
-                    leader = 32u * w + (uint32_t)(__ffs(m[w]) - 1);
-                    found = true;
-                }
-                size += __popc(m[w]);
-            }
-            if (size == 1) {
+            CtaMember c;
+            cta_member(g, e, tid, r.a, c);
+            if (c.size == 1) {
                 // the only transaction of the chunk on its counter: it waits
                 // on its own and runs as soon as it is granted
                 const bool ok1 = !tk || wait_at_least(&a.done[key], tk, a.spin_limit_ns, 500);
@@ -907,23 +861,9 @@ __global__ void __launch_bounds__(256) tpl_dc_block_kernel(TplArgs a)
                 if (pend) dc_finish_rmw(a.db, a.b, o);
                 goto next_chunk;
             }
-            // the lanes of the group on this lane's account: the first of
-            // them, the inclusive prefix of their deltas and their sum
-            uint32_t afirst = tid;
-            int64_t pre = 0, tot = 0;
-            for (int w = 0; w < 8; w++) {
-                for (uint32_t bits = m[w]; bits; bits &= bits - 1) {
-                    const uint32_t j = 32u * w + (uint32_t)(__ffs(bits) - 1);
-                    if (s_acct[j] != r.a) continue;
-                    const int64_t d = s_delta[j];
-                    tot = wrap_add(tot, d);
-                    if (j <= tid) pre = wrap_add(pre, d);
-                    if (j < afirst) afirst = j;
-                }
-            }
-            volatile uint32_t *state = &h_state[e];
+            volatile uint32_t *state = &g.state[e];
             bool ok = true;
-            if (tid == leader) {
+            if (tid == c.leader) {
                 ok = !tk || wait_at_least(&a.done[key], tk, a.spin_limit_ns, 500);
                 if (!ok) set_err(&a.ctl->err, ERR_TIMEOUT);
                 __threadfence_block();
@@ -932,43 +872,21 @@ __global__ void __launch_bounds__(256) tpl_dc_block_kernel(TplArgs a)
                 ok = false;
                 if (*state == 0u) set_err(&a.ctl->err, ERR_TIMEOUT);
             }
-            if (ok && tid == leader) ok = *state == 1u;
-            __threadfence_block();   // the leader's acquire before this lane's accesses
-            if (ok && !run && live && rows_ok) {   // history full: not executed
+            __threadfence_block();   // the leader's acquire before this member's accesses
+            if (ok && !run && rows_ok) {           // history full: not executed
                 set_err(a.b.err, ERR_CAPACITY);
                 a.b.status[r.t] = 3;
             }
             int64_t old = 0;
-            bool have = false;
-            if (ok && run) {
-                if (afirst == tid) {
-                    old = (int64_t)atomicAdd((unsigned long long *)&a.db.acc_bal[r.a], (unsigned long long)tot);
-                    s_old[tid] = old;
-                    __threadfence_block();
-                    *(volatile uint32_t *)&s_aflag[tid] = 1u;
-                    have = true;
-                } else if (wait_smem(&s_aflag[afirst], a.spin_limit_ns)) {
-                    old = *(volatile int64_t *)&s_old[afirst];
-                    have = true;
-                } else {
-                    set_err(&a.ctl->err, ERR_TIMEOUT);
-                }
-            }
+            const bool have = ok && run &&
+                              cta_account_update(g, c, tid, &a.db.acc_bal[r.a], a.spin_limit_ns, &a.ctl->err, old);
             // every member counted once its account update is done (or it gave up)
             __threadfence_block();
-            atomicAdd(&h_fin[e], 1u);
-            if (tid == leader) {
+            atomicAdd(&g.fin[e], 1u);
+            if (tid == c.leader) {
                 // the group's updates precede its one release
-                volatile uint32_t *fin = &h_fin[e];
-                const uint64_t t0 = globaltimer();
-                while (*fin < size) {
-                    __nanosleep(32);
-                    if (globaltimer() - t0 > a.spin_limit_ns) {
-                        set_err(&a.ctl->err, ERR_TIMEOUT);
-                        break;
-                    }
-                }
-                red_release_add(&a.done[key], size);
+                if (!cta_wait_members(g, e, c.size, a.spin_limit_ns)) set_err(&a.ctl->err, ERR_TIMEOUT);
+                red_release_add(&a.done[key], c.size);
             }
             if (have) {
                 atomicAdd((unsigned long long *)&a.db.tel_bal[r.tl], (unsigned long long)r.delta);
@@ -977,7 +895,7 @@ __global__ void __launch_bounds__(256) tpl_dc_block_kernel(TplArgs a)
                 o.slot = slot;
                 o.ts = r.ts;
                 o.delta = r.delta;
-                o.na = wrap_add(old, pre);
+                o.na = wrap_add(old, c.pre);
                 o.a = r.a;
                 o.tl = r.tl;
                 o.br = r.br;
@@ -1267,7 +1185,7 @@ cudaError_t launch_tpl(gputx_bulk *b, int block, bool atomic_add)
     const int64_t chunks = (b->n + block - 1) / block;
     if (grid > chunks) grid = chunks;
     a.when_hot = -1;
-    if (dc && block <= 256) {
+    if (dc && block <= kCtaMax) {
         // CTAs of up to 256 threads can group over the whole CTA: the ticket
         // scan's flag picks that executor when a counter's chain is long
         // enough to put several of its operations in one chunk, else the

@@ -7,6 +7,7 @@
 // reuses the PART executors.
 #include "engine.h"
 #include "procs.cuh"
+#include "cta_groups.cuh"
 
 namespace gtx {
 
@@ -171,6 +172,113 @@ __global__ void tpl_relaxed_kernel(TplRelaxedArgs a)
     }
 }
 
+// Relaxed TPL for debit-credit-only bulks, with the lock taken once per
+// CTA-wide group (cta_groups.cuh).  A CTA claims 256 consecutive
+// transactions; those that need the same lock (the branch under R/W, the
+// account under ADD) form a group.  Its first member takes the spin lock and
+// draws the group's commit tickets in one addition; the members get them in
+// thread order and run in that order inside the one critical section (the
+// account updates combined, one fetch-and-add per distinct account); the
+// first member unlocks once every member has its balance.  Serial execution
+// in ticket order gives these results.  Teller and branch additions, history
+// rows and outputs follow the unlock: no transaction of the bulk reads them
+// and integer additions commute.  A hot lock is then taken once per chunk
+// instead of once per warp, and far fewer threads spin on it.
+__global__ void __launch_bounds__(kCtaMax) tpl_relaxed_dc_block_kernel(TplRelaxedArgs a)
+{
+    __shared__ uint32_t s_c, s_stop;
+    __shared__ CtaGroupTables g;
+    if (*(volatile uint32_t *)&a.ctl->err) return;   // validation failed: uniform, set before this launch
+    const int64_t n = a.b.n;
+    const int64_t hb = a.ctl->base.hist;
+    const uint32_t tid = threadIdx.x;
+    const bool by_account = a.mode == GPUTX_CONFLICT_ADD;
+    while (true) {
+        if (tid == 0) {
+            s_stop = *(volatile uint32_t *)&a.ctl->err ? 1u : 0u;
+            s_c = atomicAdd(&a.ctl->chunk, 1u);
+        }
+        cta_groups_reset(g, tid, blockDim.x);
+        __syncthreads();
+        const int64_t start = (int64_t)s_c * blockDim.x;
+        if (s_stop || start >= n) break;
+        const int64_t t = start + tid;
+        const bool live = t < n;
+        DcRecord r{};
+        bool rows_ok = true;   // a debug build's check of the record's rows
+        uint32_t item = 0, e = 0;
+        if (live) {
+            r.a = (uint32_t)__ldg(&a.b.params[t * a.b.P]);
+            r.delta = __ldg(&a.b.params[t * a.b.P + 1]);
+            r.ts = __ldg(&a.b.ts[t]);
+            r.t = (uint32_t)t;
+            r.tl = a.db.div_tel.div(r.a);
+            r.br = a.db.div_br.div(r.a);
+            rows_ok = dbg_dc_rows(a.db, a.b, r.a, r.tl, r.br, r.t);
+            if (rows_ok) prefetch_l2(&a.db.acc_bal[r.a]);
+            // the transaction's one lock, as its access set names it
+            item = by_account ? a.db.o_acc + r.a : a.db.o_br + r.br;
+            e = cta_group_join(g, item, tid);
+        }
+        const int64_t slot = hb + t;
+        const bool run = live && rows_ok && slot < a.db.hist_cap;
+        g.delta[tid] = run ? r.delta : 0;
+        g.acct[tid] = r.a;
+        g.aflag[tid] = 0;
+        __syncthreads();
+        if (live) {
+            CtaMember c;
+            cta_member(g, e, tid, r.a, c);
+            uint32_t *lock = &a.lock[a.slot(item)];
+            volatile uint32_t *state = &g.state[e];
+            bool ok = true;
+            uint32_t held = 0;
+            if (tid == c.leader) {
+                held = spin_lock(lock, a.spin_limit_ns);
+                ok = held != 0;
+                if (ok) g.base[e] = atomicAdd(&a.ctl->claim, c.size);
+                else set_err(&a.ctl->err, ERR_TIMEOUT);
+                __threadfence_block();
+                *state = ok ? 1u : 2u;
+            } else if (!wait_smem(state, a.spin_limit_ns) || *state != 1u) {
+                ok = false;
+                if (*state == 0u) set_err(&a.ctl->err, ERR_TIMEOUT);
+            }
+            __threadfence_block();   // the leader's acquire before this member's accesses
+            if (ok && !run && rows_ok) {           // history full: not executed
+                set_err(a.b.err, ERR_CAPACITY);
+                a.b.status[r.t] = 3;
+            }
+            int64_t old = 0;
+            const bool have = ok && run &&
+                              cta_account_update(g, c, tid, &a.db.acc_bal[r.a], a.spin_limit_ns, &a.ctl->err, old);
+            if (ok) a.order[g.base[e] + c.rank] = r.t;
+            __threadfence_block();
+            atomicAdd(&g.fin[e], 1u);
+            if (tid == c.leader && held) {
+                // every member's account update precedes the unlock
+                if (!cta_wait_members(g, e, c.size, a.spin_limit_ns)) set_err(&a.ctl->err, ERR_TIMEOUT);
+                unlock(lock, held);
+            }
+            if (have) {
+                atomicAdd((unsigned long long *)&a.db.tel_bal[r.tl], (unsigned long long)r.delta);
+                atomicAdd((unsigned long long *)&a.db.br_bal[r.br], (unsigned long long)r.delta);
+                DcOut o;
+                o.slot = slot;
+                o.ts = r.ts;
+                o.delta = r.delta;
+                o.na = wrap_add(old, c.pre);
+                o.a = r.a;
+                o.tl = r.tl;
+                o.br = r.br;
+                o.t = r.t;
+                dc_finish(a.db, a.b, o);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_tpl_relaxed(gputx_bulk *b, uint32_t *order, bool atomic_add)
@@ -189,9 +297,24 @@ cudaError_t launch_tpl_relaxed(gputx_bulk *b, uint32_t *order, bool atomic_add)
     a.atomic_add = atomic_add;
     cudaError_t e = cudaMemsetAsync(&b->ctl->claim, 0, sizeof(uint32_t), b->stream);
     if (e) return e;
-    int64_t grid = (b->n + 255) / 256;
-    if (grid > (int64_t)db->num_sms * 8) grid = (int64_t)db->num_sms * 8;
-    tpl_relaxed_kernel<<<(unsigned)grid, 256, 0, b->stream>>>(a);
+    // debit-credit-only bulks of single-lock transactions: CTA-wide lock groups
+    const bool dc = db->dev.registered == (1u << GPUTX_T_DC_DEBIT_CREDIT) && !b->graph && db->uniform_k == 1;
+    if (dc) {
+        if ((e = cudaMemsetAsync(&b->ctl->chunk, 0, sizeof(uint32_t), b->stream))) return e;
+        static int per_sm = 0;
+        if (!per_sm) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tpl_relaxed_dc_block_kernel, kCtaMax, 0);
+            if (per_sm < 1) per_sm = 1;
+        }
+        int64_t grid = (int64_t)db->num_sms * per_sm;
+        const int64_t chunks = (b->n + kCtaMax - 1) / kCtaMax;
+        if (grid > chunks) grid = chunks;
+        tpl_relaxed_dc_block_kernel<<<(unsigned)grid, kCtaMax, 0, b->stream>>>(a);
+    } else {
+        int64_t grid = (b->n + 255) / 256;
+        if (grid > (int64_t)db->num_sms * 8) grid = (int64_t)db->num_sms * 8;
+        tpl_relaxed_kernel<<<(unsigned)grid, 256, 0, b->stream>>>(a);
+    }
     count_launches(1);
     e = cudaGetLastError();
     if (e) return e;
