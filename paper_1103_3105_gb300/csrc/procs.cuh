@@ -190,6 +190,12 @@ __device__ __forceinline__ int64_t hash_find(const HashIndex &h, unsigned long l
 // Reuses the first tombstone on the probe path.  Returns false when full.
 __device__ __forceinline__ bool hash_insert(const HashIndex &h, unsigned long long key, uint32_t row)
 {
+    // an empty home slot is the one the probe below would pick: one round trip
+    const uint64_t home = hmix(key) & h.mask;
+    if (atomicCAS(&h.keys[home], HKEY_EMPTY, key) == HKEY_EMPTY) {
+        __stcg(&h.rows[home], row);
+        return true;
+    }
     for (int attempt = 0; attempt < 64; attempt++) {
         uint64_t i = hmix(key) & h.mask;
         int64_t tomb = -1;
@@ -750,22 +756,12 @@ __device__ __forceinline__ void exec_new_order_group(const DevDB &db, const DevB
         sw = (line >> 24) & 0xFFFF;
         qty = (line >> 40) & 0xFF;
     }
-    // read phase: an unknown item aborts the order (status 1, no writes)
-    if (__any_sync(gm, mine && item >= db.n_items)) {
-        if (gl == 0) b.status[t] = 1;
-        return;
-    }
-    const int64_t oslot = b.base->ord + b.slot_ord[t];
-    const int64_t lslot = b.base->ol + b.slot_ol[t];
-    if (oslot >= db.ord_cap || lslot + cnt > db.ol_cap) {
-        if (gl == 0) {
-            set_err(b.err, ERR_CAPACITY);
-            b.status[t] = 3;
-        }
-        return;
-    }
-    // every read in one round trip: the district's counter and the rates on
-    // lane 0, each line's item and stock row on its lane
+    // every read in one round trip, issued before the checks below so that
+    // the insert slots' loads overlap them: the district's counter and the
+    // rates on lane 0, each line's item and stock row on its lane (a line
+    // with an unknown item reads nothing)
+    const int64_t ob = b.base->ord, lb = b.base->ol;
+    const int64_t os = b.slot_ord[t], ls = b.slot_ol[t];
     int64_t o_id = 0, disc = 0, w_tax = 0, d_tax = 0, price = 0, sy = 0;
     int32_t q = 0, so = 0;
     if (gl == 0) {
@@ -774,12 +770,26 @@ __device__ __forceinline__ void exec_new_order_group(const DevDB &db, const DevB
         w_tax = __ldg(&db.w_tax[w]);
         d_tax = __ldg(&db.d_tax[d]);
     }
-    if (mine) {
+    if (mine && item < db.n_items) {
         s = sw * db.n_items + item;
         price = __ldg(&db.i_price[item]);
         q = ldg_cg(&db.s_quantity[s]);
         sy = cells.ld(&db.s_ytd[s]);
         so = ldg_cg(&db.s_order_cnt[s]);
+    }
+    // read phase: an unknown item aborts the order (status 1, no writes)
+    if (__any_sync(gm, mine && item >= db.n_items)) {
+        if (gl == 0) b.status[t] = 1;
+        return;
+    }
+    const int64_t oslot = ob + os;
+    const int64_t lslot = lb + ls;
+    if (oslot >= db.ord_cap || lslot + cnt > db.ol_cap) {
+        if (gl == 0) {
+            set_err(b.err, ERR_CAPACITY);
+            b.status[t] = 3;
+        }
+        return;
     }
     int64_t amount = 0;
     if (mine) {
@@ -799,6 +809,19 @@ __device__ __forceinline__ void exec_new_order_group(const DevDB &db, const DevB
     // by compare-and-swap (other orders' inserts may race for it)
     const unsigned long long key = ord_key(d, o_id);
     bool inserted = false;
+    {
+        // an empty home slot is the slot the probe would find first: taken
+        // at once, one round trip instead of two (the common case at a load
+        // factor of at most one half)
+        const uint64_t home = hmix(key) & db.ord_idx.mask;
+        unsigned long long prev = 0;
+        if (gl == 0) prev = atomicCAS(&db.ord_idx.keys[home], HKEY_EMPTY, key);
+        prev = __shfl_sync(gm, prev, 0, kGroup);
+        if (prev == HKEY_EMPTY) {
+            if (gl == 0) __stcg(&db.ord_idx.rows[home], (uint32_t)oslot);
+            inserted = true;
+        }
+    }
     for (int attempt = 0; attempt < 64 && !inserted; attempt++) {
         unsigned long long cur = 0;
         const int64_t slot = group_probe(gm, gl, db.ord_idx, key, 2, &cur);
