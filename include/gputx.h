@@ -55,7 +55,7 @@ typedef enum {
     GPUTX_AUTO = 3,       /* Algorithm 1 over the measured d, w0, c.  The
                            * decision reads the one-pass ranks of Section 4.2
                            * (w0 and c exact there, d a lower bound); the
-                           * refinement rounds of exact depth run only when
+                           * exact-depth pass runs only when
                            * K-SET is chosen, so the reported depth of a PART
                            * or TPL pick is the one-pass depth.  On a database
                            * whose only registered type is debit-credit, AUTO
@@ -170,7 +170,8 @@ typedef struct {
     int64_t depth;            /* d: depth of the T-dependency graph */
     int64_t w0;               /* size of the 0-set */
     int64_t cross;            /* c: cross-partition transactions */
-    int64_t fixpoint_rounds;  /* refinement rounds after the one-pass ranks */
+    int64_t fixpoint_rounds;  /* exact-depth passes after the one-pass ranks
+                               * (1 when they ran, 0 when skipped) */
     float ms_h2d, ms_analysis, ms_sort, ms_execute, ms_d2h, ms_total;
 } gputx_exec_stats;
 
@@ -357,7 +358,7 @@ gputx_status gputx_execute_kset_noalloc(gputx_db *db, const int64_t *ts, const i
 /* A stream of transactions (uneven sizes, mixed types) runs as consecutive
  * bulks of one size.  For each (bulk size, strategy, block shape) a
  * fixed-capacity bulk's whole pipeline -- extraction, grouping sort, ranks,
- * refinement rounds on the device, regrouping and one persistent K-SET launch
+ * the exact-depth pass on the device, regrouping and one persistent K-SET launch
  * (or the TPL kernel) -- is captured once in a CUDA graph and replayed for
  * every bulk of that shape, shorter bulks padded with inactive transactions.
  * With tune = 1 the stream's own first bulks run under different

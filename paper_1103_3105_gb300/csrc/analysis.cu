@@ -215,208 +215,120 @@ struct TicketMode {
     }
 };
 
-// All refinement rounds in one cooperative launch (no host round trips).
+// Exact depths by dataflow (one pass, no rounds).
 //
-// A round of plain Jacobi relaxation moves a depth one run along a group per
-// round, so a group of many runs needs that many rounds.  Each round here
-// instead carries depths along whole groups at once.  An operation of run j
-// needs depth at least max over earlier runs r of the same group of
-// (runmax(r) + j - r), which is j + (exclusive segmented max of
-// runmax(r) - r).  One segmented max-scan over the runs gives that bound
-// for every run.  The bound is implied by the chain of run-to-run
-// constraints, so the fixpoint is the same longest-path depth; only the number
-// of rounds drops, to about the number of group changes along the longest
-// path.  Grid barriers separate: clearing run maxima, gathering them, the
-// scan's block, grid and apply steps, and relaxing.  Round r reports growth in
-// changed_r[r % 3]; the flag of round r+1 is cleared during round r, after
-// every thread has read it two rounds ago.
-struct SegMax {
-    uint32_t f;   // a group starts within the span
-    int32_t v;    // max of runmax(r) - r since the last start
-};
-__device__ __forceinline__ SegMax segmax_combine(const SegMax &a, const SegMax &b)
+// Within a group (one item, operations in timestamp order) the runs follow
+// one another: every operation of run q conflicts with every operation of run
+// q-1, and transitively with all earlier runs.  So a transaction's depth is
+// the largest, over its operations outside their group's first run, of one
+// more than the deepest transaction of the run before -- the longest path of
+// the conflict graph, the depth the Jacobi refinement converges to.  Here each
+// transaction computes it once the runs before its operations are complete:
+// run q keeps the number of its operations still to finish (left) and the
+// largest depth among the finished ones (runmax); a transaction polls the
+// left counts of all its preceding runs at once, then reads their maxima,
+// publishes its depth into the maxima of its own runs and counts itself off
+// with a release.  Transactions run in timestamp order, a CTA's chunk of
+// consecutive ones at a time, so every run a transaction waits for belongs to
+// earlier transactions already running: the chain of waits always ends.
+
+// per operation: its run id into the transaction's slot, its run counted
+__global__ void depth_prep_kernel(const uint32_t *sv, const uint32_t *rid, int64_t m, const uint32_t *op_off,
+                                  int kslots, uint32_t *txn_rid, uint32_t *left, const BulkCtl *ctl)
 {
-    return SegMax{a.f | b.f, b.f ? b.v : (a.v > b.v ? a.v : b.v)};
-}
-__device__ __forceinline__ unsigned long long segmax_pack(const SegMax &x)
-{
-    return ((unsigned long long)x.f << 32) | (uint32_t)x.v;
-}
-__device__ __forceinline__ SegMax segmax_unpack(unsigned long long p)
-{
-    return SegMax{(uint32_t)(p >> 32), (int32_t)(uint32_t)p};
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m || ctl->err) return;
+    const uint32_t v = sv[i];
+    if (v == OP_SENTINEL) return;
+    const uint32_t rr = rid[i];
+    const uint32_t txn = v >> 7, j = (v >> 2) & 31u;
+    const int64_t slot = (op_off ? (int64_t)op_off[txn] : (int64_t)txn * kslots) + j;
+    txn_rid[slot] = rr;
+    atomicAdd(&left[rr & 0x7fffffffu], 1u);
 }
 
-constexpr int kFixBatch = 8;   // operations a thread handles per step of the per-operation loops
+constexpr uint32_t kNoRun = 0xffffffffu;   // an operation slot with no operation
+constexpr uint32_t kFlowSleepMax = 2048;    // longest back-off between polls, ns
 
-// stamp (n words, nullable, contents arbitrary at entry): round + 1 of a
-// transaction's last level increase.  Levels only grow, so each run's maximum
-// persists across rounds and a round folds in only the levels that grew in
-// the round before (a stale stamp equal to the round only repeats a
-// maximum); a round's updates are atomics only where the bound exceeds the
-// level read.  Without stamp every operation is folded in every round.
-__global__ void __launch_bounds__(256) fixpoint_coop_kernel(const uint32_t *sv, const uint32_t *rid,
-                                                           uint32_t *runmax, uint32_t *level, int32_t *best,
-                                                           uint32_t *rfirst, unsigned long long *agg, BulkCtl *ctl,
-                                                           int64_t m, uint32_t max_rounds, uint32_t *stamp)
+__global__ void __launch_bounds__(256) depth_flow_kernel(const uint32_t *txn_rid, const uint32_t *op_off, int kslots,
+                                                        uint32_t *left, uint32_t *runmax, uint32_t *level,
+                                                        BulkCtl *ctl, int64_t n, uint64_t limit_ns)
 {
-    __shared__ SegMax s_warp[8];
-    cooperative_groups::grid_group g = cooperative_groups::this_grid();
+    __shared__ uint32_t s_c, s_stop;
     if (ctl->err) return;   // set before this launch only: every block returns
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    const SegMax ident{0u, INT32_MIN};
-    // the runs: count, and which run starts its group
-    if (i0 == 0) ctl->runs = 0;   // a replayed graph reuses the control block
-    g.sync();
-    for (int64_t i = i0; i < m; i += stride) {
-        const uint32_t v = sv[i], rr = rid[i];
-        if (v == OP_SENTINEL) continue;
-        if (i == 0 || rid[i - 1] != rr) {
-            rfirst[rr & 0x7fffffffu] = rr >> 31;
-            atomicMax(&ctl->runs, (rr & 0x7fffffffu) + 1u);
-        }
-    }
-    g.sync();
-    const int64_t R = *(volatile uint32_t *)&ctl->runs;
-    // this block's runs [b0, b1), this thread's [t0, t1)
-    const int64_t per_block = (R + gridDim.x - 1) / gridDim.x;
-    const int64_t b0 = blockIdx.x * per_block, b1 = b0 + per_block < R ? b0 + per_block : R;
-    const int64_t per_thread = (per_block + blockDim.x - 1) / blockDim.x;
-    const int64_t t0 = b0 + threadIdx.x * per_thread < b1 ? b0 + threadIdx.x * per_thread : b1;
-    const int64_t t1 = t0 + per_thread < b1 ? t0 + per_thread : b1;
-    uint32_t r = 0;
-    bool grew_any = true;
-    for (int64_t i = i0; i < R; i += stride) runmax[i] = 0;
-    for (; r < max_rounds && grew_any; r++) {
-        if (i0 == 0) ctl->changed_r[(r + 1) % 3] = 0;
-        g.sync();
-        // kFixBatch operations a thread at a time: all their loads, then the
-        // dependent gathers, then the atomics, so a thread keeps a batch of
-        // round trips in flight instead of one
-        for (int64_t i = i0; i < m; i += stride * kFixBatch) {
-            uint32_t v[kFixBatch], q[kFixBatch], lv[kFixBatch];
-            bool use[kFixBatch];
-#pragma unroll
-            for (int u = 0; u < kFixBatch; u++) {
-                const int64_t k = i + (int64_t)u * stride;
-                v[u] = k < m ? sv[k] : OP_SENTINEL;
-                q[u] = k < m ? rid[k] : 0u;
-            }
-#pragma unroll
-            for (int u = 0; u < kFixBatch; u++) {
-                const uint32_t t = v[u] >> 7;
-                use[u] = v[u] != OP_SENTINEL && (r == 0 || !stamp || stamp[t] == r);
-                lv[u] = use[u] ? level[t] : 0u;
-            }
-#pragma unroll
-            for (int u = 0; u < kFixBatch; u++)
-                if (use[u]) atomicMax(&runmax[q[u] & 0x7fffffffu], lv[u]);
-        }
-        g.sync();
-        // segmented max-scan of runmax(q) - q over the runs: thread, block
-        SegMax th = ident;
-#pragma unroll 8
-        for (int64_t q = t0; q < t1; q++)
-            th = segmax_combine(th, SegMax{rfirst[q], (int32_t)runmax[q] - (int32_t)q});
-        SegMax x = th;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            SegMax o{__shfl_up_sync(0xffffffffu, x.f, off), (int32_t)__shfl_up_sync(0xffffffffu, (uint32_t)x.v, off)};
-            if (lane >= (uint32_t)off) x = segmax_combine(o, x);
-        }
-        if (lane == 31) s_warp[warp] = x;
-        SegMax th_excl{__shfl_up_sync(0xffffffffu, x.f, 1), (int32_t)__shfl_up_sync(0xffffffffu, (uint32_t)x.v, 1)};
-        if (lane == 0) th_excl = ident;
-        __syncthreads();
-        SegMax warp_excl = ident;
-        for (uint32_t w = 0; w < warp; w++) warp_excl = segmax_combine(warp_excl, s_warp[w]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->rounds = 1;
+    while (true) {
         if (threadIdx.x == 0) {
-            SegMax blk = ident;
-            for (uint32_t w = 0; w < blockDim.x / 32; w++) blk = segmax_combine(blk, s_warp[w]);
-            agg[blockIdx.x] = segmax_pack(blk);
+            s_stop = *(volatile uint32_t *)&ctl->err ? 1u : 0u;
+            s_c = atomicAdd(&ctl->claim, 1u);
         }
-        g.sync();
-        // grid: exclusive prefixes of the block aggregates, in place, by block
-        // 0 (each thread a contiguous slice, then a block scan of the slices)
-        if (blockIdx.x == 0) {
-            const uint32_t per = (gridDim.x + blockDim.x - 1) / blockDim.x;
-            const uint32_t a0 = threadIdx.x * per < gridDim.x ? threadIdx.x * per : gridDim.x;
-            const uint32_t a1 = a0 + per < gridDim.x ? a0 + per : gridDim.x;
-            SegMax sl = ident;
-            for (uint32_t bb = a0; bb < a1; bb++) sl = segmax_combine(sl, segmax_unpack(agg[bb]));
-            SegMax y = sl;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                SegMax o{__shfl_up_sync(0xffffffffu, y.f, off),
-                         (int32_t)__shfl_up_sync(0xffffffffu, (uint32_t)y.v, off)};
-                if (lane >= (uint32_t)off) y = segmax_combine(o, y);
+        __syncthreads();
+        const int64_t start = (int64_t)s_c * blockDim.x;
+        if (s_stop || start >= n) break;
+        const int64_t t = start + threadIdx.x;
+        if (t < n) {
+            const int64_t s0 = op_off ? (int64_t)op_off[t] : t * kslots;
+            const int k = op_off ? (int)(op_off[t + 1] - op_off[t]) : kslots;
+            uint32_t rr[MAX_OPS];
+            uint32_t waits = 0;   // bit j: operation j follows an earlier run
+            for (int j = 0; j < k && j < MAX_OPS; j++) {
+                rr[j] = txn_rid[s0 + j];
+                if (rr[j] != kNoRun && !(rr[j] & 0x80000000u)) waits |= 1u << j;
             }
-            __syncthreads();   // s_warp: the block scan above has read it
-            if (lane == 31) s_warp[warp] = y;
-            SegMax sl_excl{__shfl_up_sync(0xffffffffu, y.f, 1), (int32_t)__shfl_up_sync(0xffffffffu, (uint32_t)y.v, 1)};
-            if (lane == 0) sl_excl = ident;
-            __syncthreads();
-            SegMax run = ident;
-            for (uint32_t w = 0; w < warp; w++) run = segmax_combine(run, s_warp[w]);
-            run = segmax_combine(run, sl_excl);
-            for (uint32_t bb = a0; bb < a1; bb++) {
-                const SegMax a = segmax_unpack(agg[bb]);
-                agg[bb] = segmax_pack(run);
-                run = segmax_combine(run, a);
-            }
-        }
-        g.sync();
-        // apply: best[q] = bound carried into run q from earlier runs of its group
-        SegMax carry = segmax_combine(segmax_combine(segmax_unpack(agg[blockIdx.x]), warp_excl), th_excl);
-#pragma unroll 8
-        for (int64_t q = t0; q < t1; q++) {
-            const uint32_t f = rfirst[q];
-            best[q] = f ? INT32_MIN : carry.v;
-            carry = segmax_combine(carry, SegMax{f, (int32_t)runmax[q] - (int32_t)q});
-        }
-        g.sync();
-        bool grew = false;
-        for (int64_t i = i0; i < m; i += stride * kFixBatch) {
-            uint32_t v[kFixBatch], rr[kFixBatch], cand[kFixBatch];
-            bool use[kFixBatch];
-#pragma unroll
-            for (int u = 0; u < kFixBatch; u++) {
-                const int64_t k = i + (int64_t)u * stride;
-                v[u] = k < m ? sv[k] : OP_SENTINEL;
-                rr[u] = k < m ? rid[k] : 0x80000000u;
-            }
-#pragma unroll
-            for (int u = 0; u < kFixBatch; u++) {
-                use[u] = v[u] != OP_SENTINEL && !(rr[u] & 0x80000000u);
-                const uint32_t j = rr[u] & 0x7fffffffu;
-                const int32_t bj = use[u] ? best[j] : INT32_MIN;
-                use[u] = use[u] && bj != INT32_MIN;
-                cand[u] = (uint32_t)((int64_t)j + bj);
-            }
-#pragma unroll
-            for (int u = 0; u < kFixBatch; u++)   // a stale read only costs an atomic
-                use[u] = use[u] && __ldcg(&level[v[u] >> 7]) < cand[u];
-#pragma unroll
-            for (int u = 0; u < kFixBatch; u++) {
-                if (!use[u]) continue;
-                const uint32_t t = v[u] >> 7;
-                if (atomicMax(&level[t], cand[u]) < cand[u]) {
-                    grew = true;
-                    if (stamp) stamp[t] = r + 1;
+            // the preceding runs: all polled at once (first, and after any of
+            // them completes), else only the first incomplete one, so that
+            // waiters far down a chain do not flood L2 with polls
+            uint32_t pending = waits;
+            uint64_t t_prog = globaltimer();
+            uint32_t ns = 64;
+            bool all = true;
+            while (pending) {
+                uint32_t still = 0;
+                if (all) {
+                    uint32_t c[MAX_OPS];
+                    for (int j = 0; j < k && j < MAX_OPS; j++)
+                        if (pending >> j & 1u) c[j] = ld_relaxed_gpu(&left[(rr[j] & 0x7fffffffu) - 1u]);
+                    for (int j = 0; j < k && j < MAX_OPS; j++)
+                        if ((pending >> j & 1u) && c[j]) still |= 1u << j;
+                } else {
+                    const int j0 = __ffs(pending) - 1;
+                    still = ld_relaxed_gpu(&left[(rr[j0] & 0x7fffffffu) - 1u]) ? pending : pending & ~(1u << j0);
                 }
+                if (still != pending) {
+                    pending = still;
+                    t_prog = globaltimer();
+                    ns = 64;
+                    all = true;
+                    continue;
+                }
+                all = false;
+                if (globaltimer() - t_prog > limit_ns) {
+                    set_err(&ctl->err, ERR_TIMEOUT);
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < kFlowSleepMax) ns <<= 1;
             }
+            fence_acquire_gpu();
+            uint32_t lv = 0, m[MAX_OPS];
+            for (int j = 0; j < k && j < MAX_OPS; j++)
+                if (waits >> j & 1u) m[j] = __ldcg(&runmax[(rr[j] & 0x7fffffffu) - 1u]);
+            for (int j = 0; j < k && j < MAX_OPS; j++)
+                if ((waits >> j & 1u) && m[j] + 1u > lv) lv = m[j] + 1u;
+            level[t] = lv;
+            // this transaction's depth into its runs' maxima, then counted off:
+            // one release fence orders every maximum before every count (a
+            // release on each count would wait for the one before)
+            for (int j = 0; j < k && j < MAX_OPS; j++)
+                if (rr[j] != kNoRun) atomicMax(&runmax[rr[j] & 0x7fffffffu], lv);
+            __threadfence();
+            for (int j = 0; j < k && j < MAX_OPS; j++)
+                if (rr[j] != kNoRun) atomicSub(&left[rr[j] & 0x7fffffffu], 1u);
         }
-        if (__any_sync(0xffffffffu, grew) && lane == 0) atomicOr(&ctl->changed_r[r % 3], 1u);
-        g.sync();
-        grew_any = *(volatile uint32_t *)&ctl->changed_r[r % 3] != 0;
-    }
-    if (i0 == 0) {
-        ctl->rounds = r;
-        if (grew_any) set_err(&ctl->err, ERR_TIMEOUT);   // no fixpoint within the bound
+        __syncthreads();
     }
 }
+
 
 // d and w0 (Appendix D structural parameters)
 __global__ void level_stats_kernel(const uint32_t *level, int64_t n, BulkCtl *ctl)
@@ -1207,38 +1119,40 @@ cudaError_t launch_ticket_scan(gputx_bulk *b, const uint32_t *sk, const uint32_t
     return run_scan(b, tm, m, 2);
 }
 
-cudaError_t launch_fixpoint_device(gputx_bulk *b, const uint32_t *sv, int64_t m)
+cudaError_t launch_depth_flow(gputx_bulk *b, const uint32_t *sv, int64_t m)
 {
-    if (m == 0) return cudaSuccess;
-    static int blocks_per_sm = 0;
-    if (!blocks_per_sm) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, fixpoint_coop_kernel, 256, 0);
-        if (blocks_per_sm < 1) blocks_per_sm = 1;
+    if (m == 0 || b->n == 0) return cudaSuccess;
+    cudaStream_t s = b->stream;
+    const bool fixed = b->db->uniform_k || b->graph;
+    const uint32_t *op_off = fixed ? nullptr : b->sc.op_off;
+    const int kslots = b->graph ? b->db->kmax : b->db->uniform_k;
+    // the run counts and the per-slot run ids reuse the TPL buffers (free
+    // during the analysis)
+    uint32_t *txn_rid = b->sc.lock_key, *left = b->sc.lock_ticket;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(txn_rid, 0xff, (size_t)m * sizeof(uint32_t), s))) return e;
+    if ((e = cudaMemsetAsync(left, 0, (size_t)m * sizeof(uint32_t), s))) return e;
+    if ((e = cudaMemsetAsync(b->sc.runmax, 0, (size_t)m * sizeof(uint32_t), s))) return e;
+    if ((e = cudaMemsetAsync(&b->ctl->claim, 0, sizeof(uint32_t), s))) return e;
+    depth_prep_kernel<<<grid_for(m), TB, 0, s>>>(sv, b->sc.rid, m, op_off, kslots, txn_rid, left, b->ctl);
+    static int per_sm = 0;
+    if (!per_sm) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, depth_flow_kernel, 256, 0);
+        if (per_sm < 1) per_sm = 1;
     }
-    int64_t grid = (int64_t)b->db->num_sms * blocks_per_sm;
-    const int64_t need = (m + 255) / 256;
-    if (grid > need) grid = need;
-    if (grid > kFixAggMax) grid = kFixAggMax;
-    if (!b->sc.fix_agg) return cudaErrorInvalidValue;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid, 1, 1);
-    cfg.blockDim = dim3(256, 1, 1);
-    cfg.stream = b->stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    const uint32_t max_rounds = (uint32_t)(b->n + 2 > 0xffffffffll ? 0xffffffffll : b->n + 2);
-    // the run bounds and run-start flags reuse the TPL buffers (free during
-    // the analysis)
-    // the round stamps reuse the PART sort keys (n words, free during the
-    // analysis)
-    cudaError_t e = cudaLaunchKernelEx(&cfg, fixpoint_coop_kernel, sv, (const uint32_t *)b->sc.rid, b->sc.runmax,
-                                       b->sc.level, (int32_t *)b->sc.lock_key, b->sc.lock_ticket, b->sc.fix_agg,
-                                       b->ctl, m, max_rounds, b->sc.pid_key);
-    count_launches(1);
-    return e;
+    int64_t grid = (int64_t)b->db->num_sms * per_sm;
+    const int64_t chunks = (b->n + 255) / 256;
+    if (grid > chunks) grid = chunks;
+    depth_flow_kernel<<<(unsigned)grid, 256, 0, s>>>(txn_rid, op_off, kslots, left, b->sc.runmax, b->sc.level,
+                                                     b->ctl, b->n, (uint64_t)b->db->cfg.spin_limit_ns);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+// exact depths after the one-pass ranks (A1): the dataflow pass
+cudaError_t launch_exact_depth(gputx_bulk *b, const uint32_t *sv, int64_t m)
+{
+    return launch_depth_flow(b, sv, m);
 }
 
 cudaError_t launch_level_stats(gputx_bulk *b)

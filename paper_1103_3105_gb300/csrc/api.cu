@@ -227,7 +227,6 @@ size_t carve_bulk(gputx_bulk *b, char *base, bool device_inputs)
     s.scan_tiles = (big + 2047) / 2048;
     s.scan_status = c.take<uint64_t>(s.scan_tiles);
     s.scan_vals = c.take<uint64_t>(2 * s.scan_tiles);
-    s.fix_agg = db->need_fixpoint ? c.take<unsigned long long>(kFixAggMax) : nullptr;
     s.rec_dc = db->dev.registered == (1u << GPUTX_T_DC_DEBIT_CREDIT) ? c.take<DcRecord>(nn) : nullptr;
     s.seg_off = b->graph ? c.take<uint32_t>(kSegMax + 1) : nullptr;
     s.bulk_of = b->graph ? c.take<uint32_t>(nn) : nullptr;
@@ -1096,7 +1095,7 @@ gputx_status gputx_execute(gputx_db *db, gputx_bulk *b, int strategy, const gput
         // (a transaction is a source exactly when all its operations have
         // rank 0), and the one-pass depth bounds the exact one from below.
         // The refinement rounds run only once K-SET is chosen.
-        if (db->need_fixpoint && strategy == GPUTX_KSET) CK(launch_fixpoint_device(b, sv, m), "fixpoint");
+        if (db->need_fixpoint && strategy == GPUTX_KSET) CK(launch_exact_depth(b, sv, m), "fixpoint");
         CK(launch_level_stats(b), "stats");
         if ((st = read_ctl(b))) return st;
         if (b->host_ctl.err) {
@@ -1116,7 +1115,7 @@ gputx_status gputx_execute(gputx_db *db, gputx_bulk *b, int strategy, const gput
                 b->fallback = 1;
             if (run == GPUTX_KSET && db->need_fixpoint) {
                 // exact depths for the level schedule (Property 1)
-                CK(launch_fixpoint_device(b, sv, m), "fixpoint");
+                CK(launch_exact_depth(b, sv, m), "fixpoint");
                 CK(cudaMemsetAsync(&b->ctl->depth, 0, 2 * sizeof(uint32_t), s), "stats");
                 CK(launch_level_stats(b), "stats");
                 if ((st = read_ctl(b))) return st;
@@ -1436,7 +1435,7 @@ extern "C" gputx_status gputx_execute_kset_noalloc(gputx_db *db, const int64_t *
     uint32_t *sk = b.sc.keys_a, *sv = b.sc.vals_a, *ak = b.sc.keys_b, *av = b.sc.vals_b;
     CK(launch_sort(&b, sk, sv, ak, av, m, key_bits(db, conflict_mode)), "sort");
     CK(launch_rank_scan(&b, sk, sv, m, db->need_fixpoint), "rank");
-    if (db->need_fixpoint) CK(launch_fixpoint_device(&b, sv, m), "fixpoint");
+    if (db->need_fixpoint) CK(launch_exact_depth(&b, sv, m), "fixpoint");
     CK(launch_level_stats(&b), "stats");
     if ((st = read_ctl(&b))) return st;
     if (b.host_ctl.err) return bulk_error(db, b.host_ctl.err);

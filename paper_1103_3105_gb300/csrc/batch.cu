@@ -110,7 +110,7 @@ cudaError_t enqueue_pipeline(GraphBulk *g)
     if ((e = gtx::launch_sort(b, sk, sv, ak, av, m, kbits))) return e;
     if (g->strategy == GPUTX_KSET) {
         if ((e = gtx::launch_rank_scan(b, sk, sv, m, db->need_fixpoint))) return e;
-        if (db->need_fixpoint && (e = gtx::launch_fixpoint_device(b, sv, m))) return e;
+        if (db->need_fixpoint && (e = gtx::launch_exact_depth(b, sv, m))) return e;
         if ((e = gtx::launch_level_stats(b))) return e;
         if (seg && (e = gtx::launch_seg_levels(b))) return e;
         uint32_t *rk = ak, *rv = av, *rk2 = sk, *rv2 = sv;

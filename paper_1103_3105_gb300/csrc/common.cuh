@@ -149,6 +149,18 @@ __device__ __forceinline__ void red_release_add(uint32_t *p, uint32_t v)
 {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+// a relaxed poll of a counter: several can be in flight at once (an acquire
+// load would order each behind the one before); one acquire fence follows
+// once every polled counter has reached its value
+__device__ __forceinline__ uint32_t ld_relaxed_gpu(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void fence_acquire_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 __device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t *p)
 {
     return *(const volatile uint64_t *)p;

@@ -16,15 +16,12 @@ struct BulkCtl {
     uint32_t depth;        // d: largest level
     uint32_t w0;           // 0-set size
     uint32_t cross;        // cross-partition transactions
-    uint32_t changed;      // fixpoint: a level grew in the last round
     uint32_t npart;        // PART: non-empty partitions
     uint32_t claim;        // executors: next chunk to claim
     uint32_t n_live;       // fixed-capacity bulks: live transactions (the rest pad)
     InsertBase base;       // where this bulk's inserts start (copied from the cursor)
     InsertBase total;      // inserts this bulk reserves
-    uint32_t changed_r[3]; // refinement rounds run on the device: rotating per-round flags
-    uint32_t rounds;       // refinement rounds taken
-    uint32_t runs;         // refinement: runs of the sorted operations
+    uint32_t rounds;       // exact-depth passes run (the dataflow pass: 1)
     uint32_t n_seg;        // segmented graph bulks: bulks in this segment (0 = one)
     uint32_t hot;          // TPL: some counter has a chain of at least the hot ticket
     uint32_t chunk;        // relaxed TPL: next chunk to claim (claim counts commit tickets)
@@ -32,15 +29,13 @@ struct BulkCtl {
 
 constexpr int kSegMax = 64;        // bulks in one segment of a graph bulk, at most
 
-constexpr int kFixAggMax = 4096;   // blocks of the cooperative refinement launch, at most
-
 // Scratch carved from one per-bulk allocation.
 struct Scratch {
     uint32_t *keys_a, *vals_a, *keys_b, *vals_b;  // sort ping-pong, m entries each
     uint32_t *op_off;      // n+1 exclusive op offsets (non-uniform op counts)
     uint32_t *level;       // n
-    uint32_t *rid;         // m: global run id per sorted op (fixpoint)
-    uint32_t *runmax;      // m
+    uint32_t *rid;         // m: global run id per sorted op (exact depth)
+    uint32_t *runmax;      // m: deepest finished transaction of each run (exact depth)
     uint32_t *lock_key;    // m: TPL per-op object, indexed by op slot
     uint32_t *lock_ticket; // m
     uint32_t *level_off;   // n+2
@@ -61,7 +56,6 @@ struct Scratch {
     uint32_t *tile_ctr;    // 16 counters
     uint64_t *scan_status; // tiles
     uint64_t *scan_vals;   // 2 x tiles: per-tile values of 64-bit scans
-    unsigned long long *fix_agg;   // kFixAggMax: refinement's per-block scan aggregates
     DcRecord *rec_dc;      // n packed debit-credit records (debit-credit-only databases)
     // graph bulks that carry a segment of several bulks
     uint32_t *seg_off;     // kSegMax + 1: first transaction of each bulk
@@ -158,7 +152,8 @@ cudaError_t launch_sort(gputx_bulk *b, uint32_t *&keys, uint32_t *&vals, uint32_
                         uint32_t *&vals_alt, int64_t count, int bits);
 cudaError_t launch_rank_scan(gputx_bulk *b, const uint32_t *sk, const uint32_t *sv, int64_t m, bool want_rid);
 cudaError_t launch_ticket_scan(gputx_bulk *b, const uint32_t *sk, const uint32_t *sv, int64_t m);
-cudaError_t launch_fixpoint_device(gputx_bulk *b, const uint32_t *sv, int64_t m);
+cudaError_t launch_depth_flow(gputx_bulk *b, const uint32_t *sv, int64_t m);
+cudaError_t launch_exact_depth(gputx_bulk *b, const uint32_t *sv, int64_t m);
 cudaError_t launch_level_stats(gputx_bulk *b);
 cudaError_t launch_regroup_keys(gputx_bulk *b, uint32_t *keys, uint32_t *vals);
 cudaError_t launch_level_tables(gputx_bulk *b, const uint32_t *skeys, int64_t depth, int block, bool chunks);

@@ -462,17 +462,6 @@ __device__ __forceinline__ bool tpl_skip(const TplArgs &a)
     return hot != (a.when_hot == 1);
 }
 
-// a relaxed poll of a lock counter: several can be in flight at once (an
-// acquire load would order each behind the one before); one acquire fence
-// follows once every lock of the transaction is granted
-__device__ __forceinline__ uint32_t ld_relaxed_gpu(const uint32_t *p)
-{
-    uint32_t v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void fence_acquire_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 // releases of the lanes with `rel` (every lane of the warp calls it): lanes
 // releasing the same counter are grouped by __match_any_sync and their

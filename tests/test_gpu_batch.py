@@ -46,7 +46,7 @@ def test_graph_bulks_equal_serial_execution(strategy, mode, size):
 
 @pytest.mark.parametrize("mode", [G.CONFLICT_PAPER, G.CONFLICT_ADD])
 def test_autotuned_order_entry_stream(mode):
-    """Order-entry (multi-item transactions: the refinement rounds run on the
+    """Order-entry (multi-item transactions: the exact-depth pass runs on the
     device inside the graph) with the autotuner choosing strategy, bulk size
     and block shape on the stream's first bulks."""
     n_wh, n_items = 8, 20_000

@@ -131,7 +131,7 @@ def test_order_entry_mix(strategy, mode):
 
 @pytest.mark.parametrize("mode", [G.CONFLICT_PAPER, G.CONFLICT_ADD])
 def test_order_entry_levels_exact(mode):
-    """Multi-item transactions need the refinement rounds: the engine's depth
+    """Multi-item transactions need the exact-depth pass: the engine's depth
     and 0-set size must equal the longest-path depths of the oracle."""
     n_wh, n_items = 3, 200
     g, o = oe_pair(n_wh, n_items)
@@ -161,8 +161,8 @@ def test_order_entry_part_falls_back_on_cross_partition():
 @pytest.mark.parametrize("mode", [G.CONFLICT_PAPER, G.CONFLICT_ADD])
 def test_auto_refines_only_for_kset(mode):
     """AUTO decides on the one-pass ranks: a TPL or PART pick runs no
-    refinement round; a K-SET pick (forced by a zero 0-set threshold) runs
-    them and reaches the exact longest-path depths."""
+    exact-depth pass; a K-SET pick (forced by a zero 0-set threshold) runs
+    it and reaches the exact longest-path depths."""
     n_wh, n_items = 3, 200
     bulk = W.oe_bulk(6000, n_wh, n_items=n_items, remote_frac=0.2, invalid_frac=0.02, seed=78)
     ob = oracle.OracleDB(oe=W.oe_tables(n_wh, n_items=n_items, seed=2), ord_cap=1, ol_cap=1, oid_cap=1)

@@ -75,7 +75,7 @@ def _schema_pair(G, W, schema):
 @pytest.mark.parametrize("schema", ["sub", "oe"])
 def test_noalloc_matches_regular_entry_point_on_other_schemas(schema):
     """Multi-item order-entry transactions (uneven operation counts, insert
-    slots for orders and order lines, refinement rounds) and subscriber
+    slots for orders and order lines, the exact-depth pass) and subscriber
     bulks with call-forwarding inserts and deletes: status, outputs and every
     table equal the regular K-SET path's, on two calls in a row."""
     torch = pytest.importorskip("torch")
