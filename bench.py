@@ -799,6 +799,8 @@ PROFILE_CASES = {
     "dc_tpl_paper_20": ("dc", 20, 0.0, "tpl", "paper"),
     "dc_part_20": ("dc", 20, 0.0, "part", "paper"),
     "dc_part_zipf99_20": ("dc", 20, 0.99, "part", "paper"),
+    "dc_tpl_zipf99_20": ("dc", 20, 0.99, "tpl", "paper"),
+    "dc_tpl_relaxed_zipf99_20": ("dc", 20, 0.99, "tpl_relaxed", "paper"),
     "dc_scan_22": ("dc", 22, 0.0, "scan", "paper"),
     "oe_kset_paper_16": ("oe", 16, 0.0, "kset", "paper"),
     "oe_tpl_paper_16": ("oe", 16, 0.0, "tpl", "paper"),

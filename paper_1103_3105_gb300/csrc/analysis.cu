@@ -223,18 +223,19 @@ struct TicketMode {
 // the largest, over its operations outside their group's first run, of one
 // more than the deepest transaction of the run before -- the longest path of
 // the conflict graph, the depth the Jacobi refinement converges to.  Here each
-// transaction computes it once the runs before its operations are complete:
-// run q keeps the number of its operations still to finish (left) and the
-// largest depth among the finished ones (runmax); a transaction polls the
-// left counts of all its preceding runs at once, then reads their maxima,
-// publishes its depth into the maxima of its own runs and counts itself off
-// with a release.  Transactions run in timestamp order, a CTA's chunk of
-// consecutive ones at a time, so every run a transaction waits for belongs to
-// earlier transactions already running: the chain of waits always ends.
+// transaction computes it once the runs before its operations are complete.
+// Run q keeps one 64-bit word: the number of its operations still to finish
+// (high half) and the largest depth among the finished ones (low half).  A
+// finishing operation replaces both at once by compare-and-swap, so a waiter
+// that reads a count of zero reads the run's maximum in the same word: no
+// fence and no second read.  Transactions run in timestamp order, a CTA's
+// chunk of consecutive ones at a time, so every run a transaction waits for
+// belongs to earlier transactions already running: the chain of waits always
+// ends.
 
 // per operation: its run id into the transaction's slot, its run counted
 __global__ void depth_prep_kernel(const uint32_t *sv, const uint32_t *rid, int64_t m, const uint32_t *op_off,
-                                  int kslots, uint32_t *txn_rid, uint32_t *left, const BulkCtl *ctl)
+                                  int kslots, uint32_t *txn_rid, unsigned long long *runword, const BulkCtl *ctl)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= m || ctl->err) return;
@@ -244,15 +245,23 @@ __global__ void depth_prep_kernel(const uint32_t *sv, const uint32_t *rid, int64
     const uint32_t txn = v >> 7, j = (v >> 2) & 31u;
     const int64_t slot = (op_off ? (int64_t)op_off[txn] : (int64_t)txn * kslots) + j;
     txn_rid[slot] = rr;
-    atomicAdd(&left[rr & 0x7fffffffu], 1u);
+    atomicAdd(&runword[rr & 0x7fffffffu], 1ull << 32);
 }
 
 constexpr uint32_t kNoRun = 0xffffffffu;   // an operation slot with no operation
 constexpr uint32_t kFlowSleepMax = 2048;    // longest back-off between polls, ns
+constexpr int kFlowBlocksPerSm = 1;         // resident CTAs of the pass per SM (fewer waiters poll less)
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 
 __global__ void __launch_bounds__(256) depth_flow_kernel(const uint32_t *txn_rid, const uint32_t *op_off, int kslots,
-                                                        uint32_t *left, uint32_t *runmax, uint32_t *level,
-                                                        BulkCtl *ctl, int64_t n, uint64_t limit_ns)
+                                                        unsigned long long *runword, uint32_t *level, BulkCtl *ctl,
+                                                        int64_t n, uint64_t limit_ns)
 {
     __shared__ uint32_t s_c, s_stop;
     if (ctl->err) return;   // set before this launch only: every block returns
@@ -270,29 +279,33 @@ __global__ void __launch_bounds__(256) depth_flow_kernel(const uint32_t *txn_rid
             const int64_t s0 = op_off ? (int64_t)op_off[t] : t * kslots;
             const int k = op_off ? (int)(op_off[t + 1] - op_off[t]) : kslots;
             uint32_t rr[MAX_OPS];
-            uint32_t waits = 0;   // bit j: operation j follows an earlier run
+            uint32_t waits = 0, own = 0;   // bit j: operation j follows an earlier run / has a run
             for (int j = 0; j < k && j < MAX_OPS; j++) {
                 rr[j] = txn_rid[s0 + j];
-                if (rr[j] != kNoRun && !(rr[j] & 0x80000000u)) waits |= 1u << j;
+                if (rr[j] != kNoRun) {
+                    own |= 1u << j;
+                    if (!(rr[j] & 0x80000000u)) waits |= 1u << j;
+                }
             }
             // the preceding runs: all polled at once (first, and after any of
             // them completes), else only the first incomplete one, so that
             // waiters far down a chain do not flood L2 with polls
-            uint32_t pending = waits;
+            uint32_t pending = waits, lv = 0;
             uint64_t t_prog = globaltimer();
             uint32_t ns = 64;
             bool all = true;
             while (pending) {
-                uint32_t still = 0;
-                if (all) {
-                    uint32_t c[MAX_OPS];
-                    for (int j = 0; j < k && j < MAX_OPS; j++)
-                        if (pending >> j & 1u) c[j] = ld_relaxed_gpu(&left[(rr[j] & 0x7fffffffu) - 1u]);
-                    for (int j = 0; j < k && j < MAX_OPS; j++)
-                        if ((pending >> j & 1u) && c[j]) still |= 1u << j;
-                } else {
-                    const int j0 = __ffs(pending) - 1;
-                    still = ld_relaxed_gpu(&left[(rr[j0] & 0x7fffffffu) - 1u]) ? pending : pending & ~(1u << j0);
+                // this look's runs: every pending one, or the first
+                const uint32_t look = all ? pending : pending & (0u - pending);
+                unsigned long long w[MAX_OPS];
+                for (int j = 0; j < k && j < MAX_OPS; j++)   // all loads in flight at once
+                    if (look >> j & 1u) w[j] = ld_relaxed_u64(&runword[(rr[j] & 0x7fffffffu) - 1u]);
+                uint32_t still = pending;
+                for (int j = 0; j < k && j < MAX_OPS; j++) {
+                    if ((look >> j & 1u) && !(w[j] >> 32)) {   // complete: its maximum is final
+                        still &= ~(1u << j);
+                        if ((uint32_t)w[j] + 1u > lv) lv = (uint32_t)w[j] + 1u;
+                    }
                 }
                 if (still != pending) {
                     pending = still;
@@ -309,21 +322,28 @@ __global__ void __launch_bounds__(256) depth_flow_kernel(const uint32_t *txn_rid
                 __nanosleep(ns);
                 if (ns < kFlowSleepMax) ns <<= 1;
             }
-            fence_acquire_gpu();
-            uint32_t lv = 0, m[MAX_OPS];
-            for (int j = 0; j < k && j < MAX_OPS; j++)
-                if (waits >> j & 1u) m[j] = __ldcg(&runmax[(rr[j] & 0x7fffffffu) - 1u]);
-            for (int j = 0; j < k && j < MAX_OPS; j++)
-                if ((waits >> j & 1u) && m[j] + 1u > lv) lv = m[j] + 1u;
             level[t] = lv;
-            // this transaction's depth into its runs' maxima, then counted off:
-            // one release fence orders every maximum before every count (a
-            // release on each count would wait for the one before)
+            // this transaction's depth into each of its runs, counted off in
+            // the same compare-and-swap
+            unsigned long long cur[MAX_OPS];
             for (int j = 0; j < k && j < MAX_OPS; j++)
-                if (rr[j] != kNoRun) atomicMax(&runmax[rr[j] & 0x7fffffffu], lv);
-            __threadfence();
-            for (int j = 0; j < k && j < MAX_OPS; j++)
-                if (rr[j] != kNoRun) atomicSub(&left[rr[j] & 0x7fffffffu], 1u);
+                if (own >> j & 1u) cur[j] = 1ull << 32;   // a guess: the run's only operation
+            uint32_t todo = own;
+            for (int attempt = 0; todo && attempt < (1 << 20); attempt++) {
+                unsigned long long prev[MAX_OPS];
+                for (int j = 0; j < k && j < MAX_OPS; j++) {   // every swap in flight at once
+                    if (!(todo >> j & 1u)) continue;
+                    const uint32_t mx = (uint32_t)cur[j] > lv ? (uint32_t)cur[j] : lv;
+                    const unsigned long long nv = (((cur[j] >> 32) - 1ull) << 32) | mx;
+                    prev[j] = atomicCAS(&runword[rr[j] & 0x7fffffffu], cur[j], nv);
+                }
+                for (int j = 0; j < k && j < MAX_OPS; j++) {
+                    if (!(todo >> j & 1u)) continue;
+                    if (prev[j] == cur[j]) todo &= ~(1u << j);
+                    else cur[j] = prev[j];
+                }
+            }
+            if (todo) set_err(&ctl->err, ERR_TIMEOUT);
         }
         __syncthreads();
     }
@@ -1108,9 +1128,11 @@ cudaError_t launch_ticket_scan(gputx_bulk *b, const uint32_t *sk, const uint32_t
 {
     const bool fixed = b->db->uniform_k || b->graph;
     // CTA-wide lock groups pay off once a counter's chain reaches about
-    // n/1024 operations (on debit-credit they run Zipf 0.7 accounts 15 %
-    // faster than warp groups, and uniform ones 13 % slower)
-    const int64_t hot = b->n / 1024 > 32 ? b->n / 1024 : 32;
+    // n/512 operations: on debit-credit under R/W (one lock per branch) they
+    // run Zipf 0.7 accounts (a branch chain of about n/300) 15 % faster than
+    // warp groups, and uniform ones (1,000 chains of about n/1,000) 13 %
+    // slower
+    const int64_t hot = b->n / 512 > 32 ? b->n / 512 : 32;
     TicketMode tm{sk, sv, b->sc.lock_key, b->sc.lock_ticket, fixed ? nullptr : b->sc.op_off,
                   b->graph ? b->db->kmax : b->db->uniform_k, &b->ctl->hot,
                   (uint32_t)(hot > 0xffffffffll ? 0xffffffffll : hot), b->db->dev.n_objects, &b->ctl->err};
@@ -1126,25 +1148,25 @@ cudaError_t launch_depth_flow(gputx_bulk *b, const uint32_t *sv, int64_t m)
     const bool fixed = b->db->uniform_k || b->graph;
     const uint32_t *op_off = fixed ? nullptr : b->sc.op_off;
     const int kslots = b->graph ? b->db->kmax : b->db->uniform_k;
-    // the run counts and the per-slot run ids reuse the TPL buffers (free
-    // during the analysis)
-    uint32_t *txn_rid = b->sc.lock_key, *left = b->sc.lock_ticket;
+    // the per-slot run ids reuse a TPL buffer (free during the analysis)
+    uint32_t *txn_rid = b->sc.lock_key;
+    unsigned long long *runword = reinterpret_cast<unsigned long long *>(b->sc.runmax);
     cudaError_t e;
     if ((e = cudaMemsetAsync(txn_rid, 0xff, (size_t)m * sizeof(uint32_t), s))) return e;
-    if ((e = cudaMemsetAsync(left, 0, (size_t)m * sizeof(uint32_t), s))) return e;
-    if ((e = cudaMemsetAsync(b->sc.runmax, 0, (size_t)m * sizeof(uint32_t), s))) return e;
+    if ((e = cudaMemsetAsync(runword, 0, (size_t)m * sizeof(unsigned long long), s))) return e;
     if ((e = cudaMemsetAsync(&b->ctl->claim, 0, sizeof(uint32_t), s))) return e;
-    depth_prep_kernel<<<grid_for(m), TB, 0, s>>>(sv, b->sc.rid, m, op_off, kslots, txn_rid, left, b->ctl);
+    depth_prep_kernel<<<grid_for(m), TB, 0, s>>>(sv, b->sc.rid, m, op_off, kslots, txn_rid, runword, b->ctl);
     static int per_sm = 0;
     if (!per_sm) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, depth_flow_kernel, 256, 0);
+        if (per_sm > kFlowBlocksPerSm) per_sm = kFlowBlocksPerSm;
         if (per_sm < 1) per_sm = 1;
     }
     int64_t grid = (int64_t)b->db->num_sms * per_sm;
     const int64_t chunks = (b->n + 255) / 256;
     if (grid > chunks) grid = chunks;
-    depth_flow_kernel<<<(unsigned)grid, 256, 0, s>>>(txn_rid, op_off, kslots, left, b->sc.runmax, b->sc.level,
-                                                     b->ctl, b->n, (uint64_t)b->db->cfg.spin_limit_ns);
+    depth_flow_kernel<<<(unsigned)grid, 256, 0, s>>>(txn_rid, op_off, kslots, runword, b->sc.level, b->ctl, b->n,
+                                                     (uint64_t)b->db->cfg.spin_limit_ns);
     count_launches(2);
     return cudaGetLastError();
 }

@@ -192,7 +192,7 @@ size_t carve_bulk(gputx_bulk *b, char *base, bool device_inputs)
     s.op_off = c.take<uint32_t>(nn + 1);
     s.level = c.take<uint32_t>(nn);
     s.rid = db->need_fixpoint ? c.take<uint32_t>(mm) : nullptr;
-    s.runmax = db->need_fixpoint ? c.take<uint32_t>(mm) : nullptr;
+    s.runmax = db->need_fixpoint ? c.take<uint32_t>(2 * mm) : nullptr;
     s.lock_key = c.take<uint32_t>(mm);
     s.lock_ticket = c.take<uint32_t>(mm);
     s.level_off = c.take<uint32_t>(nn + 2);

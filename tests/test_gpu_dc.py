@@ -255,25 +255,29 @@ def test_hot_accounts_at_sweep_sizes(lg, strategy, mode):
     g.close()
 
 
-@pytest.mark.parametrize("hot_ops", [64, 65])
+@pytest.mark.parametrize("hot_ops", [128, 129])
 @pytest.mark.parametrize("mode", MODES)
 def test_tpl_executor_pick_at_the_hot_chain(hot_ops, mode):
     """Debit-credit TPL runs one of two executors: lock groups over a warp, or
-    over the whole CTA once some counter's chain reaches n/1024 operations (64
-    of 2^16).  One account here takes 64 operations (warp groups) or 65 (CTA
-    groups), spread over the bulk with a cluster of them in one chunk; the
-    other accounts are few enough that lanes of a warp share them too.  Both
-    executors must give the serial result."""
+    over the whole CTA once some lock's chain reaches n/512 operations (128 of
+    2^16).  The lock is the branch under R/W and the account under ADD.  Here
+    2,048 branches of 20 accounts keep every other chain short (about 32
+    operations per branch), and one account -- alone in its branch -- takes
+    128 operations (warp groups) or 129 (CTA groups), spread over the bulk
+    with a run of 20 consecutive ones in one chunk.  Both executors must give
+    the serial result."""
     n = 1 << 16
-    g, o = make_pair(4, 40, 4000, n, max_bulk=n)
-    bulk = W.dc_bulk(n, 4000, 0.0, seed=W.seed_for(1, hot_ops))
+    B, T, A = 2048, 8192, 40960
+    g, o = make_pair(B, T, A, n, max_bulk=n)
+    bulk = W.dc_bulk(n, A, 0.0, seed=W.seed_for(1, hot_ops))
     rng = np.random.default_rng(hot_ops)
-    hot = 1234
+    hot = 777 * 20 + 3                       # an account of branch 777
     acct = bulk["params"][:, 0]
-    acct[acct == hot] = hot + 1
+    acct[acct // 20 == 777] += 20            # the rest of branch 777 moves to branch 778
     idx = np.concatenate([np.arange(1000, 1020), rng.choice(np.arange(2000, n), hot_ops - 20, replace=False)])
     acct[idx] = hot
-    assert int((acct == hot).sum()) == hot_ops
+    assert int((acct // 20 == 777).sum()) == hot_ops and int((acct == hot).sum()) == hot_ops
+    assert np.bincount(acct // 20).max() == hot_ops   # no other branch as long
     stats, st, out, ost, oout = run_both(g, o, bulk, "tpl", mode)
     assert_same(g, o, st, out, ost, oout)
     g.close()
