@@ -249,7 +249,7 @@ __global__ void depth_prep_kernel(const uint32_t *sv, const uint32_t *rid, int64
 }
 
 constexpr uint32_t kNoRun = 0xffffffffu;   // an operation slot with no operation
-constexpr uint32_t kFlowSleepMax = 2048;    // longest back-off between polls, ns
+constexpr uint32_t kFlowSleepMax = 512;     // longest back-off between polls, ns
 constexpr int kFlowBlocksPerSm = 1;         // resident CTAs of the pass per SM (fewer waiters poll less)
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
