@@ -19,6 +19,7 @@ an independent replica (the path does not shard); rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import statistics
@@ -85,31 +86,44 @@ def env_int(k, d):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons during the timed region."""
+    """nvidia-smi clocks and throttle reasons during the timed region.
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Sampling starts before the timed region (the first sample is awaited) and
+    every sample carries its timestamp; the summary keeps those that fall in
+    the marked window, widened by one sampling period on each side."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 20
 
     def __init__(self, gpu):
         self.gpu = gpu
         self.proc = None
         self.lines = []
+        self.window = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.PERIOD_MS)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t_end = time.time() + 3.0
+            while not self.lines and time.time() < t_end and self.proc.poll() is None:
+                time.sleep(0.01)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, t0, t1):
+        """the timed region, as time.time() values"""
+        self.window = (t0, t1)
 
     def __exit__(self, *a):
         if self.proc:
@@ -119,21 +133,38 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self):
+    @staticmethod
+    def _stamp(text, fallback):
+        try:
+            return datetime.datetime.strptime(text, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return fallback
+
+    def summary(self, windowed=True):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        pad = 1.5 * self.PERIOD_MS / 1e3
+        for seen, ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
+            if self.window and windowed:
+                ts = self._stamp(f[0], seen)
+                if ts < self.window[0] - pad or ts > self.window[1] + pad:
+                    continue
             try:
-                sm.append(float(f[1]))
-                mx = float(f[2])
+                sm.append(float(f[2]))
+                mx = float(f[3])
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
+            for nm, v in zip(names, f[6:10]):
                 if v.lower() == "active":
                     reasons.add(nm)
+        if not sm and windowed and self.window:
+            # no sample landed inside a short window: the whole sampled span
+            out = self.summary(windowed=False)
+            out["window"] = "sampled span (no sample inside the timed region)"
+            return out
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
                 "reasons": sorted(reasons), "samples": len(sm)}
 
@@ -212,6 +243,7 @@ def run_engine(args, rank, world, local_rank):
     with ClockSampler(local_rank) as clk:
         torch.cuda.synchronize()
         wall0 = time.perf_counter()
+        epoch0 = time.time()
         for i in range(K):
             flush.fill_(i & 0xFF)          # L2 flush between steps (outside the events)
             e0 = torch.cuda.Event(enable_timing=True)
@@ -226,6 +258,7 @@ def run_engine(args, rank, world, local_rank):
             b.free()
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
+        clk.mark(epoch0, time.time())
     launches = G.gputx_launch_count() - launches0
     # count only the engine's kernels: the L2 flushes are torch's
     total_ms = sum(times)
