@@ -189,7 +189,15 @@ __global__ void __launch_bounds__(MAXT, 1) kset_narrow_kernel(LevelArgs a)
         uint32_t npos;
         int ngl = -1;
         const bool has_next = rank < N.v && N.at(rank, npos, ngl);
-        if (has_next) nv = view_at(a.b, npos, hb);
+        if (has_next) {
+            nv = view_at(a.b, npos, hb);
+            // the parameters this lane reads beyond the first two (a group
+            // lane's order line) into L1 while this level runs
+            if (a.b.P > 2) {
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(nv.p + 2));
+                if (ngl >= 0 && 4 + ngl < a.b.P) asm volatile("prefetch.global.L1 [%0];" ::"l"(nv.p + 4 + ngl));
+            }
+        }
         if (has) exec_lane(a.db, a.b, v, gl, a.atomic_add);
         for (uint32_t x = rank + nthreads; x < L.v; x += nthreads) {
             uint32_t p2;
