@@ -58,7 +58,7 @@ DOMINANT_KERNEL = {("kset", "paper"): "kset_narrow_dc_kernel", ("kset", "add"): 
 # ncu capture at this configuration, keyed by (strategy, mode, bulk log2);
 # each entry holds the digest of the kernel and launch-planner sources it was
 # taken on, and is reported as null once those sources change
-TRAFFIC = {("kset", "paper", 22): {"bytes": 340535040 + 362240 + 290906112, "digest": "ba35a042b8637d7f"}}
+TRAFFIC = {("kset", "paper", 22): {"bytes": 341127168 + 361984 + 290942208, "digest": "3472c3d645ba694a"}}
 KERNEL_SOURCES = ("common.cuh", "fastdiv.h", "engine.h", "dc.cuh", "levels.cuh", "exec_dc.cu", "exec.cu")
 
 
