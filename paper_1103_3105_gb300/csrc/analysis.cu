@@ -278,10 +278,13 @@ __global__ void __launch_bounds__(256) depth_flow_kernel(const uint32_t *txn_rid
         if (t < n) {
             const int64_t s0 = op_off ? (int64_t)op_off[t] : t * kslots;
             const int k = op_off ? (int)(op_off[t + 1] - op_off[t]) : kslots;
+            // every per-operation array below is indexed by unrolled loop
+            // counters only, so it lives in registers
             uint32_t rr[MAX_OPS];
             uint32_t waits = 0, own = 0;   // bit j: operation j follows an earlier run / has a run
-            for (int j = 0; j < k && j < MAX_OPS; j++) {
-                rr[j] = txn_rid[s0 + j];
+#pragma unroll
+            for (int j = 0; j < MAX_OPS; j++) {
+                rr[j] = j < k ? txn_rid[s0 + j] : kNoRun;
                 if (rr[j] != kNoRun) {
                     own |= 1u << j;
                     if (!(rr[j] & 0x80000000u)) waits |= 1u << j;
@@ -298,10 +301,12 @@ __global__ void __launch_bounds__(256) depth_flow_kernel(const uint32_t *txn_rid
                 // this look's runs: every pending one, or the first
                 const uint32_t look = all ? pending : pending & (0u - pending);
                 unsigned long long w[MAX_OPS];
-                for (int j = 0; j < k && j < MAX_OPS; j++)   // all loads in flight at once
-                    if (look >> j & 1u) w[j] = ld_relaxed_u64(&runword[(rr[j] & 0x7fffffffu) - 1u]);
+#pragma unroll
+                for (int j = 0; j < MAX_OPS; j++)   // all loads in flight at once
+                    w[j] = (look >> j & 1u) ? ld_relaxed_u64(&runword[(rr[j] & 0x7fffffffu) - 1u]) : 0ull;
                 uint32_t still = pending;
-                for (int j = 0; j < k && j < MAX_OPS; j++) {
+#pragma unroll
+                for (int j = 0; j < MAX_OPS; j++) {
                     if ((look >> j & 1u) && !(w[j] >> 32)) {   // complete: its maximum is final
                         still &= ~(1u << j);
                         if ((uint32_t)w[j] + 1u > lv) lv = (uint32_t)w[j] + 1u;
@@ -326,18 +331,21 @@ __global__ void __launch_bounds__(256) depth_flow_kernel(const uint32_t *txn_rid
             // this transaction's depth into each of its runs, counted off in
             // the same compare-and-swap
             unsigned long long cur[MAX_OPS];
-            for (int j = 0; j < k && j < MAX_OPS; j++)
-                if (own >> j & 1u) cur[j] = 1ull << 32;   // a guess: the run's only operation
+#pragma unroll
+            for (int j = 0; j < MAX_OPS; j++) cur[j] = 1ull << 32;   // a guess: the run's only operation
             uint32_t todo = own;
             for (int attempt = 0; todo && attempt < (1 << 20); attempt++) {
                 unsigned long long prev[MAX_OPS];
-                for (int j = 0; j < k && j < MAX_OPS; j++) {   // every swap in flight at once
+#pragma unroll
+                for (int j = 0; j < MAX_OPS; j++) {   // every swap in flight at once
+                    prev[j] = cur[j];
                     if (!(todo >> j & 1u)) continue;
                     const uint32_t mx = (uint32_t)cur[j] > lv ? (uint32_t)cur[j] : lv;
                     const unsigned long long nv = (((cur[j] >> 32) - 1ull) << 32) | mx;
                     prev[j] = atomicCAS(&runword[rr[j] & 0x7fffffffu], cur[j], nv);
                 }
-                for (int j = 0; j < k && j < MAX_OPS; j++) {
+#pragma unroll
+                for (int j = 0; j < MAX_OPS; j++) {
                     if (!(todo >> j & 1u)) continue;
                     if (prev[j] == cur[j]) todo &= ~(1u << j);
                     else cur[j] = prev[j];
