@@ -498,7 +498,7 @@ gputx_status gputx_register_types(gputx_db *db, const int32_t *type_ids, int n)
         // one-pass ranks are exact when every transaction's items nest under
         // one item it writes (debit-credit: account within teller within
         // branch) or it touches one item (subscriber); order-entry's
-        // multi-item transactions need the refinement rounds
+        // multi-item transactions need the exact-depth pass
         if (t >= GPUTX_T_OE_NEW_ORDER) fix = true;
     }
     db->kmax = kmax;
@@ -1094,8 +1094,8 @@ gputx_status gputx_execute(gputx_db *db, gputx_bulk *b, int strategy, const gput
         // AUTO decides on the one-pass ranks first: w0 and c are exact there
         // (a transaction is a source exactly when all its operations have
         // rank 0), and the one-pass depth bounds the exact one from below.
-        // The refinement rounds run only once K-SET is chosen.
-        if (db->need_fixpoint && strategy == GPUTX_KSET) CK(launch_exact_depth(b, sv, m), "fixpoint");
+        // The exact-depth pass runs only once K-SET is chosen.
+        if (db->need_fixpoint && strategy == GPUTX_KSET) CK(launch_exact_depth(b, sv, m), "exact depth");
         CK(launch_level_stats(b), "stats");
         if ((st = read_ctl(b))) return st;
         if (b->host_ctl.err) {
@@ -1115,7 +1115,7 @@ gputx_status gputx_execute(gputx_db *db, gputx_bulk *b, int strategy, const gput
                 b->fallback = 1;
             if (run == GPUTX_KSET && db->need_fixpoint) {
                 // exact depths for the level schedule (Property 1)
-                CK(launch_exact_depth(b, sv, m), "fixpoint");
+                CK(launch_exact_depth(b, sv, m), "exact depth");
                 CK(cudaMemsetAsync(&b->ctl->depth, 0, 2 * sizeof(uint32_t), s), "stats");
                 CK(launch_level_stats(b), "stats");
                 if ((st = read_ctl(b))) return st;
@@ -1435,7 +1435,7 @@ extern "C" gputx_status gputx_execute_kset_noalloc(gputx_db *db, const int64_t *
     uint32_t *sk = b.sc.keys_a, *sv = b.sc.vals_a, *ak = b.sc.keys_b, *av = b.sc.vals_b;
     CK(launch_sort(&b, sk, sv, ak, av, m, key_bits(db, conflict_mode)), "sort");
     CK(launch_rank_scan(&b, sk, sv, m, db->need_fixpoint), "rank");
-    if (db->need_fixpoint) CK(launch_exact_depth(&b, sv, m), "fixpoint");
+    if (db->need_fixpoint) CK(launch_exact_depth(&b, sv, m), "exact depth");
     CK(launch_level_stats(&b), "stats");
     if ((st = read_ctl(&b))) return st;
     if (b.host_ctl.err) return bulk_error(db, b.host_ctl.err);

@@ -6,7 +6,7 @@
 // most the segment capacity; a bulk larger than that is cut into pieces)
 // that goes through ONE replay of a captured CUDA graph.  The graph holds
 // the whole pipeline for a fixed capacity -- extraction, grouping sort,
-// ranks, device-side refinement rounds, (level, type) regrouping and one
+// ranks, the device-side exact-depth pass, (level, type) regrouping and one
 // persistent executor launch -- and reads the segment's bulk boundaries from
 // a device descriptor array, so no host synchronisation happens inside it.
 // For K-SET every bulk keeps its own dependency graph: the bulk's index sits
