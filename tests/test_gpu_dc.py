@@ -186,15 +186,21 @@ def test_execute_twice_is_refused():
     g.close()
 
 
-@pytest.mark.parametrize("strategy,launch", [("kset", 1), ("tpl", 0)])
-def test_bounded_wait_reports_timeout(strategy, launch):
+@pytest.mark.parametrize("strategy,launch,mode", [("kset", 1, 0), ("tpl", 0, 0), ("tpl", 0, 1)])
+def test_bounded_wait_reports_timeout(strategy, launch, mode):
     """A 1 ns wait limit makes the per-level waits of a 1,000-deep persistent
     K-SET launch (or TPL's lock waits) run out: the engine must report
-    ETIMEOUT instead of hanging, and stay usable."""
+    ETIMEOUT instead of hanging, and stay usable.  TPL under R/W locks the 4
+    branches (chains of about 1,000: the CTA-group kernel); under ADD it
+    locks the 4,000 accounts (chains of a few: the warp-group kernel)."""
     g = G.Database(dc=(4, 40, 4000), history_capacity=1 << 16, max_bulk=1 << 14, spin_limit_ns=1)
     g.register(G.DC_TYPES)
     bulk = W.dc_bulk(4096, 4000, 0.0, seed=2)
-    b = g.submit_dict(bulk).execute(strategy, kset_launch=launch)
+    if mode:
+        # every account twice in a row, 2,048 apart: each second visit waits
+        acct = np.arange(2048, dtype=np.int64)
+        bulk["params"][:, 0] = np.concatenate([acct, acct])
+    b = g.submit_dict(bulk).execute(strategy, conflict_mode=mode, kset_launch=launch)
     with pytest.raises(G.GputxError) as e:
         b.sync()
     assert e.value.status == G.ETIMEOUT

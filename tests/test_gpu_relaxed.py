@@ -125,6 +125,33 @@ def test_spin_locks_time_out_instead_of_hanging():
     g.close()
 
 
+def test_spin_locks_time_out_on_other_schemas():
+    """The same 1 ns limit in the general relaxed kernel (subscriber
+    transactions on 8 subscribers, so nearly every lock is contended):
+    ETIMEOUT, and a following bulk on distinct subscribers runs clean."""
+    n_sub = 64
+    sub = W.sub_tables(n_sub, seed=61)
+    g = G.Database(sub=n_sub, sub_child_capacity=1 << 12, max_bulk=1 << 12, spin_limit_ns=1)
+    g.register(G.SUB_TYPES)
+    for t, r in W.sub_rows(sub).items():
+        g.load(t, r)
+    bulk = W.sub_bulk(4096, 8, 0.0, seed=62)
+    b = g.submit_dict(bulk).execute("tpl_relaxed")
+    with pytest.raises(G.GputxError) as e:
+        b.sync()
+    assert e.value.status == G.ETIMEOUT
+    b.free()
+    one = W.sub_bulk(n_sub, n_sub, 0.0, seed=63, ts0=10_000)
+    one["params"][:, 0] = np.arange(n_sub)          # one transaction per subscriber
+    one["type"][:] = G.T_SUB_GET_SUBSCRIBER         # reads only: nothing to insert
+    one["params"][:, 1:] = 0
+    b = g.submit_dict(one).execute("tpl_relaxed")
+    st, _ = b.results()
+    assert np.array_equal(st, np.zeros(n_sub, np.int32))
+    b.free()
+    g.close()
+
+
 def test_timestamp_strategies_report_timestamp_order():
     g = G.Database(dc=(4, 40, 4000), history_capacity=1 << 14, max_bulk=1 << 12)
     g.register(G.DC_TYPES)
