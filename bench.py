@@ -345,12 +345,16 @@ def run_engine(args, rank, world, local_rank):
         # branch additions, history row, outputs), stores in the probe
         floor_dc = probe(0, 1, 9, rmw=1)
         floor_min = probe(0, 1, 0, rmw=1)
+        # the same with the fetch-and-add on random cells of a table the size
+        # of the 10M accounts, prefetched two levels ahead like the runner's
+        floor_rand = probe(0, 1, 9, rmw=2)
         # the same level applying its updates as loads then stores
         floor_ld_st = probe(3, 3, 7)
         measured = ex * 1e6 / levels
         latency = {"levels": levels, "measured_ns_per_level": measured,
                    "floor_ns_per_level": floor_dc, "floor_ns_per_level_min": floor_min,
                    "floor_ns_per_level_load_store": floor_ld_st, "frac": floor_dc / measured,
+                   "floor_ns_per_level_random_cells": floor_rand, "frac_random_cells": floor_rand / measured,
                    "probe": "cluster 16 x 64 threads; per thread and level 1 fetch-and-add on a cell another "
                             "CTA updated at the previous level, barrier arrive (release), 9 stores, "
                             "barrier wait (acquire); best of 3 launches"}

@@ -510,12 +510,15 @@ void gputx_server_destroy(gputx_server *s);
  * rmw = 1: they are 64-bit atomic additions to cells that the previous level
  * updated on another CTA, one a fetch-and-add whose old value feeds the
  * stores after the arrival and the rest reductions (the shape of a runner
- * applying its balance updates at L2).
+ * applying its balance updates at L2); rmw = 2: as 1, but the fetch-and-add
+ * goes to a cell drawn uniformly from a table of 10,000,000 8-byte cells (the
+ * debit-credit accounts' footprint) and the cell of two levels ahead is
+ * prefetched into L2 before the barrier, as the debit-credit runner does.
  * *ns_per_level = the time of one timed launch (after a warm-up launch)
  * divided by `levels`.  Allocates and frees its own device memory
- * ((levels + 17) x cluster_size x threads x 128 bytes).  EINVAL on a parameter
- * out of range (rmw other than 0 or 1 included), ECUDA if the cluster shape
- * cannot launch. */
+ * ((levels + 17) x cluster_size x threads x 128 bytes, and 80 MB for rmw = 2).
+ * EINVAL on a parameter out of range (rmw other than 0, 1 or 2 included),
+ * ECUDA if the cluster shape cannot launch. */
 gputx_status gputx_probe_level_chain(int levels, int cluster_size, int threads, int loads, int stores,
                                      int stores_after, int rmw, double *ns_per_level);
 

@@ -29,8 +29,21 @@ constexpr int kProbeMaxLoads = 8, kProbeMaxStores = 16, kProbeLine = 16;
 // n x kProbeMaxStores cells for the fetch-and-adds, one per 128-byte line
 // (kProbeLine words): like a runner's balance rows, every update of a warp
 // goes to its own line
+constexpr int64_t kProbeTable = 10000000;   // rmw = 2: cells of a table the size of 10M accounts
+
+// rmw = 2: the cell a thread's fetch-and-add takes at level k, uniform over
+// the table (SplitMix64 of the thread and the level)
+__device__ __forceinline__ uint64_t probe_cell(uint32_t r, int k)
+{
+    uint64_t z = ((uint64_t)r << 32 | (uint32_t)k) + 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return (z ^ (z >> 31)) % (uint64_t)kProbeTable;
+}
+
 __global__ void __launch_bounds__(1024, 1) probe_chain_kernel(int64_t *buf, int64_t *sink, int levels, int loads,
-                                                            int stores, int stores_after, int rmw)
+                                                            int stores, int stores_after, int rmw,
+                                                            unsigned long long *table)
 {
     cg::cluster_group cl = cg::this_cluster();
     const uint32_t n = cl.num_threads(), r = cl.thread_rank();
@@ -49,9 +62,16 @@ __global__ void __launch_bounds__(1024, 1) probe_chain_kernel(int64_t *buf, int6
         if (rmw) {
             // the column the next CTA's thread updated at level k-1
             const uint32_t c = (uint32_t)((r + (uint64_t)k * blockDim.x) % n);
-            // one fetch-and-add whose old value is used after the arrival,
-            // the rest reductions whose results nothing reads
-            ret = (int64_t)atomicAdd(&cells[(int64_t)c * kProbeLine], (unsigned long long)acc);
+            // one fetch-and-add whose old value is used after the arrival
+            // (rmw = 2: a random cell of the table, prefetched into L2 two
+            // levels ahead as the runner prefetches its accounts), the rest
+            // reductions whose results nothing reads
+            unsigned long long *cell = &cells[(int64_t)c * kProbeLine];
+            if (rmw == 2) {
+                cell = &table[probe_cell(r, k)];
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(&table[probe_cell(r, k + 2)]));
+            }
+            ret = (int64_t)atomicAdd(cell, (unsigned long long)acc);
             for (int j = 1; j < stores; j++)
                 atomicAdd(&cells[((int64_t)j * n + c) * kProbeLine], (unsigned long long)(acc + j));
         } else {
@@ -136,11 +156,12 @@ extern "C" gputx_status gputx_probe_level_chain(int levels, int cluster_size, in
 {
     if (!ns_per_level || levels < 1 || levels > (1 << 20) || cluster_size < 1 || cluster_size > 16 ||
         threads < 32 || threads > 1024 || threads % 32 || loads < 0 || loads > kProbeMaxLoads || stores < 1 ||
-        stores_after < 0 || stores + stores_after > kProbeMaxStores || (rmw != 0 && rmw != 1))
+        stores_after < 0 || stores + stores_after > kProbeMaxStores || rmw < 0 || rmw > 2)
         return GPUTX_EINVAL;
     const int64_t n = (int64_t)cluster_size * threads;
     const int64_t words = ((int64_t)(levels + 1) + kProbeLine) * n * kProbeMaxStores;
     int64_t *buf = nullptr, *sink = nullptr;
+    unsigned long long *table = nullptr;
     cudaStream_t s = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     gputx_status st = GPUTX_OK;
@@ -148,6 +169,8 @@ extern "C" gputx_status gputx_probe_level_chain(int levels, int cluster_size, in
     if (!e) e = cudaMalloc(&buf, words * sizeof(int64_t));
     if (!e) e = cudaMalloc(&sink, n * sizeof(int64_t));
     if (!e) e = cudaMemsetAsync(buf, 0, words * sizeof(int64_t), s);
+    if (!e && rmw == 2) e = cudaMalloc(&table, kProbeTable * sizeof(unsigned long long));
+    if (!e && rmw == 2) e = cudaMemsetAsync(table, 0, kProbeTable * sizeof(unsigned long long), s);
     if (!e) e = cudaEventCreate(&e0);
     if (!e) e = cudaEventCreate(&e1);
     if (!e) e = cudaFuncSetAttribute(probe_chain_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -164,9 +187,10 @@ extern "C" gputx_status gputx_probe_level_chain(int levels, int cluster_size, in
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         // one warm-up launch, then the timed one
-        e = cudaLaunchKernelEx(&cfg, probe_chain_kernel, buf, sink, levels, loads, stores, stores_after, rmw);
+        e = cudaLaunchKernelEx(&cfg, probe_chain_kernel, buf, sink, levels, loads, stores, stores_after, rmw, table);
         if (!e) e = cudaEventRecord(e0, s);
-        if (!e) e = cudaLaunchKernelEx(&cfg, probe_chain_kernel, buf, sink, levels, loads, stores, stores_after, rmw);
+        if (!e) e = cudaLaunchKernelEx(&cfg, probe_chain_kernel, buf, sink, levels, loads, stores, stores_after, rmw,
+                                       table);
         if (!e) e = cudaEventRecord(e1, s);
         if (!e) e = cudaEventSynchronize(e1);
         float ms = 0;
@@ -179,6 +203,7 @@ extern "C" gputx_status gputx_probe_level_chain(int levels, int cluster_size, in
     if (e1) cudaEventDestroy(e1);
     if (buf) cudaFree(buf);
     if (sink) cudaFree(sink);
+    if (table) cudaFree(table);
     if (s) cudaStreamDestroy(s);
     return st;
 }

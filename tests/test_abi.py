@@ -87,7 +87,7 @@ def test_probe_rejects_bad_shapes_without_a_gpu():
         pytest.skip("library not built")
     for args in [(0, 16, 64, 3, 10), (10, 17, 64, 3, 10), (10, 16, 48, 3, 10), (10, 16, 64, 9, 10),
                  (10, 16, 64, 3, 0), (10, 16, 64, 3, 17), (10, 16, 64, 3, 3, -1), (10, 16, 64, 3, 3, 14),
-                 (10, 16, 64, 0, 3, 7, 2), (10, 16, 64, 0, 3, 7, -1)]:
+                 (10, 16, 64, 0, 3, 7, 3), (10, 16, 64, 0, 3, 7, -1)]:
         with pytest.raises(G.GputxError) as e:
             G.gputx_probe_level_chain(*args)
         assert e.value.status == G.EINVAL
