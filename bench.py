@@ -410,7 +410,9 @@ def run_engine(args, rank, world, local_rank):
     }
     if latency is not None:
         line["latency_roofline"] = {k: latency[k] for k in ("levels", "measured_ns_per_level",
-                                                             "floor_ns_per_level", "frac")}
+                                                             "floor_ns_per_level", "frac",
+                                                             "floor_ns_per_level_random_cells",
+                                                             "frac_random_cells")}
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, bulks)
     # everything else goes to the detail file; stdout ends with the compact headline

@@ -392,7 +392,8 @@ def test_level_chain_probe():
     floor_dc = G.gputx_probe_level_chain(2000, 16, 64, 3, 10)
     floor_split = G.gputx_probe_level_chain(2000, 16, 64, 3, 3, 7)
     floor_rmw = G.gputx_probe_level_chain(2000, 16, 64, 0, 3, 7, rmw=1)
-    for f in (floor_min, floor_dc, floor_split, floor_rmw):
+    floor_rand = G.gputx_probe_level_chain(2000, 16, 64, 0, 1, 9, rmw=2)
+    for f in (floor_min, floor_dc, floor_split, floor_rmw, floor_rand):
         assert 0 < f < 50_000
     assert floor_dc > 0.8 * floor_min
 
