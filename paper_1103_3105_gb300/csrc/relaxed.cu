@@ -32,18 +32,29 @@ struct TplRelaxedArgs {
 
 constexpr uint32_t kFull = 0xffffffffu;
 
-// The lock of Figure 10 with a version in the word: even = free, odd = held.
-// Taking it swaps an even value v for v + 1, releasing stores v + 2, so the
-// word changes at every hand-off.  A waiter therefore tells a lock that is
-// passed along a long queue (progress: keep waiting) from one whose holder
-// never lets go (the wait limit runs from the last change it saw).
-//
-// compare-and-swap v -> v + 1 with acquire semantics: a holder sees every
-// write its predecessors made before their release
-__device__ __forceinline__ bool try_lock(uint32_t *l, uint32_t v)
+// The lock of Figure 10, extended to shared readers, with a version in the
+// word: bits 0..19 count the readers holding it, bit 20 is set while a writer
+// holds it, bits 21..31 count the writers' hand-offs.  A writer swaps a word
+// with neither readers nor a writer for the same word with bit 20 set; a
+// reader swaps a word without a writer for the word plus one.  A writer
+// releases by storing the word with bit 20 cleared and the hand-off count
+// raised, a reader by subtracting one.  The word changes at every hand-off,
+// so a waiter tells a lock passed along a long queue (progress: keep
+// waiting) from one whose holder never lets go: the wait limit runs from the
+// last change it saw.  Transactions that only read an item share its lock.
+// Holding every lock while the commit ticket is taken (strict two-phase
+// locking), a writer's ticket follows the tickets of the readers before it
+// and precedes those of the readers after it.
+constexpr uint32_t kLockWriter = 1u << 20;
+constexpr uint32_t kLockReaders = kLockWriter - 1u;
+constexpr uint32_t kLockHandoff = 1u << 21;
+
+// compare-and-swap with acquire semantics: a holder sees every write its
+// predecessors made before their release
+__device__ __forceinline__ bool lock_swap(uint32_t *l, uint32_t v, uint32_t nv)
 {
     uint32_t old;
-    asm volatile("atom.acquire.gpu.global.cas.b32 %0, [%1], %2, %3;" : "=r"(old) : "l"(l), "r"(v), "r"(v + 1) : "memory");
+    asm volatile("atom.acquire.gpu.global.cas.b32 %0, [%1], %2, %3;" : "=r"(old) : "l"(l), "r"(v), "r"(nv) : "memory");
     return old == v;
 }
 
@@ -54,20 +65,24 @@ __device__ __forceinline__ uint32_t peek(const uint32_t *l)
     return v;
 }
 
-// the release: this transaction's writes before the lock reads free
-__device__ __forceinline__ void unlock(uint32_t *l, uint32_t held)
+__device__ __forceinline__ bool lock_open(uint32_t w, bool write)
 {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(l), "r"(held + 1) : "memory");
+    return write ? !(w & (kLockWriter | kLockReaders)) : !(w & kLockWriter);
+}
+
+__device__ __forceinline__ uint32_t lock_taken(uint32_t w, bool write)
+{
+    return write ? (w | kLockWriter) : w + 1u;
 }
 
 // test-and-test-and-set with exponential back-off: waiters read the word
-// and try the swap only when it reads free, so a hot lock's line is not
-// flooded with atomics.  Returns the held (odd) value, or 0 when the word did
-// not change for limit_ns.
-__device__ __forceinline__ uint32_t spin_lock(uint32_t *l, uint64_t limit_ns)
+// and try the swap only when it reads open, so a hot lock's line is not
+// flooded with atomics.  Returns the word as taken (never 0), or 0 when the
+// word did not change for limit_ns.
+__device__ __forceinline__ uint32_t rw_lock(uint32_t *l, bool write, uint64_t limit_ns)
 {
     uint32_t v = peek(l);
-    if (!(v & 1u) && try_lock(l, v)) return v + 1;
+    if (lock_open(v, write) && lock_swap(l, v, lock_taken(v, write))) return lock_taken(v, write);
     uint64_t t0 = globaltimer();
     uint32_t ns = 32;
     while (true) {
@@ -78,12 +93,22 @@ __device__ __forceinline__ uint32_t spin_lock(uint32_t *l, uint64_t limit_ns)
             v = w;
             t0 = globaltimer();
         }
-        if (!(w & 1u)) {
-            if (try_lock(l, w)) return w + 1;
+        if (lock_open(w, write)) {
+            if (lock_swap(l, w, lock_taken(w, write))) return lock_taken(w, write);
         } else if (globaltimer() - t0 > limit_ns) {
             return 0;
         }
     }
+}
+
+// the release: this transaction's writes before the lock opens
+__device__ __forceinline__ void rw_unlock(uint32_t *l, bool write, uint32_t held)
+{
+    if (write)
+        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(l), "r"((held & ~kLockWriter) + kLockHandoff)
+                     : "memory");
+    else
+        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(l), "r"(0xffffffffu) : "memory");
 }
 
 __global__ void tpl_relaxed_kernel(TplRelaxedArgs a)
@@ -100,6 +125,7 @@ __global__ void tpl_relaxed_kernel(TplRelaxedArgs a)
         const bool live = t < a.b.n;
         TxnView v{};
         uint32_t items[MAX_OPS];
+        uint32_t wmask = 0;   // bit j: lock j is taken to write (else shared, to read)
         int m = 0;
         if (live) {
             v = view_of(a.b, (uint32_t)t, hb);
@@ -108,13 +134,15 @@ __global__ void tpl_relaxed_kernel(TplRelaxedArgs a)
             const int k = access_set(a.db, v.type, v.p, a.mode, obj, cls, root);
             for (int j = 0; j < k; j++) {
                 if (cls[j] == CLS_A) continue;   // an atomic increment needs no lock
-                // insertion into the sorted lock list
+                // insertion into the sorted lock list (its modes alongside)
                 int q = m++;
                 while (q > 0 && items[q - 1] > obj[j]) {
                     items[q] = items[q - 1];
                     q--;
                 }
                 items[q] = obj[j];
+                const uint32_t below = wmask & ((1u << q) - 1u);
+                wmask = below | ((wmask & ~((1u << q) - 1u)) << 1) | ((cls[j] == CLS_R ? 0u : 1u) << q);
             }
             if (kDebug)
                 for (int j = 0; j < m; j++)
@@ -124,17 +152,20 @@ __global__ void tpl_relaxed_kernel(TplRelaxedArgs a)
                         break;
                     }
         }
-        // Warp combining: lanes whose only lock is the same item form a group
-        // (__match_any_sync).  Its lowest lane takes the lock once and the
-        // group runs in lane order inside one critical section, each lane
-        // with consecutive commit tickets, so the serial order the tickets
-        // report is the order the group ran in.
+        // Warp combining: lanes whose only lock is the same item, taken in
+        // the same mode, form a group (__match_any_sync).  Its lowest lane
+        // takes the lock once and draws the group's consecutive commit
+        // tickets.  Writers run in lane order inside the one critical
+        // section, so the ticket order is the order they ran in; readers
+        // change nothing another reader sees, so they run at once.
         const bool single = live && m == 1;
-        const uint32_t grp = __match_any_sync(kFull, single ? items[0] : (0xFFFFFFE0u | lane));
+        const bool write1 = single && (wmask & 1u);
+        const uint32_t grp = __match_any_sync(kFull, single ? (items[0] | (write1 ? 0x80000000u : 0u))
+                                                            : (0xFFFFFFE0u | lane));
         const uint32_t leader = __ffs(grp) - 1;
         if (single) {
             uint32_t held = 0;
-            if (lane == leader) held = spin_lock(&a.lock[a.slot(items[0])], a.spin_limit_ns);
+            if (lane == leader) held = rw_lock(&a.lock[a.slot(items[0])], write1, a.spin_limit_ns);
             held = __shfl_sync(grp, held, leader);
             if (!held) {
                 if (lane == leader) set_err(&a.ctl->err, ERR_TIMEOUT);
@@ -142,21 +173,24 @@ __global__ void tpl_relaxed_kernel(TplRelaxedArgs a)
                 uint32_t tk = 0;
                 if (lane == leader) tk = atomicAdd(&a.ctl->claim, (uint32_t)__popc(grp));
                 tk = __shfl_sync(grp, tk, leader);
-                for (uint32_t rest = grp; rest; rest &= rest - 1) {   // lane order
-                    if (lane == (uint32_t)(__ffs(rest) - 1)) {
+                __syncwarp(grp);   // the leader's acquire before every member's accesses
+                // writers one lane at a time in lane order, readers all in one
+                // pass (one call site of the procedures keeps the register count)
+                for (uint32_t rest = grp; rest; rest = write1 ? (rest & (rest - 1)) : 0u) {
+                    if (!write1 || lane == (uint32_t)(__ffs(rest) - 1)) {
                         exec_txn(a.db, a.b, v, a.atomic_add);
                         a.order[tk + __popc(grp & lanemask_lt())] = (uint32_t)t;
                     }
-                    __syncwarp(grp);   // each lane's writes before the next one's reads
+                    __syncwarp(grp);   // each writer's writes before the next one's reads
                 }
-                if (lane == leader) unlock(&a.lock[a.slot(items[0])], held);
+                if (lane == leader) rw_unlock(&a.lock[a.slot(items[0])], write1, held);
             }
         } else if (live) {
             uint32_t held_v[MAX_OPS];
             int held = 0;
             bool ok = true;
             for (; held < m; held++) {
-                held_v[held] = spin_lock(&a.lock[a.slot(items[held])], a.spin_limit_ns);
+                held_v[held] = rw_lock(&a.lock[a.slot(items[held])], (wmask >> held) & 1u, a.spin_limit_ns);
                 if (!held_v[held]) {
                     set_err(&a.ctl->err, ERR_TIMEOUT);
                     ok = false;
@@ -167,7 +201,7 @@ __global__ void tpl_relaxed_kernel(TplRelaxedArgs a)
                 exec_txn(a.db, a.b, v, a.atomic_add);
                 a.order[atomicAdd(&a.ctl->claim, 1u)] = (uint32_t)t;
             }
-            for (int j = 0; j < held; j++) unlock(&a.lock[a.slot(items[j])], held_v[j]);
+            for (int j = 0; j < held; j++) rw_unlock(&a.lock[a.slot(items[j])], (wmask >> j) & 1u, held_v[j]);
         }
     }
 }
@@ -234,7 +268,7 @@ __global__ void __launch_bounds__(kCtaMax) tpl_relaxed_dc_block_kernel(TplRelaxe
             bool ok = true;
             uint32_t held = 0;
             if (tid == c.leader) {
-                held = spin_lock(lock, a.spin_limit_ns);
+                held = rw_lock(lock, true, a.spin_limit_ns);
                 ok = held != 0;
                 if (ok) g.base[e] = atomicAdd(&a.ctl->claim, c.size);
                 else set_err(&a.ctl->err, ERR_TIMEOUT);
@@ -258,7 +292,7 @@ __global__ void __launch_bounds__(kCtaMax) tpl_relaxed_dc_block_kernel(TplRelaxe
             if (tid == c.leader && held) {
                 // every member's account update precedes the unlock
                 if (!cta_wait_members(g, e, c.size, a.spin_limit_ns)) set_err(&a.ctl->err, ERR_TIMEOUT);
-                unlock(lock, held);
+                rw_unlock(lock, true, held);
             }
             if (have) {
                 atomicAdd((unsigned long long *)&a.db.tel_bal[r.tl], (unsigned long long)r.delta);
