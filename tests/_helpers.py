@@ -229,8 +229,8 @@ def gpu_logical_state(db, dc=False, sub=False, oe=False, n_sub=0, n_wh=0, n_item
 
 
 # ---------------------------------------------------------------------------
-# primary-index consistency (the survey's "every live row is found by its
-# key, and every index entry points to a live row with that key")
+# primary-index consistency: every live row is found by its key, and every
+# index entry points to a live row with that key
 # ---------------------------------------------------------------------------
 HKEY_EMPTY = np.uint64((1 << 64) - 1)
 HKEY_TOMB = np.uint64((1 << 64) - 2)
