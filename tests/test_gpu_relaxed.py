@@ -152,6 +152,51 @@ def test_spin_locks_time_out_on_other_schemas():
     g.close()
 
 
+@pytest.mark.parametrize("theta", [0.0, 0.99])
+@pytest.mark.parametrize("mode", [G.CONFLICT_PAPER, G.CONFLICT_ADD])
+def test_debit_credit_at_the_benchmark_size(theta, mode):
+    """TPL_RELAXED on the benchmark's tables (1,000 branches, 10,000 tellers,
+    10,000,000 accounts) at 2^22 transactions: the CTA-combining kernel.  The
+    oracle replays the reported order over the whole bulk; every output and
+    every table must match."""
+    A = 10_000_000
+    tabs = W.dc_tables(1000, 10000, A)
+    g = G.Database(dc=(1000, 10000, A), history_capacity=1 << 22, max_bulk=1 << 22)
+    g.register(G.DC_TYPES)
+    for t, r in W.dc_rows(tabs).items():
+        g.load(t, r)
+    o = oracle.OracleDB(dc=tabs, hist_cap=1 << 22)
+    bulk = W.dc_bulk(1 << 22, A, theta, seed=W.seed_for(2, 700 + int(theta * 100)))
+    run_relaxed(g, o, bulk, "tpl_relaxed", mode)
+    assert np.array_equal(g.read(G.TBL_DC_ACCOUNT)[:, 0], o["acc_bal"])
+    assert np.array_equal(g.read(G.TBL_DC_BRANCH)[:, 0], o["br_bal"])
+    assert np.array_equal(g.read(G.TBL_DC_TELLER)[:, 0], o["tel_bal"])
+    # the history rows are the same set; the oracle appended them in the
+    # replayed order, so both sides are compared by timestamp
+    h, oh = g.read(G.TBL_DC_HISTORY), o.history()
+    assert np.array_equal(h[np.argsort(h[:, 0])], oh[np.argsort(oh[:, 0])])
+    g.close()
+
+
+def test_subscribers_at_the_benchmark_size():
+    """TPL_RELAXED (shared readers) on 10,000,000 subscribers with their child
+    tables, a bulk of 2^20 mixed transactions, Zipf 0.8: the oracle replays
+    the reported order; outputs and the logical state must match."""
+    n_sub = 10_000_000
+    sub = W.sub_tables(n_sub, seed=W.seed_for(3))
+    g = G.Database(sub=n_sub, sub_child_capacity=6 * n_sub, max_bulk=1 << 20)
+    g.register(G.SUB_TYPES)
+    for t, r in W.sub_rows(sub).items():
+        g.load(t, r)
+    o = oracle.OracleDB(sub=sub)
+    bulk = W.sub_bulk(1 << 20, n_sub, 0.8, seed=W.seed_for(3, 1))
+    run_relaxed(g, o, bulk, "tpl_relaxed", R=g.width)
+    gs = gpu_logical_state(g, sub=True, n_sub=n_sub)
+    os_ = oracle_logical_state(o)
+    assert states_equal(gs, os_), state_diff(gs, os_)
+    g.close()
+
+
 def test_timestamp_strategies_report_timestamp_order():
     g = G.Database(dc=(4, 40, 4000), history_capacity=1 << 14, max_bulk=1 << 12)
     g.register(G.DC_TYPES)
