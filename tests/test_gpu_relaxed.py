@@ -153,12 +153,13 @@ def test_spin_locks_time_out_on_other_schemas():
 
 
 @pytest.mark.parametrize("theta", [0.0, 0.99])
-@pytest.mark.parametrize("mode", [G.CONFLICT_PAPER, G.CONFLICT_ADD])
-def test_debit_credit_at_the_benchmark_size(theta, mode):
-    """TPL_RELAXED on the benchmark's tables (1,000 branches, 10,000 tellers,
-    10,000,000 accounts) at 2^22 transactions: the CTA-combining kernel.  The
-    oracle replays the reported order over the whole bulk; every output and
-    every table must match."""
+@pytest.mark.parametrize("strategy,mode", [("tpl_relaxed", G.CONFLICT_PAPER), ("tpl_relaxed", G.CONFLICT_ADD),
+                                           ("part_relaxed", G.CONFLICT_PAPER)])
+def test_debit_credit_at_the_benchmark_size(theta, strategy, mode):
+    """The relaxed strategies on the benchmark's tables (1,000 branches, 10,000
+    tellers, 10,000,000 accounts) at 2^22 transactions (TPL_RELAXED: the
+    CTA-combining kernel).  The oracle replays the reported order over the
+    whole bulk; every output and every table must match."""
     A = 10_000_000
     tabs = W.dc_tables(1000, 10000, A)
     g = G.Database(dc=(1000, 10000, A), history_capacity=1 << 22, max_bulk=1 << 22)
@@ -167,7 +168,7 @@ def test_debit_credit_at_the_benchmark_size(theta, mode):
         g.load(t, r)
     o = oracle.OracleDB(dc=tabs, hist_cap=1 << 22)
     bulk = W.dc_bulk(1 << 22, A, theta, seed=W.seed_for(2, 700 + int(theta * 100)))
-    run_relaxed(g, o, bulk, "tpl_relaxed", mode)
+    run_relaxed(g, o, bulk, strategy, mode)
     assert np.array_equal(g.read(G.TBL_DC_ACCOUNT)[:, 0], o["acc_bal"])
     assert np.array_equal(g.read(G.TBL_DC_BRANCH)[:, 0], o["br_bal"])
     assert np.array_equal(g.read(G.TBL_DC_TELLER)[:, 0], o["tel_bal"])
