@@ -179,10 +179,12 @@ def test_debit_credit_at_the_benchmark_size(theta, strategy, mode):
     g.close()
 
 
-def test_subscribers_at_the_benchmark_size():
-    """TPL_RELAXED (shared readers) on 10,000,000 subscribers with their child
-    tables, a bulk of 2^20 mixed transactions, Zipf 0.8: the oracle replays
-    the reported order; outputs and the logical state must match."""
+@pytest.mark.parametrize("strategy", ["tpl_relaxed", "part_relaxed"])
+def test_subscribers_at_the_benchmark_size(strategy):
+    """The relaxed strategies (TPL_RELAXED with shared readers) on 10,000,000
+    subscribers with their child tables, a bulk of 2^20 mixed transactions,
+    Zipf 0.8: the oracle replays the reported order; outputs and the logical
+    state must match."""
     n_sub = 10_000_000
     sub = W.sub_tables(n_sub, seed=W.seed_for(3))
     g = G.Database(sub=n_sub, sub_child_capacity=6 * n_sub, max_bulk=1 << 20)
@@ -191,7 +193,7 @@ def test_subscribers_at_the_benchmark_size():
         g.load(t, r)
     o = oracle.OracleDB(sub=sub)
     bulk = W.sub_bulk(1 << 20, n_sub, 0.8, seed=W.seed_for(3, 1))
-    run_relaxed(g, o, bulk, "tpl_relaxed", R=g.width)
+    run_relaxed(g, o, bulk, strategy, R=g.width)
     gs = gpu_logical_state(g, sub=True, n_sub=n_sub)
     os_ = oracle_logical_state(o)
     assert states_equal(gs, os_), state_diff(gs, os_)
